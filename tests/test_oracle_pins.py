@@ -1,0 +1,558 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: Newman's
+all-pairs modularity in exact rationals, brute-force re-evaluation of every
+candidate move, recomputation from scratch, closed forms and special cases.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from tests.exact import dense_matrix, edges_of, move, newman_q, random_graph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make(oracle_mod, n, off, idx, w, loops=False):
+    return oracle_mod.Oracle(n, off, idx, w, allow_self_loops=loops)
+
+
+def q_fraction(o):
+    q, num, den = o.modularity()
+    return q, Fraction(num, den) if den else Fraction(0)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1 -- modularity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(12))
+def test_modularity_equals_newman_all_pairs(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 12))
+    off, idx, w = random_graph(rng, n, 0.45, wmax=5)
+    if len(idx) == 0:
+        pytest.skip("empty graph")
+    o = make(oracle_mod, n, off, idx, w)
+    A = dense_matrix(n, off, idx, w)
+    for _ in range(4):
+        C = rng.integers(0, n, n).astype(np.uint32)
+        o.set_membership(C)
+        q, qf = q_fraction(o)
+        assert qf == newman_q(A, list(C))
+        assert abs(q - float(qf)) <= 1e-15
+        assert Fraction(-1, 2) <= qf <= 1  # range stated in Section 2.2
+
+
+def test_modularity_special_cases(oracle_mod):
+    # one community: Q = 0
+    rng = np.random.default_rng(5)
+    off, idx, w = random_graph(rng, 9, 0.5, wmax=3)
+    o = make(oracle_mod, 9, off, idx, w)
+    o.set_membership(np.zeros(9, np.uint32))
+    assert q_fraction(o)[1] == 0
+    # singletons on a simple graph: Q = -sum K_i^2 / (2m)^2
+    o.set_membership(np.arange(9, dtype=np.uint32))
+    K, _, m2 = o.weights()
+    assert q_fraction(o)[1] == -Fraction(int((K.astype(object) ** 2).sum()), m2 * m2)
+    # two disjoint equal cliques, each its own community: Q = 1/2
+    edges = [(a, b, 1) for a, b in itertools.combinations(range(4), 2)]
+    edges += [(a + 4, b + 4, 1) for a, b in itertools.combinations(range(4), 2)]
+    g = synth.EdgeList(8, np.array([e[0] for e in edges], np.uint32),
+                       np.array([e[1] for e in edges], np.uint32), np.ones(len(edges), np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = make(oracle_mod, 8, off, idx, w)
+    o.set_membership(np.array([0, 0, 0, 0, 4, 4, 4, 4], np.uint32))
+    assert q_fraction(o)[1] == Fraction(1, 2)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2 -- delta-modularity equals the recomputed difference of Eq. 1
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("loops", [False, True])
+def test_delta_modularity_matches_q_difference(oracle_mod, seed, loops):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(3, 10))
+    off, idx, w = random_graph(rng, n, 0.5, wmax=4, self_loops=loops)
+    if len(idx) == 0:
+        pytest.skip("empty graph")
+    o = make(oracle_mod, n, off, idx, w, loops)
+    A = dense_matrix(n, off, idx, w)
+    C = list(rng.integers(0, n, n))
+    o.set_membership(np.array(C, np.uint32))
+    _, _, m2 = o.weights()
+    q0 = newman_q(A, C)
+    for i in range(n):
+        for c in range(n):
+            if c == C[i]:
+                continue
+            num = o.delta_q_num(i, c)  # 2m^2 * dQ = (m2^2 / 2) * dQ
+            assert Fraction(2 * num, m2 * m2) == newman_q(A, move(C, i, c)) - q0
+
+
+# ---------------------------------------------------------------------------
+# Alg. 5 -- local-moving decisions against brute force
+# ---------------------------------------------------------------------------
+
+def substep_class(i, k):
+    return ((i * 0x9E3779B1) & 0xFFFFFFFF) * k >> 32
+
+
+def brute_force_iteration(A, C, F, R, k):
+    """One local-moving iteration by exhaustive search over neighbour
+    communities with exact Q recomputation; same schedule as the oracle."""
+    n = len(A)
+    C = list(C)
+    F = list(F)
+    Fnext = [0] * n
+    S = Fraction(0)
+    m2 = sum(sum(r) for r in A)
+    for sub in range(k):
+        snap = list(C)
+        size = [snap.count(c) for c in range(n)]
+        q0 = newman_q(A, snap)
+        moves = []
+        for i in range(n):
+            if not F[i] or substep_class(i, k) != sub:
+                continue
+            F[i] = 0
+            if not R[i]:
+                continue
+            d = snap[i]
+            cands = sorted({snap[j] for j in range(n) if j != i and A[i][j] > 0} - {d})
+            best, gain = None, None
+            for c in cands:
+                g = newman_q(A, move(snap, i, c)) - q0
+                if gain is None or g > gain:
+                    best, gain = c, g
+            if best is None or gain <= 0:
+                continue
+            if size[d] == 1 and size[best] == 1 and best > d:
+                continue
+            moves.append((i, best, gain))
+        for i, c, g in moves:
+            C[i] = c
+            S += g
+            for j in range(n):
+                if j != i and A[i][j] > 0 and R[j]:
+                    Fnext[j] = 1
+    return C, Fnext, S * m2 * m2 / 2
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("kind", ["weighted", "unit", "loops"])
+def test_move_iteration_matches_brute_force(oracle_mod, seed, k, kind):
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(4, 12))
+    off, idx, w = random_graph(rng, n, 0.4, wmax=1 if kind == "unit" else 3,
+                               self_loops=kind == "loops")
+    if len(idx) == 0:
+        pytest.skip("empty graph")
+    o = make(oracle_mod, n, off, idx, w, kind == "loops")
+    o.set_options(substeps=k)
+    A = dense_matrix(n, off, idx, w)
+    C = list(rng.integers(0, max(2, n // 2), n))
+    F = list((rng.random(n) < 0.8).astype(np.uint8))
+    R = list((rng.random(n) < 0.85).astype(np.uint8))
+    o.set_membership(np.array(C, np.uint32))
+    Fo, moved, dq = o.move_iteration(np.array(F, np.uint8), np.array(R, np.uint8))
+    Cexp, Fexp, Sexp = brute_force_iteration(A, C, F, R, k)
+    assert list(o.membership()) == Cexp
+    assert list(Fo) == Fexp
+    assert Fraction(dq) == Sexp
+    # Sigma after the iteration equals recomputation from the new membership
+    K, S, _ = o.weights()
+    exp = np.zeros(n, np.int64)
+    np.add.at(exp, np.array(Cexp, np.int64), K)
+    assert np.array_equal(S, exp)
+
+
+def test_tie_break_smallest_community(oracle_mod):
+    # vertex 0 links equally to communities 3 and 5 of equal totals: it joins 3
+    e = [(0, 1), (0, 2), (1, 3), (2, 5), (3, 4), (5, 6)]
+    g = synth.EdgeList(7, np.array([a for a, _ in e], np.uint32),
+                       np.array([b for _, b in e], np.uint32), np.ones(len(e), np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = make(oracle_mod, 7, off, idx, w)
+    o.set_options(substeps=1)
+    o.set_membership(np.array([0, 5, 3, 3, 3, 5, 5], np.uint32)[[0, 2, 1, 3, 4, 5, 6]])
+    C = o.membership()
+    assert C[1] != C[2]
+    F = np.zeros(7, np.uint8)
+    F[0] = 1
+    o.move_iteration(F, np.ones(7, np.uint8))
+    assert o.membership()[0] == min(C[1], C[2])
+
+
+def test_singleton_swap_guard(oracle_mod):
+    # two singletons joined by a heavy edge would swap forever under plain
+    # synchronous moves; the minimum-label guard lets only the larger id move
+    g = synth.EdgeList(4, np.array([0, 2], np.uint32), np.array([1, 3], np.uint32),
+                       np.array([5, 1], np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = make(oracle_mod, 4, off, idx, w)
+    o.set_options(substeps=1)
+    o.set_membership(np.arange(4, dtype=np.uint32))
+    o.move_iteration(np.ones(4, np.uint8), np.ones(4, np.uint8))
+    assert list(o.membership()) == [0, 0, 2, 2]
+
+
+# ---------------------------------------------------------------------------
+# Alg. 7 -- incremental K and Sigma equal recomputation from scratch
+# ---------------------------------------------------------------------------
+
+def recompute(o):
+    off, idx, w = o.graph()
+    K = np.add.reduceat(w.astype(np.int64), off[:-1].astype(np.int64)) if len(w) else None
+    deg = np.diff(off.astype(np.int64))
+    Kr = np.zeros(o.n, np.int64)
+    rows = np.repeat(np.arange(o.n), deg)
+    np.add.at(Kr, rows, w.astype(np.int64))
+    C = o.membership()
+    Sr = np.zeros(o.n, np.int64)
+    np.add.at(Sr, C.astype(np.int64), Kr)
+    return Kr, Sr, int(w.astype(np.int64).sum())
+
+
+def weighted_batch(rng, o, n_ins, n_del, wmax=3):
+    off, idx, w = o.graph()
+    edges = edges_of(o.n, off, idx, w)
+    pick = rng.choice(len(edges), size=min(n_del, len(edges)), replace=False)
+    dels = []
+    for p in pick:
+        u, v, wt = edges[p]
+        mode = rng.integers(0, 3)
+        wd = 0 if mode == 0 else int(rng.integers(1, wt + 1))
+        dels.append((v, u, wd) if rng.random() < 0.5 else (u, v, wd))
+    ins = []
+    for _ in range(n_ins):
+        a = int(rng.integers(0, o.n))
+        b = int(rng.integers(0, o.n - 1))
+        b += b >= a
+        ins.append((a, b, int(rng.integers(1, wmax + 1))))
+    if ins and rng.random() < 0.5:
+        ins.append(ins[0])  # the same pair twice: weights add
+    return np.array(dels, np.uint32).reshape(-1, 3), np.array(ins, np.uint32).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_incremental_weights_equal_recomputation(oracle_mod, mode):
+    rng = np.random.default_rng(7 + mode)
+    g = synth.planted_partition(600, 12, 0.3, 8, 4, 9)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    for _ in range(6):
+        d, i = weighted_batch(rng, o, 40, 15)
+        assert o.apply_batch(d, i) == 0
+        K, S, m2 = o.weights()
+        Kr, Sr, m2r = recompute(o)  # against C^{t-1}
+        assert np.array_equal(K, Kr) and np.array_equal(S, Sr) and m2 == m2r
+        o.update(mode)
+        K, S, m2 = o.weights()
+        Kr, Sr, m2r = recompute(o)  # against C^t
+        assert np.array_equal(K, Kr) and np.array_equal(S, Sr) and m2 == m2r
+        assert S.sum() == m2 and K.sum() == m2  # sum Sigma_c = 2m
+
+
+def test_batch_graph_semantics(oracle_mod):
+    # deletions first (w = 0 removes the whole edge, w > 0 decrements), then
+    # insertions (add weight, or create the edge)
+    g = synth.EdgeList(5, np.array([0, 1, 2], np.uint32), np.array([1, 2, 3], np.uint32),
+                       np.array([4, 2, 1], np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(5, off, idx, w)
+    o.static()
+    assert o.apply_batch([(1, 0, 1), (2, 1, 0)], [(2, 1, 3), (3, 4, 2), (4, 3, 1)]) == 0
+    off2, idx2, w2 = o.graph()
+    got = set(edges_of(5, off2, idx2, w2))
+    assert got == {(0, 1, 3), (1, 2, 3), (2, 3, 1), (3, 4, 3)}
+
+
+def test_batch_errors_leave_state_unchanged(oracle_mod):
+    g = synth.sbm(200, 4, 0.2, 0.01, 3)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    with pytest.raises(oracle_mod.OracleError):
+        o.update(2)  # before static
+    assert o.apply_batch([], [(0, 1, 1)]) == -7
+    o.static()
+    before = (o.graph(), o.weights(), o.membership())
+    u, v = int(g.u[0]), int(g.v[0])
+    absent = next((a, b) for a in range(g.n) for b in range(a + 1, g.n)
+                  if b not in set(idx[int(off[a]):int(off[a + 1])]))
+    cases = [
+        ([], [(0, 0, 1)], -1),                       # self-loop
+        ([], [(0, g.n, 1)], -1),                     # vertex out of range
+        ([], [(0, 1, 0)], -1),                       # zero insertion weight
+        ([(u, v, 0), (v, u, 0)], [], -1),            # same edge deleted twice
+        ([absent + (0,)], [], -2),                   # absent edge
+        ([(u, v, 2)], [], -2),                       # more weight than present
+        ([], [(u, v, 0xFFFFFFFF)], -3),              # u32 weight overflow
+        ([absent + (0,)], [(0, 0, 1)], -1),          # invalid wins over not-found
+    ]
+    for d, i, code in cases:
+        assert o.apply_batch(np.array(d, np.uint32).reshape(-1, 3),
+                             np.array(i, np.uint32).reshape(-1, 3)) == code
+        after = (o.graph(), o.weights(), o.membership())
+        for x, y in zip(before[0] + before[1][:2] + (before[2],),
+                        after[0] + after[1][:2] + (after[2],)):
+            assert np.array_equal(x, y)
+        assert before[1][2] == after[1][2]
+
+
+def test_two_m_limit(oracle_mod):
+    # 2m (the sum of all arc weights) must stay below 2^32
+    g = synth.EdgeList(3, np.array([0], np.uint32), np.array([1], np.uint32),
+                       np.array([0x80000000], np.uint32))
+    off, idx, w = synth.to_csr(g)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(3, off, idx, w)  # 2m = 2^32
+    g.w[:] = 0x7FFFFFFF
+    off, idx, w = synth.to_csr(g)
+    oracle_mod.Oracle(3, off, idx, w)  # 2m = 2^32 - 2 is accepted
+    g.w[:] = 0x3FFFFFFF
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(3, off, idx, w)
+    o.static()
+    assert o.apply_batch([], [(1, 2, 0x40000001)]) == -3  # 2m would reach 2^32
+    assert o.apply_batch([], [(1, 2, 0x40000000)]) == 0   # 2m = 2^32 - 2
+
+
+# ---------------------------------------------------------------------------
+# Alg. 6 -- aggregation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("loops", [False, True])
+def test_aggregation_preserves_weight_and_modularity(oracle_mod, seed, loops):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(4, 12))
+    off, idx, w = random_graph(rng, n, 0.45, wmax=4, self_loops=loops)
+    if len(idx) == 0:
+        pytest.skip("empty graph")
+    o = make(oracle_mod, n, off, idx, w, loops)
+    C = rng.integers(0, n, n).astype(np.uint32)
+    o.set_membership(C)
+    soff, sidx, sw = o.aggregate()
+    nv = len(soff) - 1
+    assert nv == len(set(C.tolist()))
+    A = dense_matrix(n, off, idx, w)
+    S = dense_matrix(nv, soff, sidx, sw)
+    assert sum(map(sum, S)) == sum(map(sum, A))  # total weight preserved
+    assert all(S[a][b] == S[b][a] for a in range(nv) for b in range(nv))  # symmetric
+    # renumbering by ascending old label
+    ren = {c: r for r, c in enumerate(sorted(set(C.tolist())))}
+    for a in range(nv):
+        for b in range(nv):
+            exp = sum(A[i][j] for i in range(n) for j in range(n)
+                      if ren[int(C[i])] == a and ren[int(C[j])] == b)
+            assert S[a][b] == exp
+    # Q of the super graph with singletons equals Q of G under C
+    assert newman_q(S, list(range(nv))) == newman_q(A, [ren[int(c)] for c in C])
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1-3 -- marking of initially affected vertices
+# ---------------------------------------------------------------------------
+
+def four_case_graph(oracle_mod):
+    # communities A = {0..3}, B = {4..7}, X = {8, 9, 10}
+    e = [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 7), (3, 4), (0, 7), (8, 9), (9, 10)]
+    g = synth.EdgeList(11, np.array([a for a, _ in e], np.uint32),
+                       np.array([b for _, b in e], np.uint32), np.ones(len(e), np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(11, off, idx, w)
+    o.set_membership(np.array([0, 0, 0, 0, 4, 4, 4, 4, 8, 8, 8], np.uint32))
+    # deletion inside A, deletion across A-B, insertion across A-B,
+    # insertion inside B
+    assert o.apply_batch([(0, 1, 0), (3, 4, 0)], [(2, 5, 1), (4, 6, 1)]) == 0
+    return o
+
+
+def test_dynamic_frontier_marking_rules(oracle_mod):
+    o = four_case_graph(oracle_mod)
+    F, R = o.mark(2)
+    assert set(np.flatnonzero(F)) == {0, 1, 2, 5}  # both endpoints, two rules
+    assert R.all()
+
+
+def test_naive_dynamic_marks_everything(oracle_mod):
+    o = four_case_graph(oracle_mod)
+    F, R = o.mark(0)
+    assert F.all() and R.all()
+
+
+def test_delta_screening_marking(oracle_mod):
+    o = four_case_graph(oracle_mod)
+    F, R = o.mark(1)
+    # intra deletion (0,1) flags community A; insertion (2,5) flags B via the
+    # best community of both sources; X stays untouched
+    assert set(np.flatnonzero(F)) == set(range(8))
+    assert np.array_equal(F, R)
+
+
+def test_delta_screening_best_community(oracle_mod):
+    # source 0 (community 0) gets insertions to communities 5 and 9; the
+    # better one by 2m*H[c] - K_0*Sigma_c is the heavier link
+    e = [(0, 1), (5, 6), (9, 10), (10, 11), (6, 7), (2, 3)]
+    g = synth.EdgeList(12, np.array([a for a, _ in e], np.uint32),
+                       np.array([b for _, b in e], np.uint32), np.ones(len(e), np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(12, off, idx, w)
+    C = np.array([0, 0, 2, 2, 4, 5, 5, 5, 8, 9, 9, 9], np.uint32)
+    o.set_membership(C)
+    assert o.apply_batch([], [(0, 5, 1), (0, 9, 3)]) == 0
+    F, _ = o.mark(1)
+    marked = set(np.flatnonzero(F))
+    assert {9, 10, 11}.issubset(marked)        # community of the best link
+    assert {0, 1, 5, 6}.issubset(marked)        # sources (both ends) and neighbours
+    assert 7 not in marked                      # community 5 itself is not flagged
+    assert not {2, 3, 4, 8} & marked
+
+
+@pytest.mark.parametrize("intra", [1, 6])
+def test_delta_screening_choice_is_best_delta_modularity(oracle_mod, intra):
+    """When all of a source's cross-community links are the inserted ones,
+    H[c] = K_{i->c}, so the DS choice (Alg. 3) must be the neighbour community
+    with the largest exact dQ of moving the source (Eq. 2, recomputed from
+    Eq. 1).  The source's own degree K_i decides between a small community
+    with one new link and a large one with two: intra = 1 picks the large one,
+    intra = 6 the small one."""
+    e = [(0, 1 + k) for k in range(intra)]               # source 0 and its community
+    e += [(10, 11), (11, 12)]                            # community 10: path
+    e += [(20 + k, 21 + k) for k in range(7)]            # community 20: path ...
+    e += [(a, b) for a in range(23, 28) for b in range(a + 2, 28)]  # ... and chords
+    e += [(a, b) for a in range(30, 41) for b in range(a + 1, 41)]  # filler clique
+    n = 41
+    g = synth.EdgeList(n, np.array([a for a, _ in e], np.uint32),
+                       np.array([b for _, b in e], np.uint32), np.ones(len(e), np.uint32))
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(n, off, idx, w)
+    C = np.arange(n, dtype=np.uint32)
+    C[: intra + 1] = 0
+    C[10:13] = 10
+    C[20:28] = 20
+    C[30:41] = 30
+    o.set_membership(C)
+    assert o.apply_batch([], [(0, 10, 1), (0, 20, 1), (0, 21, 1)]) == 0
+    off2, idx2, w2 = o.graph()
+    A = dense_matrix(n, off2, idx2, w2)
+    q0 = newman_q(A, list(C))
+    gains = {c: newman_q(A, move(list(C), 0, c)) - q0 for c in (10, 20)}
+    best = 20 if gains[20] > gains[10] else 10
+    assert best == (20 if intra == 1 else 10)  # the case is built to flip
+    far = {10: {12}, 20: set(range(23, 28))}   # members no source is adjacent to
+    marked = set(np.flatnonzero(o.mark(1)[0]))
+    assert far[best] <= marked
+    assert not far[30 - best] & marked
+    assert not set(range(30, 41)) & marked
+
+
+def test_figure3_initial_frontier(oracle_mod):
+    """Fig. 3 (Section 3.1.1): deletion (1,2) inside the red community and
+    insertion (4,12) across red/blue make {1, 2, 4, 12} the initial frontier;
+    in the first iteration vertex 2 moves to green, marking 8 and 10."""
+    path = os.path.join(GOLDEN, "fig3_frontier.txt")
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            key, _, val = line.partition(":")
+            rows[key.strip()] = [int(x) for x in val.split()]
+    n = rows["n"][0]
+    ed = np.array(rows["edges"], np.uint32).reshape(-1, 3)
+    g = synth.EdgeList(n, ed[:, 0], ed[:, 1], ed[:, 2])
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(n, off, idx, w)
+    o.set_membership(np.array(rows["membership"], np.uint32))
+    assert o.apply_batch(np.array(rows["delete"], np.uint32).reshape(-1, 3),
+                         np.array(rows["insert"], np.uint32).reshape(-1, 3)) == 0
+    F, R = o.mark(2)
+    assert set(np.flatnonzero(F)) == set(rows["initial_frontier"])
+    o.set_options(substeps=1)
+    F1, moved, _ = o.move_iteration(F, R)
+    v, c = rows["first_move"]
+    assert o.membership()[v] == c and moved[v]
+    assert set(rows["first_marked"]).issubset(set(np.flatnonzero(F1)))
+
+
+# ---------------------------------------------------------------------------
+# Alg. 4 -- driver: tolerance, mode equivalences, empty batch
+# ---------------------------------------------------------------------------
+
+def test_iteration_tolerance_is_exact(oracle_mod):
+    g = synth.sbm(2000, 20, 0.05, 0.002, 12)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    _, _, m2 = o.weights()
+    tr = o.trace()
+    tau = Fraction(1, 100)
+    for t, (_, _, s) in enumerate(tr):
+        converged = Fraction(s, m2 * m2 // 2) <= tau  # sum dQ = S / (2 m^2)
+        if t < len(tr) - 1:
+            assert not converged
+        else:
+            assert converged or len(tr) == 20
+
+
+def test_static_equals_nd_from_singletons(oracle_mod):
+    g = synth.sbm(1500, 15, 0.06, 0.003, 21)
+    off, idx, w = synth.to_csr(g)
+    a = oracle_mod.Oracle(g.n, off, idx, w)
+    a.static()
+    b = oracle_mod.Oracle(g.n, off, idx, w)
+    b.set_membership(np.arange(g.n, dtype=np.uint32))
+    b.update(0)
+    assert np.array_equal(a.membership(), b.membership())
+
+
+def test_df_with_everything_affected_equals_nd(oracle_mod):
+    g = synth.sbm(1500, 15, 0.06, 0.003, 22)
+    off, idx, w = synth.to_csr(g)
+    d, i = synth.random_batch(g.n, g, 40, 10, 5)
+    a = oracle_mod.Oracle(g.n, off, idx, w)
+    a.static()
+    a.apply_batch(d, i)
+    b = oracle_mod.Oracle(g.n, off, idx, w)
+    b.static()
+    b.apply_batch(d, i)
+    a.update(0)
+    ones = np.ones(g.n, np.uint8)
+    b.louvain_from(ones, ones)  # DF marking replaced by "all affected"
+    assert np.array_equal(a.membership(), b.membership())
+
+
+def test_empty_batch_leaves_state_unchanged(oracle_mod):
+    g = synth.sbm(1000, 10, 0.08, 0.004, 23)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    before = (o.membership(), o.weights())
+    o.apply_batch([], [])
+    o.update(2)
+    assert np.array_equal(before[0], o.membership())
+    assert np.array_equal(before[1][0], o.weights()[0])
+    assert np.array_equal(before[1][1], o.weights()[1])
+    assert o.stats()["iterations"] == [1] and o.stats()["affected_ever"] == 0
+
+
+def test_planted_partition_sanity(oracle_mod):
+    # not a parity pin: Louvain should find most of the planted structure
+    g = synth.sbm(10000, 50, 0.02, 0.0002, 1)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    q_static = o.modularity()[0]
+    o.set_membership(np.repeat(np.arange(50), 200).astype(np.uint32))
+    q_planted = o.modularity()[0]
+    assert 0.6 < q_planted < 0.7
+    assert q_static > q_planted - 0.15
