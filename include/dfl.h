@@ -1,0 +1,233 @@
+/*
+ * dfl.h -- C ABI of the GB300 Dynamic Frontier Louvain library (libdfl.so).
+ *
+ * The library keeps one dynamic graph and its community state on the GPU
+ * and updates the communities after each batch of edge deletions and
+ * insertions, as in "DF Louvain: Fast Incrementally Expanding Approach for
+ * Community Detection on Dynamic Graphs" (arXiv 2404.19634):
+ *   - the batch is applied to a slack CSR graph kept on the device,
+ *   - vertex weighted degrees K_i and community totals Sigma_c are updated
+ *     incrementally (Alg. 7),
+ *   - the initially affected vertices are marked (Alg. 1 DF, Alg. 2 ND,
+ *     Alg. 3 DS),
+ *   - Louvain runs from the previous membership (Alg. 4): local-moving with
+ *     frontier expansion (Alg. 5), aggregation into a super-vertex graph
+ *     (Alg. 6), later passes on the super-vertex graph.
+ *
+ * Conventions for every call:
+ *   - Return DFL_OK (0) on success or a negative DFL_ERR_* code.  On error
+ *     the handle's state is unchanged (batches are validated before any
+ *     mutation) and dfl_last_error() describes the cause.  After
+ *     DFL_ERR_CUDA the handle should be destroyed.
+ *   - Vertex ids are uint32 in [0, n); edge weights are uint32 > 0; the sum
+ *     of all arc weights, 2m, must stay below 2^32 (DFL_ERR_OVERFLOW).
+ *     K, Sigma and 2m are reported as int64.
+ *   - `mem_kind` says where a caller buffer lives: DFL_MEM_HOST (pageable or
+ *     pinned host memory) or DFL_MEM_DEVICE (device memory of the handle's
+ *     GPU).  Input buffers are only read during the call and are copied;
+ *     output buffers are owned and sized by the caller.
+ *   - All device work runs on the handle's CUDA stream, in stream order.
+ *     Calls return after the work they started is complete unless stated
+ *     otherwise.  A handle must not be used from two threads at once.
+ *   - The computation is deterministic: the same inputs give the same
+ *     membership, K, Sigma and modularity on every run.
+ *
+ * Local-moving schedule (the paper's own is asynchronous; this library fixes
+ * a deterministic one): each iteration visits the frontier in `substeps`
+ * hash classes (class of vertex i = top bits of i * 0x9E3779B1 mod 2^32);
+ * the vertices of one class decide together against the state left by the
+ * previous class, then their moves are applied at once.  A vertex moves to
+ * the neighbour community with the largest 2m*K_{i->c} - K_i*Sigma_c (ties to
+ * the smallest id) if that beats staying (delta-modularity > 0, Eq. 2), except
+ * that a singleton never moves into a singleton community with a larger id.
+ * The per-iteration tolerance test on the summed delta-modularity is exact.
+ */
+#ifndef DFL_H
+#define DFL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handle: graph, K, Sigma, 2m, membership and work buffers, all owned
+ * by the library and released by dfl_destroy. */
+typedef struct dfl_handle dfl_handle;
+
+/* One undirected edge of a batch, given once (the library adds both arcs).
+ * For a deletion, w = 0 removes the whole edge and w > 0 removes that much
+ * weight; for an insertion, w > 0 is added to the edge (created if absent). */
+typedef struct {
+  uint32_t u, v, w;
+} dfl_edge;
+
+enum { DFL_ND = 0, DFL_DS = 1, DFL_DF = 2 };
+enum { DFL_MEM_HOST = 0, DFL_MEM_DEVICE = 1 };
+
+enum {
+  DFL_OK = 0,
+  DFL_ERR_INVALID = -1,   /* bad argument: vertex id >= n, self-loop, zero insert
+                             weight, an edge deleted twice in one call, a
+                             non-symmetric / unsorted / duplicated input CSR */
+  DFL_ERR_NOT_FOUND = -2, /* deletion of an absent edge, or of more weight than present */
+  DFL_ERR_OVERFLOW = -3,  /* an edge weight would exceed 2^32-1, or 2m would reach 2^32 */
+  DFL_ERR_NOMEM = -4,     /* device or pinned host allocation failed */
+  DFL_ERR_CUDA = -5,      /* a CUDA runtime call failed */
+  DFL_ERR_TIMEOUT = -6,   /* reserved for bounded device waits */
+  DFL_ERR_STATE = -7      /* call out of order, e.g. dfl_update before dfl_static */
+};
+
+/* Option flags. */
+enum {
+  DFL_FLAG_PROFILE = 1u, /* time every kernel class with CUDA events (dfl_profile) */
+  DFL_FLAG_TRACE = 2u    /* reserved */
+};
+
+/* Algorithm options; defaults from Section 4.1.2 of the paper. */
+typedef struct {
+  uint32_t max_iterations; /* MAX_ITERATIONS per pass, default 20 */
+  uint32_t max_passes;     /* MAX_PASSES, default 10 */
+  uint64_t tau_num;        /* iteration tolerance tau = tau_num / tau_den, default 1/100 */
+  uint64_t tau_den;
+  uint64_t tolerance_drop; /* tau is divided by this after every pass, default 10 */
+  double tau_agg;          /* aggregation tolerance, default 0.8 (1.0 disables) */
+  uint32_t substeps;       /* synchronous sub-steps per iteration: 1, 2, 4 (default) or 8 */
+  uint32_t flags;          /* DFL_FLAG_* */
+} dfl_options;
+
+/* Statistics of the last dfl_static / dfl_update. */
+typedef struct {
+  uint32_t passes;             /* Louvain passes executed */
+  uint32_t iterations[16];     /* local-moving iterations of each pass (first 16) */
+  uint64_t affected_initial;   /* vertices in the initial frontier */
+  uint64_t affected_ever;      /* vertices processed at least once in the first pass */
+  uint64_t kernel_launches;    /* kernels launched by this handle since creation */
+  uint64_t num_arcs;           /* arcs of the current graph G^t (2 per edge) */
+  uint64_t arc_pool;           /* arc slots allocated for the slack CSR */
+  uint32_t max_degree;         /* largest vertex degree of G^t (upper bound) */
+  uint32_t num_communities;    /* distinct labels of the last first-pass membership */
+} dfl_stats_t;
+
+/* Per kernel class timing and algorithmic traffic (DFL_FLAG_PROFILE). */
+enum {
+  DFL_PROF_APPLY = 0,   /* batch apply, K/Sigma update */
+  DFL_PROF_MARK = 1,    /* initial frontier marking */
+  DFL_PROF_MOVE = 2,    /* local-moving decide kernels (the hot loop) */
+  DFL_PROF_COMMIT = 3,  /* local-moving move-apply kernels */
+  DFL_PROF_AGG = 4,     /* renumbering and aggregation */
+  DFL_PROF_OTHER = 5,
+  DFL_PROF_CLASSES = 6
+};
+typedef struct {
+  uint64_t launches[DFL_PROF_CLASSES];
+  double ms[DFL_PROF_CLASSES];         /* summed kernel durations (CUDA events) */
+  uint64_t bytes[DFL_PROF_CLASSES];    /* algorithmic bytes moved (see DESIGN) */
+} dfl_profile_t;
+
+/* Fill *opt with the defaults above. */
+void dfl_default_options(dfl_options* opt);
+
+/* Create a handle from a symmetric CSR graph (Section 2: undirected, both
+ * arcs of every edge present with equal weights).  offsets[n+1] (uint64),
+ * indices[nnz], weights[nnz]; rows must be sorted by neighbour id with no
+ * duplicates and no self-loops; nnz = offsets[n].  The graph is copied into
+ * a slack CSR on the device; communities are not computed (call dfl_static).
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream); opt may
+ * be NULL for defaults.  n must be below 2^31. */
+int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint32_t* indices,
+               const uint32_t* weights, uint64_t nnz, int mem_kind, const dfl_options* opt,
+               void* cuda_stream);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void dfl_destroy(dfl_handle* h);
+
+/* Replace the options or the stream (the stream change is stream-ordered:
+ * the caller must make the new stream wait for the old one if needed). */
+int dfl_set_options(dfl_handle* h, const dfl_options* opt);
+int dfl_set_stream(dfl_handle* h, void* cuda_stream);
+
+/* Static Louvain (the paper's "Static" baseline, GVE-Louvain): K from
+ * scratch, every vertex its own community, every vertex affected.  Clears
+ * the pending batch. */
+int dfl_static(dfl_handle* h);
+
+/* Apply a batch update (Section 2.4): deletions first, then insertions,
+ * each edge given once.  Updates the graph, K, Sigma (with the current
+ * membership C^{t-1}, Alg. 7) and 2m immediately, and appends the batch to
+ * the pending list consumed by the next dfl_update.  Several calls may
+ * precede one dfl_update.  Requires dfl_static first (DFL_ERR_STATE).
+ * Errors (nothing is changed): DFL_ERR_INVALID, DFL_ERR_NOT_FOUND,
+ * DFL_ERR_OVERFLOW; if several apply, INVALID is reported before NOT_FOUND
+ * before OVERFLOW. */
+int dfl_apply_batch(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const dfl_edge* ins,
+                    uint64_t n_ins, int mem_kind);
+
+/* Update the communities for the pending batch with DFL_ND (Alg. 2),
+ * DFL_DS (Alg. 3) or DFL_DF (Alg. 1); runs Louvain (Alg. 4-6) from the
+ * current membership and clears the pending list. */
+int dfl_update(dfl_handle* h, int mode);
+
+/* Membership C^t (n uint32 labels in [0, n)). */
+int dfl_membership(const dfl_handle* h, uint32_t* out, int mem_kind);
+
+/* Modularity of the current membership (Eq. 1): Q = (2m*sum_c sigma_c -
+ * sum_c Sigma_c^2) / (2m)^2, computed exactly in integers and converted once
+ * to double (0 when 2m = 0).  parts (optional, may be NULL) receives the
+ * numerator and denominator as {num_hi, num_lo, den_hi, den_lo}. */
+int dfl_modularity(dfl_handle* h, double* q, int64_t* parts);
+
+/* K (n), Sigma (n, indexed by community label) and 2m; any pointer may be NULL. */
+int dfl_weights(dfl_handle* h, int64_t* K, int64_t* Sigma, int64_t* two_m, int mem_kind);
+
+/* Number of arcs of G^t, and G^t as a compact CSR with sorted rows
+ * (offsets n+1, indices and weights num_arcs). */
+int dfl_num_arcs(dfl_handle* h, uint64_t* num_arcs);
+int dfl_graph(dfl_handle* h, uint64_t* offsets, uint32_t* indices, uint32_t* weights,
+              int mem_kind);
+
+int dfl_stats(dfl_handle* h, dfl_stats_t* s);
+
+/* Timings and algorithmic bytes per kernel class accumulated since the last
+ * reset (only with DFL_FLAG_PROFILE).  Synchronizes the stream. */
+int dfl_profile(dfl_handle* h, dfl_profile_t* p, int reset);
+
+/* First-pass trace of the last Louvain run: for each iteration
+ * {vertices processed, vertices moved, S_hi, S_lo} where S is the sum of the
+ * movers' numerators 2m^2 * dQ (Eq. 2).  Returns the iteration count in
+ * *len; writes at most cap iterations. */
+int dfl_trace(dfl_handle* h, uint64_t* out, uint32_t cap, uint32_t* len);
+
+/* Message of the last error on this handle ("" if none). */
+const char* dfl_last_error(const dfl_handle* h);
+
+/* ---- Inspection entry points used by the parity tests ------------------ */
+
+/* Replace the membership; K, Sigma, community sizes and 2m are recomputed
+ * from the graph and the pending batch is cleared. */
+int dfl_set_membership(dfl_handle* h, const uint32_t* C, int mem_kind);
+
+/* Initial frontier and affected range (one byte per vertex) that `mode`
+ * would use for the pending batch, without running Louvain. */
+int dfl_mark(dfl_handle* h, int mode, uint8_t* F, uint8_t* R, int mem_kind);
+
+/* Run Louvain from the current membership with an explicit initial
+ * frontier F0 and first-pass range R0 (one byte per vertex). */
+int dfl_louvain_from(dfl_handle* h, const uint8_t* F0, const uint8_t* R0, int mem_kind);
+
+/* One local-moving iteration (all sub-steps) on G^t: F (in: frontier, out:
+ * next frontier), R range, moved (out: 1 for movers), dq = {S_hi, S_lo}. */
+int dfl_move_iteration(dfl_handle* h, uint8_t* F, const uint8_t* R, uint8_t* moved,
+                       int64_t* dq, int mem_kind);
+
+/* Aggregate G^t with the current membership renumbered by ascending label
+ * (Alg. 6) and export the super-vertex graph as CSR with rows sorted by
+ * neighbour.  With offsets == NULL only *nv and *na are written. */
+int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets,
+                  uint32_t* indices, uint64_t* weights);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFL_H */

@@ -1,0 +1,363 @@
+"""GB300 (sm_103a) Dynamic Frontier Louvain: Python binding of libdfl.so.
+
+Thin ctypes marshalling over the C ABI declared in include/dfl.h: the module
+functions carry the C names (dfl_create, dfl_static, dfl_apply_batch,
+dfl_update, dfl_membership, dfl_modularity, ...) and the `Dfl` class wraps a
+handle.  Every step of the computation runs in the CUDA kernels of
+`csrc/`; this module only converts arguments.  Host inputs are numpy arrays;
+device inputs are CUDA tensors (PyTorch supplies device memory and streams).
+There is no CPU fallback: if the library is not built, importing the
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import glob
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libdfl.so")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+
+ND, DS, DF = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+FLAG_PROFILE = 1
+PROF_APPLY, PROF_MARK, PROF_MOVE, PROF_COMMIT, PROF_AGG, PROF_OTHER = range(6)
+PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other"]
+
+ERRORS = {0: "ok", -1: "invalid", -2: "not_found", -3: "overflow", -4: "nomem", -5: "cuda",
+          -6: "timeout", -7: "state"}
+
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
+              "-Xcompiler", "-fPIC"]
+
+
+class DflError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"dfl error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def _nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a (one nvcc per file, in parallel) and link
+    _build/libdfl.so.  Rebuilds only what is older than its sources."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(_CSRC, "*.cu")))
+    headers = glob.glob(os.path.join(_CSRC, "*.cuh")) + glob.glob(os.path.join(_INCLUDE, "*.h"))
+    newest_hdr = max(os.path.getmtime(p) for p in headers)
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.basename(src)[:-3] + ".o")
+        if (not force and os.path.exists(obj)
+                and os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_hdr)):
+            return obj
+        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        os.replace(obj + ".tmp", obj)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(map(os.path.getmtime, objs)):
+        tmp = _LIB + ".tmp"
+        subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a"] + objs
+                              + ["-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Options(ct.Structure):
+    _fields_ = [("max_iterations", ct.c_uint32), ("max_passes", ct.c_uint32),
+                ("tau_num", ct.c_uint64), ("tau_den", ct.c_uint64),
+                ("tolerance_drop", ct.c_uint64), ("tau_agg", ct.c_double),
+                ("substeps", ct.c_uint32), ("flags", ct.c_uint32)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("passes", ct.c_uint32), ("iterations", ct.c_uint32 * 16),
+                ("affected_initial", ct.c_uint64), ("affected_ever", ct.c_uint64),
+                ("kernel_launches", ct.c_uint64), ("num_arcs", ct.c_uint64),
+                ("arc_pool", ct.c_uint64), ("max_degree", ct.c_uint32),
+                ("num_communities", ct.c_uint32)]
+
+
+class Profile(ct.Structure):
+    _fields_ = [("launches", ct.c_uint64 * 6), ("ms", ct.c_double * 6), ("bytes", ct.c_uint64 * 6)]
+
+
+_lib = None
+
+# Every function the header declares, with its argument types.
+_P = ct.c_void_p
+_SIGS = {
+    "dfl_default_options": (None, [ct.POINTER(Options)]),
+    "dfl_create": (ct.c_int, [ct.POINTER(_P), ct.c_uint32, _P, _P, _P, ct.c_uint64, ct.c_int,
+                              ct.POINTER(Options), _P]),
+    "dfl_destroy": (None, [_P]),
+    "dfl_set_options": (ct.c_int, [_P, ct.POINTER(Options)]),
+    "dfl_set_stream": (ct.c_int, [_P, _P]),
+    "dfl_static": (ct.c_int, [_P]),
+    "dfl_apply_batch": (ct.c_int, [_P, _P, ct.c_uint64, _P, ct.c_uint64, ct.c_int]),
+    "dfl_update": (ct.c_int, [_P, ct.c_int]),
+    "dfl_membership": (ct.c_int, [_P, _P, ct.c_int]),
+    "dfl_modularity": (ct.c_int, [_P, ct.POINTER(ct.c_double), _P]),
+    "dfl_weights": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_int64), ct.c_int]),
+    "dfl_num_arcs": (ct.c_int, [_P, ct.POINTER(ct.c_uint64)]),
+    "dfl_graph": (ct.c_int, [_P, _P, _P, _P, ct.c_int]),
+    "dfl_stats": (ct.c_int, [_P, ct.POINTER(Stats)]),
+    "dfl_profile": (ct.c_int, [_P, ct.POINTER(Profile), ct.c_int]),
+    "dfl_trace": (ct.c_int, [_P, _P, ct.c_uint32, ct.POINTER(ct.c_uint32)]),
+    "dfl_last_error": (ct.c_char_p, [_P]),
+    "dfl_set_membership": (ct.c_int, [_P, _P, ct.c_int]),
+    "dfl_mark": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "dfl_louvain_from": (ct.c_int, [_P, _P, _P, ct.c_int]),
+    "dfl_move_iteration": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
+    "dfl_aggregate": (ct.c_int, [_P, ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint64), _P, _P, _P]),
+}
+
+
+def library_path() -> str:
+    return _LIB
+
+
+def load(path: str | None = None):
+    """Load libdfl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or _LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdfl.so not built ({p}); run __graft_entry__.build()")
+        lib = ct.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().dfl_default_options(ct.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _is_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch") and hasattr(x, "data_ptr")
+
+
+def _buf(x, dtype):
+    """(pointer, mem_kind, keepalive) for a numpy array or a CUDA tensor."""
+    if x is None:
+        return None, MEM_HOST, None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ct.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ct.c_void_p(a.ctypes.data), MEM_HOST, a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ct.c_void_p(stream.cuda_stream)
+    return ct.c_void_p(int(stream))
+
+
+def _i128(hi: int, lo: int) -> int:
+    v = ((hi & 0xFFFFFFFFFFFFFFFF) << 64) | (lo & 0xFFFFFFFFFFFFFFFF)
+    return v - (1 << 128) if v >> 127 else v
+
+
+class Dfl:
+    """One dynamic graph and its community state on the GPU."""
+
+    def __init__(self, n, offsets, indices, weights, options: Options | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        h = ct.c_void_p()
+        off, mk, k0 = _buf(offsets, np.uint64)
+        idx, _, k1 = _buf(indices, np.uint32)
+        w, _, k2 = _buf(weights, np.uint32)
+        nnz = int(indices.shape[0]) if hasattr(indices, "shape") else len(indices)
+        self.n = int(n)
+        rc = lib.dfl_create(ct.byref(h), self.n, off, idx, w, nnz, mk,
+                            ct.byref(options) if options is not None else None, _stream_ptr(stream))
+        if rc != 0:
+            raise DflError(rc, "dfl_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dfl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DflError(rc, self._lib.dfl_last_error(self._h).decode())
+        return rc
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_options(self, options: Options):
+        self._check(self._lib.dfl_set_options(self._h, ct.byref(options)))
+
+    def set_stream(self, stream):
+        self._check(self._lib.dfl_set_stream(self._h, _stream_ptr(stream)))
+
+    def static(self):
+        self._check(self._lib.dfl_static(self._h))
+
+    def apply_batch(self, dels, ins, check: bool = True) -> int:
+        """dels/ins: (k, 3) uint32 arrays (u, v, w) or CUDA tensors (int32/uint32)."""
+        d, mk1, k0 = _buf(dels, np.uint32)
+        i, mk2, k1 = _buf(ins, np.uint32)
+        nd = int(dels.shape[0]) if dels is not None else 0
+        ni = int(ins.shape[0]) if ins is not None else 0
+        mk = mk1 if nd else mk2
+        rc = self._lib.dfl_apply_batch(self._h, d, nd, i, ni, mk)
+        if check:
+            self._check(rc)
+        return rc
+
+    def update(self, mode: int):
+        self._check(self._lib.dfl_update(self._h, mode))
+
+    def membership(self, out=None):
+        if out is None:
+            out = np.zeros(self.n, np.uint32)
+        p, mk, _ = _buf(out, np.uint32)
+        self._check(self._lib.dfl_membership(self._h, p, mk))
+        return out
+
+    def modularity(self):
+        q = ct.c_double()
+        parts = np.zeros(4, np.int64)
+        self._check(self._lib.dfl_modularity(self._h, ct.byref(q), parts.ctypes.data_as(ct.c_void_p)))
+        return q.value, _i128(int(parts[0]), int(parts[1])), _i128(int(parts[2]), int(parts[3]))
+
+    def weights(self):
+        K = np.zeros(self.n, np.int64)
+        S = np.zeros(self.n, np.int64)
+        m2 = ct.c_int64()
+        self._check(self._lib.dfl_weights(self._h, K.ctypes.data_as(ct.c_void_p),
+                                          S.ctypes.data_as(ct.c_void_p), ct.byref(m2), MEM_HOST))
+        return K, S, int(m2.value)
+
+    def num_arcs(self) -> int:
+        na = ct.c_uint64()
+        self._check(self._lib.dfl_num_arcs(self._h, ct.byref(na)))
+        return int(na.value)
+
+    def graph(self):
+        na = self.num_arcs()
+        off = np.zeros(self.n + 1, np.uint64)
+        idx = np.zeros(max(na, 1), np.uint32)
+        w = np.zeros(max(na, 1), np.uint32)
+        self._check(self._lib.dfl_graph(self._h, off.ctypes.data_as(ct.c_void_p),
+                                        idx.ctypes.data_as(ct.c_void_p),
+                                        w.ctypes.data_as(ct.c_void_p), MEM_HOST))
+        return off, idx[:na], w[:na]
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._lib.dfl_stats(self._h, ct.byref(s)))
+        return {"passes": s.passes, "iterations": list(s.iterations)[: s.passes],
+                "affected_initial": s.affected_initial, "affected_ever": s.affected_ever,
+                "kernel_launches": s.kernel_launches, "num_arcs": s.num_arcs,
+                "arc_pool": s.arc_pool, "max_degree": s.max_degree,
+                "num_communities": s.num_communities}
+
+    def profile(self, reset: bool = False) -> dict:
+        p = Profile()
+        self._check(self._lib.dfl_profile(self._h, ct.byref(p), 1 if reset else 0))
+        return {PROF_NAMES[k]: {"launches": p.launches[k], "ms": p.ms[k], "bytes": p.bytes[k]}
+                for k in range(6)}
+
+    def trace(self):
+        ln = ct.c_uint32()
+        self._check(self._lib.dfl_trace(self._h, None, 0, ct.byref(ln)))
+        out = np.zeros(4 * max(ln.value, 1), np.uint64)
+        self._check(self._lib.dfl_trace(self._h, out.ctypes.data_as(ct.c_void_p), ln.value,
+                                        ct.byref(ln)))
+        return [(int(out[4 * k]), int(out[4 * k + 1]), (int(out[4 * k + 2]) << 64) | int(out[4 * k + 3]))
+                for k in range(ln.value)]
+
+    def set_membership(self, C):
+        p, mk, _ = _buf(C, np.uint32)
+        self._check(self._lib.dfl_set_membership(self._h, p, mk))
+
+    def mark(self, mode: int):
+        F = np.zeros(self.n, np.uint8)
+        R = np.zeros(self.n, np.uint8)
+        self._check(self._lib.dfl_mark(self._h, mode, F.ctypes.data_as(ct.c_void_p),
+                                       R.ctypes.data_as(ct.c_void_p), MEM_HOST))
+        return F, R
+
+    def louvain_from(self, F0, R0):
+        f, _, k0 = _buf(np.asarray(F0, np.uint8), np.uint8)
+        r, _, k1 = _buf(np.asarray(R0, np.uint8), np.uint8)
+        self._check(self._lib.dfl_louvain_from(self._h, f, r, MEM_HOST))
+
+    def move_iteration(self, F, R):
+        F = np.array(F, np.uint8)
+        R = np.ascontiguousarray(R, np.uint8)
+        moved = np.zeros(self.n, np.uint8)
+        dq = np.zeros(2, np.int64)
+        self._check(self._lib.dfl_move_iteration(self._h, F.ctypes.data_as(ct.c_void_p),
+                                                 R.ctypes.data_as(ct.c_void_p),
+                                                 moved.ctypes.data_as(ct.c_void_p),
+                                                 dq.ctypes.data_as(ct.c_void_p), MEM_HOST))
+        return F, moved, (int(dq[0]) << 64) | (int(dq[1]) & 0xFFFFFFFFFFFFFFFF)
+
+    def aggregate(self):
+        nv = ct.c_uint32()
+        na = ct.c_uint64()
+        self._check(self._lib.dfl_aggregate(self._h, ct.byref(nv), ct.byref(na), None, None, None))
+        off = np.zeros(nv.value + 1, np.uint64)
+        idx = np.zeros(max(na.value, 1), np.uint32)
+        w = np.zeros(max(na.value, 1), np.uint64)
+        self._check(self._lib.dfl_aggregate(self._h, ct.byref(nv), ct.byref(na),
+                                            off.ctypes.data_as(ct.c_void_p),
+                                            idx.ctypes.data_as(ct.c_void_p),
+                                            w.ctypes.data_as(ct.c_void_p)))
+        return off, idx[: na.value], w[: na.value]
+
+
+def __getattr__(name):
+    # module-level access to the raw C functions under their C names
+    if name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)

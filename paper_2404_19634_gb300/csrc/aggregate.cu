@@ -1,0 +1,359 @@
+// Aggregation phase (Alg. 6): collapse each community of G' into one
+// super-vertex of G''.
+//   1. community vertex counts and total degrees (one pass over vertices),
+//   2. exclusive scans: community-vertex CSR offsets, and super-vertex row
+//      offsets from the total degree (an over-estimate, so rows have holes),
+//   3. community-vertex CSR fill,
+//   4. per community, a hash merge of its members' arcs keyed by the
+//      neighbour's community, self-loops included (scanCommunities with
+//      self = true); distinct keys are written as the super-vertex's row, and
+//      its weight K'' = Sigma'' is the row sum (Alg. 4, weight reset).
+// Communities are binned by total degree: one warp with a shared-memory
+// table (<= 256), one block with a shared-memory table (<= 4096), one block
+// with a global-memory table (larger).
+#include "common.cuh"
+
+namespace dfl {
+
+namespace {
+
+__global__ void k_agg_count(GraphView g, const uint32_t* __restrict__ Cp, uint32_t* __restrict__ cnt,
+                            unsigned long long* __restrict__ tdeg) {
+  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < g.nv;
+       v += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t c = Cp[v];
+    atomicAdd(&cnt[c], 1u);
+    uint32_t d = g.deg[v];
+    if (d) atomicAdd(&tdeg[c], (unsigned long long)d);
+  }
+}
+
+// Round every community's total degree up to an even count (rows then start
+// 16-byte aligned), track the maximum, and bin the community.
+__global__ void k_agg_bins(uint32_t ncomm, unsigned long long* __restrict__ tdeg, uint32_t* lists,
+                           Segs seg, Ctrl* ctrl) {
+  uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t c0 = blockIdx.x * uint64_t(blockDim.x); c0 < ncomm; c0 += stride) {
+    uint64_t c = c0 + threadIdx.x;
+    bool valid = c < ncomm;
+    uint32_t key = 0;
+    if (valid) {
+      unsigned long long t = tdeg[c];
+      unsigned long long te = (t + 1) & ~1ull;
+      tdeg[c] = te;
+      uint32_t tc = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(t);
+      key = tc <= kBinWarpHash ? 0u : tc <= kBinBlock ? 1u : 2u;
+      if (key == 2) atomicMax(&ctrl->red_u, tc);
+    }
+    append_vertex(uint32_t(c), valid, key, lists, seg, ctrl, 1);
+  }
+}
+
+__global__ void k_agg_fill(uint32_t nv, const uint32_t* __restrict__ Cp, const uint32_t* __restrict__ coff,
+                           uint32_t* __restrict__ fillc, uint32_t* __restrict__ members) {
+  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < nv;
+       v += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t c = Cp[v];
+    members[coff[c] + atomicAdd(&fillc[c], 1u)] = uint32_t(v);
+  }
+}
+
+struct AggArgs {
+  GraphView g;
+  const uint32_t* Cp;
+  const uint32_t* coff;
+  const uint32_t* members;
+  const unsigned long long* soff;
+  uint32_t* deg_out;
+  uint2* arcs_out;
+  long long* Knew;
+  const uint32_t* list;
+  const unsigned int* count;
+  uint32_t ncomm;
+  Ctrl* ctrl;
+  uint2* gtable;
+  uint32_t gslots;
+};
+
+__device__ __forceinline__ bool agg_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
+                                        uint32_t w) {
+  uint32_t s = hash32(c) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    uint32_t prev = atomicCAS(&keys[s], kEmpty, c);
+    if (prev == kEmpty || prev == c) {
+      atomicAdd(&vals[s], w);
+      return true;
+    }
+    s = (s + 1) & mask;
+  }
+  return false;
+}
+
+constexpr uint32_t kAggWarpSlots = 512;
+constexpr int kAggWarps = 8;
+
+// Bin 0: one warp per community (total degree <= 256).
+__global__ void __launch_bounds__(256) k_agg_warp(AggArgs a) {
+  __shared__ uint32_t skeys[kAggWarps][kAggWarpSlots];
+  __shared__ uint32_t svals[kAggWarps][kAggWarpSlots];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  uint32_t* keys = skeys[wib];
+  uint32_t* vals = svals[wib];
+  const uint32_t cnt = *a.count;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned int maxd = 0;
+  for (uint64_t t = warp; t < cnt; t += nwarps) {
+    const uint32_t c = a.list[t];
+    const unsigned long long td = a.soff[c + 1] - a.soff[c];
+    uint32_t slots = 32;
+    while (slots < 2 * td && slots < kAggWarpSlots) slots <<= 1;
+    const uint32_t mask = slots - 1;
+    for (uint32_t s = lane; s < slots; s += 32) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (uint32_t m = a.coff[c]; m < a.coff[c + 1]; ++m) {
+      uint32_t v = a.members[m];
+      unsigned long long o = a.g.off[v];
+      uint32_t d = a.g.deg[v];
+      for (uint32_t k = lane; k < d; k += 32) {
+        uint2 arc = a.g.arcs[o + k];
+        ok &= agg_add(keys, vals, mask, a.Cp[arc.x], arc.y);
+      }
+    }
+    if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
+    __syncwarp();
+    const unsigned long long base = a.soff[c];
+    uint32_t pos = 0;
+    unsigned long long ksum = 0;
+    for (uint32_t s0 = 0; s0 < slots; s0 += 32) {
+      uint32_t s = s0 + lane;
+      uint32_t key = s < slots ? keys[s] : kEmpty;
+      bool has = key != kEmpty;
+      unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+      if (has) {
+        uint32_t val = vals[s];
+        a.arcs_out[base + pos + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, val);
+        ksum += val;
+      }
+      pos += __popc(m);
+    }
+    for (int x = 16; x; x >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, x);
+    if (lane == 0) {
+      a.deg_out[c] = pos;
+      a.Knew[c] = (long long)ksum;
+    }
+    maxd = max(maxd, pos);
+    __syncwarp();
+  }
+  if (lane == 0 && maxd) atomicMax(&a.ctrl->max_deg, maxd);
+}
+
+// Bins 1 and 2: one block per community; a warp per member.
+template <bool kGlobal>
+__global__ void __launch_bounds__(512) k_agg_block(AggArgs a) {
+  extern __shared__ uint32_t dyn[];
+  __shared__ unsigned int s_pos;
+  __shared__ unsigned long long s_sum;
+  __shared__ int s_ok;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t cnt = *a.count;
+  unsigned int maxd = 0;
+  for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+    const uint32_t c = a.list[t];
+    const unsigned long long td = a.soff[c + 1] - a.soff[c];
+    unsigned long long distinct_max = td < a.ncomm ? td : a.ncomm;
+    uint32_t slots = 1024;
+    while (slots < 2 * distinct_max) slots <<= 1;
+    uint32_t* keys;
+    uint32_t* vals;
+    if (kGlobal) {
+      if (slots > a.gslots) slots = a.gslots;
+      keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
+      vals = keys + a.gslots;
+    } else {
+      keys = dyn;
+      vals = dyn + slots;
+    }
+    const uint32_t mask = slots - 1;
+    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    if (threadIdx.x == 0) {
+      s_pos = 0;
+      s_sum = 0;
+      s_ok = 1;
+    }
+    __syncthreads();
+    bool ok = true;
+    for (uint32_t m = a.coff[c] + wib; m < a.coff[c + 1]; m += nw) {
+      uint32_t v = a.members[m];
+      unsigned long long o = a.g.off[v];
+      uint32_t d = a.g.deg[v];
+      for (uint32_t k = lane; k < d; k += 32) {
+        uint2 arc = a.g.arcs[o + k];
+        ok &= agg_add(keys, vals, mask, a.Cp[arc.x], arc.y);
+      }
+    }
+    if (!ok) s_ok = 0;
+    __syncthreads();
+    if (!s_ok && threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
+    const unsigned long long base = a.soff[c];
+    unsigned long long ksum = 0;
+    for (uint32_t s0 = wib * 32; s0 < slots; s0 += blockDim.x) {
+      uint32_t s = s0 + lane;
+      uint32_t key = s < slots ? keys[s] : kEmpty;
+      bool has = key != kEmpty;
+      unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+      uint32_t wbase = 0;
+      if (lane == 0 && m) wbase = atomicAdd(&s_pos, __popc(m));
+      wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+      if (has) {
+        uint32_t val = vals[s];
+        a.arcs_out[base + wbase + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, val);
+        ksum += val;
+      }
+    }
+    for (int x = 16; x; x >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, x);
+    if (lane == 0 && ksum) atomicAdd(&s_sum, ksum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.deg_out[c] = s_pos;
+      a.Knew[c] = (long long)s_sum;
+      maxd = max(maxd, s_pos);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && maxd) atomicMax(&a.ctrl->max_deg, maxd);
+}
+
+int read_ctrl(Handle* h) {
+  DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return uint32_t(p);
+}
+
+}  // namespace
+
+// Aggregate g under the renumbered membership Cp (labels in [0, ncomm)) into
+// super graph sg[dst]; Knew receives the super-vertex weights.  Returns the
+// super graph's maximum degree in h->hctrl->max_deg.
+int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm, int dst,
+              long long* Knew) {
+  SuperGraph& sg = h->sg[dst];
+  if (ncomm + 1 > sg.nv_cap) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(sg.off);
+    cudaFree(sg.deg);
+    sg.off = nullptr;
+    sg.deg = nullptr;
+    sg.nv_cap = 0;
+    DFL_CUDA(h, cudaMalloc(&sg.off, sizeof(unsigned long long) * (uint64_t(h->n) + 1)));
+    DFL_CUDA(h, cudaMalloc(&sg.deg, sizeof(uint32_t) * (uint64_t(h->n) + 1)));
+    sg.nv_cap = h->n + 1;
+  }
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->cnt, 0, sizeof(uint32_t) * (uint64_t(ncomm) + 1), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fillc, 0, sizeof(uint32_t) * uint64_t(ncomm), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(sg.off, 0, sizeof(unsigned long long) * (uint64_t(ncomm) + 1),
+                              h->stream));
+  {
+    LaunchScope ls(h, DFL_PROF_AGG);
+    k_agg_count<<<grid_for(g.nv, 256), 256, 0, h->stream>>>(g, Cp, h->cnt, sg.off);
+    DFL_TRY(check_launch(h, "agg count"));
+  }
+  Segs seg;
+  for (int b = 0; b < kMaxSubsteps * kBins; ++b) {
+    seg.off[b] = b < 3 ? uint32_t(b) * h->n : 0;
+    seg.cap[b] = b < 3 ? h->n : 0;
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_AGG);
+    k_agg_bins<<<grid_for(ncomm, 256), 256, 0, h->stream>>>(ncomm, sg.off, h->lists[1], seg, h->ctrl);
+    DFL_TRY(check_launch(h, "agg bins"));
+  }
+  DFL_TRY(scan_u32(h, h->cnt, h->cnt, ncomm));
+  DFL_TRY(scan_u64(h, sg.off, sg.off, ncomm));
+  {
+    LaunchScope ls(h, DFL_PROF_AGG);
+    k_agg_fill<<<grid_for(g.nv, 256), 256, 0, h->stream>>>(g.nv, Cp, h->cnt, h->fillc, h->members);
+    DFL_TRY(check_launch(h, "agg fill"));
+  }
+  unsigned long long total = 0;
+  DFL_CUDA(h, cudaMemcpyAsync(&total, sg.off + ncomm, sizeof(total), cudaMemcpyDeviceToHost, h->stream));
+  DFL_TRY(read_ctrl(h));
+  const Ctrl c = *h->hctrl;
+  if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in aggregation lists");
+  if (total > sg.arc_cap) {
+    cudaFree(sg.arcs);
+    sg.arcs = nullptr;
+    sg.arc_cap = 0;
+    uint64_t want = total + total / 8 + 1024;
+    DFL_CUDA(h, cudaMalloc(&sg.arcs, sizeof(uint2) * want));
+    sg.arc_cap = want;
+  }
+  // global tables for the largest communities
+  uint32_t gslots = 0;
+  const uint32_t gblocks = 152;
+  if (c.count[1][0][2]) {
+    uint64_t dmax = c.red_u < ncomm ? c.red_u : ncomm;
+    gslots = next_pow2(2 * dmax);
+    if (gslots < 2 * kBinBlock) gslots = 2 * kBinBlock;
+    if (uint64_t(gblocks) * gslots > h->gtable_cap) {
+      cudaFree(h->gtable);
+      h->gtable = nullptr;
+      h->gtable_cap = 0;
+      DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(gblocks) * gslots));
+      h->gtable_cap = uint64_t(gblocks) * gslots;
+    }
+  }
+  static bool smem_set = false;
+  if (!smem_set) {
+    DFL_CUDA(h, cudaFuncSetAttribute(k_agg_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 4 * kBinBlock)));
+    smem_set = true;
+  }
+  AggArgs a;
+  a.g = g;
+  a.Cp = Cp;
+  a.coff = h->cnt;
+  a.members = h->members;
+  a.soff = sg.off;
+  a.deg_out = sg.deg;
+  a.arcs_out = sg.arcs;
+  a.Knew = Knew;
+  a.ncomm = ncomm;
+  a.ctrl = h->ctrl;
+  a.gtable = h->gtable;
+  a.gslots = gslots;
+  for (int b = 0; b < 3; ++b) {
+    uint32_t nc = c.count[1][0][b];
+    if (!nc) continue;
+    a.list = h->lists[1] + seg.off[b];
+    a.count = &h->ctrl->count[1][0][b];
+    LaunchScope ls(h, DFL_PROF_AGG);
+    if (b == 0)
+      k_agg_warp<<<grid_for(uint64_t(nc) * 32, 256, 152 * 16), 256, 0, h->stream>>>(a);
+    else if (b == 1)
+      k_agg_block<false><<<grid_for(nc, 1, 152 * 4), 256, sizeof(uint32_t) * 4 * kBinBlock,
+                           h->stream>>>(a);
+    else
+      k_agg_block<true><<<grid_for(nc, 1, gblocks), 512, 0, h->stream>>>(a);
+    DFL_TRY(check_launch(h, "aggregate"));
+  }
+  DFL_TRY(read_ctrl(h));
+  if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in aggregation (table overflow)");
+  return DFL_OK;
+}
+
+}  // namespace dfl

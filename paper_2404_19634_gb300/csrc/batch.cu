@@ -1,0 +1,619 @@
+// Batch update of the slack CSR (Section 2.4), incremental K and Sigma
+// (Alg. 7), and marking of the initially affected vertices (Alg. 1 DF,
+// Alg. 2 ND, Alg. 3 DS).
+//
+// A batch is expanded into directed arcs keyed u << (b+1) | v << 1 | type
+// (type 0 = deletion, 1 = insertion; b = bits of n-1) and sorted, so the
+// arcs of one row are contiguous, ordered by neighbour, deletions before
+// insertions.  A maximal run of equal (u, v) is one arc change.  Everything
+// is validated (one host read-back) before any state is touched.
+#include "common.cuh"
+
+namespace dfl {
+
+namespace {
+
+// b_flag bits
+constexpr uint32_t kRunHead = 1u;     // first arc of a (u, v) run
+constexpr uint32_t kRunStruct = 2u;   // the run adds or removes the arc
+constexpr uint32_t kRowStruct = 4u;   // (row head) the row gains or loses arcs
+constexpr uint32_t kRowMove = 8u;     // (row head) the row is relocated
+
+__host__ __device__ inline uint32_t grow_cap(uint32_t d) {
+  uint64_t c = uint64_t(d) + d / 2 + 4;
+  c = (c + 1) & ~uint64_t(1);
+  return c > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(c);
+}
+
+struct KeyFmt {
+  uint32_t b;          // bits of a vertex id
+  uint64_t vmask;
+  __device__ uint32_t u(unsigned long long k) const { return uint32_t(k >> (b + 1)); }
+  __device__ uint32_t v(unsigned long long k) const { return uint32_t((k >> 1) & vmask); }
+  __device__ unsigned long long pair(unsigned long long k) const { return k >> 1; }
+};
+
+// Expand edges into both arcs; reject ids >= n, self-loops, zero insertions.
+__global__ void k_expand(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
+                         KeyFmt f, unsigned long long* __restrict__ key, uint32_t* __restrict__ w,
+                         Ctrl* ctrl) {
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < ne;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    dfl_edge x = e[t];
+    unsigned long long type = t >= nd ? 1ull : 0ull;
+    bool bad = x.u >= n || x.v >= n || x.u == x.v || (type && x.w == 0);
+    if (bad) {
+      atomicOr(&ctrl->err, kErrInvalid);
+      key[2 * t] = key[2 * t + 1] = 0;
+      w[2 * t] = w[2 * t + 1] = 0;
+      continue;
+    }
+    key[2 * t] = ((unsigned long long)x.u << (f.b + 1)) | ((unsigned long long)x.v << 1) | type;
+    key[2 * t + 1] = ((unsigned long long)x.v << (f.b + 1)) | ((unsigned long long)x.u << 1) | type;
+    w[2 * t] = w[2 * t + 1] = x.w;
+  }
+}
+
+// Thread per sorted arc: run heads evaluate their (u, v) change against the
+// current row; row heads are listed.
+__global__ void k_runs(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
+                       uint64_t na, KeyFmt f, uint32_t n, const unsigned long long* __restrict__ off,
+                       const uint32_t* __restrict__ deg, const uint2* __restrict__ arcs,
+                       unsigned long long* __restrict__ pos_out, uint32_t* __restrict__ wnew_out,
+                       uint32_t* __restrict__ flag, long long* __restrict__ delta_out,
+                       uint32_t* __restrict__ rowlist, Ctrl* ctrl) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    unsigned long long k = key[p];
+    bool head = p == 0 || f.pair(key[p - 1]) != f.pair(k);
+    if (!head) {
+      flag[p] = 0;
+      continue;
+    }
+    uint32_t u = f.u(k), v = f.v(k);
+    if (p == 0 || f.u(key[p - 1]) != u) {
+      uint32_t slot = atomicAdd(&ctrl->rows, 1u);
+      rowlist[slot] = uint32_t(p);
+    }
+    uint32_t ndel = 0, wdel = 0;
+    unsigned long long wins = 0;
+    for (uint64_t q = p; q < na && f.pair(key[q]) == f.pair(k); ++q) {
+      if (key[q] & 1ull) wins += w[q];
+      else {
+        ++ndel;
+        wdel = w[q];
+      }
+    }
+    if (u >= n || v >= n) {
+      atomicOr(&ctrl->err, kErrInvalid);
+      flag[p] = kRunHead;
+      continue;
+    }
+    if (ndel > 1) atomicOr(&ctrl->err, kErrInvalid);  // the same edge deleted twice
+    // binary search of v in the sorted row u
+    unsigned long long base = off[u];
+    uint32_t lo = 0, hi = deg[u];
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (arcs[base + mid].x < v) lo = mid + 1;
+      else hi = mid;
+    }
+    bool found = lo < deg[u] && arcs[base + lo].x == v;
+    unsigned long long wold = found ? arcs[base + lo].y : 0ull;
+    unsigned long long weff = 0;
+    if (ndel) {
+      if (!found || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);
+      else weff = wdel ? wdel : wold;
+    }
+    unsigned long long wn = (found ? wold - weff : 0ull) + wins;
+    if (wn > 0xFFFFFFFFull) atomicOr(&ctrl->err, kErrOverflow);
+    bool structural = (found && wn == 0) || (!found && wn > 0);
+    long long delta = (long long)wins - (long long)weff;
+    pos_out[p] = (unsigned long long)lo | ((unsigned long long)found << 63);
+    wnew_out[p] = uint32_t(wn);
+    flag[p] = kRunHead | (structural ? kRunStruct : 0u);
+    delta_out[p] = delta;
+    if (delta) atomicAdd((unsigned long long*)&ctrl->m2_delta, (unsigned long long)delta);
+  }
+}
+
+// Thread per touched row: new degree, relocation and scratch needs.
+__global__ void k_rows(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                       const uint32_t* __restrict__ rowlist, const uint32_t* __restrict__ deg,
+                       const uint32_t* __restrict__ cap, const unsigned long long* __restrict__ pos,
+                       const uint32_t* __restrict__ wnew, uint32_t* __restrict__ flag,
+                       uint32_t* __restrict__ newdeg, Ctrl* ctrl) {
+  const uint32_t rows = ctrl->rows;
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < rows;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t p = rowlist[t];
+    uint32_t u = f.u(key[p]);
+    long long d = deg[u];
+    bool structural = false;
+    for (uint64_t q = p; q < na && f.u(key[q]) == u; ++q) {
+      uint32_t fl = flag[q];
+      if ((fl & kRunHead) && (fl & kRunStruct)) {
+        structural = true;
+        d += (pos[q] >> 63) ? -1 : 1;  // found and emptied, or created
+      }
+    }
+    (void)wnew;
+    uint32_t nd = uint32_t(d);
+    bool move = structural && nd > cap[u];
+    flag[p] |= (structural ? kRowStruct : 0u) | (move ? kRowMove : 0u);
+    newdeg[p] = nd;
+    if (move) atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(nd));
+    else if (structural) atomicAdd(&ctrl->scratch_need, (unsigned long long)nd);
+    atomicMax(&ctrl->max_deg, nd);
+    if (d != (long long)deg[u]) atomicAdd((unsigned long long*)&ctrl->arc_delta,
+                                           (unsigned long long)(d - (long long)deg[u]));
+  }
+}
+
+// Warp per touched row: write the merged row.  Weight-only changes are done
+// in place; structural changes are merged into scratch (or straight into a
+// relocated slot) in one ordered walk over the row's runs.
+__global__ void k_merge(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                        const uint32_t* __restrict__ rowlist, unsigned long long* __restrict__ off,
+                        uint32_t* __restrict__ deg, uint32_t* __restrict__ cap, uint2* __restrict__ arcs,
+                        const unsigned long long* __restrict__ pos, const uint32_t* __restrict__ wnew,
+                        const uint32_t* __restrict__ flag, const uint32_t* __restrict__ newdeg,
+                        uint2* __restrict__ scratch, unsigned long long pool_base,
+                        unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t rows = ctrl->rows;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t t = warp; t < rows; t += nwarps) {
+    uint32_t p = rowlist[t];
+    uint32_t u = f.u(key[p]);
+    uint32_t rf = flag[p];
+    unsigned long long base = off[u];
+    uint32_t d = deg[u];
+    uint64_t end = p;
+    while (end < na && f.u(key[end]) == u) ++end;
+    if (!(rf & kRowStruct)) {
+      for (uint64_t q = p + lane; q < end; q += 32)
+        if ((flag[q] & kRunHead) && (pos[q] >> 63)) arcs[base + (pos[q] & ~(1ull << 63))].y = wnew[q];
+      continue;
+    }
+    uint32_t nd = newdeg[p];
+    uint2* out;
+    unsigned long long dst = 0;
+    if (rf & kRowMove) {
+      uint32_t nc = grow_cap(nd);
+      if (lane == 0) dst = pool_base + atomicAdd(&ctrl->pool_top, (unsigned long long)nc);
+      dst = __shfl_sync(0xFFFFFFFFu, dst, 0);
+      if (dst + nc > pool_cap) {
+        if (lane == 0) atomicOr(&ctrl->err, kErrInternal);
+        continue;
+      }
+      out = arcs + dst;
+    } else {
+      if (lane == 0) dst = atomicAdd(&ctrl->scratch_top, (unsigned long long)nd);
+      dst = __shfl_sync(0xFFFFFFFFu, dst, 0);
+      if (dst + nd > scratch_cap) {
+        if (lane == 0) atomicOr(&ctrl->err, kErrInternal);
+        continue;
+      }
+      out = scratch + dst;
+    }
+    const uint2* old = arcs + base;
+    uint32_t prev = 0, o = 0;
+    for (uint64_t q = p; q < end; ++q) {
+      uint32_t fl = flag[q];
+      if (!(fl & kRunHead)) continue;
+      bool found = pos[q] >> 63;
+      uint32_t ps = uint32_t(pos[q] & 0xFFFFFFFFull);
+      uint32_t v = f.v(key[q]);
+      uint32_t len = ps - prev;
+      for (uint32_t k = lane; k < len; k += 32) out[o + k] = old[prev + k];
+      o += len;
+      uint32_t wn = wnew[q];
+      if (found) {
+        if (wn) {
+          if (lane == 0) out[o] = make_uint2(v, wn);
+          ++o;
+        }
+        prev = ps + 1;
+      } else {
+        if (lane == 0) out[o] = make_uint2(v, wn);
+        ++o;
+        prev = ps;
+      }
+    }
+    for (uint32_t k = lane; k < d - prev; k += 32) out[o + k] = old[prev + k];
+    o += d - prev;
+    if (o != nd && lane == 0) atomicOr(&ctrl->err, kErrInternal);
+    __syncwarp();
+    if (rf & kRowMove) {
+      if (lane == 0) {
+        off[u] = dst;
+        cap[u] = grow_cap(nd);
+        deg[u] = nd;
+      }
+    } else {
+      for (uint32_t k = lane; k < nd; k += 32) arcs[base + k] = out[k];
+      if (lane == 0) deg[u] = nd;
+    }
+  }
+}
+
+// Alg. 7: K[i] and Sigma[C^{t-1}[i]] change by the net weight of each arc.
+__global__ void k_update_weights(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                                 const uint32_t* __restrict__ flag, const long long* __restrict__ delta,
+                                 const uint32_t* __restrict__ C, long long* __restrict__ K,
+                                 long long* __restrict__ Sigma) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    if (!(flag[p] & kRunHead)) continue;
+    long long dl = delta[p];
+    if (!dl) continue;
+    uint32_t u = f.u(key[p]);
+    atomicAdd((unsigned long long*)&K[u], (unsigned long long)dl);
+    atomicAdd((unsigned long long*)&Sigma[C[u]], (unsigned long long)dl);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Marking
+// ---------------------------------------------------------------------------
+
+// Alg. 1: a deletion inside a community or an insertion across communities
+// marks its source (both arcs are present, so both endpoints).
+__global__ void k_mark_df(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                          const uint32_t* __restrict__ C, const uint32_t* __restrict__ deg,
+                          uint32_t* __restrict__ fbits, uint32_t* lists, Segs seg, Ctrl* ctrl,
+                          uint32_t k) {
+  uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x); p0 < na; p0 += stride) {
+    uint64_t p = p0 + threadIdx.x;
+    bool valid = false;
+    uint32_t u = 0, lk = 0;
+    if (p < na) {
+      unsigned long long kk = key[p];
+      u = f.u(kk);
+      uint32_t v = f.v(kk);
+      bool ins = kk & 1ull;
+      bool same = C[u] == C[v];
+      if (ins != same && bit_set(fbits, u)) {
+        valid = true;
+        lk = substep_class(u, k) * kBins + degree_bin(deg[u]);
+      }
+    }
+    append_vertex(u, valid, lk, lists, seg, ctrl, 0);
+  }
+}
+
+// Alg. 3, deletions inside a community: dV[i], dE[i], dC[C[j]].
+__global__ void k_ds_del(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                         const uint32_t* __restrict__ C, uint32_t* dV, uint32_t* dE, uint32_t* dC) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    unsigned long long kk = key[p];
+    if (kk & 1ull) continue;
+    uint32_t u = f.u(kk), v = f.v(kk);
+    if (C[u] == C[v]) {
+      bit_set(dV, u);
+      bit_set(dE, u);
+      bit_set(dC, C[v]);
+    }
+  }
+}
+
+// Alg. 3, insertions across communities: collect (source, C[target]) keys.
+__global__ void k_ds_keys(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
+                          uint64_t na, KeyFmt f, const uint32_t* __restrict__ C,
+                          unsigned long long* __restrict__ okey, uint32_t* __restrict__ ow,
+                          Ctrl* ctrl) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    unsigned long long kk = key[p];
+    if (!(kk & 1ull)) continue;
+    uint32_t u = f.u(kk), v = f.v(kk);
+    uint32_t cv = C[v];
+    if (C[u] == cv) continue;
+    unsigned long long slot = atomicAdd(&ctrl->red_a, 1ull);
+    okey[slot] = ((unsigned long long)u << 32) | cv;
+    ow[slot] = w[p];
+  }
+}
+
+// Per source u (sorted keys u << 32 | c): H[c] = summed inserted weight;
+// best c by 2m*H[c] - K_u*Sigma_c, ties to the smallest c.
+__global__ void k_ds_best(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
+                          uint64_t na, long long m2, const long long* __restrict__ K,
+                          const long long* __restrict__ Sigma, uint32_t* dV, uint32_t* dE,
+                          uint32_t* dC) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t u = uint32_t(key[p] >> 32);
+    if (p > 0 && uint32_t(key[p - 1] >> 32) == u) continue;
+    bool have = false;
+    i128 best_s = 0;
+    uint32_t best = 0;
+    uint64_t q = p;
+    while (q < na && uint32_t(key[q] >> 32) == u) {
+      uint32_t c = uint32_t(key[q]);
+      unsigned long long hsum = 0;
+      while (q < na && key[q] == (((unsigned long long)u << 32) | c)) hsum += w[q++];
+      i128 s = (i128)m2 * (i128)hsum - (i128)K[u] * (i128)Sigma[c];
+      if (!have || s > best_s) {
+        have = true;
+        best_s = s;
+        best = c;
+      }
+    }
+    bit_set(dV, u);
+    bit_set(dE, u);
+    bit_set(dC, best);
+  }
+}
+
+// Alg. 3: neighbours of dE vertices join dV (warp per bitmap word).
+__global__ void k_ds_expand(const uint32_t* __restrict__ dE, uint32_t words, uint32_t n,
+                            GraphView g, uint32_t* dV) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t wd = warp; wd < words; wd += nwarps) {
+    uint32_t x = dE[wd];
+    while (x) {
+      int b = __ffs(x) - 1;
+      x &= x - 1;
+      uint32_t i = uint32_t(wd * 32 + b);
+      if (i >= n) break;
+      unsigned long long o = g.off[i];
+      uint32_t d = g.deg[i];
+      for (uint32_t k = lane; k < d; k += 32) bit_set(dV, g.arcs[o + k].x);
+    }
+  }
+}
+
+// Alg. 3: vertices of dC communities join dV.
+__global__ void k_ds_comm(uint32_t n, const uint32_t* __restrict__ C, const uint32_t* __restrict__ dC,
+                          uint32_t* dV) {
+  uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x); i0 < n; i0 += stride) {
+    uint64_t i = i0 + threadIdx.x;
+    bool set = i < n && bit_test(dC, C[i]);
+    unsigned m = __ballot_sync(0xFFFFFFFFu, set);
+    if ((threadIdx.x & 31u) == 0 && m) atomicOr(&dV[i >> 5], m);
+  }
+}
+
+int read_ctrl(Handle* h) {
+  DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+template <typename T>
+int grow(Handle* h, T** p, uint64_t need, uint64_t* cap_out, uint64_t cap_now, bool keep = false,
+         uint64_t keep_items = 0) {
+  if (need <= cap_now) return DFL_OK;
+  uint64_t want = need + need / 2 + 256;
+  T* q = nullptr;
+  DFL_CUDA(h, cudaMalloc(&q, sizeof(T) * want));
+  if (keep && *p && keep_items)
+    DFL_CUDA(h, cudaMemcpyAsync(q, *p, sizeof(T) * keep_items, cudaMemcpyDeviceToDevice, h->stream));
+  if (*p) {
+    DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaFree(*p);
+  }
+  *p = q;
+  if (cap_out) *cap_out = want;
+  return DFL_OK;
+}
+
+KeyFmt key_fmt(const Handle* h) {
+  KeyFmt f;
+  f.b = h->key_shift;
+  f.vmask = (1ull << h->key_shift) - 1;
+  return f;
+}
+
+}  // namespace
+
+int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                int mem_kind) {
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_apply_batch before dfl_static");
+  const uint64_t ne = nd + ni;
+  if (ne == 0) return DFL_OK;
+  const uint64_t na = 2 * ne;
+  // scratch sized for this batch
+  if (ne > h->b_edges_cap) {
+    uint64_t cap = 0;
+    DFL_TRY(grow(h, &h->b_edges, ne, &cap, h->b_edges_cap));
+    h->b_edges_cap = cap;
+  }
+  if (na > h->b_cap) {
+    uint64_t want = na + na / 2 + 256, c = 0;
+    DFL_TRY(grow(h, &h->b_key, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_key2, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_w, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_w2, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_pos, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_wnew, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_flag, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_delta, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_rowlist, want, &c, 0));
+    DFL_TRY(grow(h, &h->b_newdeg, want, &c, 0));
+    h->b_cap = c;
+  }
+  cudaMemcpyKind kind = mem_kind == DFL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, kind, h->stream));
+  if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, kind, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  const KeyFmt f = key_fmt(h);
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_expand<<<grid_for(ne, 256), 256, 0, h->stream>>>(h->b_edges, nd, ne, h->n, f, h->b_key, h->b_w,
+                                                       h->ctrl);
+    DFL_TRY(check_launch(h, "expand"));
+  }
+  DFL_TRY(sort_pairs(h, h->b_key, h->b_w, h->b_key2, h->b_w2, na, h->key_bits));
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_runs<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, h->b_w, na, f, h->n, h->off, h->deg,
+                                                     h->arcs, h->b_pos, h->b_wnew, h->b_flag,
+                                                     h->b_delta, h->b_rowlist, h->ctrl);
+    DFL_TRY(check_launch(h, "runs"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_rows<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, na, f, h->b_rowlist, h->deg, h->cap,
+                                                     h->b_pos, h->b_wnew, h->b_flag, h->b_newdeg,
+                                                     h->ctrl);
+    DFL_TRY(check_launch(h, "rows"));
+  }
+  DFL_TRY(read_ctrl(h));
+  const Ctrl c = *h->hctrl;
+  if (c.err & kErrInvalid) return set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
+  if (c.err & kErrNotFound) return set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
+  if (c.err & kErrOverflow) return set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
+  if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
+  if (h->m2 + c.m2_delta >= (1ll << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+  // --- mutation starts here ---
+  if (h->pool_top + c.reloc_need > h->pool_cap) {
+    uint64_t c2 = 0;
+    uint64_t need = h->pool_top + c.reloc_need;
+    need = need + need / 4 + 1024;
+    DFL_TRY(grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top));
+    h->pool_cap = c2;
+  }
+  if (c.scratch_need > h->scratch_cap) {
+    uint64_t c2 = 0;
+    DFL_TRY(grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap));
+    h->scratch_cap = c2;
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_merge<<<grid_for(uint64_t(c.rows) * 32, 256), 256, 0, h->stream>>>(
+        h->b_key, na, f, h->b_rowlist, h->off, h->deg, h->cap, h->arcs, h->b_pos, h->b_wnew, h->b_flag,
+        h->b_newdeg, h->scratch, h->pool_top, h->pool_cap, h->scratch_cap, h->ctrl);
+    DFL_TRY(check_launch(h, "merge"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_update_weights<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, na, f, h->b_flag,
+                                                               h->b_delta, h->C, h->K, h->Sigma);
+    DFL_TRY(check_launch(h, "update weights"));
+  }
+  // pending arcs for the next dfl_update
+  if (h->pend_count + na > h->pend_cap) {
+    uint64_t c2 = 0, need = h->pend_count + na;
+    DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
+    uint64_t c3 = 0;
+    DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
+    h->pend_cap = c2 < c3 ? c2 : c3;
+  }
+  DFL_CUDA(h, cudaMemcpyAsync(h->pend_key + h->pend_count, h->b_key, sizeof(unsigned long long) * na,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  DFL_CUDA(h, cudaMemcpyAsync(h->pend_w + h->pend_count, h->b_w, sizeof(uint32_t) * na,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  h->pend_count += na;
+  h->m2 += c.m2_delta;
+  h->pool_top += c.reloc_need;
+  h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
+  if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
+  return DFL_OK;
+}
+
+// Initial frontier into list buffer 0 (and fbits[0]); `all` when every
+// vertex is affected; `use_range` when the first pass is limited to rbits.
+int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
+  const uint32_t n = h->n;
+  const uint32_t k = h->opt.substeps;
+  make_segs(h, k);
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[0], 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream));
+  *all = false;
+  *use_range = false;
+  const KeyFmt f = key_fmt(h);
+  if (mode == DFL_ND) {
+    *all = true;
+    DFL_TRY(lists_all(h, n, h->deg, 0, k));
+    *initial = n;
+    return DFL_OK;
+  }
+  if (mode == DFL_DF) {
+    if (h->pend_count) {
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_mark_df<<<grid_for(h->pend_count, 256), 256, 0, h->stream>>>(
+          h->pend_key, h->pend_count, f, h->C, h->deg, h->fbits[0], h->lists[0], h->segs, h->ctrl, k);
+      DFL_TRY(check_launch(h, "mark df"));
+    }
+    DFL_TRY(read_ctrl(h));
+    uint64_t tot = 0;
+    for (uint32_t s = 0; s < k; ++s)
+      for (int b = 0; b < kBins; ++b) tot += h->hctrl->count[0][s][b];
+    *initial = tot;
+    if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in marking");
+    return DFL_OK;
+  }
+  if (mode != DFL_DS) return set_error(h, DFL_ERR_INVALID, "unknown mode");
+  // Delta-screening
+  const uint64_t na = h->pend_count;
+  DFL_CUDA(h, cudaMemsetAsync(h->dsV, 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->dsE, 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->dsC, 0, sizeof(uint32_t) * h->words, h->stream));
+  if (na) {
+    if (na > h->b_cap) {
+      uint64_t want = na + na / 2 + 256, c = 0;
+      DFL_TRY(grow(h, &h->b_key, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_key2, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_w, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_w2, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_pos, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_wnew, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_flag, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_delta, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_rowlist, want, &c, 0));
+      DFL_TRY(grow(h, &h->b_newdeg, want, &c, 0));
+      h->b_cap = c;
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_ds_del<<<grid_for(na, 256), 256, 0, h->stream>>>(h->pend_key, na, f, h->C, h->dsV, h->dsE,
+                                                         h->dsC);
+      DFL_TRY(check_launch(h, "ds del"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_ds_keys<<<grid_for(na, 256), 256, 0, h->stream>>>(h->pend_key, h->pend_w, na, f, h->C,
+                                                          h->b_key, h->b_w, h->ctrl);
+      DFL_TRY(check_launch(h, "ds keys"));
+    }
+    DFL_TRY(read_ctrl(h));
+    uint64_t nk = h->hctrl->red_a;
+    if (nk) {
+      DFL_TRY(sort_pairs(h, h->b_key, h->b_w, h->b_key2, h->b_w2, nk, 32 + h->key_shift));
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_ds_best<<<grid_for(nk, 256), 256, 0, h->stream>>>(h->b_key, h->b_w, nk, h->m2, h->K, h->Sigma,
+                                                          h->dsV, h->dsE, h->dsC);
+      DFL_TRY(check_launch(h, "ds best"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_ds_expand<<<grid_for(uint64_t(h->words) * 32, 256), 256, 0, h->stream>>>(
+          h->dsE, h->words, n, base_view(h), h->dsV);
+      DFL_TRY(check_launch(h, "ds expand"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_MARK);
+      k_ds_comm<<<grid_for(n, 256), 256, 0, h->stream>>>(n, h->C, h->dsC, h->dsV);
+      DFL_TRY(check_launch(h, "ds comm"));
+    }
+  }
+  DFL_CUDA(h, cudaMemcpyAsync(h->rbits, h->dsV, sizeof(uint32_t) * h->words,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  DFL_TRY(lists_from_bits(h, h->dsV, n, h->deg, 0, k));
+  *use_range = true;
+  int rc = DFL_OK;
+  *initial = popcount_bits(h, h->dsV, h->words, &rc);
+  return rc;
+}
+
+}  // namespace dfl

@@ -1,0 +1,379 @@
+// Internal declarations of the GB300 DF Louvain library (sm_103a).
+//
+// Device data layout (all arrays in HBM, owned by the handle):
+//   slack CSR of G^t   off[n] (u64 arc offset), deg[n] (u32), cap[n] (u32),
+//                      arcs[pool] as uint2 {neighbour, weight}; every row starts
+//                      on an even arc index (16-byte aligned) so two arcs load
+//                      as one 128-bit word
+//   state              K[n], Sigma[n] (int64), csize[n] (int32), C[n] (u32)
+//   super-vertex CSR   two ping-pong graphs (off, deg, arcs) for passes >= 1
+//   frontier           bitmaps (n/32 words) + per (sub-step class, degree bin)
+//                      vertex lists, double-buffered (current / next)
+//   control block      counters, error word and 128-bit sums, mirrored into
+//                      pinned host memory once per iteration
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dfl.h"
+
+namespace dfl {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// Compile-time configuration
+// ---------------------------------------------------------------------------
+constexpr int kWarp = 32;
+constexpr int kBins = 4;            // degree bins of the local-moving kernels
+constexpr uint32_t kBinWarp = 32;   // deg <= 32: one warp, registers only
+constexpr uint32_t kBinWarpHash = 256;   // deg <= 256: one warp, shared-memory table
+constexpr uint32_t kBinBlock = 4096;     // deg <= 4096: one block, shared-memory table
+                                          // larger: one block, global-memory table
+constexpr uint32_t kMaxSubsteps = 8;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // empty hash-table key
+
+// Error bits raised by kernels (ctrl.err)
+enum : uint32_t {
+  kErrInvalid = 1u,
+  kErrNotFound = 2u,
+  kErrOverflow = 4u,
+  kErrInternal = 8u,  // a hash table overflowed or an index check failed
+};
+
+// ---------------------------------------------------------------------------
+// Control block (device), mirrored to pinned host memory.
+// ---------------------------------------------------------------------------
+struct Ctrl {
+  unsigned long long s_lo;           // sum of the low 32 bits of the movers' dQ numerators
+  unsigned long long s_hi;           // sum of the high parts (value = s_hi * 2^32 + s_lo)
+  unsigned long long processed;      // frontier vertices processed in the iteration
+  unsigned long long moved;          // movers in the iteration
+  unsigned long long move_bytes;     // algorithmic bytes of the decide kernels
+  unsigned int movers;               // movers of the current sub-step (list length)
+  unsigned int err;                  // kErr* bits
+  unsigned int count[2][kMaxSubsteps][kBins];  // frontier list lengths [buffer][class][bin]
+  // batch apply
+  unsigned long long reloc_need;     // arc slots needed for relocated rows
+  unsigned long long scratch_need;   // scratch slots for in-place merges
+  long long m2_delta;                // change of 2m by the batch
+  unsigned int max_deg;              // largest new degree of a touched row
+  unsigned int rows;                 // touched rows
+  long long arc_delta;               // change of the arc count by the batch
+  unsigned long long pool_top;       // first free arc slot of the pool
+  unsigned long long scratch_top;
+  // misc reductions
+  unsigned long long red_a;
+  unsigned long long red_b;
+  unsigned long long red_c;
+  unsigned int red_u;
+  unsigned int pad;
+};
+
+// A CSR whose rows are addressed by (offset, degree): the slack CSR of G^t
+// and the super-vertex graphs with holes (Alg. 6) share this view.
+struct GraphView {
+  const unsigned long long* off;
+  const uint32_t* deg;
+  const uint2* arcs;
+  uint32_t nv;
+};
+
+struct SuperGraph {
+  unsigned long long* off = nullptr;
+  uint32_t* deg = nullptr;
+  uint2* arcs = nullptr;
+  uint64_t arc_cap = 0;
+  uint32_t nv_cap = 0;
+};
+
+// Frontier list layout: segment (class s, bin b) starts at off[s*kBins+b]
+// and holds at most the number of ids in [0, n) of class s.
+struct Segs {
+  uint32_t off[kMaxSubsteps * kBins];
+  uint32_t cap[kMaxSubsteps * kBins];
+};
+
+struct Handle {
+  uint32_t n = 0;
+  cudaStream_t stream = nullptr;
+  dfl_options opt;
+  std::string err;
+  int device = 0;
+
+  // slack CSR of G^t
+  unsigned long long* off = nullptr;
+  uint32_t* deg = nullptr;
+  uint32_t* cap = nullptr;
+  uint2* arcs = nullptr;
+  uint64_t pool_cap = 0;   // arc slots allocated
+  uint64_t pool_top = 0;   // first free slot (host mirror)
+  uint64_t num_arcs = 0;   // arcs in use
+  uint32_t max_deg = 0;    // upper bound of the degrees of G^t
+
+  // community state
+  long long* K = nullptr;
+  long long* Sigma = nullptr;
+  int* csize = nullptr;
+  uint32_t* C = nullptr;
+  long long m2 = 0;
+  bool have_communities = false;
+
+  // pending batch arcs (sorted keys and weights of every dfl_apply_batch
+  // since the last update)
+  unsigned long long* pend_key = nullptr;
+  uint32_t* pend_w = nullptr;
+  uint64_t pend_count = 0, pend_cap = 0;
+  uint32_t key_shift = 0;  // key = u << (key_shift + 1) | v << 1 | type
+  uint32_t key_bits = 0;
+
+  // Louvain work buffers (sized n)
+  uint32_t* Ctop = nullptr;     // dendrogram: vertex of G^t -> vertex of G'
+  uint32_t* Cs = nullptr;       // membership of the super-vertex graph
+  long long* Ks = nullptr;
+  long long* Ss = nullptr;
+  int* sizes = nullptr;
+  uint32_t* used = nullptr;     // n+1: flags, then exclusive scan = new ids
+  uint32_t* cnt = nullptr;      // n+1: community vertex counts / offsets
+  unsigned long long* tdeg = nullptr;  // n+1: community total degree / super offsets
+  uint32_t* fillc = nullptr;    // n
+  uint32_t* members = nullptr;  // n
+  SuperGraph sg[2];
+
+  // frontier
+  uint32_t words = 0;           // bitmap words = ceil(n / 32)
+  uint32_t* fbits[2] = {nullptr, nullptr};
+  uint32_t* rbits = nullptr;    // affected range (DS first pass)
+  uint32_t* ever = nullptr;     // ever processed in the first pass
+  uint32_t* lists[2] = {nullptr, nullptr};  // kBins * n ids each, split by `segs`
+  Segs segs;
+  uint32_t segs_k = 0;          // sub-step count the layout was made for
+  uint32_t* mv_i = nullptr;     // movers of a sub-step
+  uint32_t* mv_c = nullptr;
+  uint32_t* mv_d = nullptr;
+
+  // DS marking scratch
+  uint32_t* dsV = nullptr;
+  uint32_t* dsE = nullptr;
+  uint32_t* dsC = nullptr;
+
+  // batch apply scratch (grown on demand)
+  unsigned long long* b_key = nullptr;
+  uint32_t* b_w = nullptr;
+  unsigned long long* b_key2 = nullptr;
+  uint32_t* b_w2 = nullptr;
+  uint64_t b_cap = 0;
+  uint32_t* b_rowlist = nullptr;   // row-head positions
+  unsigned long long* b_pos = nullptr;  // per run head: position in row | found << 63
+  uint32_t* b_wnew = nullptr;      // per run head: new weight
+  uint32_t* b_flag = nullptr;      // per arc: run/row head flags (see batch.cu)
+  long long* b_delta = nullptr;    // per run head: weight change of the arc
+  uint32_t* b_newdeg = nullptr;    // per row head
+  dfl_edge* b_edges = nullptr;     // staging copy of the caller's edges
+  uint64_t b_edges_cap = 0;
+  uint2* scratch = nullptr;        // merge scratch
+  uint64_t scratch_cap = 0;
+
+  // generic scratch
+  void* tmp = nullptr;
+  uint64_t tmp_cap = 0;
+  uint2* gtable = nullptr;         // global hash tables of the largest bin
+  uint64_t gtable_cap = 0;
+
+  // control
+  Ctrl* ctrl = nullptr;       // device
+  Ctrl* hctrl = nullptr;      // pinned host mirror
+
+  // statistics
+  dfl_stats_t stats;
+  std::vector<uint64_t> trace;  // 4 per first-pass iteration
+  uint64_t launches = 0;
+
+  // profiling
+  struct Ev {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Ev> ev_pending;
+  std::vector<cudaEvent_t> ev_free;
+  dfl_profile_t prof;
+};
+
+// ---------------------------------------------------------------------------
+// Error handling
+// ---------------------------------------------------------------------------
+int set_error(Handle* h, int code, const std::string& msg);
+
+#define DFL_CUDA(h, call)                                                          \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return ::dfl::set_error((h), e_ == cudaErrorMemoryAllocation ? DFL_ERR_NOMEM \
+                                                                   : DFL_ERR_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define DFL_TRY(expr)        \
+  do {                       \
+    int r_ = (expr);         \
+    if (r_ != DFL_OK) return r_; \
+  } while (0)
+
+// Launch bookkeeping: counts launches and, with DFL_FLAG_PROFILE, brackets
+// the launch with CUDA events of class `cls`.
+struct LaunchScope {
+  Handle* h;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(Handle* h_, int cls_);
+  ~LaunchScope();
+};
+
+int check_launch(Handle* h, const char* what);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t substep_class(uint32_t i, uint32_t k) {
+  return uint32_t((uint64_t(i * 0x9E3779B1u) * k) >> 32);
+}
+
+__host__ __device__ __forceinline__ uint32_t degree_bin(uint32_t d) {
+  return d <= kBinWarp ? 0u : d <= kBinWarpHash ? 1u : d <= kBinBlock ? 2u : 3u;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) { return x * 0x9E3779B1u; }
+
+// Warp-wide maximum of (score, -c): larger score wins, ties to the smaller c.
+// Lanes without a candidate pass have = false.
+__device__ __forceinline__ void warp_argmax(bool& have, i128& score, uint32_t& c) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    unsigned long long lo = (unsigned long long)(u128)score;
+    unsigned long long hi = (unsigned long long)((u128)score >> 64);
+    unsigned long long olo = __shfl_xor_sync(0xFFFFFFFFu, lo, s);
+    unsigned long long ohi = __shfl_xor_sync(0xFFFFFFFFu, hi, s);
+    uint32_t oc = __shfl_xor_sync(0xFFFFFFFFu, c, s);
+    bool oh = __shfl_xor_sync(0xFFFFFFFFu, have ? 1 : 0, s) != 0;
+    i128 os = (i128)(((u128)ohi << 64) | (u128)olo);
+    if (oh && (!have || os > score || (os == score && oc < c))) {
+      have = true;
+      score = os;
+      c = oc;
+    }
+  }
+}
+
+// Bitmap helpers
+__device__ __forceinline__ bool bit_test(const uint32_t* bits, uint32_t i) {
+  return (bits[i >> 5] >> (i & 31u)) & 1u;
+}
+// Returns true if the bit was newly set.
+__device__ __forceinline__ bool bit_set(uint32_t* bits, uint32_t i) {
+  uint32_t m = 1u << (i & 31u);
+  return (atomicOr(bits + (i >> 5), m) & m) == 0;
+}
+
+// Add a non-negative 128-bit value to the (s_hi, s_lo) limb pair.
+__device__ __forceinline__ void add_s(Ctrl* ctrl, u128 v) {
+  unsigned long long lo = (unsigned long long)(v & 0xFFFFFFFFull);
+  unsigned long long hi = (unsigned long long)(v >> 32);
+  if (lo) atomicAdd(&ctrl->s_lo, lo);
+  if (hi) atomicAdd(&ctrl->s_hi, hi);
+}
+
+// Append vertex v (if valid) to frontier list `key` = class * kBins + bin of
+// buffer `buf`; one atomic per distinct key in the warp.  Every lane of the
+// warp must call this (with valid = false where it has nothing).
+__device__ __forceinline__ void append_vertex(uint32_t v, bool valid, uint32_t key,
+                                              uint32_t* lists, const Segs& seg, Ctrl* ctrl,
+                                              int buf) {
+  unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
+  if (!act) return;
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu);
+  if (!valid) return;
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&ctrl->count[buf][key / kBins][key % kBins], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  uint32_t r = base + __popc(peers & ((1u << lane) - 1u));
+  if (r < seg.cap[key]) lists[seg.off[key] + r] = v;
+  else atomicOr(&ctrl->err, kErrInternal);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side entry points of the other translation units
+// ---------------------------------------------------------------------------
+// prim.cu
+void make_segs(Handle* h, uint32_t k);
+int ensure_tmp(Handle* h, uint64_t bytes);
+int scan_u32(Handle* h, const uint32_t* in, uint32_t* out, uint64_t n);  // exclusive, out[n] = total
+int scan_u64(Handle* h, const unsigned long long* in, unsigned long long* out, uint64_t n);
+int sort_pairs(Handle* h, unsigned long long* key, uint32_t* val, unsigned long long* key2,
+               uint32_t* val2, uint64_t n, uint32_t bits);  // result in key/val
+int fill_u32(Handle* h, uint32_t* p, uint32_t v, uint64_t n);
+int iota_u32(Handle* h, uint32_t* p, uint64_t n);
+int fill_i32(Handle* h, int* p, int v, uint64_t n);
+int copy_i64(Handle* h, long long* dst, const long long* src, uint64_t n);
+int lists_from_bits(Handle* h, const uint32_t* bits, uint32_t nv, const uint32_t* deg, int buf,
+                    uint32_t substeps);
+int lists_all(Handle* h, uint32_t nv, const uint32_t* deg, int buf, uint32_t substeps);
+int bits_to_bytes(Handle* h, const uint32_t* bits, uint8_t* out, uint32_t n);
+int bytes_to_bits(Handle* h, const uint8_t* in, uint32_t* bits, uint32_t n);
+uint64_t popcount_bits(Handle* h, const uint32_t* bits, uint32_t words, int* rc);
+
+// graph.cu
+int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx_in,
+                const uint32_t* w_in, uint64_t nnz);
+int weighted_degrees(Handle* h);  // K from scratch, m2 on host
+int modularity_parts(Handle* h, i128* num, i128* den);
+int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool device_out);
+int recompute_sigma_sizes(Handle* h, const uint32_t* C);
+
+// batch.cu
+int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                int mem_kind);
+int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial);
+
+// move.cu
+struct MoveArgs {
+  GraphView g;
+  uint32_t* C;
+  const long long* K;
+  long long* Sigma;
+  int* size;
+  long long m2;
+  uint32_t max_deg;  // upper bound of the degrees of g
+  bool use_range;
+  bool track_ever;
+};
+int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
+               bool record_trace);
+
+// aggregate.cu
+int count_communities(Handle* h, const uint32_t* Cp, uint32_t nv, uint32_t* ncomm);
+int renumber(Handle* h, uint32_t* Cp, uint32_t nv, bool first_level);
+int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm, int dst,
+              long long* Knew);
+int louvain(Handle* h, bool all, bool use_range, uint64_t initial);
+
+inline GraphView base_view(const Handle* h) {
+  return GraphView{h->off, h->deg, h->arcs, h->n};
+}
+
+inline uint32_t grid_for(uint64_t items, uint32_t per_block, uint32_t cap = 152u * 16u) {
+  uint64_t g = (items + per_block - 1) / per_block;
+  if (g == 0) g = 1;
+  if (g > cap) g = cap;
+  return uint32_t(g);
+}
+
+}  // namespace dfl

@@ -1,0 +1,327 @@
+// Graph storage: input validation, slack CSR build, weighted degrees,
+// modularity (Eq. 1) and CSR export.
+#include "common.cuh"
+
+namespace dfl {
+
+namespace {
+
+// Capacity of a row of degree d in the slack CSR: 25% headroom plus two
+// slots, rounded up to an even count so every row starts 16-byte aligned.
+__host__ __device__ inline uint32_t slack_cap(uint32_t d) {
+  uint64_t c = uint64_t(d) + d / 4 + 2;
+  c = (c + 1) & ~uint64_t(1);
+  return c > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(c);
+}
+
+// Warp per row: checks of Section 2's graph (undirected: both arcs with equal
+// weights), plus sorted rows, no self-loops, no duplicates, weights > 0.
+__global__ void k_validate(uint32_t n, const unsigned long long* __restrict__ off,
+                           const uint32_t* __restrict__ idx, const uint32_t* __restrict__ w,
+                           uint64_t nnz, Ctrl* ctrl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  if (warp == 0 && lane == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(&ctrl->err, kErrInvalid);
+  unsigned long long wsum = 0;
+  uint32_t dmax = 0;
+  for (uint64_t i = warp; i < n; i += nwarps) {
+    unsigned long long a = off[i], b = off[i + 1];
+    if (b < a || b > nnz) {
+      if (lane == 0) atomicOr(&ctrl->err, kErrInvalid);
+      continue;
+    }
+    unsigned long long rd = b - a;
+    dmax = max(dmax, rd > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(rd));
+    bool bad = false;
+    for (unsigned long long k = a + lane; k < b; k += 32) {
+      uint32_t j = idx[k], wt = w[k];
+      wsum += wt;
+      if (j >= n || j == uint32_t(i) || wt == 0) { bad = true; continue; }
+      if (k > a && idx[k - 1] >= j) bad = true;
+      // symmetric arc (j, i) with the same weight: binary search in row j
+      unsigned long long lo = off[j], hi = off[j + 1];
+      if (hi < lo || hi > nnz) { bad = true; continue; }
+      while (lo < hi) {
+        unsigned long long mid = (lo + hi) >> 1;
+        if (idx[mid] < uint32_t(i)) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= off[j + 1] || idx[lo] != uint32_t(i) || w[lo] != wt) bad = true;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&ctrl->err, kErrInvalid);
+  }
+  for (int o = 16; o; o >>= 1) wsum += __shfl_xor_sync(0xFFFFFFFFu, wsum, o);
+  if (lane == 0) {
+    if (wsum) atomicAdd(&ctrl->red_a, wsum);
+    atomicMax(&ctrl->max_deg, dmax);
+  }
+}
+
+__global__ void k_caps(uint32_t n, const unsigned long long* __restrict__ off_in,
+                       uint32_t* __restrict__ deg, uint32_t* __restrict__ cap,
+                       unsigned long long* __restrict__ capl) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t d = uint32_t(off_in[i + 1] - off_in[i]);
+    deg[i] = d;
+    cap[i] = slack_cap(d);
+    capl[i] = cap[i];
+  }
+}
+
+// Warp per row: copy the input row into its slack-CSR slot.
+__global__ void k_fill_rows(uint32_t n, const unsigned long long* __restrict__ off_in,
+                            const uint32_t* __restrict__ idx, const uint32_t* __restrict__ w,
+                            const unsigned long long* __restrict__ off, uint2* __restrict__ arcs) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < n; i += nwarps) {
+    unsigned long long a = off_in[i], b = off_in[i + 1], o = off[i];
+    for (unsigned long long k = a + lane; k < b; k += 32) arcs[o + (k - a)] = make_uint2(idx[k], w[k]);
+  }
+}
+
+// K_i = sum_j w_ij (Section 2), warp per row; 2m accumulated in ctrl->red_a.
+__global__ void k_weighted_degree(GraphView g, long long* __restrict__ K, Ctrl* ctrl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long tot = 0;
+  for (uint64_t i = warp; i < g.nv; i += nwarps) {
+    unsigned long long s = 0;
+    unsigned long long o = g.off[i];
+    uint32_t d = g.deg[i];
+    for (uint32_t k = lane; k < d; k += 32) s += g.arcs[o + k].y;
+    for (int x = 16; x; x >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, x);
+    if (lane == 0) K[i] = (long long)s;
+    tot += s;
+  }
+  if (lane == 0 && tot) atomicAdd(&ctrl->red_a, tot);
+}
+
+// sigma = sum of arc weights with both ends in one community (red_a);
+// sum_c Sigma_c^2 split into low (red_b) and high (red_c) 32-bit parts.
+__global__ void k_modularity(GraphView g, const uint32_t* __restrict__ C,
+                             const long long* __restrict__ Sigma, uint32_t n, Ctrl* ctrl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long sig = 0;
+  for (uint64_t i = warp; i < g.nv; i += nwarps) {
+    uint32_t ci = C[i];
+    unsigned long long o = g.off[i];
+    uint32_t d = g.deg[i];
+    for (uint32_t k = lane; k < d; k += 32) {
+      uint2 a = g.arcs[o + k];
+      if (C[a.x] == ci) sig += a.y;
+    }
+  }
+  unsigned long long lo = 0, hi = 0;
+  for (uint64_t c = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; c < n;
+       c += uint64_t(gridDim.x) * blockDim.x) {
+    unsigned long long s = (unsigned long long)Sigma[c];
+    u128 sq = (u128)s * s;
+    lo += (unsigned long long)(sq & 0xFFFFFFFFull);
+    hi += (unsigned long long)(sq >> 32);
+  }
+  for (int x = 16; x; x >>= 1) {
+    sig += __shfl_xor_sync(0xFFFFFFFFu, sig, x);
+    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, x);
+    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, x);
+  }
+  if (lane == 0) {
+    if (sig) atomicAdd(&ctrl->red_a, sig);
+    if (lo) atomicAdd(&ctrl->red_b, lo);
+    if (hi) atomicAdd(&ctrl->red_c, hi);
+  }
+}
+
+__global__ void k_deg_u32(const uint32_t* __restrict__ deg, uint32_t* __restrict__ out, uint32_t n) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x)
+    out[i] = deg[i];
+}
+
+__global__ void k_export_rows(GraphView g, const uint32_t* __restrict__ eoff,
+                              unsigned long long* __restrict__ off_out, uint32_t* __restrict__ idx,
+                              uint32_t* __restrict__ w) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < g.nv; i += nwarps) {
+    unsigned long long o = g.off[i];
+    uint32_t d = g.deg[i], e = eoff[i];
+    for (uint32_t k = lane; k < d; k += 32) {
+      uint2 a = g.arcs[o + k];
+      idx[e + k] = a.x;
+      w[e + k] = a.y;
+    }
+    if (lane == 0) off_out[i] = e;
+    if (lane == 0 && i + 1 == g.nv) off_out[g.nv] = e + d;
+  }
+}
+
+__global__ void k_sigma_sizes(uint32_t n, const uint32_t* __restrict__ C,
+                              const long long* __restrict__ K, long long* __restrict__ Sigma,
+                              int* __restrict__ size) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t c = C[i];
+    atomicAdd((unsigned long long*)&Sigma[c], (unsigned long long)K[i]);
+    atomicAdd(&size[c], 1);
+  }
+}
+
+int read_ctrl(Handle* h) {
+  DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+}  // namespace
+
+int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx_in,
+                const uint32_t* w_in, uint64_t nnz) {
+  const uint32_t n = h->n;
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_validate<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(n, off_in, idx_in, w_in,
+                                                                         nnz, h->ctrl);
+    DFL_TRY(check_launch(h, "validate"));
+  }
+  DFL_TRY(read_ctrl(h));
+  if (h->hctrl->err) return set_error(h, DFL_ERR_INVALID, "input CSR is not a valid symmetric graph");
+  if (h->hctrl->red_a >= (1ull << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m >= 2^32");
+  h->max_deg = h->hctrl->max_deg;
+  h->num_arcs = nnz;
+  // slack capacities and offsets
+  unsigned long long* capl = nullptr;
+  DFL_CUDA(h, cudaMalloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
+  int rc = DFL_OK;
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_caps<<<grid_for(n, 256), 256, 0, h->stream>>>(n, off_in, h->deg, h->cap, capl);
+    rc = check_launch(h, "caps");
+  }
+  if (!rc) rc = scan_u64(h, capl, h->off, n);  // off has n+1 entries during the build
+  unsigned long long total = 0;
+  if (!rc && cudaMemcpyAsync(&total, h->off + n, sizeof(total), cudaMemcpyDeviceToHost,
+                             h->stream) != cudaSuccess)
+    rc = set_error(h, DFL_ERR_CUDA, "copy total");
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "sync");
+  cudaFree(capl);
+  if (rc) return rc;
+  uint64_t pool = total + total / 8 + 1024;
+  pool = (pool + 1) & ~uint64_t(1);
+  DFL_CUDA(h, cudaMalloc(&h->arcs, sizeof(uint2) * pool));
+  h->pool_cap = pool;
+  h->pool_top = total;
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_fill_rows<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(n, off_in, idx_in, w_in,
+                                                                         h->off, h->arcs);
+    DFL_TRY(check_launch(h, "fill rows"));
+  }
+  return DFL_OK;
+}
+
+int weighted_degrees(Handle* h) {
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->red_a, 0, sizeof(unsigned long long), h->stream));
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_weighted_degree<<<grid_for(uint64_t(h->n) * 32, 256), 256, 0, h->stream>>>(base_view(h), h->K,
+                                                                                  h->ctrl);
+    DFL_TRY(check_launch(h, "weighted degree"));
+  }
+  DFL_TRY(read_ctrl(h));
+  h->m2 = (long long)h->hctrl->red_a;
+  return DFL_OK;
+}
+
+int modularity_parts(Handle* h, i128* num, i128* den) {
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->red_a, 0, 3 * sizeof(unsigned long long), h->stream));
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_modularity<<<grid_for(uint64_t(h->n) * 32, 256), 256, 0, h->stream>>>(base_view(h), h->C,
+                                                                             h->Sigma, h->n, h->ctrl);
+    DFL_TRY(check_launch(h, "modularity"));
+  }
+  DFL_TRY(read_ctrl(h));
+  i128 sig = (i128)h->hctrl->red_a;
+  i128 sq = ((i128)h->hctrl->red_c << 32) + (i128)h->hctrl->red_b;
+  *num = (i128)h->m2 * sig - sq;
+  *den = (i128)h->m2 * (i128)h->m2;
+  return DFL_OK;
+}
+
+int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool device_out) {
+  const uint32_t n = h->n;
+  uint32_t *d32 = nullptr, *eoff = nullptr, *didx = nullptr, *dw = nullptr;
+  unsigned long long* doff = nullptr;
+  int rc = DFL_OK;
+  auto cleanup = [&]() {
+    cudaFree(d32);
+    cudaFree(eoff);
+    if (!device_out) {
+      cudaFree(didx);
+      cudaFree(dw);
+      cudaFree(doff);
+    }
+  };
+  if (cudaMalloc(&d32, sizeof(uint32_t) * (uint64_t(n) + 1)) != cudaSuccess ||
+      cudaMalloc(&eoff, sizeof(uint32_t) * (uint64_t(n) + 1)) != cudaSuccess) {
+    cleanup();
+    return set_error(h, DFL_ERR_NOMEM, "export buffers");
+  }
+  if (device_out) {
+    doff = reinterpret_cast<unsigned long long*>(off);
+    didx = idx;
+    dw = w;
+  } else if (cudaMalloc(&doff, sizeof(unsigned long long) * (uint64_t(n) + 1)) != cudaSuccess ||
+             cudaMalloc(&didx, sizeof(uint32_t) * (h->num_arcs + 1)) != cudaSuccess ||
+             cudaMalloc(&dw, sizeof(uint32_t) * (h->num_arcs + 1)) != cudaSuccess) {
+    cleanup();
+    return set_error(h, DFL_ERR_NOMEM, "export buffers");
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_deg_u32<<<grid_for(n, 256), 256, 0, h->stream>>>(h->deg, d32, n);
+    rc = check_launch(h, "export deg");
+  }
+  if (!rc) rc = scan_u32(h, d32, eoff, n);
+  if (!rc) {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    if (n) {
+      k_export_rows<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(base_view(h), eoff,
+                                                                             doff, didx, dw);
+      rc = check_launch(h, "export rows");
+    } else if (cudaMemsetAsync(doff, 0, sizeof(unsigned long long), h->stream) != cudaSuccess) {
+      rc = set_error(h, DFL_ERR_CUDA, "memset");
+    }
+  }
+  if (!rc && !device_out) {
+    if (cudaMemcpyAsync(off, doff, sizeof(uint64_t) * (uint64_t(n) + 1), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(idx, didx, sizeof(uint32_t) * h->num_arcs, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(w, dw, sizeof(uint32_t) * h->num_arcs, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      rc = set_error(h, DFL_ERR_CUDA, "export copy");
+  }
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "sync");
+  cleanup();
+  return rc;
+}
+
+int recompute_sigma_sizes(Handle* h, const uint32_t* C) {
+  DFL_CUDA(h, cudaMemsetAsync(h->Sigma, 0, sizeof(long long) * h->n, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->csize, 0, sizeof(int) * h->n, h->stream));
+  LaunchScope ls(h, DFL_PROF_OTHER);
+  k_sigma_sizes<<<grid_for(h->n, 256), 256, 0, h->stream>>>(h->n, C, h->K, h->Sigma, h->csize);
+  return check_launch(h, "sigma sizes");
+}
+
+}  // namespace dfl

@@ -1,0 +1,507 @@
+// Local-moving phase (Alg. 5) with Dynamic Frontier expansion.
+//
+// One iteration visits the frontier in `substeps` hash classes.  For each
+// class, the decide kernels (one per degree bin) evaluate every frontier
+// vertex i against the membership C', totals Sigma' and sizes left by the
+// previous class:
+//   scanCommunities: H[c] = sum of w_ij over neighbours j != i with C'[j] = c
+//   best c != d = C'[i] by score(c) = 2m*H[c] - K_i*Sigma_c (ties: smaller c)
+//   move iff score(c*) > stay = 2m*H[d] - K_i*(Sigma_d - K_i)   (Eq. 2 > 0)
+//   except a singleton moving into a singleton community with a larger id.
+// A mover is recorded, its numerator score - stay is added to S, and its
+// neighbours (in the affected range) are marked for the next iteration
+// (Section 3.1: "mark neighbours as affected").  The commit kernel then
+// applies the class's moves to C', Sigma' and the sizes.
+#include "common.cuh"
+
+namespace dfl {
+
+namespace {
+
+struct DecideArgs {
+  GraphView g;
+  const uint32_t* C;
+  const long long* K;
+  const long long* Sigma;
+  const int* size;
+  long long m2;
+  const uint32_t* list;
+  const unsigned int* count;
+  uint32_t* fbits_next;
+  uint32_t* next_lists;
+  Segs seg;
+  int next_buf;
+  const uint32_t* rbits;  // affected range, nullptr = every vertex
+  uint32_t* ever;         // first-pass processed set, nullptr = not tracked
+  uint32_t* mv_i;
+  uint32_t* mv_c;
+  uint32_t* mv_d;
+  Ctrl* ctrl;
+  uint32_t k;
+  uint2* gtable;          // bin 3: per-block global tables
+  uint32_t gslots;        // slots per block (power of two)
+};
+
+// Outcome of one vertex's decision, identical on every lane / thread.
+__device__ __forceinline__ bool decide_move(const DecideArgs& a, uint32_t i, uint32_t d, long long Ki,
+                                            bool have, i128 best, uint32_t bc, unsigned long long Hd,
+                                            i128* gain) {
+  if (!have) return false;
+  i128 stay = (i128)a.m2 * (i128)Hd - (i128)Ki * (i128)(a.Sigma[d] - Ki);
+  if (!(best > stay)) return false;
+  if (a.size[d] == 1 && a.size[bc] == 1 && bc > d) return false;  // singleton-swap guard
+  *gain = best - stay;
+  return true;
+}
+
+__device__ __forceinline__ void record_move(const DecideArgs& a, uint32_t i, uint32_t c, uint32_t d,
+                                            i128 gain) {
+  uint32_t slot = atomicAdd(&a.ctrl->movers, 1u);
+  a.mv_i[slot] = i;
+  a.mv_c[slot] = c;
+  a.mv_d[slot] = d;
+  add_s(a.ctrl, (u128)gain);
+}
+
+// Mark neighbour j of a mover for the next iteration (warp-collective).
+__device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool valid) {
+  bool fresh = false;
+  uint32_t key = 0;
+  if (valid && (!a.rbits || bit_test(a.rbits, j)) && bit_set(a.fbits_next, j)) {
+    fresh = true;
+    key = substep_class(j, a.k) * kBins + degree_bin(a.g.deg[j]);
+  }
+  append_vertex(j, fresh, key, a.next_lists, a.seg, a.ctrl, a.next_buf);
+}
+
+// ---------------------------------------------------------------------------
+// Bin 0: deg <= 32, one warp per vertex, one arc per lane, aggregation by
+// community with match/reduce in registers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t cnt = *a.count;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long bytes = 0, processed = 0;
+  for (uint64_t t = warp; t < cnt; t += nwarps) {
+    const uint32_t i = a.list[t];
+    if (a.ever && lane == 0) bit_set(a.ever, i);
+    ++processed;
+    if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
+    const uint32_t d = a.C[i];
+    const long long Ki = a.K[i];
+    const unsigned long long o = a.g.off[i];
+    const uint32_t dg = a.g.deg[i];
+    uint2 arc = lane < dg ? a.g.arcs[o + lane] : make_uint2(i, 0u);
+    bool valid = lane < dg && arc.x != i;
+    uint32_t c = valid ? a.C[arc.x] : kEmpty;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
+    uint32_t hsum = __reduce_add_sync(peers, valid ? arc.y : 0u);
+    bool leader = valid && lane == uint32_t(__ffs(peers) - 1);
+    unsigned dm = __ballot_sync(0xFFFFFFFFu, leader && c == d);
+    unsigned long long Hd = dm ? __shfl_sync(0xFFFFFFFFu, hsum, __ffs(dm) - 1) : 0u;
+    bool cand = leader && c != d;
+    unsigned cm = __ballot_sync(0xFFFFFFFFu, cand);
+    i128 score = 0;
+    if (cand) score = (i128)a.m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
+    bool have = cand;
+    uint32_t bc = c;
+    warp_argmax(have, score, bc);
+    i128 gain = 0;
+    bool mv = decide_move(a, i, d, Ki, have, score, bc, Hd, &gain);
+    bytes += 24 + 12ull * dg + 12ull * __popc(cm);
+    if (mv) {
+      if (lane == 0) record_move(a, i, bc, d, gain);
+      mark_next(a, arc.x, valid);
+      bytes += 16 + 4ull * dg;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&a.ctrl->move_bytes, bytes);
+    if (processed) atomicAdd(&a.ctrl->processed, processed);
+  }
+}
+
+// Open-addressing insert (linear probing) of weight w under key c.
+__device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
+                                          uint32_t w) {
+  uint32_t s = hash32(c) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    uint32_t prev = atomicCAS(&keys[s], kEmpty, c);
+    if (prev == kEmpty || prev == c) {
+      atomicAdd(&vals[s], w);
+      return true;
+    }
+    s = (s + 1) & mask;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Bin 1: 32 < deg <= 256, one warp per vertex with a 512-slot shared table.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kWarpSlots = 512;
+constexpr int kWarpHashWarps = 8;
+
+__global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
+  __shared__ uint32_t skeys[kWarpHashWarps][kWarpSlots];
+  __shared__ uint32_t svals[kWarpHashWarps][kWarpSlots];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  uint32_t* keys = skeys[wib];
+  uint32_t* vals = svals[wib];
+  const uint32_t cnt = *a.count;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long bytes = 0, processed = 0;
+  for (uint64_t t = warp; t < cnt; t += nwarps) {
+    const uint32_t i = a.list[t];
+    if (a.ever && lane == 0) bit_set(a.ever, i);
+    ++processed;
+    if (a.rbits && !bit_test(a.rbits, i)) continue;
+    const uint32_t d = a.C[i];
+    const long long Ki = a.K[i];
+    const unsigned long long o = a.g.off[i];
+    const uint32_t dg = a.g.deg[i];
+    uint32_t slots = 64;
+    while (slots < 2 * dg && slots < kWarpSlots) slots <<= 1;
+    const uint32_t mask = slots - 1;
+    for (uint32_t s = lane; s < slots; s += 32) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (uint32_t k = lane; k < dg; k += 32) {
+      uint2 arc = a.g.arcs[o + k];
+      if (arc.x != i) ok &= table_add(keys, vals, mask, a.C[arc.x], arc.y);
+    }
+    if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
+    __syncwarp();
+    bool have = false;
+    i128 best = 0;
+    uint32_t bc = 0;
+    unsigned long long Hd = 0;
+    uint32_t ncand = 0;
+    for (uint32_t s = lane; s < slots; s += 32) {
+      uint32_t c = keys[s];
+      if (c == kEmpty) continue;
+      if (c == d) {
+        Hd = vals[s];
+        continue;
+      }
+      ++ncand;
+      i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+      if (!have || sc > best || (sc == best && c < bc)) {
+        have = true;
+        best = sc;
+        bc = c;
+      }
+    }
+    for (int x = 16; x; x >>= 1) {
+      Hd += __shfl_xor_sync(0xFFFFFFFFu, Hd, x);
+      ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+    }
+    warp_argmax(have, best, bc);
+    i128 gain = 0;
+    bool mv = decide_move(a, i, d, Ki, have, best, bc, Hd, &gain);
+    bytes += 24 + 12ull * dg + 12ull * ncand;
+    if (mv) {
+      if (lane == 0) record_move(a, i, bc, d, gain);
+      for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
+        uint32_t k = k0 + lane;
+        uint32_t j = k < dg ? a.g.arcs[o + k].x : i;
+        mark_next(a, j, k < dg && j != i);
+      }
+      bytes += 16 + 4ull * dg;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&a.ctrl->move_bytes, bytes);
+    if (processed) atomicAdd(&a.ctrl->processed, processed);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bins 2 and 3: one block per vertex; the table is in shared memory (bin 2,
+// dynamic shared memory) or in a per-block slice of global memory (bin 3).
+// ---------------------------------------------------------------------------
+template <bool kGlobal>
+__global__ void __launch_bounds__(512) k_decide_block(DecideArgs a) {
+  extern __shared__ uint32_t dyn[];
+  __shared__ unsigned long long s_hd;
+  __shared__ uint32_t s_ncand;
+  __shared__ unsigned long long s_lo[16], s_hi[16];
+  __shared__ uint32_t s_c[16];
+  __shared__ int s_have[16];
+  __shared__ int s_ok;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t cnt = *a.count;
+  unsigned long long bytes = 0, processed = 0;
+  for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+    const uint32_t i = a.list[t];
+    if (a.ever && threadIdx.x == 0) bit_set(a.ever, i);
+    ++processed;
+    if (a.rbits && !bit_test(a.rbits, i)) continue;
+    const uint32_t d = a.C[i];
+    const long long Ki = a.K[i];
+    const unsigned long long o = a.g.off[i];
+    const uint32_t dg = a.g.deg[i];
+    uint32_t slots = 1024;
+    while (slots < 2 * dg) slots <<= 1;
+    uint32_t* keys;
+    uint32_t* vals;
+    if (kGlobal) {
+      if (slots > a.gslots) slots = a.gslots;  // gslots >= 2 * max degree
+      keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
+      vals = keys + a.gslots;
+    } else {
+      keys = dyn;
+      vals = dyn + slots;
+    }
+    const uint32_t mask = slots - 1;
+    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    if (threadIdx.x == 0) {
+      s_hd = 0;
+      s_ncand = 0;
+      s_ok = 1;
+    }
+    __syncthreads();
+    bool ok = true;
+    for (uint32_t k = threadIdx.x; k < dg; k += blockDim.x) {
+      uint2 arc = a.g.arcs[o + k];
+      if (arc.x != i) ok &= table_add(keys, vals, mask, a.C[arc.x], arc.y);
+    }
+    if (!ok) s_ok = 0;
+    __syncthreads();
+    if (!s_ok && threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
+    bool have = false;
+    i128 best = 0;
+    uint32_t bc = 0;
+    uint32_t ncand = 0;
+    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
+      uint32_t c = keys[s];
+      if (c == kEmpty) continue;
+      if (c == d) {
+        s_hd = vals[s];  // exactly one slot holds d
+        continue;
+      }
+      ++ncand;
+      i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+      if (!have || sc > best || (sc == best && c < bc)) {
+        have = true;
+        best = sc;
+        bc = c;
+      }
+    }
+    for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+    warp_argmax(have, best, bc);
+    if (lane == 0) {
+      s_lo[wib] = (unsigned long long)(u128)best;
+      s_hi[wib] = (unsigned long long)((u128)best >> 64);
+      s_c[wib] = bc;
+      s_have[wib] = have;
+      if (ncand) atomicAdd(&s_ncand, ncand);
+    }
+    __syncthreads();
+    if (wib == 0) {
+      have = lane < nw && s_have[lane];
+      best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
+      bc = lane < nw ? s_c[lane] : 0;
+      warp_argmax(have, best, bc);
+      if (lane == 0) {
+        s_lo[0] = (unsigned long long)(u128)best;
+        s_hi[0] = (unsigned long long)((u128)best >> 64);
+        s_c[0] = bc;
+        s_have[0] = have;
+      }
+    }
+    __syncthreads();
+    have = s_have[0];
+    best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
+    bc = s_c[0];
+    i128 gain = 0;
+    bool mv = decide_move(a, i, d, Ki, have, best, bc, s_hd, &gain);
+    bytes += 24 + 12ull * dg + 12ull * s_ncand;
+    if (mv) {
+      if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
+      for (uint32_t k0 = wib * 32; k0 < dg; k0 += blockDim.x) {
+        uint32_t k = k0 + lane;
+        uint32_t j = k < dg ? a.g.arcs[o + k].x : i;
+        mark_next(a, j, k < dg && j != i);
+      }
+      bytes += 16 + 4ull * dg;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.ctrl->move_bytes, bytes);
+    if (processed) atomicAdd(&a.ctrl->processed, processed);
+  }
+}
+
+// Apply the moves of one sub-step.
+__global__ void k_commit(const uint32_t* __restrict__ mv_i, const uint32_t* __restrict__ mv_c,
+                         const uint32_t* __restrict__ mv_d, uint32_t* __restrict__ C,
+                         const long long* __restrict__ K, long long* __restrict__ Sigma,
+                         int* __restrict__ size, Ctrl* ctrl) {
+  const uint32_t m = ctrl->movers;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && m) atomicAdd(&ctrl->moved, (unsigned long long)m);
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < m;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t i = mv_i[t], c = mv_c[t], d = mv_d[t];
+    long long ki = K[i];
+    C[i] = c;
+    atomicAdd((unsigned long long*)&Sigma[d], (unsigned long long)(-ki));
+    atomicAdd((unsigned long long*)&Sigma[c], (unsigned long long)ki);
+    atomicSub(&size[d], 1);
+    atomicAdd(&size[c], 1);
+  }
+}
+
+int read_ctrl(Handle* h) {
+  DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+// floor(tau_num * m2^2 / (2 * tau_den * drop^pass)), the exact form of
+// "sum of dQ <= tau" (Alg. 5) with S = sum of the movers' 2m^2 * dQ.
+u128 tolerance_threshold(const dfl_options& o, long long m2, uint32_t pass) {
+  u128 num = (u128)o.tau_num * (u128)(uint64_t)m2 * (u128)(uint64_t)m2;
+  u128 den = (u128)2 * (u128)o.tau_den;
+  for (uint32_t p = 0; p < pass; ++p) {
+    if (den > num) return 0;
+    den *= (u128)o.tolerance_drop;
+  }
+  if (den == 0) return ~(u128)0;
+  return num / den;
+}
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return uint32_t(p);
+}
+
+}  // namespace
+
+int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
+               bool record_trace) {
+  const uint32_t k = h->opt.substeps;
+  make_segs(h, k);
+  const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
+  DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
+  unsigned int cur_count[kMaxSubsteps][kBins];
+  for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+    for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
+  // global tables for the largest bin: one slice of gslots keys + gslots
+  // values per block, gslots >= 2 * (max degree of the current graph)
+  const uint32_t gblocks = 2 * 152;
+  const uint32_t gslots = next_pow2(2ull * (ma.max_deg > kBinBlock ? ma.max_deg : kBinBlock));
+  if (ma.max_deg > kBinBlock && uint64_t(gblocks) * gslots > h->gtable_cap) {
+    if (h->gtable) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->gtable);
+      h->gtable = nullptr;
+      h->gtable_cap = 0;
+    }
+    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(gblocks) * gslots));
+    h->gtable_cap = uint64_t(gblocks) * gslots;
+  }
+  static bool smem_set = false;
+  if (!smem_set) {
+    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 4 * kBinBlock)));
+    smem_set = true;
+  }
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->move_bytes, 0, sizeof(unsigned long long), h->stream));
+  int cur = 0;
+  uint32_t it = 0;
+  while (it < h->opt.max_iterations) {
+    ++it;
+    const int nxt = cur ^ 1;
+    // reset the iteration's sums and the next buffer's list lengths
+    DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
+    DecideArgs a;
+    a.g = ma.g;
+    a.C = ma.C;
+    a.K = ma.K;
+    a.Sigma = ma.Sigma;
+    a.size = ma.size;
+    a.m2 = ma.m2;
+    a.fbits_next = h->fbits[nxt];
+    a.next_lists = h->lists[nxt];
+    a.seg = h->segs;
+    a.next_buf = nxt;
+    a.rbits = ma.use_range ? h->rbits : nullptr;
+    a.ever = ma.track_ever ? h->ever : nullptr;
+    a.mv_i = h->mv_i;
+    a.mv_c = h->mv_c;
+    a.mv_d = h->mv_d;
+    a.ctrl = h->ctrl;
+    a.k = k;
+    a.gtable = h->gtable;
+    a.gslots = gslots;
+    for (uint32_t s = 0; s < k; ++s) {
+      bool any = false;
+      for (int b = 0; b < kBins; ++b) {
+        uint32_t c = cur_count[s][b];
+        if (!c) continue;
+        any = true;
+        a.list = h->lists[cur] + h->segs.off[s * kBins + b];
+        a.count = &h->ctrl->count[cur][s][b];
+        LaunchScope ls(h, DFL_PROF_MOVE);
+        if (b == 0) {
+          k_decide_warp<<<grid_for(uint64_t(c) * 32, 256, 152 * 64), 256, 0, h->stream>>>(a);
+        } else if (b == 1) {
+          k_decide_warp_hash<<<grid_for(uint64_t(c) * 32, 256, 152 * 16), 256, 0, h->stream>>>(a);
+        } else if (b == 2) {
+          uint32_t slots = next_pow2(2ull * kBinBlock);
+          k_decide_block<false><<<grid_for(c, 1, 152 * 4), 256, sizeof(uint32_t) * 2 * slots,
+                                  h->stream>>>(a);
+        } else {
+          k_decide_block<true><<<grid_for(c, 1, gblocks), 512, 0, h->stream>>>(a);
+        }
+        DFL_TRY(check_launch(h, "decide"));
+      }
+      if (any) {
+        {
+          LaunchScope ls(h, DFL_PROF_COMMIT);
+          k_commit<<<152 * 2, 256, 0, h->stream>>>(h->mv_i, h->mv_c, h->mv_d, ma.C, ma.K, ma.Sigma,
+                                                   ma.size, h->ctrl);
+          DFL_TRY(check_launch(h, "commit"));
+        }
+        DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+      }
+    }
+    DFL_TRY(read_ctrl(h));
+    const Ctrl& c = *h->hctrl;
+    if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
+    u128 S = ((u128)c.s_hi << 32) + (u128)c.s_lo;
+    if (record_trace) {
+      h->trace.push_back(c.processed);
+      h->trace.push_back(c.moved);
+      h->trace.push_back(uint64_t(S >> 64));
+      h->trace.push_back(uint64_t(S));
+    }
+    DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
+    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+      for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
+    cur = nxt;
+    if (S <= threshold) break;  // locally converged
+  }
+  h->prof.bytes[DFL_PROF_MOVE] += h->hctrl->move_bytes;
+  // leave the unprocessed frontier behind: clear the other buffer's bitmap
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
+  *iterations = it;
+  return DFL_OK;
+}
+
+}  // namespace dfl

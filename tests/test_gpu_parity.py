@@ -1,0 +1,344 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer state must match bit for bit: the slack CSR as sorted adjacency,
+K, Sigma, 2m, membership, frontiers and the first-pass trace (vertices
+processed, movers and the exact 128-bit sum S of the movers' dQ numerators
+per iteration).  Modularity must match within 1e-12 relative; its exact
+integer numerator and denominator must be equal.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dfl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2404_19634_gb300 as mod
+    mod.build()
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def pair(dfl, orc, g, substeps=4, tau_agg=0.8, **kw):
+    off, idx, w = synth.to_csr(g)
+    opt = dfl.default_options(substeps=substeps, tau_agg=tau_agg, **kw)
+    a = dfl.Dfl(g.n, off, idx, w, options=opt)
+    b = orc.Oracle(g.n, off, idx, w)
+    b.set_options(substeps=substeps, tau_agg=tau_agg,
+                  **{k: v for k, v in kw.items() if k in ("max_iterations", "max_passes")})
+    return a, b
+
+
+def same_state(a, b, stats=True):
+    Ca, Cb = a.membership(), b.membership()
+    assert np.array_equal(Ca, Cb), f"membership differs at {np.flatnonzero(Ca != Cb)[:10]}"
+    Ka, Sa, ma = a.weights()
+    Kb, Sb, mb = b.weights()
+    assert ma == mb
+    assert np.array_equal(Ka, Kb), "K differs"
+    assert np.array_equal(Sa, Sb), "Sigma differs"
+    qa, na, da = a.modularity()
+    qb, nb, db = b.modularity()
+    assert (na, da) == (nb, db)
+    assert abs(qa - qb) <= 1e-12 * max(1.0, abs(qb))
+    if stats:
+        sa, sb = a.stats(), b.stats()
+        assert sa["passes"] == sb["passes"] and sa["iterations"] == sb["iterations"]
+        assert sa["affected_initial"] == sb["affected_initial"]
+        assert sa["affected_ever"] == sb["affected_ever"]
+        assert a.trace() == b.trace()
+
+
+def same_graph(a, b):
+    for x, y in zip(a.graph(), b.graph()):
+        assert np.array_equal(x, y), "graph differs"
+
+
+# ---------------------------------------------------------------------------
+
+def test_static_sbm_10k(dfl, orc):
+    g = synth.sbm(10000, 50, 0.02, 0.0002, 1)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    same_state(a, b)
+    same_graph(a, b)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sbm_batch_update(dfl, orc, mode):
+    """10,000-vertex SBM, static, then one 100-edge batch (80% insertions,
+    20% deletions) updated with ND, DS or DF."""
+    g = synth.sbm(10000, 50, 0.02, 0.0002, 1)
+    dels, ins = synth.random_batch(g.n, g, 80, 20, 11)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+    same_graph(a, b)
+    same_state(a, b, stats=False)  # K, Sigma after the batch, before the update
+    Fa, Ra = a.mark(mode)
+    Fb, Rb = b.mark(mode)
+    assert np.array_equal(Fa, Fb) and np.array_equal(Ra, Rb)
+    a.update(mode)
+    b.update(mode)
+    same_state(a, b)
+
+
+@pytest.mark.parametrize("substeps", [1, 2, 4, 8])
+@pytest.mark.parametrize("scale", [10, 13])
+def test_rmat_stream(dfl, orc, substeps, scale):
+    g = synth.rmat(scale, 8 << scale, 30 + scale)
+    a, b = pair(dfl, orc, g, substeps=substeps)
+    a.static()
+    b.static()
+    same_state(a, b)
+    stream = synth.BatchStream(g, 99)
+    for t, size in enumerate([3, 40, 500, 3000]):
+        dels, ins = stream.next(size)
+        assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+        mode = [2, 0, 1, 2][t]
+        a.update(mode)
+        b.update(mode)
+        same_state(a, b)
+    same_graph(a, b)
+
+
+def test_weighted_graph_partial_deletions(dfl, orc):
+    rng = np.random.default_rng(5)
+    g = synth.planted_partition(3000, 40, 0.3, 12, 16, 6)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    for t in range(5):
+        off, idx, w = b.graph()
+        edges = [(i, int(idx[k]), int(w[k])) for i in range(g.n)
+                 for k in range(int(off[i]), int(off[i + 1])) if i < idx[k]]
+        pick = rng.choice(len(edges), 60, replace=False)
+        dels = np.array([(edges[p][0], edges[p][1], int(rng.integers(0, edges[p][2] + 1)))
+                         for p in pick], np.uint32)
+        ins = np.stack([rng.integers(0, g.n, 200), rng.integers(0, g.n, 200),
+                        rng.integers(1, 17, 200)], 1).astype(np.uint32)
+        ins = ins[ins[:, 0] != ins[:, 1]]
+        ins = np.concatenate([ins, ins[:5]])  # repeated insertions add up
+        assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+        same_graph(a, b)
+        a.update(t % 3)
+        b.update(t % 3)
+        same_state(a, b)
+
+
+def test_high_degree_bins(dfl, orc):
+    """Hubs of degree ~300, ~5,000 and ~20,000 exercise the block kernels
+    with shared-memory and global-memory tables."""
+    rng = np.random.default_rng(8)
+    n = 40000
+    base = synth.planted_partition(n, 100, 0.2, 6, 1, 3)
+    us, vs = [base.u], [base.v]
+    for hub, deg in [(5, 300), (17, 5000), (123, 20000)]:
+        nb = rng.choice(n, deg, replace=False)
+        nb = nb[nb != hub]
+        us.append(np.full(nb.shape[0], hub, np.uint32))
+        vs.append(nb.astype(np.uint32))
+    u = np.concatenate(us)
+    v = np.concatenate(vs)
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    key = np.unique((lo.astype(np.uint64) << np.uint64(32)) | hi.astype(np.uint64))
+    g = synth.EdgeList(n, (key >> np.uint64(32)).astype(np.uint32),
+                       (key & np.uint64(0xFFFFFFFF)).astype(np.uint32),
+                       np.ones(key.shape[0], np.uint32))
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    same_state(a, b)
+    stream = synth.BatchStream(g, 4)
+    dels, ins = stream.next(2000)
+    ins = np.concatenate([ins, np.array([[17, 9, 1], [123, 77, 2], [5, 31, 1]], np.uint32)])
+    assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+    a.update(0)
+    b.update(0)
+    same_state(a, b)
+    same_graph(a, b)
+
+
+def test_move_iteration_random_states(dfl, orc):
+    rng = np.random.default_rng(11)
+    g = synth.rmat(11, 12 << 11, 4)
+    for k in (1, 4):
+        a, b = pair(dfl, orc, g, substeps=k)
+        for _ in range(3):
+            C = rng.integers(0, g.n // 8, g.n).astype(np.uint32)
+            F = (rng.random(g.n) < 0.6).astype(np.uint8)
+            R = (rng.random(g.n) < 0.9).astype(np.uint8)
+            a.set_membership(C)
+            b.set_membership(C)
+            Fa, ma, Sa = a.move_iteration(F, R)
+            Fb, mb, Sb = b.move_iteration(F, R)
+            assert np.array_equal(ma, mb)
+            assert np.array_equal(Fa, Fb)
+            assert Sa == Sb
+            same_state(a, b, stats=False)
+
+
+def test_aggregation_export(dfl, orc):
+    rng = np.random.default_rng(3)
+    g = synth.sbm(3000, 30, 0.04, 0.002, 9)
+    a, b = pair(dfl, orc, g)
+    for C in [rng.integers(0, 3000, 3000), np.repeat(np.arange(30), 100), np.zeros(3000)]:
+        C = C.astype(np.uint32)
+        a.set_membership(C)
+        b.set_membership(C)
+        for x, y in zip(a.aggregate(), b.aggregate()):
+            assert np.array_equal(x, y)
+
+
+def test_louvain_from_random_frontier(dfl, orc):
+    rng = np.random.default_rng(12)
+    g = synth.sbm(5000, 25, 0.03, 0.001, 13)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    F = (rng.random(g.n) < 0.3).astype(np.uint8)
+    R = (rng.random(g.n) < 0.7).astype(np.uint8)
+    a.louvain_from(F, R)
+    b.louvain_from(F, R)
+    same_state(a, b)
+
+
+def test_temporal_no_aggregation(dfl, orc):
+    """tau_agg = 1 (Section 4.1.2, real-world dynamic graphs): never aggregate."""
+    src, dst = synth.temporal_pa_stream(3000, 40000, 0.3, 21)
+    base = synth.temporal_edges(src[:36000], dst[:36000], 3000)
+    a, b = pair(dfl, orc, base, tau_agg=1.0)
+    a.static()
+    b.static()
+    same_state(a, b)
+    for t in range(4):
+        s = slice(36000 + t * 1000, 36000 + (t + 1) * 1000)
+        ins = np.stack([src[s], dst[s], np.ones(1000, np.uint32)], 1)
+        ins = ins[ins[:, 0] != ins[:, 1]]
+        old = slice(t * 1000, (t + 1) * 1000)
+        exp = np.stack([src[old], dst[old], np.ones(1000, np.uint32)], 1)
+        exp = exp[exp[:, 0] != exp[:, 1]]
+        # expire the oldest interactions (weight 1 each); group repeats
+        lo, hi = np.minimum(exp[:, 0], exp[:, 1]), np.maximum(exp[:, 0], exp[:, 1])
+        key, cnt = np.unique((lo.astype(np.uint64) << np.uint64(32)) | hi, return_counts=True)
+        dels = np.stack([(key >> np.uint64(32)).astype(np.uint32),
+                         (key & np.uint64(0xFFFFFFFF)).astype(np.uint32), cnt.astype(np.uint32)], 1)
+        assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+        a.update(2)
+        b.update(2)
+        same_state(a, b)
+
+
+def test_empty_and_degenerate(dfl, orc):
+    g = synth.sbm(1000, 10, 0.08, 0.004, 23)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    C0 = a.membership().copy()
+    empty = np.zeros((0, 3), np.uint32)
+    assert a.apply_batch(empty, empty) == 0 and b.apply_batch(empty, empty) == 0
+    a.update(2)
+    b.update(2)
+    same_state(a, b)
+    assert np.array_equal(a.membership(), C0)
+    assert a.stats()["affected_ever"] == 0
+    # a graph without edges
+    e = synth.EdgeList(50, np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    a, b = pair(dfl, orc, e)
+    a.static()
+    b.static()
+    same_state(a, b)
+    assert a.modularity()[0] == 0.0
+    assert a.apply_batch(empty, np.array([[1, 2, 3]], np.uint32)) == 0
+    b.apply_batch(empty, np.array([[1, 2, 3]], np.uint32))
+    a.update(2)
+    b.update(2)
+    same_state(a, b)
+    # two vertices
+    t = synth.EdgeList(2, np.array([0], np.uint32), np.array([1], np.uint32), np.array([1], np.uint32))
+    a, b = pair(dfl, orc, t)
+    a.static()
+    b.static()
+    same_state(a, b)
+
+
+def test_batch_errors_leave_state_unchanged(dfl, orc):
+    g = synth.sbm(500, 5, 0.1, 0.01, 3)
+    a, b = pair(dfl, orc, g)
+    with pytest.raises(dfl.DflError):
+        a.update(2)
+    assert a.apply_batch(None, np.array([[0, 1, 1]], np.uint32), check=False) == -7
+    a.static()
+    b.static()
+    before_g = a.graph()
+    before_w = a.weights()
+    u, v = int(g.u[0]), int(g.v[0])
+    off, idx, _ = synth.to_csr(g)
+    absent = next((x, y) for x in range(g.n) for y in range(x + 1, g.n)
+                  if y not in set(idx[int(off[x]):int(off[x + 1])]))
+    cases = [
+        ([], [(0, 0, 1)], -1),
+        ([], [(0, g.n, 1)], -1),
+        ([], [(0, 1, 0)], -1),
+        ([(u, v, 0), (v, u, 0)], [], -1),
+        ([absent + (0,)], [], -2),
+        ([(u, v, 2)], [], -2),
+        ([], [(u, v, 0xFFFFFFFF)], -3),
+        ([absent + (0,)], [(0, 0, 1)], -1),
+    ]
+    for d, i, code in cases:
+        d = np.array(d, np.uint32).reshape(-1, 3)
+        i = np.array(i, np.uint32).reshape(-1, 3)
+        assert a.apply_batch(d, i, check=False) == code
+        assert b.apply_batch(d, i) == code
+        for x, y in zip(before_g, a.graph()):
+            assert np.array_equal(x, y)
+        after = a.weights()
+        assert np.array_equal(before_w[0], after[0]) and np.array_equal(before_w[1], after[1])
+    same_state(a, b, stats=False)
+
+
+def test_invalid_graph_rejected(dfl):
+    off = np.array([0, 1, 1], np.uint64)  # arc (0,1) without (1,0)
+    with pytest.raises(dfl.DflError):
+        dfl.Dfl(2, off, np.array([1], np.uint32), np.array([1], np.uint32))
+    off = np.array([0, 1, 2], np.uint64)  # unequal weights
+    with pytest.raises(dfl.DflError):
+        dfl.Dfl(2, off, np.array([1, 0], np.uint32), np.array([1, 2], np.uint32))
+
+
+def test_device_buffers_and_stream(dfl, orc):
+    import torch
+    g = synth.sbm(4000, 20, 0.04, 0.002, 31)
+    off, idx, w = synth.to_csr(g)
+    s = torch.cuda.Stream()
+    dev = lambda x: torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else x.view(np.int32)).cuda()
+    a = dfl.Dfl(g.n, dev(off), dev(idx), dev(w), stream=s)
+    b = orc.Oracle(g.n, off, idx, w)
+    a.static()
+    b.static()
+    dels, ins = synth.random_batch(g.n, g, 200, 50, 2)
+    a.apply_batch(dev(np.ascontiguousarray(dels)), dev(np.ascontiguousarray(ins)))
+    b.apply_batch(dels, ins)
+    a.update(2)
+    b.update(2)
+    out = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    a.membership(out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), b.membership())
+    same_state(a, b)
