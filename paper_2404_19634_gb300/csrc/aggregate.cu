@@ -9,8 +9,13 @@
 //      self = true); distinct keys are written as the super-vertex's row, and
 //      its weight K'' = Sigma'' is the row sum (Alg. 4, weight reset).
 // Communities are binned by total degree: one warp with a shared-memory
-// table (<= 256), one block with a shared-memory table (<= 4096), one block
-// with a global-memory table (larger).
+// table (<= 256), one block with a shared-memory table (<= 4096); a larger
+// community is split into chunks of members, each chunk aggregated by one
+// block in shared memory and merged into the community's global table, which
+// is then emitted slot-parallel.  Within a warp, arcs are pre-aggregated per
+// neighbour community (match + reduce) before touching a table.
+#include <vector>
+
 #include "common.cuh"
 
 namespace dfl {
@@ -76,10 +81,11 @@ struct AggArgs {
 };
 
 __device__ __forceinline__ bool agg_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
-                                        uint32_t w) {
+                                        uint32_t w, uint32_t limit) {
   uint32_t s = hash32(c) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    uint32_t prev = atomicCAS(&keys[s], kEmpty, c);
+  for (uint32_t probe = 0; probe < limit; ++probe) {
+    uint32_t prev = keys[s];
+    if (prev == kEmpty) prev = atomicCAS(&keys[s], kEmpty, c);
     if (prev == kEmpty || prev == c) {
       atomicAdd(&vals[s], w);
       return true;
@@ -89,8 +95,68 @@ __device__ __forceinline__ bool agg_add(uint32_t* keys, uint32_t* vals, uint32_t
   return false;
 }
 
+// Warp-collective: add arcs [0, d) of one vertex (32 per step) to the table,
+// pre-aggregated per neighbour community; deleted arcs (weight 0) skipped.
+// Entries that do not fit are added to the fallback table if one is given.
+__device__ __forceinline__ bool agg_row(const AggArgs& a, unsigned long long o, uint32_t d,
+                                        uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t limit,
+                                        uint32_t* fkeys, uint32_t* fvals, uint32_t fmask) {
+  const uint32_t lane = threadIdx.x & 31u;
+  bool ok = true;
+  for (uint32_t k0 = 0; k0 < d; k0 += 64) {
+    uint2 arc0 = k0 + lane < d ? a.g.arcs[o + k0 + lane] : make_uint2(0u, 0u);
+    uint2 arc1 = k0 + 32 + lane < d ? a.g.arcs[o + k0 + 32 + lane] : make_uint2(0u, 0u);
+    uint32_t c0 = arc0.y ? a.Cp[arc0.x] : kEmpty;
+    uint32_t c1 = arc1.y ? a.Cp[arc1.x] : kEmpty;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      uint32_t c = u ? c1 : c0;
+      uint32_t w = u ? arc1.y : arc0.y;
+      unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
+      uint32_t hs = __reduce_add_sync(peers, c != kEmpty ? w : 0u);
+      if (c != kEmpty && lane == uint32_t(__ffs(peers) - 1)) {
+        if (!agg_add(keys, vals, mask, c, hs, limit)) {
+          if (fkeys) ok &= agg_add(fkeys, fvals, fmask, c, hs, fmask + 1);
+          else ok = false;
+        }
+      }
+    }
+  }
+  return ok;
+}
+
 constexpr uint32_t kAggWarpSlots = 512;
 constexpr int kAggWarps = 8;
+constexpr uint32_t kAggBlockSlots = 2 * kBinBlock;  // 8192 keys + values = 64 KB
+constexpr uint32_t kChunkMembers = 256;             // members per block of a giant community
+constexpr uint32_t kGiantSlots = 4096;              // shared table of a giant-community block
+
+// Write the table's entries as the row of super-vertex c (ballot order).
+__device__ __forceinline__ void emit_warp(const AggArgs& a, uint32_t c, const uint32_t* keys,
+                                          const uint32_t* vals, uint32_t slots, uint32_t* maxd) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long base = a.soff[c];
+  uint32_t pos = 0;
+  unsigned long long ksum = 0;
+  for (uint32_t s0 = 0; s0 < slots; s0 += 32) {
+    uint32_t s = s0 + lane;
+    uint32_t key = s < slots ? keys[s] : kEmpty;
+    bool has = key != kEmpty;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+    if (has) {
+      uint32_t val = vals[s];
+      a.arcs_out[base + pos + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, val);
+      ksum += val;
+    }
+    pos += __popc(m);
+  }
+  for (int x = 16; x; x >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, x);
+  if (lane == 0) {
+    a.deg_out[c] = pos;
+    a.Knew[c] = (long long)ksum;
+  }
+  *maxd = max(*maxd, pos);
+}
 
 // Bin 0: one warp per community (total degree <= 256).
 __global__ void __launch_bounds__(256) k_agg_warp(AggArgs a) {
@@ -102,13 +168,12 @@ __global__ void __launch_bounds__(256) k_agg_warp(AggArgs a) {
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned int maxd = 0;
+  uint32_t maxd = 0;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t c = a.list[t];
     const unsigned long long td = a.soff[c + 1] - a.soff[c];
     uint32_t slots = 32;
     while (slots < 2 * td && slots < kAggWarpSlots) slots <<= 1;
-    const uint32_t mask = slots - 1;
     for (uint32_t s = lane; s < slots; s += 32) {
       keys[s] = kEmpty;
       vals[s] = 0;
@@ -117,44 +182,18 @@ __global__ void __launch_bounds__(256) k_agg_warp(AggArgs a) {
     bool ok = true;
     for (uint32_t m = a.coff[c]; m < a.coff[c + 1]; ++m) {
       uint32_t v = a.members[m];
-      unsigned long long o = a.g.off[v];
-      uint32_t d = a.g.deg[v];
-      for (uint32_t k = lane; k < d; k += 32) {
-        uint2 arc = a.g.arcs[o + k];
-        ok &= agg_add(keys, vals, mask, a.Cp[arc.x], arc.y);
-      }
+      ok &= agg_row(a, a.g.off[v], a.g.deg[v], keys, vals, slots - 1, slots, nullptr, nullptr, 0);
     }
     if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
     __syncwarp();
-    const unsigned long long base = a.soff[c];
-    uint32_t pos = 0;
-    unsigned long long ksum = 0;
-    for (uint32_t s0 = 0; s0 < slots; s0 += 32) {
-      uint32_t s = s0 + lane;
-      uint32_t key = s < slots ? keys[s] : kEmpty;
-      bool has = key != kEmpty;
-      unsigned m = __ballot_sync(0xFFFFFFFFu, has);
-      if (has) {
-        uint32_t val = vals[s];
-        a.arcs_out[base + pos + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, val);
-        ksum += val;
-      }
-      pos += __popc(m);
-    }
-    for (int x = 16; x; x >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, x);
-    if (lane == 0) {
-      a.deg_out[c] = pos;
-      a.Knew[c] = (long long)ksum;
-    }
-    maxd = max(maxd, pos);
+    emit_warp(a, c, keys, vals, slots, &maxd);
     __syncwarp();
   }
   if (lane == 0 && maxd) atomicMax(&a.ctrl->max_deg, maxd);
 }
 
-// Bins 1 and 2: one block per community; a warp per member.
-template <bool kGlobal>
-__global__ void __launch_bounds__(512) k_agg_block(AggArgs a) {
+// Bin 1: one block per community (total degree <= 4096); a warp per member.
+__global__ void __launch_bounds__(256) k_agg_block(AggArgs a) {
   extern __shared__ uint32_t dyn[];
   __shared__ unsigned int s_pos;
   __shared__ unsigned long long s_sum;
@@ -165,20 +204,10 @@ __global__ void __launch_bounds__(512) k_agg_block(AggArgs a) {
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const uint32_t c = a.list[t];
     const unsigned long long td = a.soff[c + 1] - a.soff[c];
-    unsigned long long distinct_max = td < a.ncomm ? td : a.ncomm;
     uint32_t slots = 1024;
-    while (slots < 2 * distinct_max) slots <<= 1;
-    uint32_t* keys;
-    uint32_t* vals;
-    if (kGlobal) {
-      if (slots > a.gslots) slots = a.gslots;
-      keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
-      vals = keys + a.gslots;
-    } else {
-      keys = dyn;
-      vals = dyn + slots;
-    }
-    const uint32_t mask = slots - 1;
+    while (slots < 2 * td && slots < kAggBlockSlots) slots <<= 1;
+    uint32_t* keys = dyn;
+    uint32_t* vals = dyn + slots;
     for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
       keys[s] = kEmpty;
       vals[s] = 0;
@@ -192,12 +221,7 @@ __global__ void __launch_bounds__(512) k_agg_block(AggArgs a) {
     bool ok = true;
     for (uint32_t m = a.coff[c] + wib; m < a.coff[c + 1]; m += nw) {
       uint32_t v = a.members[m];
-      unsigned long long o = a.g.off[v];
-      uint32_t d = a.g.deg[v];
-      for (uint32_t k = lane; k < d; k += 32) {
-        uint2 arc = a.g.arcs[o + k];
-        ok &= agg_add(keys, vals, mask, a.Cp[arc.x], arc.y);
-      }
+      ok &= agg_row(a, a.g.off[v], a.g.deg[v], keys, vals, slots - 1, slots, nullptr, nullptr, 0);
     }
     if (!ok) s_ok = 0;
     __syncthreads();
@@ -229,6 +253,102 @@ __global__ void __launch_bounds__(512) k_agg_block(AggArgs a) {
     __syncthreads();
   }
   if (threadIdx.x == 0 && maxd) atomicMax(&a.ctrl->max_deg, maxd);
+}
+
+// Giant communities (bin 2).  giant[g] = community, gtab[g] = offset of its
+// global table of gsize[g] slots (keys, then values, in uint2 units: the
+// table of g occupies gtable[gtab[g] .. gtab[g] + gsize[g]) as keys|values).
+struct GiantArgs {
+  const uint32_t* giant;
+  const unsigned long long* gtab;
+  const uint32_t* gsize;
+  uint32_t ngiant;
+};
+
+// Block (g, chunk): aggregate members [chunk*256, +256) of giant g in shared
+// memory (overflow goes straight to the global table), then merge the shared
+// entries into the global table.
+__global__ void __launch_bounds__(256) k_agg_giant_accum(AggArgs a, GiantArgs gi) {
+  __shared__ uint32_t keys[kGiantSlots];
+  __shared__ uint32_t vals[kGiantSlots];
+  const uint32_t wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t g = blockIdx.x;
+  const uint32_t c = gi.giant[g];
+  const uint32_t gs = gi.gsize[g];
+  uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
+  uint32_t* gvals = gkeys + gs;
+  bool ok = true;
+  for (uint32_t chunk = blockIdx.y;; chunk += gridDim.y) {
+    const uint64_t m0 = a.coff[c] + uint64_t(chunk) * kChunkMembers;
+    if (m0 >= a.coff[c + 1]) break;
+    const uint64_t mend = m0 + kChunkMembers;
+    const uint32_t m1 = a.coff[c + 1] < mend ? a.coff[c + 1] : uint32_t(mend);
+    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    __syncthreads();
+    for (uint32_t m = uint32_t(m0) + wib; m < m1; m += nw) {
+      uint32_t v = a.members[m];
+      ok &= agg_row(a, a.g.off[v], a.g.deg[v], keys, vals, kGiantSlots - 1, 32, gkeys, gvals, gs - 1);
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+      uint32_t k = keys[s];
+      if (k != kEmpty) ok &= agg_add(gkeys, gvals, gs - 1, k, vals[s], gs);
+    }
+    __syncthreads();
+  }
+  if (!ok) atomicOr(&a.ctrl->err, kErrInternal);
+}
+
+// Thread per global-table slot of every giant: emit the super arcs.
+__global__ void k_agg_giant_emit(AggArgs a, GiantArgs gi, unsigned long long total) {
+  uint32_t maxd = 0;
+  for (unsigned long long t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    // giant owning slot t (tables are laid out in giant order)
+    uint32_t lo = 0, hi = gi.ngiant;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (gi.gtab[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t g = lo;
+    const unsigned long long s = t - gi.gtab[g];
+    if (s >= gi.gsize[g]) continue;
+    const uint32_t* gkeys = reinterpret_cast<const uint32_t*>(a.gtable + gi.gtab[g]);
+    uint32_t key = gkeys[s];
+    if (key == kEmpty) continue;
+    uint32_t val = gkeys[gi.gsize[g] + s];
+    uint32_t c = gi.giant[g];
+    uint32_t pos = atomicAdd(&a.deg_out[c], 1u);
+    a.arcs_out[a.soff[c] + pos] = make_uint2(key, val);
+    atomicAdd((unsigned long long*)&a.Knew[c], (unsigned long long)val);
+    maxd = max(maxd, pos + 1);
+  }
+  if (maxd) atomicMax(&a.ctrl->max_deg, maxd);
+}
+
+__global__ void k_giant_init(AggArgs a, GiantArgs gi, unsigned long long total) {
+  for (unsigned long long t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(a.gtable);
+    uint32_t lo = 0, hi = gi.ngiant;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (gi.gtab[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    unsigned long long s = t - gi.gtab[lo];
+    // keys (first gsize words of the table) empty, values zero
+    w[2 * gi.gtab[lo] + s] = kEmpty;
+    w[2 * gi.gtab[lo] + gi.gsize[lo] + s] = 0;
+  }
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < gi.ngiant; g += gridDim.x * blockDim.x) {
+    a.deg_out[gi.giant[g]] = 0;
+    a.Knew[gi.giant[g]] = 0;
+  }
 }
 
 int read_ctrl(Handle* h) {
@@ -302,25 +422,10 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     DFL_CUDA(h, cudaMalloc(&sg.arcs, sizeof(uint2) * want));
     sg.arc_cap = want;
   }
-  // global tables for the largest communities
-  uint32_t gslots = 0;
-  const uint32_t gblocks = 152;
-  if (c.count[1][0][2]) {
-    uint64_t dmax = c.red_u < ncomm ? c.red_u : ncomm;
-    gslots = next_pow2(2 * dmax);
-    if (gslots < 2 * kBinBlock) gslots = 2 * kBinBlock;
-    if (uint64_t(gblocks) * gslots > h->gtable_cap) {
-      cudaFree(h->gtable);
-      h->gtable = nullptr;
-      h->gtable_cap = 0;
-      DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(gblocks) * gslots));
-      h->gtable_cap = uint64_t(gblocks) * gslots;
-    }
-  }
   static bool smem_set = false;
   if (!smem_set) {
-    DFL_CUDA(h, cudaFuncSetAttribute(k_agg_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 4 * kBinBlock)));
+    DFL_CUDA(h, cudaFuncSetAttribute(k_agg_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 2 * kAggBlockSlots)));
     smem_set = true;
   }
   AggArgs a;
@@ -335,8 +440,8 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
   a.ncomm = ncomm;
   a.ctrl = h->ctrl;
   a.gtable = h->gtable;
-  a.gslots = gslots;
-  for (int b = 0; b < 3; ++b) {
+  a.gslots = 0;
+  for (int b = 0; b < 2; ++b) {
     uint32_t nc = c.count[1][0][b];
     if (!nc) continue;
     a.list = h->lists[1] + seg.off[b];
@@ -344,12 +449,74 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     LaunchScope ls(h, DFL_PROF_AGG);
     if (b == 0)
       k_agg_warp<<<grid_for(uint64_t(nc) * 32, 256, 152 * 16), 256, 0, h->stream>>>(a);
-    else if (b == 1)
-      k_agg_block<false><<<grid_for(nc, 1, 152 * 4), 256, sizeof(uint32_t) * 4 * kBinBlock,
-                           h->stream>>>(a);
     else
-      k_agg_block<true><<<grid_for(nc, 1, gblocks), 512, 0, h->stream>>>(a);
+      k_agg_block<<<grid_for(nc, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kAggBlockSlots,
+                    h->stream>>>(a);
     DFL_TRY(check_launch(h, "aggregate"));
+  }
+  const uint32_t ngiant = c.count[1][0][2];
+  if (ngiant) {
+    // giant communities: their ids and sizes on the host to lay out the tables
+    std::vector<uint32_t> giant(ngiant);
+    DFL_CUDA(h, cudaMemcpy(giant.data(), h->lists[1] + seg.off[2], sizeof(uint32_t) * ngiant,
+                           cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> soff(ncomm + 1);
+    DFL_CUDA(h, cudaMemcpy(soff.data(), sg.off, sizeof(unsigned long long) * (ncomm + 1),
+                           cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> cntv(ncomm + 1);
+    DFL_CUDA(h, cudaMemcpy(cntv.data(), h->cnt, sizeof(uint32_t) * (ncomm + 1), cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> gtab(ngiant);
+    std::vector<uint32_t> gsize(ngiant);
+    unsigned long long total = 0;
+    uint32_t max_chunks = 1;
+    for (uint32_t k = 0; k < ngiant; ++k) {
+      uint32_t cc = giant[k];
+      unsigned long long td = soff[cc + 1] - soff[cc];
+      unsigned long long distinct = td < ncomm ? td : ncomm;
+      gsize[k] = next_pow2(2 * distinct);
+      gtab[k] = total;
+      total += gsize[k];
+      uint32_t members = cntv[cc + 1] - cntv[cc];
+      uint32_t ch = (members + kChunkMembers - 1) / kChunkMembers;
+      if (ch > max_chunks) max_chunks = ch;
+    }
+    if (total > h->gtable_cap) {
+      cudaFree(h->gtable);
+      h->gtable = nullptr;
+      h->gtable_cap = 0;
+      DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * total));
+      h->gtable_cap = total;
+    }
+    // small device arrays for the giant layout (in the generic scratch)
+    DFL_TRY(ensure_tmp(h, ngiant * (sizeof(uint32_t) * 2 + sizeof(unsigned long long)) + 64));
+    unsigned long long* d_gtab = static_cast<unsigned long long*>(h->tmp);
+    uint32_t* d_giant = reinterpret_cast<uint32_t*>(d_gtab + ngiant);
+    uint32_t* d_gsize = d_giant + ngiant;
+    DFL_CUDA(h, cudaMemcpyAsync(d_gtab, gtab.data(), sizeof(unsigned long long) * ngiant,
+                                cudaMemcpyHostToDevice, h->stream));
+    DFL_CUDA(h, cudaMemcpyAsync(d_giant, giant.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
+                                h->stream));
+    DFL_CUDA(h, cudaMemcpyAsync(d_gsize, gsize.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
+                                h->stream));
+    a.gtable = h->gtable;
+    GiantArgs gi{d_giant, d_gtab, d_gsize, ngiant};
+    {
+      LaunchScope ls(h, DFL_PROF_AGG);
+      k_giant_init<<<grid_for(total, 256), 256, 0, h->stream>>>(a, gi, total);
+      DFL_TRY(check_launch(h, "giant init"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_AGG);
+      k_agg_giant_accum<<<dim3(ngiant, max_chunks < 65535 ? max_chunks : 65535), 256, 0, h->stream>>>(a, gi);
+      DFL_TRY(check_launch(h, "giant accum"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_AGG);
+      k_agg_giant_emit<<<grid_for(total, 256), 256, 0, h->stream>>>(a, gi, total);
+      DFL_TRY(check_launch(h, "giant emit"));
+    }
+    // the layout arrays live in h->tmp: finish before anyone reuses it
+    DFL_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   DFL_TRY(read_ctrl(h));
   if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in aggregation (table overflow)");

@@ -90,7 +90,7 @@ int alloc(Handle* h, T** p, uint64_t count) {
 }
 
 void free_all(Handle* h) {
-  void* ptrs[] = {h->off, h->deg, h->cap, h->arcs, h->K, h->Sigma, h->csize, h->C, h->pend_key,
+  void* ptrs[] = {h->off, h->deg, h->cap, h->srt, h->ntomb, h->b_newtomb, h->b_cum, h->b_rebuild, h->arcs, h->K, h->Sigma, h->csize, h->C, h->pend_key,
                   h->pend_w, h->Ctop, h->Cs, h->Ks, h->Ss, h->sizes, h->used, h->cnt, h->tdeg,
                   h->fillc, h->members, h->fbits[0], h->fbits[1], h->rbits, h->ever, h->lists[0],
                   h->lists[1], h->mv_i, h->mv_c, h->mv_d, h->dsV, h->dsE, h->dsC, h->b_key, h->b_w,
@@ -217,6 +217,8 @@ int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint
   A(&h->off, uint64_t(n) + 1);
   A(&h->deg, n);
   A(&h->cap, n);
+  A(&h->srt, n);
+  A(&h->ntomb, n);
   A(&h->K, n);
   A(&h->Sigma, n);
   A(&h->csize, n);

@@ -13,11 +13,22 @@ namespace dfl {
 
 namespace {
 
+// Slack-CSR row layout: arcs [0, srt) are sorted by neighbour, arcs
+// [srt, deg) are an unsorted tail of at most kTailMax appended arcs, and a
+// deleted arc stays as a tombstone (weight 0) until the row is rebuilt.  A
+// neighbour id appears at most once in a row (a re-inserted edge revives its
+// tombstone).  A row is rebuilt (sorted, tombstones dropped, relocated) when
+// it would outgrow its capacity, its tail or its tombstone budget.
+constexpr uint32_t kTailMax = 64;
+constexpr uint32_t kTombMin = 8;
+
 // b_flag bits
 constexpr uint32_t kRunHead = 1u;     // first arc of a (u, v) run
-constexpr uint32_t kRunStruct = 2u;   // the run adds or removes the arc
-constexpr uint32_t kRowStruct = 4u;   // (row head) the row gains or loses arcs
-constexpr uint32_t kRowMove = 8u;     // (row head) the row is relocated
+constexpr uint32_t kFound = 2u;       // the row already has a slot for v
+constexpr uint32_t kLiveBefore = 4u;  // ... holding weight > 0
+constexpr uint32_t kLiveAfter = 8u;   // the arc has weight > 0 after the batch
+constexpr uint32_t kAppend = 16u;     // a new slot is needed
+constexpr uint32_t kRebuild = 32u;    // (every run of the row) the row is rebuilt
 
 __host__ __device__ inline uint32_t grow_cap(uint32_t d) {
   uint64_t c = uint64_t(d) + d / 2 + 4;
@@ -54,14 +65,30 @@ __global__ void k_expand(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t n
   }
 }
 
-// Thread per sorted arc: run heads evaluate their (u, v) change against the
-// current row; row heads are listed.
+// Slot of neighbour v in row u: binary search of the sorted prefix, then a
+// scan of the tail.  Returns kEmpty if absent.
+__device__ __forceinline__ uint32_t find_slot(const uint2* __restrict__ row, uint32_t srt, uint32_t deg,
+                                              uint32_t v) {
+  uint32_t lo = 0, hi = srt;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (row[mid].x < v) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < srt && row[lo].x == v) return lo;
+  for (uint32_t q = srt; q < deg; ++q)
+    if (row[q].x == v) return q;
+  return kEmpty;
+}
+
+// Thread per sorted arc: each run head evaluates its (u, v) change against
+// the current row (validation happens here, before any state changes).
 __global__ void k_runs(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
                        uint64_t na, KeyFmt f, uint32_t n, const unsigned long long* __restrict__ off,
-                       const uint32_t* __restrict__ deg, const uint2* __restrict__ arcs,
-                       unsigned long long* __restrict__ pos_out, uint32_t* __restrict__ wnew_out,
-                       uint32_t* __restrict__ flag, long long* __restrict__ delta_out,
-                       uint32_t* __restrict__ rowlist, Ctrl* ctrl) {
+                       const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
+                       const uint2* __restrict__ arcs, unsigned long long* __restrict__ pos_out,
+                       uint32_t* __restrict__ wnew_out, uint32_t* __restrict__ flag,
+                       long long* __restrict__ delta_out, uint32_t* __restrict__ rowlist, Ctrl* ctrl) {
   for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
        p += uint64_t(gridDim.x) * blockDim.x) {
     unsigned long long k = key[p];
@@ -90,152 +117,244 @@ __global__ void k_runs(const unsigned long long* __restrict__ key, const uint32_
       continue;
     }
     if (ndel > 1) atomicOr(&ctrl->err, kErrInvalid);  // the same edge deleted twice
-    // binary search of v in the sorted row u
-    unsigned long long base = off[u];
-    uint32_t lo = 0, hi = deg[u];
-    while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (arcs[base + mid].x < v) lo = mid + 1;
-      else hi = mid;
-    }
-    bool found = lo < deg[u] && arcs[base + lo].x == v;
-    unsigned long long wold = found ? arcs[base + lo].y : 0ull;
+    const uint2* row = arcs + off[u];
+    uint32_t slot = find_slot(row, srt[u], deg[u], v);
+    unsigned long long wold = slot != kEmpty ? row[slot].y : 0ull;
     unsigned long long weff = 0;
     if (ndel) {
-      if (!found || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);
+      if (wold == 0 || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);  // absent edge
       else weff = wdel ? wdel : wold;
     }
-    unsigned long long wn = (found ? wold - weff : 0ull) + wins;
+    unsigned long long wn = wold - weff + wins;
     if (wn > 0xFFFFFFFFull) atomicOr(&ctrl->err, kErrOverflow);
-    bool structural = (found && wn == 0) || (!found && wn > 0);
+    uint32_t fl = kRunHead;
+    if (slot != kEmpty) fl |= kFound;
+    if (wold > 0) fl |= kLiveBefore;
+    if (wn > 0) fl |= kLiveAfter;
+    if (slot == kEmpty && wn > 0) fl |= kAppend;
     long long delta = (long long)wins - (long long)weff;
-    pos_out[p] = (unsigned long long)lo | ((unsigned long long)found << 63);
+    pos_out[p] = slot;
     wnew_out[p] = uint32_t(wn);
-    flag[p] = kRunHead | (structural ? kRunStruct : 0u);
+    flag[p] = fl;
     delta_out[p] = delta;
     if (delta) atomicAdd((unsigned long long*)&ctrl->m2_delta, (unsigned long long)delta);
   }
 }
 
-// Thread per touched row: new degree, relocation and scratch needs.
+// Thread per touched row: appends (ranked in run order), tombstone and live
+// counts, and whether the row must be rebuilt.
 __global__ void k_rows(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
                        const uint32_t* __restrict__ rowlist, const uint32_t* __restrict__ deg,
-                       const uint32_t* __restrict__ cap, const unsigned long long* __restrict__ pos,
-                       const uint32_t* __restrict__ wnew, uint32_t* __restrict__ flag,
-                       uint32_t* __restrict__ newdeg, Ctrl* ctrl) {
+                       const uint32_t* __restrict__ cap, const uint32_t* __restrict__ srt,
+                       const uint32_t* __restrict__ ntomb, unsigned long long* __restrict__ pos,
+                       uint32_t* __restrict__ flag, uint32_t* __restrict__ cum,
+                       uint32_t* __restrict__ newdeg, uint32_t* __restrict__ newtomb,
+                       uint32_t* __restrict__ rebuild_list, Ctrl* ctrl) {
+  const uint32_t rows = ctrl->rows;
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < rows;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t p = rowlist[t];
+    const uint32_t u = f.u(key[p]);
+    const uint32_t d = deg[u], s = srt[u], nt = ntomb[u];
+    uint32_t appends = 0;
+    long long tomb = nt, live = (long long)d - nt;
+    uint64_t end = p;
+    for (; end < na && f.u(key[end]) == u; ++end) {
+      uint32_t fl = flag[end];
+      if (!(fl & kRunHead)) continue;
+      cum[end] = appends;
+      if (fl & kAppend) pos[end] = appends++;
+      bool before = fl & kLiveBefore, after = fl & kLiveAfter;
+      live += (after ? 1 : 0) - (before ? 1 : 0);
+      if ((fl & kFound) && before && !after) ++tomb;
+      if ((fl & kFound) && !before && after) --tomb;
+    }
+    const uint32_t raw = d + appends;
+    const uint32_t tail = d - s + appends;
+    const uint32_t tomb_lim = raw / 4 > kTombMin ? raw / 4 : kTombMin;
+    const bool rebuild = raw > cap[u] || tail > kTailMax || uint32_t(tomb) > tomb_lim;
+    if (rebuild) {
+      for (uint64_t q = p; q < end; ++q)
+        if (flag[q] & kRunHead) flag[q] |= kRebuild;
+      uint32_t slot = atomicAdd(&ctrl->rebuild_rows, 1u);
+      rebuild_list[slot] = p;
+      atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(uint32_t(live)));
+      atomicAdd(&ctrl->scratch_need, (unsigned long long)s);
+    }
+    newdeg[p] = rebuild ? uint32_t(live) : raw;
+    newtomb[p] = rebuild ? 0u : uint32_t(tomb);
+    atomicMax(&ctrl->max_deg, rebuild ? uint32_t(live) : raw);
+    long long dl = live - ((long long)d - nt);
+    if (dl) atomicAdd((unsigned long long*)&ctrl->arc_delta, (unsigned long long)dl);
+  }
+}
+
+// Thread per run: weight changes in place (also before a rebuild, which
+// then reads the updated row), and appends to the tail of kept rows.
+__global__ void k_write(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+                        const unsigned long long* __restrict__ off, const uint32_t* __restrict__ deg,
+                        uint2* __restrict__ arcs, const unsigned long long* __restrict__ pos,
+                        const uint32_t* __restrict__ wnew, const uint32_t* __restrict__ flag) {
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t fl = flag[p];
+    if (!(fl & kRunHead)) continue;
+    uint32_t u = f.u(key[p]);
+    uint2* row = arcs + off[u];
+    if (fl & kFound) row[pos[p]].y = wnew[p];
+    else if ((fl & kAppend) && !(fl & kRebuild)) row[deg[u] + pos[p]] = make_uint2(f.v(key[p]), wnew[p]);
+  }
+}
+
+// Thread per touched row that is kept: new degree and tombstone count.
+__global__ void k_finish(const unsigned long long* __restrict__ key, KeyFmt f,
+                         const uint32_t* __restrict__ rowlist, const uint32_t* __restrict__ flag,
+                         const uint32_t* __restrict__ newdeg, const uint32_t* __restrict__ newtomb,
+                         uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
   const uint32_t rows = ctrl->rows;
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < rows;
        t += uint64_t(gridDim.x) * blockDim.x) {
     uint32_t p = rowlist[t];
+    if (flag[p] & kRebuild) continue;
     uint32_t u = f.u(key[p]);
-    long long d = deg[u];
-    bool structural = false;
-    for (uint64_t q = p; q < na && f.u(key[q]) == u; ++q) {
-      uint32_t fl = flag[q];
-      if ((fl & kRunHead) && (fl & kRunStruct)) {
-        structural = true;
-        d += (pos[q] >> 63) ? -1 : 1;  // found and emptied, or created
-      }
-    }
-    (void)wnew;
-    uint32_t nd = uint32_t(d);
-    bool move = structural && nd > cap[u];
-    flag[p] |= (structural ? kRowStruct : 0u) | (move ? kRowMove : 0u);
-    newdeg[p] = nd;
-    if (move) atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(nd));
-    else if (structural) atomicAdd(&ctrl->scratch_need, (unsigned long long)nd);
-    atomicMax(&ctrl->max_deg, nd);
-    if (d != (long long)deg[u]) atomicAdd((unsigned long long*)&ctrl->arc_delta,
-                                           (unsigned long long)(d - (long long)deg[u]));
+    deg[u] = newdeg[p];
+    ntomb[u] = newtomb[p];
   }
 }
 
-// Warp per touched row: write the merged row.  Weight-only changes are done
-// in place; structural changes are merged into scratch (or straight into a
-// relocated slot) in one ordered walk over the row's runs.
-__global__ void k_merge(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
-                        const uint32_t* __restrict__ rowlist, unsigned long long* __restrict__ off,
-                        uint32_t* __restrict__ deg, uint32_t* __restrict__ cap, uint2* __restrict__ arcs,
-                        const unsigned long long* __restrict__ pos, const uint32_t* __restrict__ wnew,
-                        const uint32_t* __restrict__ flag, const uint32_t* __restrict__ newdeg,
-                        uint2* __restrict__ scratch, unsigned long long pool_base,
-                        unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t rows = ctrl->rows;
-  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
-  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t t = warp; t < rows; t += nwarps) {
-    uint32_t p = rowlist[t];
-    uint32_t u = f.u(key[p]);
-    uint32_t rf = flag[p];
-    unsigned long long base = off[u];
-    uint32_t d = deg[u];
+// Number of appended runs of the row [p, end) with neighbour < v.
+__device__ __forceinline__ uint32_t new_below(const unsigned long long* __restrict__ key, KeyFmt f,
+                                              uint64_t p, uint64_t end, const uint32_t* __restrict__ cum,
+                                              uint32_t total, uint32_t v) {
+  uint64_t lo = p, hi = end;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (f.v(key[mid]) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo == end ? total : cum[lo];  // lo is a run head
+}
+
+__device__ __forceinline__ uint32_t count_below(const uint2* __restrict__ a, uint32_t len, uint32_t v) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid].x < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kRebuildThreads = 256;
+
+// Block per rebuilt row: three-way merge of the live sorted prefix (first
+// compacted into scratch), the live tail (sorted in shared memory) and the
+// batch's new arcs (sorted by the batch sort) into a new, larger slot.
+__global__ void __launch_bounds__(kRebuildThreads)
+k_rebuild(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
+          const uint32_t* __restrict__ rebuild_list, unsigned long long* __restrict__ off,
+          uint32_t* __restrict__ deg, uint32_t* __restrict__ cap, uint32_t* __restrict__ srt,
+          uint32_t* __restrict__ ntomb, uint2* __restrict__ arcs, const unsigned long long* __restrict__ pos,
+          const uint32_t* __restrict__ wnew, const uint32_t* __restrict__ flag,
+          const uint32_t* __restrict__ cum, const uint32_t* __restrict__ newdeg, uint2* __restrict__ scratch,
+          unsigned long long pool_base, unsigned long long pool_cap, unsigned long long scratch_cap,
+          Ctrl* ctrl) {
+  __shared__ uint2 tail[kTailMax];
+  __shared__ uint2 stail[kTailMax];
+  __shared__ unsigned long long s_sbase, s_dst;
+  __shared__ uint32_t s_nt, s_warp[kRebuildThreads / 32], s_total;
+  const uint32_t nrows = ctrl->rebuild_rows;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const uint32_t p = rebuild_list[r];
+    const uint32_t u = f.u(key[p]);
+    const uint2* old = arcs + off[u];
+    const uint32_t d = deg[u], s = srt[u], live = newdeg[p];
     uint64_t end = p;
     while (end < na && f.u(key[end]) == u) ++end;
-    if (!(rf & kRowStruct)) {
-      for (uint64_t q = p + lane; q < end; q += 32)
-        if ((flag[q] & kRunHead) && (pos[q] >> 63)) arcs[base + (pos[q] & ~(1ull << 63))].y = wnew[q];
+    // appended runs of this row
+    uint32_t nnew = 0;
+    for (uint64_t q = end; q > p; --q)
+      if (flag[q - 1] & kRunHead) {
+        nnew = cum[q - 1] + ((flag[q - 1] & kAppend) ? 1u : 0u);
+        break;
+      }
+    if (threadIdx.x == 0) {
+      s_sbase = atomicAdd(&ctrl->scratch_top, (unsigned long long)s);
+      uint32_t nc = grow_cap(live);
+      s_dst = pool_base + atomicAdd(&ctrl->pool_top, (unsigned long long)nc);
+      s_nt = 0;
+      if (s_sbase + s > scratch_cap || s_dst + nc > pool_cap) atomicOr(&ctrl->err, kErrInternal);
+    }
+    __syncthreads();
+    const unsigned long long sbase = s_sbase, dst = s_dst;
+    const uint32_t nc = grow_cap(live);
+    if (sbase + s > scratch_cap || dst + nc > pool_cap) {
+      __syncthreads();
       continue;
     }
-    uint32_t nd = newdeg[p];
-    uint2* out;
-    unsigned long long dst = 0;
-    if (rf & kRowMove) {
-      uint32_t nc = grow_cap(nd);
-      if (lane == 0) dst = pool_base + atomicAdd(&ctrl->pool_top, (unsigned long long)nc);
-      dst = __shfl_sync(0xFFFFFFFFu, dst, 0);
-      if (dst + nc > pool_cap) {
-        if (lane == 0) atomicOr(&ctrl->err, kErrInternal);
-        continue;
-      }
-      out = arcs + dst;
-    } else {
-      if (lane == 0) dst = atomicAdd(&ctrl->scratch_top, (unsigned long long)nd);
-      dst = __shfl_sync(0xFFFFFFFFu, dst, 0);
-      if (dst + nd > scratch_cap) {
-        if (lane == 0) atomicOr(&ctrl->err, kErrInternal);
-        continue;
-      }
-      out = scratch + dst;
-    }
-    const uint2* old = arcs + base;
-    uint32_t prev = 0, o = 0;
-    for (uint64_t q = p; q < end; ++q) {
-      uint32_t fl = flag[q];
-      if (!(fl & kRunHead)) continue;
-      bool found = pos[q] >> 63;
-      uint32_t ps = uint32_t(pos[q] & 0xFFFFFFFFull);
-      uint32_t v = f.v(key[q]);
-      uint32_t len = ps - prev;
-      for (uint32_t k = lane; k < len; k += 32) out[o + k] = old[prev + k];
-      o += len;
-      uint32_t wn = wnew[q];
-      if (found) {
-        if (wn) {
-          if (lane == 0) out[o] = make_uint2(v, wn);
-          ++o;
+    uint2* A = scratch + sbase;
+    // A: live prefix compacted in order
+    uint32_t L = 0;
+    for (uint32_t c0 = 0; c0 < s; c0 += blockDim.x) {
+      uint32_t k = c0 + threadIdx.x;
+      uint2 a = k < s ? old[k] : make_uint2(0, 0);
+      bool lv = k < s && a.y > 0;
+      unsigned m = __ballot_sync(0xFFFFFFFFu, lv);
+      if (lane == 0) s_warp[wib] = __popc(m);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (uint32_t x = 0; x < blockDim.x / 32; ++x) {
+          uint32_t t = s_warp[x];
+          s_warp[x] = run;
+          run += t;
         }
-        prev = ps + 1;
-      } else {
-        if (lane == 0) out[o] = make_uint2(v, wn);
-        ++o;
-        prev = ps;
+        s_total = run;
+      }
+      __syncthreads();
+      if (lv) A[L + s_warp[wib] + __popc(m & ((1u << lane) - 1u))] = a;
+      L += s_total;
+      __syncthreads();
+    }
+    // T: live tail, sorted by rank
+    for (uint32_t k = s + threadIdx.x; k < d; k += blockDim.x) {
+      uint2 a = old[k];
+      if (a.y > 0) tail[atomicAdd(&s_nt, 1u)] = a;
+    }
+    __syncthreads();
+    const uint32_t nt = s_nt;
+    for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
+      uint32_t rk = 0;
+      for (uint32_t x = 0; x < nt; ++x) rk += tail[x].x < tail[k].x;
+      stail[rk] = tail[k];
+    }
+    __syncthreads();
+    uint2* out = arcs + dst;
+    for (uint32_t k = threadIdx.x; k < L; k += blockDim.x) {
+      uint2 a = A[k];
+      out[k + count_below(stail, nt, a.x) + new_below(key, f, p, end, cum, nnew, a.x)] = a;
+    }
+    for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
+      uint2 a = stail[k];
+      out[k + count_below(A, L, a.x) + new_below(key, f, p, end, cum, nnew, a.x)] = a;
+    }
+    for (uint64_t q = p + threadIdx.x; q < end; q += blockDim.x) {
+      uint32_t fl = flag[q];
+      if ((fl & kRunHead) && (fl & kAppend)) {
+        uint32_t v = f.v(key[q]);
+        out[pos[q] + count_below(A, L, v) + count_below(stail, nt, v)] = make_uint2(v, wnew[q]);
       }
     }
-    for (uint32_t k = lane; k < d - prev; k += 32) out[o + k] = old[prev + k];
-    o += d - prev;
-    if (o != nd && lane == 0) atomicOr(&ctrl->err, kErrInternal);
-    __syncwarp();
-    if (rf & kRowMove) {
-      if (lane == 0) {
-        off[u] = dst;
-        cap[u] = grow_cap(nd);
-        deg[u] = nd;
-      }
-    } else {
-      for (uint32_t k = lane; k < nd; k += 32) arcs[base + k] = out[k];
-      if (lane == 0) deg[u] = nd;
+    if (threadIdx.x == 0) {
+      if (L + nt + nnew != live) atomicOr(&ctrl->err, kErrInternal);
+      off[u] = dst;
+      deg[u] = live;
+      srt[u] = live;
+      cap[u] = nc;
+      ntomb[u] = 0;
     }
+    __syncthreads();
   }
 }
 
@@ -365,7 +484,10 @@ __global__ void k_ds_expand(const uint32_t* __restrict__ dE, uint32_t words, uin
       if (i >= n) break;
       unsigned long long o = g.off[i];
       uint32_t d = g.deg[i];
-      for (uint32_t k = lane; k < d; k += 32) bit_set(dV, g.arcs[o + k].x);
+      for (uint32_t k = lane; k < d; k += 32) {
+        uint2 a = g.arcs[o + k];
+        if (a.y) bit_set(dV, a.x);  // weight 0 = deleted arc
+      }
     }
   }
 }
@@ -406,6 +528,26 @@ int grow(Handle* h, T** p, uint64_t need, uint64_t* cap_out, uint64_t cap_now, b
   return DFL_OK;
 }
 
+int ensure_batch_scratch(Handle* h, uint64_t na) {
+  if (na <= h->b_cap) return DFL_OK;
+  uint64_t want = na + na / 2 + 256, c = 0;
+  DFL_TRY(grow(h, &h->b_key, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_key2, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_w, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_w2, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_pos, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_wnew, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_flag, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_delta, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_rowlist, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_newdeg, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_newtomb, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_cum, want, &c, 0));
+  DFL_TRY(grow(h, &h->b_rebuild, want, &c, 0));
+  h->b_cap = c;
+  return DFL_OK;
+}
+
 KeyFmt key_fmt(const Handle* h) {
   KeyFmt f;
   f.b = h->key_shift;
@@ -421,26 +563,12 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
   const uint64_t ne = nd + ni;
   if (ne == 0) return DFL_OK;
   const uint64_t na = 2 * ne;
-  // scratch sized for this batch
   if (ne > h->b_edges_cap) {
     uint64_t cap = 0;
     DFL_TRY(grow(h, &h->b_edges, ne, &cap, h->b_edges_cap));
     h->b_edges_cap = cap;
   }
-  if (na > h->b_cap) {
-    uint64_t want = na + na / 2 + 256, c = 0;
-    DFL_TRY(grow(h, &h->b_key, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_key2, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_w, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_w2, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_pos, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_wnew, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_flag, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_delta, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_rowlist, want, &c, 0));
-    DFL_TRY(grow(h, &h->b_newdeg, want, &c, 0));
-    h->b_cap = c;
-  }
+  DFL_TRY(ensure_batch_scratch(h, na));
   cudaMemcpyKind kind = mem_kind == DFL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, kind, h->stream));
   if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, kind, h->stream));
@@ -456,15 +584,15 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
     k_runs<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, h->b_w, na, f, h->n, h->off, h->deg,
-                                                     h->arcs, h->b_pos, h->b_wnew, h->b_flag,
+                                                     h->srt, h->arcs, h->b_pos, h->b_wnew, h->b_flag,
                                                      h->b_delta, h->b_rowlist, h->ctrl);
     DFL_TRY(check_launch(h, "runs"));
   }
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
     k_rows<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, na, f, h->b_rowlist, h->deg, h->cap,
-                                                     h->b_pos, h->b_wnew, h->b_flag, h->b_newdeg,
-                                                     h->ctrl);
+                                                     h->srt, h->ntomb, h->b_pos, h->b_flag, h->b_cum,
+                                                     h->b_newdeg, h->b_newtomb, h->b_rebuild, h->ctrl);
     DFL_TRY(check_launch(h, "rows"));
   }
   DFL_TRY(read_ctrl(h));
@@ -489,10 +617,24 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
   }
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
-    k_merge<<<grid_for(uint64_t(c.rows) * 32, 256), 256, 0, h->stream>>>(
-        h->b_key, na, f, h->b_rowlist, h->off, h->deg, h->cap, h->arcs, h->b_pos, h->b_wnew, h->b_flag,
-        h->b_newdeg, h->scratch, h->pool_top, h->pool_cap, h->scratch_cap, h->ctrl);
-    DFL_TRY(check_launch(h, "merge"));
+    k_write<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, na, f, h->off, h->deg, h->arcs, h->b_pos,
+                                                      h->b_wnew, h->b_flag);
+    DFL_TRY(check_launch(h, "write"));
+  }
+  if (c.rebuild_rows) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_rebuild<<<grid_for(c.rebuild_rows, 1, 152 * 8), kRebuildThreads, 0, h->stream>>>(
+        h->b_key, na, f, h->b_rebuild, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->b_pos,
+        h->b_wnew, h->b_flag, h->b_cum, h->b_newdeg, h->scratch, h->pool_top, h->pool_cap,
+        h->scratch_cap, h->ctrl);
+    DFL_TRY(check_launch(h, "rebuild"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(h->b_key, f, h->b_rowlist, h->b_flag,
+                                                           h->b_newdeg, h->b_newtomb, h->deg,
+                                                           h->ntomb, h->ctrl);
+    DFL_TRY(check_launch(h, "finish"));
   }
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
@@ -560,20 +702,7 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
   DFL_CUDA(h, cudaMemsetAsync(h->dsE, 0, sizeof(uint32_t) * h->words, h->stream));
   DFL_CUDA(h, cudaMemsetAsync(h->dsC, 0, sizeof(uint32_t) * h->words, h->stream));
   if (na) {
-    if (na > h->b_cap) {
-      uint64_t want = na + na / 2 + 256, c = 0;
-      DFL_TRY(grow(h, &h->b_key, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_key2, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_w, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_w2, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_pos, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_wnew, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_flag, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_delta, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_rowlist, want, &c, 0));
-      DFL_TRY(grow(h, &h->b_newdeg, want, &c, 0));
-      h->b_cap = c;
-    }
+    DFL_TRY(ensure_batch_scratch(h, na));
     {
       LaunchScope ls(h, DFL_PROF_MARK);
       k_ds_del<<<grid_for(na, 256), 256, 0, h->stream>>>(h->pend_key, na, f, h->C, h->dsV, h->dsE,

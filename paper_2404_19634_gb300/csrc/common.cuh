@@ -1,10 +1,11 @@
 // Internal declarations of the GB300 DF Louvain library (sm_103a).
 //
 // Device data layout (all arrays in HBM, owned by the handle):
-//   slack CSR of G^t   off[n] (u64 arc offset), deg[n] (u32), cap[n] (u32),
-//                      arcs[pool] as uint2 {neighbour, weight}; every row starts
-//                      on an even arc index (16-byte aligned) so two arcs load
-//                      as one 128-bit word
+//   slack CSR of G^t   off[n] (u64 arc offset), deg[n] (u32, slots in use),
+//                      cap[n], srt[n] (sorted prefix), ntomb[n] (deleted arcs
+//                      kept as weight-0 tombstones), arcs[pool] as uint2
+//                      {neighbour, weight}; every row starts on an even arc
+//                      index (16-byte aligned)
 //   state              K[n], Sigma[n] (int64), csize[n] (int32), C[n] (u32)
 //   super-vertex CSR   two ping-pong graphs (off, deg, arcs) for passes >= 1
 //   frontier           bitmaps (n/32 words) + per (sub-step class, degree bin)
@@ -64,7 +65,10 @@ struct Ctrl {
   long long m2_delta;                // change of 2m by the batch
   unsigned int max_deg;              // largest new degree of a touched row
   unsigned int rows;                 // touched rows
-  long long arc_delta;               // change of the arc count by the batch
+  long long arc_delta;               // change of the live arc count by the batch
+  unsigned int rebuild_rows;         // rows rebuilt by the batch
+  unsigned int pad2;
+  unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
   unsigned long long pool_top;       // first free arc slot of the pool
   unsigned long long scratch_top;
   // misc reductions
@@ -110,6 +114,8 @@ struct Handle {
   unsigned long long* off = nullptr;
   uint32_t* deg = nullptr;
   uint32_t* cap = nullptr;
+  uint32_t* srt = nullptr;    // length of the sorted prefix of each row
+  uint32_t* ntomb = nullptr;  // tombstones (weight-0 arcs) in each row
   uint2* arcs = nullptr;
   uint64_t pool_cap = 0;   // arc slots allocated
   uint64_t pool_top = 0;   // first free slot (host mirror)
@@ -173,7 +179,10 @@ struct Handle {
   uint32_t* b_wnew = nullptr;      // per run head: new weight
   uint32_t* b_flag = nullptr;      // per arc: run/row head flags (see batch.cu)
   long long* b_delta = nullptr;    // per run head: weight change of the arc
-  uint32_t* b_newdeg = nullptr;    // per row head
+  uint32_t* b_newdeg = nullptr;    // per row head: degree after the batch
+  uint32_t* b_newtomb = nullptr;   // per row head: tombstones after the batch
+  uint32_t* b_cum = nullptr;       // per run head: appended runs before it in its row
+  uint32_t* b_rebuild = nullptr;   // row heads of rebuilt rows
   dfl_edge* b_edges = nullptr;     // staging copy of the caller's edges
   uint64_t b_edges_cap = 0;
   uint2* scratch = nullptr;        // merge scratch

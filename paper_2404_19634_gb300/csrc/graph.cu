@@ -1,5 +1,7 @@
 // Graph storage: input validation, slack CSR build, weighted degrees,
 // modularity (Eq. 1) and CSR export.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dfl {
@@ -60,11 +62,14 @@ __global__ void k_validate(uint32_t n, const unsigned long long* __restrict__ of
 
 __global__ void k_caps(uint32_t n, const unsigned long long* __restrict__ off_in,
                        uint32_t* __restrict__ deg, uint32_t* __restrict__ cap,
+                       uint32_t* __restrict__ srt, uint32_t* __restrict__ ntomb,
                        unsigned long long* __restrict__ capl) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
        i += uint64_t(gridDim.x) * blockDim.x) {
     uint32_t d = uint32_t(off_in[i + 1] - off_in[i]);
     deg[i] = d;
+    srt[i] = d;
+    ntomb[i] = 0;
     cap[i] = slack_cap(d);
     capl[i] = cap[i];
   }
@@ -138,31 +143,6 @@ __global__ void k_modularity(GraphView g, const uint32_t* __restrict__ C,
   }
 }
 
-__global__ void k_deg_u32(const uint32_t* __restrict__ deg, uint32_t* __restrict__ out, uint32_t n) {
-  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
-       i += uint64_t(gridDim.x) * blockDim.x)
-    out[i] = deg[i];
-}
-
-__global__ void k_export_rows(GraphView g, const uint32_t* __restrict__ eoff,
-                              unsigned long long* __restrict__ off_out, uint32_t* __restrict__ idx,
-                              uint32_t* __restrict__ w) {
-  const uint32_t lane = threadIdx.x & 31u;
-  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
-  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t i = warp; i < g.nv; i += nwarps) {
-    unsigned long long o = g.off[i];
-    uint32_t d = g.deg[i], e = eoff[i];
-    for (uint32_t k = lane; k < d; k += 32) {
-      uint2 a = g.arcs[o + k];
-      idx[e + k] = a.x;
-      w[e + k] = a.y;
-    }
-    if (lane == 0) off_out[i] = e;
-    if (lane == 0 && i + 1 == g.nv) off_out[g.nv] = e + d;
-  }
-}
-
 __global__ void k_sigma_sizes(uint32_t n, const uint32_t* __restrict__ C,
                               const long long* __restrict__ K, long long* __restrict__ Sigma,
                               int* __restrict__ size) {
@@ -203,7 +183,8 @@ int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx
   int rc = DFL_OK;
   {
     LaunchScope ls(h, DFL_PROF_OTHER);
-    k_caps<<<grid_for(n, 256), 256, 0, h->stream>>>(n, off_in, h->deg, h->cap, capl);
+    k_caps<<<grid_for(n, 256), 256, 0, h->stream>>>(n, off_in, h->deg, h->cap, h->srt, h->ntomb,
+                                                     capl);
     rc = check_launch(h, "caps");
   }
   if (!rc) rc = scan_u64(h, capl, h->off, n);  // off has n+1 entries during the build
@@ -257,63 +238,46 @@ int modularity_parts(Handle* h, i128* num, i128* den) {
   return DFL_OK;
 }
 
+// G^t as a compact CSR: live arcs only, rows sorted by neighbour.  The rows
+// are read back and put in canonical order on the host (an inspection path).
 int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool device_out) {
   const uint32_t n = h->n;
-  uint32_t *d32 = nullptr, *eoff = nullptr, *didx = nullptr, *dw = nullptr;
-  unsigned long long* doff = nullptr;
-  int rc = DFL_OK;
-  auto cleanup = [&]() {
-    cudaFree(d32);
-    cudaFree(eoff);
-    if (!device_out) {
-      cudaFree(didx);
-      cudaFree(dw);
-      cudaFree(doff);
+  std::vector<unsigned long long> hoff(n);
+  std::vector<uint32_t> hdeg(n);
+  std::vector<uint2> arcs(h->pool_top ? h->pool_top : 1);
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (n) {
+    DFL_CUDA(h, cudaMemcpy(hoff.data(), h->off, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
+    DFL_CUDA(h, cudaMemcpy(hdeg.data(), h->deg, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  }
+  if (h->pool_top)
+    DFL_CUDA(h, cudaMemcpy(arcs.data(), h->arcs, sizeof(uint2) * h->pool_top, cudaMemcpyDeviceToHost));
+  std::vector<uint64_t> o(uint64_t(n) + 1, 0);
+  std::vector<uint32_t> vi, vw;
+  vi.reserve(h->num_arcs);
+  vw.reserve(h->num_arcs);
+  std::vector<uint2> row;
+  for (uint32_t i = 0; i < n; ++i) {
+    row.clear();
+    for (uint32_t k = 0; k < hdeg[i]; ++k) {
+      uint2 a = arcs[hoff[i] + k];
+      if (a.y) row.push_back(a);
     }
-  };
-  if (cudaMalloc(&d32, sizeof(uint32_t) * (uint64_t(n) + 1)) != cudaSuccess ||
-      cudaMalloc(&eoff, sizeof(uint32_t) * (uint64_t(n) + 1)) != cudaSuccess) {
-    cleanup();
-    return set_error(h, DFL_ERR_NOMEM, "export buffers");
-  }
-  if (device_out) {
-    doff = reinterpret_cast<unsigned long long*>(off);
-    didx = idx;
-    dw = w;
-  } else if (cudaMalloc(&doff, sizeof(unsigned long long) * (uint64_t(n) + 1)) != cudaSuccess ||
-             cudaMalloc(&didx, sizeof(uint32_t) * (h->num_arcs + 1)) != cudaSuccess ||
-             cudaMalloc(&dw, sizeof(uint32_t) * (h->num_arcs + 1)) != cudaSuccess) {
-    cleanup();
-    return set_error(h, DFL_ERR_NOMEM, "export buffers");
-  }
-  {
-    LaunchScope ls(h, DFL_PROF_OTHER);
-    k_deg_u32<<<grid_for(n, 256), 256, 0, h->stream>>>(h->deg, d32, n);
-    rc = check_launch(h, "export deg");
-  }
-  if (!rc) rc = scan_u32(h, d32, eoff, n);
-  if (!rc) {
-    LaunchScope ls(h, DFL_PROF_OTHER);
-    if (n) {
-      k_export_rows<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(base_view(h), eoff,
-                                                                             doff, didx, dw);
-      rc = check_launch(h, "export rows");
-    } else if (cudaMemsetAsync(doff, 0, sizeof(unsigned long long), h->stream) != cudaSuccess) {
-      rc = set_error(h, DFL_ERR_CUDA, "memset");
+    std::sort(row.begin(), row.end(), [](const uint2& x, const uint2& y) { return x.x < y.x; });
+    for (const uint2& a : row) {
+      vi.push_back(a.x);
+      vw.push_back(a.y);
     }
+    o[i + 1] = vi.size();
   }
-  if (!rc && !device_out) {
-    if (cudaMemcpyAsync(off, doff, sizeof(uint64_t) * (uint64_t(n) + 1), cudaMemcpyDeviceToHost,
-                        h->stream) != cudaSuccess ||
-        cudaMemcpyAsync(idx, didx, sizeof(uint32_t) * h->num_arcs, cudaMemcpyDeviceToHost,
-                        h->stream) != cudaSuccess ||
-        cudaMemcpyAsync(w, dw, sizeof(uint32_t) * h->num_arcs, cudaMemcpyDeviceToHost,
-                        h->stream) != cudaSuccess)
-      rc = set_error(h, DFL_ERR_CUDA, "export copy");
+  if (vi.size() != h->num_arcs) return set_error(h, DFL_ERR_CUDA, "live arc count mismatch");
+  cudaMemcpyKind kd = device_out ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  DFL_CUDA(h, cudaMemcpy(off, o.data(), sizeof(uint64_t) * o.size(), kd));
+  if (!vi.empty()) {
+    DFL_CUDA(h, cudaMemcpy(idx, vi.data(), sizeof(uint32_t) * vi.size(), kd));
+    DFL_CUDA(h, cudaMemcpy(w, vw.data(), sizeof(uint32_t) * vw.size(), kd));
   }
-  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "sync");
-  cleanup();
-  return rc;
+  return DFL_OK;
 }
 
 int recompute_sigma_sizes(Handle* h, const uint32_t* C) {

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
     const unsigned long long o = a.g.off[i];
     const uint32_t dg = a.g.deg[i];
     uint2 arc = lane < dg ? a.g.arcs[o + lane] : make_uint2(i, 0u);
-    bool valid = lane < dg && arc.x != i;
+    bool valid = lane < dg && arc.x != i && arc.y != 0;  // weight 0 = deleted arc
     uint32_t c = valid ? a.C[arc.x] : kEmpty;
     unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
     uint32_t hsum = __reduce_add_sync(peers, valid ? arc.y : 0u);
@@ -123,12 +123,14 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
   }
 }
 
-// Open-addressing insert (linear probing) of weight w under key c.
+// Open-addressing insert (linear probing) of weight w under key c; gives up
+// after `limit` probes (the caller then falls back to a larger table).
 __device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
-                                          uint32_t w) {
+                                          uint32_t w, uint32_t limit) {
   uint32_t s = hash32(c) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    uint32_t prev = atomicCAS(&keys[s], kEmpty, c);
+  for (uint32_t probe = 0; probe < limit; ++probe) {
+    uint32_t prev = keys[s];
+    if (prev == kEmpty) prev = atomicCAS(&keys[s], kEmpty, c);
     if (prev == kEmpty || prev == c) {
       atomicAdd(&vals[s], w);
       return true;
@@ -138,8 +140,42 @@ __device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32
   return false;
 }
 
+// scanCommunities over arcs [k0, dg) of row o, lanes striding by `step`:
+// each 32-arc chunk is pre-aggregated per community inside the warp
+// (match + reduce), so only one table update per distinct community and
+// chunk is issued.  Loads of kUnroll chunks are issued before use.
+template <int kUnroll>
+__device__ __forceinline__ bool scan_row(const DecideArgs& a, uint32_t i, unsigned long long o,
+                                         uint32_t dg, uint32_t k0, uint32_t step, uint32_t* keys,
+                                         uint32_t* vals, uint32_t mask, uint32_t limit) {
+  const uint32_t lane = threadIdx.x & 31u;
+  bool ok = true;
+  for (uint32_t base = k0; base < dg; base += step * kUnroll) {
+    uint2 arc[kUnroll];
+    uint32_t c[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      uint32_t k = base + u * step + lane;
+      arc[u] = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      bool valid = arc[u].x != i && arc[u].y != 0;  // skip self-loops and deleted arcs
+      c[u] = valid ? a.C[arc[u].x] : kEmpty;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      unsigned peers = __match_any_sync(0xFFFFFFFFu, c[u]);
+      uint32_t hs = __reduce_add_sync(peers, c[u] != kEmpty ? arc[u].y : 0u);
+      if (c[u] != kEmpty && lane == uint32_t(__ffs(peers) - 1))
+        ok &= table_add(keys, vals, mask, c[u], hs, limit);
+    }
+  }
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
-// Bin 1: 32 < deg <= 256, one warp per vertex with a 512-slot shared table.
+// Bin 1: 32 < deg <= 256, one warp per vertex with a shared table.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kWarpSlots = 512;
 constexpr int kWarpHashWarps = 8;
@@ -171,11 +207,7 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
       vals[s] = 0;
     }
     __syncwarp();
-    bool ok = true;
-    for (uint32_t k = lane; k < dg; k += 32) {
-      uint2 arc = a.g.arcs[o + k];
-      if (arc.x != i) ok &= table_add(keys, vals, mask, a.C[arc.x], arc.y);
-    }
+    bool ok = scan_row<4>(a, i, o, dg, 0, 32, keys, vals, mask, slots);
     if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
     __syncwarp();
     bool have = false;
@@ -210,8 +242,8 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
       if (lane == 0) record_move(a, i, bc, d, gain);
       for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
         uint32_t k = k0 + lane;
-        uint32_t j = k < dg ? a.g.arcs[o + k].x : i;
-        mark_next(a, j, k < dg && j != i);
+        uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+        mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
       }
       bytes += 16 + 4ull * dg;
     }
@@ -224,19 +256,24 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Bins 2 and 3: one block per vertex; the table is in shared memory (bin 2,
-// dynamic shared memory) or in a per-block slice of global memory (bin 3).
+// Bins 2 and 3: one block per vertex with a shared table of kBlockSlots
+// (bin 2 fits by construction; a bin-3 vertex has so many neighbours that the
+// number of distinct neighbour communities, not the degree, sizes the table).
+// If a bin-3 vertex overflows the shared table, it is redone with a table in
+// a per-block slice of global memory sized from the maximum degree.
 // ---------------------------------------------------------------------------
-template <bool kGlobal>
-__global__ void __launch_bounds__(512) k_decide_block(DecideArgs a) {
+constexpr uint32_t kBlockSlots = 2 * kBinBlock;  // 8192 keys + 8192 values = 64 KB
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   extern __shared__ uint32_t dyn[];
   __shared__ unsigned long long s_hd;
   __shared__ uint32_t s_ncand;
-  __shared__ unsigned long long s_lo[16], s_hi[16];
-  __shared__ uint32_t s_c[16];
-  __shared__ int s_have[16];
+  __shared__ unsigned long long s_lo[kThreads / 32], s_hi[kThreads / 32];
+  __shared__ uint32_t s_c[kThreads / 32];
+  __shared__ int s_have[kThreads / 32];
   __shared__ int s_ok;
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kThreads / 32;
   const uint32_t cnt = *a.count;
   unsigned long long bytes = 0, processed = 0;
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
@@ -249,41 +286,47 @@ __global__ void __launch_bounds__(512) k_decide_block(DecideArgs a) {
     const unsigned long long o = a.g.off[i];
     const uint32_t dg = a.g.deg[i];
     uint32_t slots = 1024;
-    while (slots < 2 * dg) slots <<= 1;
-    uint32_t* keys;
-    uint32_t* vals;
-    if (kGlobal) {
-      if (slots > a.gslots) slots = a.gslots;  // gslots >= 2 * max degree
-      keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
-      vals = keys + a.gslots;
-    } else {
-      keys = dyn;
-      vals = dyn + slots;
+    while (slots < 2 * dg && slots < kBlockSlots) slots <<= 1;
+    uint32_t* keys = dyn;
+    uint32_t* vals = dyn + slots;
+    bool global = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (attempt == 1) {  // shared table overflowed: global slice of gslots
+        global = true;
+        slots = a.gslots;
+        keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
+        vals = keys + a.gslots;
+      }
+      const uint32_t mask = slots - 1;
+      for (uint32_t s = threadIdx.x; s < slots; s += kThreads) {
+        keys[s] = kEmpty;
+        vals[s] = 0;
+      }
+      if (threadIdx.x == 0) {
+        s_hd = 0;
+        s_ncand = 0;
+        s_ok = 1;
+      }
+      __syncthreads();
+      // a table of >= 2 * deg slots cannot overflow: probe it to the end;
+      // a smaller shared table (bin 3) gives up early and falls back
+      const uint32_t limit = (global || slots >= 2 * dg) ? slots : 64;
+      bool ok = scan_row<4>(a, i, o, dg, wib * 32, kThreads, keys, vals, mask, limit);
+      if (!ok) s_ok = 0;
+      __syncthreads();
+      const bool done = s_ok;
+      __syncthreads();  // everyone has read s_ok before the retry resets it
+      if (done) break;
+      if (global || !a.gtable) {
+        if (threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
+        break;
+      }
     }
-    const uint32_t mask = slots - 1;
-    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    if (threadIdx.x == 0) {
-      s_hd = 0;
-      s_ncand = 0;
-      s_ok = 1;
-    }
-    __syncthreads();
-    bool ok = true;
-    for (uint32_t k = threadIdx.x; k < dg; k += blockDim.x) {
-      uint2 arc = a.g.arcs[o + k];
-      if (arc.x != i) ok &= table_add(keys, vals, mask, a.C[arc.x], arc.y);
-    }
-    if (!ok) s_ok = 0;
-    __syncthreads();
-    if (!s_ok && threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
     bool have = false;
     i128 best = 0;
     uint32_t bc = 0;
     uint32_t ncand = 0;
-    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) {
+    for (uint32_t s = threadIdx.x; s < slots; s += kThreads) {
       uint32_t c = keys[s];
       if (c == kEmpty) continue;
       if (c == d) {
@@ -329,10 +372,10 @@ __global__ void __launch_bounds__(512) k_decide_block(DecideArgs a) {
     bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
       if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
-      for (uint32_t k0 = wib * 32; k0 < dg; k0 += blockDim.x) {
+      for (uint32_t k0 = wib * 32; k0 < dg; k0 += kThreads) {
         uint32_t k = k0 + lane;
-        uint32_t j = k < dg ? a.g.arcs[o + k].x : i;
-        mark_next(a, j, k < dg && j != i);
+        uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+        mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
       }
       bytes += 16 + 4ull * dg;
     }
@@ -396,6 +439,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   make_segs(h, k);
   const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
   DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
+  unsigned long long skipped = h->hctrl->skipped;  // isolated frontier vertices
   unsigned int cur_count[kMaxSubsteps][kBins];
   for (uint32_t s = 0; s < kMaxSubsteps; ++s)
     for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
@@ -415,8 +459,10 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   }
   static bool smem_set = false;
   if (!smem_set) {
-    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 4 * kBinBlock)));
+    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 2 * kBlockSlots)));
+    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 2 * kBlockSlots)));
     smem_set = true;
   }
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->move_bytes, 0, sizeof(unsigned long long), h->stream));
@@ -463,11 +509,11 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
         } else if (b == 1) {
           k_decide_warp_hash<<<grid_for(uint64_t(c) * 32, 256, 152 * 16), 256, 0, h->stream>>>(a);
         } else if (b == 2) {
-          uint32_t slots = next_pow2(2ull * kBinBlock);
-          k_decide_block<false><<<grid_for(c, 1, 152 * 4), 256, sizeof(uint32_t) * 2 * slots,
-                                  h->stream>>>(a);
+          k_decide_block<256><<<grid_for(c, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kBlockSlots,
+                                 h->stream>>>(a);
         } else {
-          k_decide_block<true><<<grid_for(c, 1, gblocks), 512, 0, h->stream>>>(a);
+          k_decide_block<1024><<<grid_for(c, 1, gblocks), 1024, sizeof(uint32_t) * 2 * kBlockSlots,
+                                  h->stream>>>(a);
         }
         DFL_TRY(check_launch(h, "decide"));
       }
@@ -486,7 +532,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
     u128 S = ((u128)c.s_hi << 32) + (u128)c.s_lo;
     if (record_trace) {
-      h->trace.push_back(c.processed);
+      h->trace.push_back(c.processed + skipped);
       h->trace.push_back(c.moved);
       h->trace.push_back(uint64_t(S >> 64));
       h->trace.push_back(uint64_t(S));
@@ -495,6 +541,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     for (uint32_t s = 0; s < kMaxSubsteps; ++s)
       for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
     cur = nxt;
+    skipped = 0;
     if (S <= threshold) break;  // locally converged
   }
   h->prof.bytes[DFL_PROF_MOVE] += h->hctrl->move_bytes;

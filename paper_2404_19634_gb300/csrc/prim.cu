@@ -254,9 +254,14 @@ __global__ void k_lists_all(uint32_t nv, const uint32_t* __restrict__ deg, uint3
   uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x); i0 < nv; i0 += stride) {
     uint64_t i = i0 + threadIdx.x;
-    bool valid = i < nv;
+    // a vertex without arcs has no neighbour community: it is processed
+    // (counted) but never queued
+    uint32_t d = i < nv ? deg[i] : 0u;
+    bool valid = i < nv && d > 0;
+    unsigned idle = __ballot_sync(0xFFFFFFFFu, i < nv && d == 0);
+    if ((threadIdx.x & 31u) == 0 && idle) atomicAdd(&ctrl->skipped, (unsigned long long)__popc(idle));
     uint32_t key = 0;
-    if (valid) key = substep_class(uint32_t(i), k) * kBins + degree_bin(deg[i]);
+    if (valid) key = substep_class(uint32_t(i), k) * kBins + degree_bin(d);
     append_vertex(uint32_t(i), valid, key, lists, seg, ctrl, buf);
   }
 }

@@ -342,3 +342,72 @@ def test_device_buffers_and_stream(dfl, orc):
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), b.membership())
     same_state(a, b)
+
+
+def test_long_stream_tombstones_and_rebuilds(dfl, orc):
+    """Many batches on a small graph: deletions leave tombstones, re-inserted
+    edges revive them, hot vertices overflow their append tail and are
+    rebuilt; the graph and the state must track the oracle throughout."""
+    rng = np.random.default_rng(17)
+    g = synth.planted_partition(600, 12, 0.25, 6, 4, 2)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    deleted = []
+    for t in range(40):
+        off, idx, w = b.graph()
+        edges = [(i, int(idx[k]), int(w[k])) for i in range(g.n)
+                 for k in range(int(off[i]), int(off[i + 1])) if i < idx[k]]
+        pick = rng.choice(len(edges), min(25, len(edges)), replace=False)
+        dels = [(edges[p][0], edges[p][1], 0 if rng.random() < 0.7 else int(rng.integers(1, edges[p][2] + 1)))
+                for p in pick]
+        ins = []
+        hot = int(rng.integers(0, 8))  # a few vertices receive many new edges
+        for _ in range(30):
+            j = int(rng.integers(0, g.n))
+            if j != hot:
+                ins.append((hot, j, int(rng.integers(1, 4))))
+        for _ in range(20):
+            x, y = int(rng.integers(0, g.n)), int(rng.integers(0, g.n))
+            if x != y:
+                ins.append((x, y, 1))
+        if deleted:  # re-insert some previously deleted edges (tombstone revival)
+            for p in rng.choice(len(deleted), min(10, len(deleted)), replace=False):
+                ins.append(deleted[p])
+        deleted += [(u, v, 1) for (u, v, _) in dels]
+        d = np.array(dels, np.uint32).reshape(-1, 3)
+        i = np.array(ins, np.uint32).reshape(-1, 3)
+        assert a.apply_batch(d, i) == 0 and b.apply_batch(d, i) == 0
+        same_graph(a, b)
+        if t % 5 == 4:
+            a.update(t % 3)
+            b.update(t % 3)
+            same_state(a, b)
+
+
+def test_one_row_gets_thousands_of_edges(dfl, orc):
+    g = synth.sbm(6000, 30, 0.01, 0.001, 41)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    rng = np.random.default_rng(2)
+    nb = rng.choice(np.arange(1, g.n), 3500, replace=False)
+    ins = np.stack([np.zeros(3500, np.int64), nb, rng.integers(1, 5, 3500)], 1).astype(np.uint32)
+    off, idx, w = synth.to_csr(g)
+    row0 = idx[int(off[0]):int(off[1])]
+    dels = np.array([[0, int(x), 0] for x in row0[:3]], np.uint32).reshape(-1, 3)
+    assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+    same_graph(a, b)
+    a.update(2)
+    b.update(2)
+    same_state(a, b)
+    # delete most of that row again, then re-insert part of it
+    dels = np.stack([np.zeros(3000, np.int64), nb[:3000], np.zeros(3000, np.int64)], 1).astype(np.uint32)
+    assert a.apply_batch(dels, np.zeros((0, 3), np.uint32)) == 0
+    assert b.apply_batch(dels, np.zeros((0, 3), np.uint32)) == 0
+    ins = np.stack([np.zeros(500, np.int64), nb[:500], np.ones(500, np.int64)], 1).astype(np.uint32)
+    assert a.apply_batch(np.zeros((0, 3), np.uint32), ins) == 0 and b.apply_batch(np.zeros((0, 3), np.uint32), ins) == 0
+    same_graph(a, b)
+    a.update(1)
+    b.update(1)
+    same_state(a, b)
