@@ -262,7 +262,9 @@ struct GiantArgs {
   const uint32_t* giant;
   const unsigned long long* gtab;
   const uint32_t* gsize;
+  const uint32_t* chunk0;  // first work item of each giant (exclusive scan of chunk counts)
   uint32_t ngiant;
+  uint32_t nitems;         // total (giant, chunk) work items
 };
 
 // Block (g, chunk): aggregate members [chunk*256, +256) of giant g in shared
@@ -272,15 +274,22 @@ __global__ void __launch_bounds__(256) k_agg_giant_accum(AggArgs a, GiantArgs gi
   __shared__ uint32_t keys[kGiantSlots];
   __shared__ uint32_t vals[kGiantSlots];
   const uint32_t wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t g = blockIdx.x;
-  const uint32_t c = gi.giant[g];
-  const uint32_t gs = gi.gsize[g];
-  uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
-  uint32_t* gvals = gkeys + gs;
   bool ok = true;
-  for (uint32_t chunk = blockIdx.y;; chunk += gridDim.y) {
+  for (uint32_t item = blockIdx.x; item < gi.nitems; item += gridDim.x) {
+    // giant owning this work item
+    uint32_t lo = 0, hi = gi.ngiant;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (gi.chunk0[mid] <= item) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t g = lo;
+    const uint32_t chunk = item - gi.chunk0[g];
+    const uint32_t c = gi.giant[g];
+    const uint32_t gs = gi.gsize[g];
+    uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
+    uint32_t* gvals = gkeys + gs;
     const uint64_t m0 = a.coff[c] + uint64_t(chunk) * kChunkMembers;
-    if (m0 >= a.coff[c + 1]) break;
     const uint64_t mend = m0 + kChunkMembers;
     const uint32_t m1 = a.coff[c + 1] < mend ? a.coff[c + 1] : uint32_t(mend);
     for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
@@ -468,7 +477,8 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     std::vector<unsigned long long> gtab(ngiant);
     std::vector<uint32_t> gsize(ngiant);
     unsigned long long total = 0;
-    uint32_t max_chunks = 1;
+    std::vector<uint32_t> chunk0(ngiant);
+    uint32_t nitems = 0;
     for (uint32_t k = 0; k < ngiant; ++k) {
       uint32_t cc = giant[k];
       unsigned long long td = soff[cc + 1] - soff[cc];
@@ -477,8 +487,8 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
       gtab[k] = total;
       total += gsize[k];
       uint32_t members = cntv[cc + 1] - cntv[cc];
-      uint32_t ch = (members + kChunkMembers - 1) / kChunkMembers;
-      if (ch > max_chunks) max_chunks = ch;
+      chunk0[k] = nitems;
+      nitems += (members + kChunkMembers - 1) / kChunkMembers;
     }
     if (total > h->gtable_cap) {
       cudaFree(h->gtable);
@@ -488,10 +498,13 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
       h->gtable_cap = total;
     }
     // small device arrays for the giant layout (in the generic scratch)
-    DFL_TRY(ensure_tmp(h, ngiant * (sizeof(uint32_t) * 2 + sizeof(unsigned long long)) + 64));
+    DFL_TRY(ensure_tmp(h, ngiant * (sizeof(uint32_t) * 3 + sizeof(unsigned long long)) + 64));
     unsigned long long* d_gtab = static_cast<unsigned long long*>(h->tmp);
     uint32_t* d_giant = reinterpret_cast<uint32_t*>(d_gtab + ngiant);
     uint32_t* d_gsize = d_giant + ngiant;
+    uint32_t* d_chunk0 = d_gsize + ngiant;
+    DFL_CUDA(h, cudaMemcpyAsync(d_chunk0, chunk0.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
+                                h->stream));
     DFL_CUDA(h, cudaMemcpyAsync(d_gtab, gtab.data(), sizeof(unsigned long long) * ngiant,
                                 cudaMemcpyHostToDevice, h->stream));
     DFL_CUDA(h, cudaMemcpyAsync(d_giant, giant.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
@@ -499,7 +512,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     DFL_CUDA(h, cudaMemcpyAsync(d_gsize, gsize.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
                                 h->stream));
     a.gtable = h->gtable;
-    GiantArgs gi{d_giant, d_gtab, d_gsize, ngiant};
+    GiantArgs gi{d_giant, d_gtab, d_gsize, d_chunk0, ngiant, nitems};
     {
       LaunchScope ls(h, DFL_PROF_AGG);
       k_giant_init<<<grid_for(total, 256), 256, 0, h->stream>>>(a, gi, total);
@@ -507,7 +520,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     }
     {
       LaunchScope ls(h, DFL_PROF_AGG);
-      k_agg_giant_accum<<<dim3(ngiant, max_chunks < 65535 ? max_chunks : 65535), 256, 0, h->stream>>>(a, gi);
+      k_agg_giant_accum<<<grid_for(nitems, 1, 152 * 8), 256, 0, h->stream>>>(a, gi);
       DFL_TRY(check_launch(h, "giant accum"));
     }
     {

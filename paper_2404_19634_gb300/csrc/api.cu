@@ -21,7 +21,7 @@ int check_launch(Handle* h, const char* what) {
   return DFL_OK;
 }
 
-LaunchScope::LaunchScope(Handle* h_, int cls_) : h(h_), cls(cls_) {
+LaunchScope::LaunchScope(Handle* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
   h->launches++;
   h->prof.launches[cls]++;
   if (h->opt.flags & DFL_FLAG_PROFILE) {
@@ -35,13 +35,13 @@ LaunchScope::LaunchScope(Handle* h_, int cls_) : h(h_), cls(cls_) {
       }
       (k ? b : a) = e;
     }
-    if (a) cudaEventRecord(a, h->stream);
+    if (a) cudaEventRecord(a, s);
   }
 }
 
 LaunchScope::~LaunchScope() {
   if (a && b) {
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, s);
     h->ev_pending.push_back(Handle::Ev{a, b, cls});
   } else {
     if (a) h->ev_free.push_back(a);
@@ -101,6 +101,11 @@ void free_all(Handle* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
+  for (int k = 0; k < kBins - 1; ++k) {
+    if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
+    if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   for (auto& e : h->ev_pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);

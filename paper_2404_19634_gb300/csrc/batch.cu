@@ -687,12 +687,7 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
           h->pend_key, h->pend_count, f, h->C, h->deg, h->fbits[0], h->lists[0], h->segs, h->ctrl, k);
       DFL_TRY(check_launch(h, "mark df"));
     }
-    DFL_TRY(read_ctrl(h));
-    uint64_t tot = 0;
-    for (uint32_t s = 0; s < k; ++s)
-      for (int b = 0; b < kBins; ++b) tot += h->hctrl->count[0][s][b];
-    *initial = tot;
-    if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in marking");
+    *initial = ~0ull;  // counted from the frontier lists when local-moving starts
     return DFL_OK;
   }
   if (mode != DFL_DS) return set_error(h, DFL_ERR_INVALID, "unknown mode");

@@ -69,6 +69,7 @@ struct Ctrl {
   unsigned int rebuild_rows;         // rows rebuilt by the batch
   unsigned int pad2;
   unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
+  unsigned long long ever_count;     // vertices newly added to the first-pass processed set
   unsigned long long pool_top;       // first free arc slot of the pool
   unsigned long long scratch_top;
   // misc reductions
@@ -194,6 +195,11 @@ struct Handle {
   uint2* gtable = nullptr;         // global hash tables of the largest bin
   uint64_t gtable_cap = 0;
 
+  // auxiliary streams for the concurrent degree bins of a sub-step
+  cudaStream_t aux[kBins - 1] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kBins - 1] = {nullptr, nullptr, nullptr};
+
   // control
   Ctrl* ctrl = nullptr;       // device
   Ctrl* hctrl = nullptr;      // pinned host mirror
@@ -238,8 +244,10 @@ int set_error(Handle* h, int code, const std::string& msg);
 struct LaunchScope {
   Handle* h;
   int cls;
+  cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
-  LaunchScope(Handle* h_, int cls_);
+  LaunchScope(Handle* h_, int cls_, cudaStream_t s_);
+  LaunchScope(Handle* h_, int cls_) : LaunchScope(h_, cls_, h_->stream) {}
   ~LaunchScope();
 };
 
@@ -365,7 +373,7 @@ struct MoveArgs {
   bool track_ever;
 };
 int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
-               bool record_trace);
+               bool record_trace, uint64_t* initial = nullptr, uint64_t* ever = nullptr);
 
 // aggregate.cu
 int count_communities(Handle* h, const uint32_t* Cp, uint32_t nv, uint32_t* ncomm);

@@ -113,13 +113,13 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
     a.use_range = use_range && pass == 0;
     a.track_ever = pass == 0 && !all;
     uint32_t it = 0;
-    DFL_TRY(local_move(h, a, pass, &it, pass == 0));
+    uint64_t init0 = 0, ever0 = 0;
+    DFL_TRY(local_move(h, a, pass, &it, pass == 0, &init0, &ever0));
     if (pass < 16) st.iterations[pass] = it;
     st.passes = pass + 1;
     if (pass == 0) {
-      int rc = DFL_OK;
-      st.affected_ever = all ? n : popcount_bits(h, h->ever, h->words, &rc);
-      if (rc) return rc;
+      if (initial == ~0ull) st.affected_initial = init0;
+      st.affected_ever = all ? n : ever0;
     }
     if (it <= 1) break;  // globally converged
     uint32_t ncomm = 0;

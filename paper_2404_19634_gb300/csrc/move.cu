@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long bytes = 0, processed = 0;
+  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t i = a.list[t];
-    if (a.ever && lane == 0) bit_set(a.ever, i);
+    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
     const uint32_t d = a.C[i];
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
   if (lane == 0) {
     atomicAdd(&a.ctrl->move_bytes, bytes);
     if (processed) atomicAdd(&a.ctrl->processed, processed);
+    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
   }
 }
 
@@ -189,10 +190,10 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long bytes = 0, processed = 0;
+  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t i = a.list[t];
-    if (a.ever && lane == 0) bit_set(a.ever, i);
+    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
     const uint32_t d = a.C[i];
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
   if (lane == 0) {
     atomicAdd(&a.ctrl->move_bytes, bytes);
     if (processed) atomicAdd(&a.ctrl->processed, processed);
+    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
   }
 }
 
@@ -275,10 +277,10 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   __shared__ int s_ok;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kThreads / 32;
   const uint32_t cnt = *a.count;
-  unsigned long long bytes = 0, processed = 0;
+  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const uint32_t i = a.list[t];
-    if (a.ever && threadIdx.x == 0) bit_set(a.ever, i);
+    if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
     const uint32_t d = a.C[i];
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   if (threadIdx.x == 0) {
     atomicAdd(&a.ctrl->move_bytes, bytes);
     if (processed) atomicAdd(&a.ctrl->processed, processed);
+    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
   }
 }
 
@@ -434,12 +437,18 @@ uint32_t next_pow2(uint64_t x) {
 }  // namespace
 
 int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
-               bool record_trace) {
+               bool record_trace, uint64_t* initial, uint64_t* ever) {
   const uint32_t k = h->opt.substeps;
   make_segs(h, k);
   const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
   DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
   unsigned long long skipped = h->hctrl->skipped;  // isolated frontier vertices
+  if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
+  if (initial) {
+    *initial = skipped;
+    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+      for (int b = 0; b < kBins; ++b) *initial += h->hctrl->count[0][s][b];
+  }
   unsigned int cur_count[kMaxSubsteps][kBins];
   for (uint32_t s = 0; s < kMaxSubsteps; ++s)
     for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
@@ -465,7 +474,15 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
                                      int(sizeof(uint32_t) * 2 * kBlockSlots)));
     smem_set = true;
   }
+  if (!h->ev_fork) {
+    DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    for (int b = 0; b < kBins - 1; ++b) {
+      DFL_CUDA(h, cudaStreamCreateWithFlags(&h->aux[b], cudaStreamNonBlocking));
+      DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
+    }
+  }
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->move_bytes, 0, sizeof(unsigned long long), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->ever_count, 0, sizeof(unsigned long long), h->stream));
   int cur = 0;
   uint32_t it = 0;
   while (it < h->opt.max_iterations) {
@@ -496,27 +513,45 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     a.gtable = h->gtable;
     a.gslots = gslots;
     for (uint32_t s = 0; s < k; ++s) {
-      bool any = false;
-      for (int b = 0; b < kBins; ++b) {
+      // the degree bins of one class are independent: the largest ones run
+      // on auxiliary streams, concurrently with the rest
+      int nb = 0;
+      for (int b = 0; b < kBins; ++b) nb += cur_count[s][b] ? 1 : 0;
+      const bool any = nb > 0;
+      bool forked = false;
+      if (nb > 1) {
+        DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+        forked = true;
+      }
+      bool joined[kBins - 1] = {false, false, false};
+      for (int b = kBins - 1; b >= 0; --b) {
         uint32_t c = cur_count[s][b];
         if (!c) continue;
-        any = true;
+        cudaStream_t st = h->stream;
+        if (forked && b > 0) {
+          st = h->aux[b - 1];
+          DFL_CUDA(h, cudaStreamWaitEvent(st, h->ev_fork, 0));
+          joined[b - 1] = true;
+        }
         a.list = h->lists[cur] + h->segs.off[s * kBins + b];
         a.count = &h->ctrl->count[cur][s][b];
-        LaunchScope ls(h, DFL_PROF_MOVE);
+        LaunchScope ls(h, DFL_PROF_MOVE, st);
         if (b == 0) {
-          k_decide_warp<<<grid_for(uint64_t(c) * 32, 256, 152 * 64), 256, 0, h->stream>>>(a);
+          k_decide_warp<<<grid_for(uint64_t(c) * 32, 256, 152 * 64), 256, 0, st>>>(a);
         } else if (b == 1) {
-          k_decide_warp_hash<<<grid_for(uint64_t(c) * 32, 256, 152 * 16), 256, 0, h->stream>>>(a);
+          k_decide_warp_hash<<<grid_for(uint64_t(c) * 32, 256, 152 * 16), 256, 0, st>>>(a);
         } else if (b == 2) {
-          k_decide_block<256><<<grid_for(c, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kBlockSlots,
-                                 h->stream>>>(a);
+          k_decide_block<256><<<grid_for(c, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
         } else {
-          k_decide_block<1024><<<grid_for(c, 1, gblocks), 1024, sizeof(uint32_t) * 2 * kBlockSlots,
-                                  h->stream>>>(a);
+          k_decide_block<1024><<<grid_for(c, 1, gblocks), 1024, sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
         }
         DFL_TRY(check_launch(h, "decide"));
       }
+      for (int b = 0; b < kBins - 1; ++b)
+        if (joined[b]) {
+          DFL_CUDA(h, cudaEventRecord(h->ev_join[b], h->aux[b]));
+          DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
+        }
       if (any) {
         {
           LaunchScope ls(h, DFL_PROF_COMMIT);
@@ -545,6 +580,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     if (S <= threshold) break;  // locally converged
   }
   h->prof.bytes[DFL_PROF_MOVE] += h->hctrl->move_bytes;
+  if (ever) *ever = h->hctrl->ever_count;
   // leave the unprocessed frontier behind: clear the other buffer's bitmap
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
   *iterations = it;
