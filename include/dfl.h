@@ -113,16 +113,23 @@ typedef struct {
 enum {
   DFL_PROF_APPLY = 0,   /* batch apply, K/Sigma update */
   DFL_PROF_MARK = 1,    /* initial frontier marking */
-  DFL_PROF_MOVE = 2,    /* local-moving decide kernels (the hot loop) */
+  DFL_PROF_MOVE = 2,    /* local-moving decide phase of each sub-step: wall time from the
+                           first to the end of the last (concurrent) decide kernel */
   DFL_PROF_COMMIT = 3,  /* local-moving move-apply kernels */
   DFL_PROF_AGG = 4,     /* renumbering and aggregation */
   DFL_PROF_OTHER = 5,
-  DFL_PROF_CLASSES = 6
+  DFL_PROF_BIN0 = 6,    /* decide kernels by degree bin (<= 32, <= 256, <= 4096, larger); */
+  DFL_PROF_BIN1 = 7,    /* these run concurrently inside the DFL_PROF_MOVE wall time */
+  DFL_PROF_BIN2 = 8,
+  DFL_PROF_BIN3 = 9,
+  DFL_PROF_CLASSES = 10
 };
 typedef struct {
   uint64_t launches[DFL_PROF_CLASSES];
   double ms[DFL_PROF_CLASSES];         /* summed kernel durations (CUDA events) */
-  uint64_t bytes[DFL_PROF_CLASSES];    /* algorithmic bytes moved (see DESIGN) */
+  uint64_t bytes[DFL_PROF_CLASSES];    /* algorithmic bytes: for the decide phase, per
+                                          processed vertex 24 + 12*deg + 12*candidates, plus
+                                          16 + 4*deg per mover */
 } dfl_profile_t;
 
 /* Fill *opt with the defaults above. */

@@ -28,8 +28,9 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 ND, DS, DF = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_PROFILE = 1
+PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other", "bin0", "bin1", "bin2",
+              "bin3"]
 PROF_APPLY, PROF_MARK, PROF_MOVE, PROF_COMMIT, PROF_AGG, PROF_OTHER = range(6)
-PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other"]
 
 ERRORS = {0: "ok", -1: "invalid", -2: "not_found", -3: "overflow", -4: "nomem", -5: "cuda",
           -6: "timeout", -7: "state"}
@@ -96,7 +97,7 @@ class Stats(ct.Structure):
 
 
 class Profile(ct.Structure):
-    _fields_ = [("launches", ct.c_uint64 * 6), ("ms", ct.c_double * 6), ("bytes", ct.c_uint64 * 6)]
+    _fields_ = [("launches", ct.c_uint64 * 10), ("ms", ct.c_double * 10), ("bytes", ct.c_uint64 * 10)]
 
 
 _lib = None
@@ -304,7 +305,7 @@ class Dfl:
         p = Profile()
         self._check(self._lib.dfl_profile(self._h, ct.byref(p), 1 if reset else 0))
         return {PROF_NAMES[k]: {"launches": p.launches[k], "ms": p.ms[k], "bytes": p.bytes[k]}
-                for k in range(6)}
+                for k in range(len(PROF_NAMES))}
 
     def trace(self):
         ln = ct.c_uint32()

@@ -96,6 +96,7 @@ void free_all(Handle* h) {
                   h->lists[1], h->mv_i, h->mv_c, h->mv_d, h->dsV, h->dsE, h->dsC, h->b_key, h->b_w,
                   h->b_key2, h->b_w2, h->b_rowlist, h->b_pos, h->b_wnew, h->b_flag, h->b_delta,
                   h->b_newdeg, h->b_edges, h->scratch, h->tmp, h->gtable, h->ctrl,
+                  h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial,
                   h->sg[0].off, h->sg[0].deg, h->sg[0].arcs, h->sg[1].off, h->sg[1].deg,
                   h->sg[1].arcs};
   for (void* p : ptrs)

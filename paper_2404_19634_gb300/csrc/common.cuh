@@ -70,6 +70,7 @@ struct Ctrl {
   unsigned int pad2;
   unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
   unsigned long long ever_count;     // vertices newly added to the first-pass processed set
+  unsigned int giant_chunks[2];      // chunk work items of the largest bin (per buffer parity)
   unsigned long long pool_top;       // first free arc slot of the pool
   unsigned long long scratch_top;
   // misc reductions
@@ -194,6 +195,15 @@ struct Handle {
   uint64_t tmp_cap = 0;
   uint2* gtable = nullptr;         // global hash tables of the largest bin
   uint64_t gtable_cap = 0;
+  // chunked decisions of the largest bin: per list item partial-sum region
+  // offset, chunk prefix, finished chunks and partial count; partial sums
+  unsigned long long* g_poff = nullptr;
+  uint32_t* g_cpre = nullptr;
+  uint32_t* g_done = nullptr;
+  uint32_t* g_pcount = nullptr;
+  uint64_t g_items_cap = 0;
+  uint2* g_partial = nullptr;
+  uint64_t g_partial_cap = 0;
 
   // auxiliary streams for the concurrent degree bins of a sub-step
   cudaStream_t aux[kBins - 1] = {nullptr, nullptr, nullptr};

@@ -390,6 +390,277 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bin 3 (deg > 4096): a vertex is split into chunks of kGiantChunk arcs, one
+// block per chunk.  A chunk block aggregates its arcs in shared memory and
+// writes the distinct (community, weight) partial sums to the vertex's region
+// of g_partial; the last chunk block of the vertex merges the partial sums
+// (in hash-partitioned passes that each fit the shared table) and decides.
+// If a pass still overflows, the last block redoes the vertex alone with a
+// global table slice.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kGiantChunk = 4096;
+constexpr uint32_t kGiantSlots = 2 * kGiantChunk;  // 8192 keys + values = 64 KB
+constexpr int kGiantThreads = 256;
+
+struct GiantDecide {
+  unsigned long long* poff;
+  uint32_t* cpre;
+  uint32_t* done;
+  uint32_t* pcount;
+  uint2* partial;
+  unsigned int* nitems;
+};
+
+// One block: exclusive prefix over the bin-3 list of deg (partial regions)
+// and of the chunk counts (work items).
+__global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd) {
+  __shared__ unsigned long long s_d[32];
+  __shared__ uint32_t s_c[32];
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_cbase;
+  const uint32_t cnt = *a.count;
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    s_base = 0;
+    s_cbase = 0;
+  }
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < cnt; t0 += blockDim.x) {
+    uint32_t t = t0 + threadIdx.x;
+    unsigned long long d = t < cnt ? a.g.deg[a.list[t]] : 0ull;
+    uint32_t ch = uint32_t((d + kGiantChunk - 1) / kGiantChunk);
+    unsigned long long xd = d;
+    uint32_t xc = ch;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long yd = __shfl_up_sync(0xFFFFFFFFu, xd, o);
+      uint32_t yc = __shfl_up_sync(0xFFFFFFFFu, xc, o);
+      if (lane >= (uint32_t)o) {
+        xd += yd;
+        xc += yc;
+      }
+    }
+    if (lane == 31) {
+      s_d[w] = xd;
+      s_c[w] = xc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long rd = s_base;
+      uint32_t rc = s_cbase;
+      for (uint32_t k = 0; k < blockDim.x / 32; ++k) {
+        unsigned long long td = s_d[k];
+        uint32_t tc = s_c[k];
+        s_d[k] = rd;
+        s_c[k] = rc;
+        rd += td;
+        rc += tc;
+      }
+      s_base = rd;
+      s_cbase = rc;
+    }
+    __syncthreads();
+    if (t < cnt) {
+      gd.poff[t] = s_d[w] + xd - d;
+      gd.cpre[t] = s_c[w] + xc - ch;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    gd.cpre[cnt] = s_cbase;
+    *gd.nitems = s_cbase;
+  }
+}
+
+__global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a, GiantDecide gd) {
+  extern __shared__ uint32_t dyn[];
+  uint32_t* keys = dyn;
+  uint32_t* vals = dyn + kGiantSlots;
+  __shared__ int s_last, s_ok, s_have[kGiantThreads / 32];
+  __shared__ unsigned long long s_hd, s_lo[kGiantThreads / 32], s_hi[kGiantThreads / 32];
+  __shared__ uint32_t s_c[kGiantThreads / 32], s_ncand;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kGiantThreads / 32;
+  const uint32_t cnt = *a.count;
+  const uint32_t nitems = *gd.nitems;
+  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
+  for (uint32_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    uint32_t lo = 0, hi = cnt;  // list position owning this chunk
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (gd.cpre[mid] <= item) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t t = lo;
+    const uint32_t chunk = item - gd.cpre[t];
+    const uint32_t nch = gd.cpre[t + 1] - gd.cpre[t];
+    const uint32_t i = a.list[t];
+    if (chunk == 0) {
+      if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
+      ++processed;
+    }
+    if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
+    const unsigned long long o = a.g.off[i];
+    const uint32_t dg = a.g.deg[i];
+    const uint32_t k0 = chunk * kGiantChunk;
+    const uint32_t k1 = min(dg, k0 + kGiantChunk);
+    // 1. this chunk's partial sums
+    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    __syncthreads();
+    // a table of 2x the chunk's arcs cannot overflow
+    scan_row<4>(a, i, o, k1, k0 + wib * 32, kGiantThreads, keys, vals, kGiantSlots - 1, kGiantSlots);
+    __syncthreads();
+    for (uint32_t s0 = wib * 32; s0 < kGiantSlots; s0 += kGiantThreads) {
+      uint32_t s = s0 + lane;
+      uint32_t key = keys[s];
+      unsigned m = __ballot_sync(0xFFFFFFFFu, key != kEmpty);
+      uint32_t base = 0;
+      if (lane == 0 && m) base = atomicAdd(&gd.pcount[t], __popc(m));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (key != kEmpty) gd.partial[gd.poff[t] + base + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, vals[s]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&gd.done[t], 1u) == nch - 1;
+    __syncthreads();
+    if (!s_last) continue;
+    __threadfence();
+    // 2. last block of the vertex: merge the partial sums and decide
+    const uint32_t d = a.C[i];
+    const long long Ki = a.K[i];
+    const uint32_t np = __ldcg(gd.pcount + t);
+    const uint32_t passes = (np + kGiantChunk - 1) / kGiantChunk > 0 ? (np + kGiantChunk - 1) / kGiantChunk : 1;
+    bool have = false;
+    i128 best = 0;
+    uint32_t bc = 0;
+    uint32_t ncand = 0;
+    unsigned long long hd_local = 0;
+    if (threadIdx.x == 0) {
+      s_ok = 1;
+      s_hd = 0;
+      s_ncand = 0;
+    }
+    for (uint32_t pass = 0; pass < passes; ++pass) {
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
+        keys[s] = kEmpty;
+        vals[s] = 0;
+      }
+      __syncthreads();
+      bool ok = true;
+      for (uint32_t e = threadIdx.x; e < np; e += kGiantThreads) {
+        uint2 pe = __ldcg(gd.partial + gd.poff[t] + e);  // written by other blocks: bypass L1
+        if (passes == 1 || hash32(pe.x ^ 0x5bd1e995u) % passes == pass)
+          ok &= table_add(keys, vals, kGiantSlots - 1, pe.x, pe.y, kGiantSlots);
+      }
+      if (!ok) s_ok = 0;
+      __syncthreads();
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
+        uint32_t c = keys[s];
+        if (c == kEmpty) continue;
+        if (c == d) {
+          hd_local = vals[s];
+          continue;
+        }
+        ++ncand;
+        i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+        if (!have || sc > best || (sc == best && c < bc)) {
+          have = true;
+          best = sc;
+          bc = c;
+        }
+      }
+      __syncthreads();
+    }
+    const bool overflow = !s_ok;
+    __syncthreads();
+    if (overflow) {
+      // rare: redo the whole vertex with this block's global table slice
+      have = false;
+      ncand = 0;
+      hd_local = 0;
+      uint32_t* gk = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
+      uint32_t* gv = gk + a.gslots;
+      uint32_t slots = a.gslots;
+      for (uint32_t s = threadIdx.x; s < slots; s += kGiantThreads) {
+        gk[s] = kEmpty;
+        gv[s] = 0;
+      }
+      __syncthreads();
+      scan_row<4>(a, i, o, dg, wib * 32, kGiantThreads, gk, gv, slots - 1, slots);
+      __syncthreads();
+      for (uint32_t s = threadIdx.x; s < slots; s += kGiantThreads) {
+        uint32_t c = gk[s];
+        if (c == kEmpty) continue;
+        if (c == d) {
+          hd_local = gv[s];
+          continue;
+        }
+        ++ncand;
+        i128 sc = (i128)a.m2 * (i128)gv[s] - (i128)Ki * (i128)a.Sigma[c];
+        if (!have || sc > best || (sc == best && c < bc)) {
+          have = true;
+          best = sc;
+          bc = c;
+        }
+      }
+    }
+    for (int x = 16; x; x >>= 1) {
+      ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+      hd_local += __shfl_xor_sync(0xFFFFFFFFu, hd_local, x);
+    }
+    warp_argmax(have, best, bc);
+    if (lane == 0) {
+      s_lo[wib] = (unsigned long long)(u128)best;
+      s_hi[wib] = (unsigned long long)((u128)best >> 64);
+      s_c[wib] = bc;
+      s_have[wib] = have;
+      if (ncand) atomicAdd(&s_ncand, ncand);
+      if (hd_local) atomicAdd(&s_hd, hd_local);
+    }
+    __syncthreads();
+    if (wib == 0) {
+      have = lane < nw && s_have[lane];
+      best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
+      bc = lane < nw ? s_c[lane] : 0;
+      warp_argmax(have, best, bc);
+      if (lane == 0) {
+        s_lo[0] = (unsigned long long)(u128)best;
+        s_hi[0] = (unsigned long long)((u128)best >> 64);
+        s_c[0] = bc;
+        s_have[0] = have;
+      }
+    }
+    __syncthreads();
+    have = s_have[0];
+    best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
+    bc = s_c[0];
+    i128 gain = 0;
+    bool mv = decide_move(a, i, d, Ki, have, best, bc, s_hd, &gain);
+    bytes += 24 + 12ull * dg + 12ull * s_ncand;
+    if (mv) {
+      if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
+      for (uint32_t q0 = wib * 32; q0 < dg; q0 += kGiantThreads) {
+        uint32_t q = q0 + lane;
+        uint2 arc = q < dg ? a.g.arcs[o + q] : make_uint2(i, 0u);
+        mark_next(a, arc.x, q < dg && arc.x != i && arc.y != 0);
+      }
+      bytes += 16 + 4ull * dg;
+    }
+    if (threadIdx.x == 0) {  // ready for the next use of this list position
+      gd.done[t] = 0;
+      gd.pcount[t] = 0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.ctrl->move_bytes, bytes);
+    if (processed) atomicAdd(&a.ctrl->processed, processed);
+    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
+  }
+}
+
 // Apply the moves of one sub-step.
 __global__ void k_commit(const uint32_t* __restrict__ mv_i, const uint32_t* __restrict__ mv_c,
                          const uint32_t* __restrict__ mv_d, uint32_t* __restrict__ C,
@@ -470,9 +741,43 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   if (!smem_set) {
     DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(sizeof(uint32_t) * 2 * kBlockSlots)));
-    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 2 * kBlockSlots)));
+    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 2 * kGiantSlots)));
     smem_set = true;
+  }
+  // chunked bin-3 buffers: per list item offsets/counters (sized by the
+  // largest bin-3 list: at most arcs / 4097 vertices) and partial sums
+  {
+    uint64_t items = h->pool_top / (kBinBlock + 1) + 64;
+    uint64_t parts = h->pool_top + 64;
+    for (int q = 0; q < 2; ++q) parts = parts > h->sg[q].arc_cap ? parts : h->sg[q].arc_cap;
+    if (items > h->g_items_cap) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->g_poff);
+      cudaFree(h->g_cpre);
+      cudaFree(h->g_done);
+      cudaFree(h->g_pcount);
+      h->g_poff = nullptr;
+      h->g_cpre = h->g_done = h->g_pcount = nullptr;
+      h->g_items_cap = 0;
+      uint64_t want = items + items / 2;
+      DFL_CUDA(h, cudaMalloc(&h->g_poff, sizeof(unsigned long long) * want));
+      DFL_CUDA(h, cudaMalloc(&h->g_cpre, sizeof(uint32_t) * (want + 1)));
+      DFL_CUDA(h, cudaMalloc(&h->g_done, sizeof(uint32_t) * want));
+      DFL_CUDA(h, cudaMalloc(&h->g_pcount, sizeof(uint32_t) * want));
+      DFL_CUDA(h, cudaMemsetAsync(h->g_done, 0, sizeof(uint32_t) * want, h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(h->g_pcount, 0, sizeof(uint32_t) * want, h->stream));
+      h->g_items_cap = want;
+    }
+    if (ma.max_deg > kBinBlock && parts > h->g_partial_cap) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->g_partial);
+      h->g_partial = nullptr;
+      h->g_partial_cap = 0;
+      uint64_t want = parts + parts / 4;
+      DFL_CUDA(h, cudaMalloc(&h->g_partial, sizeof(uint2) * want));
+      h->g_partial_cap = want;
+    }
   }
   if (!h->ev_fork) {
     DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -518,6 +823,13 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
       int nb = 0;
       for (int b = 0; b < kBins; ++b) nb += cur_count[s][b] ? 1 : 0;
       const bool any = nb > 0;
+      // wall time of the sub-step's decide phase (profiling only)
+      cudaEvent_t pa = nullptr, pb = nullptr;
+      if (any && (h->opt.flags & DFL_FLAG_PROFILE)) {
+        cudaEventCreate(&pa);
+        cudaEventCreate(&pb);
+        cudaEventRecord(pa, h->stream);
+      }
       bool forked = false;
       if (nb > 1) {
         DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -535,7 +847,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
         }
         a.list = h->lists[cur] + h->segs.off[s * kBins + b];
         a.count = &h->ctrl->count[cur][s][b];
-        LaunchScope ls(h, DFL_PROF_MOVE, st);
+        LaunchScope ls(h, DFL_PROF_BIN0 + b, st);
         if (b == 0) {
           k_decide_warp<<<grid_for(uint64_t(c) * 32, 256, 152 * 64), 256, 0, st>>>(a);
         } else if (b == 1) {
@@ -543,7 +855,11 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
         } else if (b == 2) {
           k_decide_block<256><<<grid_for(c, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
         } else {
-          k_decide_block<1024><<<grid_for(c, 1, gblocks), 1024, sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
+          GiantDecide gd{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial,
+                         &h->ctrl->giant_chunks[cur]};
+          k_giant_prefix<<<1, 1024, 0, st>>>(a, gd);
+          DFL_TRY(check_launch(h, "giant prefix"));
+          k_decide_giant<<<gblocks, kGiantThreads, sizeof(uint32_t) * 2 * kGiantSlots, st>>>(a, gd);
         }
         DFL_TRY(check_launch(h, "decide"));
       }
@@ -552,6 +868,11 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
           DFL_CUDA(h, cudaEventRecord(h->ev_join[b], h->aux[b]));
           DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
         }
+      if (pa && pb) {
+        cudaEventRecord(pb, h->stream);
+        h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
+        h->prof.launches[DFL_PROF_MOVE]++;
+      }
       if (any) {
         {
           LaunchScope ls(h, DFL_PROF_COMMIT);

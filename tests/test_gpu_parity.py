@@ -411,3 +411,29 @@ def test_one_row_gets_thousands_of_edges(dfl, orc):
     a.update(1)
     b.update(1)
     same_state(a, b)
+
+
+def test_giant_vertex_many_distinct_communities(dfl, orc):
+    """A vertex of degree 20,000 whose neighbours sit in 20,000 different
+    communities: its chunked decision needs several merge passes."""
+    n = 20001
+    u = np.zeros(20000, np.uint32)
+    v = np.arange(1, n, dtype=np.uint32)
+    # a sparse ring among the leaves, weights vary
+    ring = np.arange(1, n - 1, dtype=np.uint32)
+    g = synth.EdgeList(n, np.concatenate([u, ring]), np.concatenate([v, ring + 1]),
+                       np.concatenate([np.ones(20000, np.uint32), (ring % 7 + 1).astype(np.uint32)]))
+    for k in (1, 4):
+        a, b = pair(dfl, orc, g, substeps=k)
+        C = np.arange(n, dtype=np.uint32)
+        a.set_membership(C)
+        b.set_membership(C)
+        F = np.ones(n, np.uint8)
+        R = np.ones(n, np.uint8)
+        Fa, ma, Sa = a.move_iteration(F, R)
+        Fb, mb, Sb = b.move_iteration(F, R)
+        assert np.array_equal(ma, mb) and np.array_equal(Fa, Fb) and Sa == Sb
+        same_state(a, b, stats=False)
+        a.static()
+        b.static()
+        same_state(a, b)
