@@ -84,7 +84,7 @@ enum {
   DFL_FLAG_TRACE = 2u    /* reserved */
 };
 
-/* Algorithm options; defaults from Section 4.1.2 of the paper. */
+/* Algorithm options; defaults from Section 5.1.2 of the paper. */
 typedef struct {
   uint32_t max_iterations; /* MAX_ITERATIONS per pass, default 20 */
   uint32_t max_passes;     /* MAX_PASSES, default 10 */
@@ -135,7 +135,7 @@ typedef struct {
 /* Fill *opt with the defaults above. */
 void dfl_default_options(dfl_options* opt);
 
-/* Create a handle from a symmetric CSR graph (Section 2: undirected, both
+/* Create a handle from a symmetric CSR graph (Section 3: undirected, both
  * arcs of every edge present with equal weights).  offsets[n+1] (uint64),
  * indices[nnz], weights[nnz]; rows must be sorted by neighbour id with no
  * duplicates and no self-loops; nnz = offsets[n].  The graph is copied into
@@ -159,7 +159,7 @@ int dfl_set_stream(dfl_handle* h, void* cuda_stream);
  * the pending batch. */
 int dfl_static(dfl_handle* h);
 
-/* Apply a batch update (Section 2.4): deletions first, then insertions,
+/* Apply a batch update (Section 3.4): deletions first, then insertions,
  * each edge given once.  Updates the graph, K, Sigma (with the current
  * membership C^{t-1}, Alg. 7) and 2m immediately, and appends the batch to
  * the pending list consumed by the next dfl_update.  Several calls may

@@ -82,7 +82,7 @@ struct BatchArc {
 };
 
 struct Options {
-  uint32_t max_iterations = 20;  // MAX_ITERATIONS (Section 4.1.2)
+  uint32_t max_iterations = 20;  // MAX_ITERATIONS (Section 5.1.2)
   uint32_t max_passes = 10;      // MAX_PASSES
   uint64_t tau_num = 1;          // iteration tolerance tau = tau_num/tau_den = 1e-2
   uint64_t tau_den = 100;
@@ -131,7 +131,7 @@ long find_arc(const std::vector<Arc>& row, uint32_t j) {
   return long(it - row.begin());
 }
 
-// K_i = sum_j w_ij (Section 2); a self-loop arc counts once.
+// K_i = sum_j w_ij (Section 3); a self-loop arc counts once.
 std::vector<int64_t> weighted_degrees(const Graph& G) {
   std::vector<int64_t> K(G.size(), 0);
   for (size_t i = 0; i < G.size(); ++i)
@@ -139,7 +139,7 @@ std::vector<int64_t> weighted_degrees(const Graph& G) {
   return K;
 }
 
-// Sigma_c = sum of K_i over the vertices of community c (Section 2).
+// Sigma_c = sum of K_i over the vertices of community c (Section 3.1).
 std::vector<int64_t> community_totals(const std::vector<uint32_t>& C,
                                       const std::vector<int64_t>& K, size_t labels) {
   std::vector<int64_t> S(labels, 0);

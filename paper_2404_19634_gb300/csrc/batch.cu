@@ -1,4 +1,4 @@
-// Batch update of the slack CSR (Section 2.4), incremental K and Sigma
+// Batch update of the slack CSR (Section 3.4), incremental K and Sigma
 // (Alg. 7), and marking of the initially affected vertices (Alg. 1 DF,
 // Alg. 2 ND, Alg. 3 DS).
 //

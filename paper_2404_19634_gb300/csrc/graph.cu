@@ -16,7 +16,7 @@ __host__ __device__ inline uint32_t slack_cap(uint32_t d) {
   return c > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(c);
 }
 
-// Warp per row: checks of Section 2's graph (undirected: both arcs with equal
+// Warp per row: checks of Section 3's graph (undirected: both arcs with equal
 // weights), plus sorted rows, no self-loops, no duplicates, weights > 0.
 __global__ void k_validate(uint32_t n, const unsigned long long* __restrict__ off,
                            const uint32_t* __restrict__ idx, const uint32_t* __restrict__ w,
@@ -88,7 +88,7 @@ __global__ void k_fill_rows(uint32_t n, const unsigned long long* __restrict__ o
   }
 }
 
-// K_i = sum_j w_ij (Section 2), warp per row; 2m accumulated in ctrl->red_a.
+// K_i = sum_j w_ij (Section 3), warp per row; 2m accumulated in ctrl->red_a.
 __global__ void k_weighted_degree(GraphView g, long long* __restrict__ K, Ctrl* ctrl) {
   const uint32_t lane = threadIdx.x & 31u;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;

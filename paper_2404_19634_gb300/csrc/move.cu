@@ -10,7 +10,7 @@
 //   except a singleton moving into a singleton community with a larger id.
 // A mover is recorded, its numerator score - stay is added to S, and its
 // neighbours (in the affected range) are marked for the next iteration
-// (Section 3.1: "mark neighbours as affected").  The commit kernel then
+// (Section 4.1: a mover makes its neighbours affected).  The commit kernel then
 // applies the class's moves to C', Sigma' and the sizes.
 #include "common.cuh"
 

@@ -5,7 +5,7 @@ form, and batch updates (edge deletions and insertions).  It holds none of the
 method's arithmetic (no degrees, no communities, no modularity), so it can
 feed both the CPU oracle and the GPU library without coupling them.
 
-Workload shapes follow the paper's evaluation (Section 4.1.3 and 4.1.4):
+Workload shapes follow the paper's evaluation (Sections 5.1.3 and 5.1.4):
 undirected graphs with unit weights, random batch updates made of 80%
 insertions between uniformly chosen vertex pairs and 20% deletions of
 uniformly chosen existing edges, and temporal streams loaded 90% as a base

@@ -1,7 +1,7 @@
 """Exact (rational) restatements of the paper's definitions, used to pin the
 oracle.  Plain Python over tiny graphs; no code shared with the oracle.
 
-Conventions (Section 2): each undirected edge is stored as two arcs (i, j)
+Conventions (Section 3): each undirected edge is stored as two arcs (i, j)
 and (j, i); a self-loop is one arc (i, i).  K_i is the sum of the weights of
 the arcs leaving i, and 2m the sum of all arc weights.
 """

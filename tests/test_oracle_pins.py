@@ -45,7 +45,7 @@ def test_modularity_equals_newman_all_pairs(oracle_mod, seed):
         q, qf = q_fraction(o)
         assert qf == newman_q(A, list(C))
         assert abs(q - float(qf)) <= 1e-15
-        assert Fraction(-1, 2) <= qf <= 1  # range stated in Section 2.2
+        assert Fraction(-1, 2) <= qf <= 1  # range stated in Section 3.2
 
 
 def test_modularity_special_cases(oracle_mod):
@@ -457,7 +457,7 @@ def test_delta_screening_choice_is_best_delta_modularity(oracle_mod, intra):
 
 
 def test_figure3_initial_frontier(oracle_mod):
-    """Fig. 3 (Section 3.1.1): deletion (1,2) inside the red community and
+    """Fig. 3 (Section 4.1.1): deletion (1,2) inside the red community and
     insertion (4,12) across red/blue make {1, 2, 4, 12} the initial frontier;
     in the first iteration vertex 2 moves to green, marking 8 and 10."""
     path = os.path.join(GOLDEN, "fig3_frontier.txt")
