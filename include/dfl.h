@@ -233,6 +233,36 @@ int dfl_move_iteration(dfl_handle* h, uint8_t* F, const uint8_t* R, uint8_t* mov
 int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets,
                   uint32_t* indices, uint64_t* weights);
 
+/* ---- Allocation-free entry point --------------------------------------- */
+
+/* Largest vertex count accepted by dfl_modularity_csr_noalloc. */
+#define DFL_NOALLOC_MAX_VERTICES (1u << 20)
+
+/* Modularity Q of a caller-supplied graph and membership, computed without
+ * allocating any memory (no cudaMalloc, cudaFree or allocating library call).
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run it -- e.g. a service whose
+ * device memory is owned by another allocator or fixed at start-up, or a
+ * latency-critical path where cudaMalloc/cudaFree would block or synchronize
+ * the device.  It computes the same Q, numerator and denominator as
+ * dfl_modularity does for a handle holding that graph and membership.
+ *   n: vertices, at most DFL_NOALLOC_MAX_VERTICES (else DFL_ERR_INVALID)
+ *   offsets[n+1] (uint64), indices[nnz], weights[nnz]: symmetric CSR in DEVICE
+ *   memory (both arcs of every edge); membership[n]: DEVICE memory, labels < n
+ *   q: HOST output; parts: optional HOST output {num_hi, num_lo, den_hi, den_lo}
+ *   cuda_stream: cudaStream_t the work is ordered on; returns when it is done.
+ * Errors: DFL_ERR_INVALID (n too large, a label or neighbour id >= n, null
+ * pointer), DFL_ERR_OVERFLOW (2m >= 2^32), DFL_ERR_CUDA.
+ * Its scratch (8 MiB of per-community totals plus a few counters) is a fixed
+ * array in the library's device memory, held by every GPU that loads the
+ * library until the process exits, and shared by all calls: each call clears
+ * it first, but calls whose GPU work overlaps race and must be serialized.
+ * The first call on a device also looks up that array's device address with
+ * the device current. */
+int dfl_modularity_csr_noalloc(uint32_t n, const uint64_t* offsets, const uint32_t* indices,
+                               const uint32_t* weights, const uint32_t* membership, double* q,
+                               int64_t* parts, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

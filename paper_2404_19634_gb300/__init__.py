@@ -128,7 +128,24 @@ _SIGS = {
     "dfl_louvain_from": (ct.c_int, [_P, _P, _P, ct.c_int]),
     "dfl_move_iteration": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
     "dfl_aggregate": (ct.c_int, [_P, ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint64), _P, _P, _P]),
+    "dfl_modularity_csr_noalloc": (ct.c_int, [ct.c_uint32, _P, _P, _P, _P, ct.POINTER(ct.c_double),
+                                              _P, _P]),
 }
+
+NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def modularity_csr_noalloc(n, offsets, indices, weights, membership, stream=None):
+    """dfl_modularity_csr_noalloc on CUDA tensors (offsets int64/uint64,
+    indices, weights and membership 32-bit).  Returns (rc, q, num, den)."""
+    lib = load()
+    q = ct.c_double()
+    parts = np.zeros(4, np.int64)
+    rc = lib.dfl_modularity_csr_noalloc(int(n), _buf(offsets, np.uint64)[0], _buf(indices, np.uint32)[0],
+                                        _buf(weights, np.uint32)[0], _buf(membership, np.uint32)[0],
+                                        ct.byref(q), parts.ctypes.data_as(ct.c_void_p),
+                                        _stream_ptr(stream))
+    return rc, q.value, _i128(int(parts[0]), int(parts[1])), _i128(int(parts[2]), int(parts[3]))
 
 
 def library_path() -> str:
