@@ -186,7 +186,10 @@ def gpu_arm(args):
     dfl.build()
     g, off, idx, w = make_workload(args, rank)
     size = batch_size(g, BATCH_FRAC)
-    stream = torch.cuda.current_stream()
+    # a side stream: the library replays its captured local-moving iteration
+    # (a CUDA graph) only on a non-default stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     opt = dfl.default_options(flags=dfl.FLAG_PROFILE)
     h = dfl.Dfl(g.n, off, idx, w, options=opt, stream=stream)
     torch.cuda.synchronize()
@@ -296,8 +299,6 @@ def gpu_arm(args):
     # membership (4 bytes per vertex) out, every step
     e2e = None
     if not args.profile_only:
-        pin_d = [torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory() for d, _ in batches]
-        pin_i = [torch.from_numpy(np.ascontiguousarray(i).view(np.int32)).pin_memory() for _, i in batches]
         out = torch.empty(g.n, dtype=torch.int32).pin_memory()
         e2e_batches = [bstream.next(size) for _ in range(args.steps)]
         pin_d = [torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory() for d, _ in e2e_batches]

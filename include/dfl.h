@@ -81,7 +81,10 @@ enum {
 /* Option flags. */
 enum {
   DFL_FLAG_PROFILE = 1u, /* time every kernel class with CUDA events (dfl_profile) */
-  DFL_FLAG_TRACE = 2u    /* reserved */
+  DFL_FLAG_TRACE = 2u,   /* reserved */
+  DFL_FLAG_NO_GRAPH = 4u /* launch every kernel from the host instead of replaying the captured
+                            local-moving iteration (a CUDA graph, used on the first pass when the
+                            handle's stream is not the legacy default stream) */
 };
 
 /* Algorithm options; defaults from Section 5.1.2 of the paper. */

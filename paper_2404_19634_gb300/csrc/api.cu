@@ -90,6 +90,8 @@ int alloc(Handle* h, T** p, uint64_t count) {
 }
 
 void free_all(Handle* h) {
+  destroy_iteration_graph(h, 0);
+  destroy_iteration_graph(h, 1);
   void* ptrs[] = {h->off, h->deg, h->cap, h->srt, h->ntomb, h->b_newtomb, h->b_cum, h->b_rebuild, h->arcs, h->K, h->Sigma, h->csize, h->C, h->pend_key,
                   h->pend_w, h->Ctop, h->Cs, h->Ks, h->Ss, h->sizes, h->used, h->cnt, h->tdeg,
                   h->fillc, h->members, h->fbits[0], h->fbits[1], h->rbits, h->ever, h->lists[0],

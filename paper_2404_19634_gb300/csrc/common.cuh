@@ -71,6 +71,7 @@ struct Ctrl {
   unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
   unsigned long long ever_count;     // vertices newly added to the first-pass processed set
   unsigned int giant_chunks[2];      // chunk work items of the largest bin (per buffer parity)
+  long long m2v;                     // 2m of the current local-moving call
   unsigned long long pool_top;       // first free arc slot of the pool
   unsigned long long scratch_top;
   // misc reductions
@@ -225,6 +226,15 @@ struct Handle {
     int cls;
   };
   std::vector<Ev> ev_pending;
+  // captured local-moving iteration per list-buffer parity (base graph only)
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> key;
+    std::vector<Ev> evs;
+    uint64_t kernels = 0;
+    uint64_t class_launches[DFL_PROF_CLASSES] = {0};
+  };
+  IterGraph igraph[2];
   std::vector<cudaEvent_t> ev_free;
   dfl_profile_t prof;
 };
@@ -382,6 +392,7 @@ struct MoveArgs {
   bool use_range;
   bool track_ever;
 };
+void destroy_iteration_graph(Handle* h, int cur);
 int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial = nullptr, uint64_t* ever = nullptr);
 

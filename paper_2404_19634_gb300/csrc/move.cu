@@ -12,6 +12,8 @@
 // neighbours (in the affected range) are marked for the next iteration
 // (Section 4.1: a mover makes its neighbours affected).  The commit kernel then
 // applies the class's moves to C', Sigma' and the sizes.
+#include <cstring>
+
 #include "common.cuh"
 
 namespace dfl {
@@ -24,7 +26,7 @@ struct DecideArgs {
   const long long* K;
   const long long* Sigma;
   const int* size;
-  long long m2;
+  const long long* m2p;   // 2m, read from device memory so captured graphs stay valid
   const uint32_t* list;
   const unsigned int* count;
   uint32_t* fbits_next;
@@ -43,11 +45,11 @@ struct DecideArgs {
 };
 
 // Outcome of one vertex's decision, identical on every lane / thread.
-__device__ __forceinline__ bool decide_move(const DecideArgs& a, uint32_t i, uint32_t d, long long Ki,
-                                            bool have, i128 best, uint32_t bc, unsigned long long Hd,
-                                            i128* gain) {
+__device__ __forceinline__ bool decide_move(const DecideArgs& a, long long m2, uint32_t i, uint32_t d,
+                                            long long Ki, bool have, i128 best, uint32_t bc,
+                                            unsigned long long Hd, i128* gain) {
   if (!have) return false;
-  i128 stay = (i128)a.m2 * (i128)Hd - (i128)Ki * (i128)(a.Sigma[d] - Ki);
+  i128 stay = (i128)m2 * (i128)Hd - (i128)Ki * (i128)(a.Sigma[d] - Ki);
   if (!(best > stay)) return false;
   if (a.size[d] == 1 && a.size[bc] == 1 && bc > d) return false;  // singleton-swap guard
   *gain = best - stay;
@@ -79,6 +81,7 @@ __device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool 
 // community with match/reduce in registers.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
+  const long long m2 = *a.m2p;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -104,12 +107,12 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
     bool cand = leader && c != d;
     unsigned cm = __ballot_sync(0xFFFFFFFFu, cand);
     i128 score = 0;
-    if (cand) score = (i128)a.m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
+    if (cand) score = (i128)m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
     bool have = cand;
     uint32_t bc = c;
     warp_argmax(have, score, bc);
     i128 gain = 0;
-    bool mv = decide_move(a, i, d, Ki, have, score, bc, Hd, &gain);
+    bool mv = decide_move(a, m2, i, d, Ki, have, score, bc, Hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * __popc(cm);
     if (mv) {
       if (lane == 0) record_move(a, i, bc, d, gain);
@@ -182,6 +185,7 @@ constexpr uint32_t kWarpSlots = 512;
 constexpr int kWarpHashWarps = 8;
 
 __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
+  const long long m2 = *a.m2p;
   __shared__ uint32_t skeys[kWarpHashWarps][kWarpSlots];
   __shared__ uint32_t svals[kWarpHashWarps][kWarpSlots];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
         continue;
       }
       ++ncand;
-      i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+      i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
       if (!have || sc > best || (sc == best && c < bc)) {
         have = true;
         best = sc;
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
     }
     warp_argmax(have, best, bc);
     i128 gain = 0;
-    bool mv = decide_move(a, i, d, Ki, have, best, bc, Hd, &gain);
+    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * ncand;
     if (mv) {
       if (lane == 0) record_move(a, i, bc, d, gain);
@@ -268,6 +272,7 @@ constexpr uint32_t kBlockSlots = 2 * kBinBlock;  // 8192 keys + 8192 values = 64
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
+  const long long m2 = *a.m2p;
   extern __shared__ uint32_t dyn[];
   __shared__ unsigned long long s_hd;
   __shared__ uint32_t s_ncand;
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
         continue;
       }
       ++ncand;
-      i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+      i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
       if (!have || sc > best || (sc == best && c < bc)) {
         have = true;
         best = sc;
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
     best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
     bc = s_c[0];
     i128 gain = 0;
-    bool mv = decide_move(a, i, d, Ki, have, best, bc, s_hd, &gain);
+    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
       if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
@@ -473,6 +478,7 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
 }
 
 __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a, GiantDecide gd) {
+  const long long m2 = *a.m2p;
   extern __shared__ uint32_t dyn[];
   uint32_t* keys = dyn;
   uint32_t* vals = dyn + kGiantSlots;
@@ -564,7 +570,7 @@ __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a,
           continue;
         }
         ++ncand;
-        i128 sc = (i128)a.m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
+        i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
         if (!have || sc > best || (sc == best && c < bc)) {
           have = true;
           best = sc;
@@ -598,7 +604,7 @@ __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a,
           continue;
         }
         ++ncand;
-        i128 sc = (i128)a.m2 * (i128)gv[s] - (i128)Ki * (i128)a.Sigma[c];
+        i128 sc = (i128)m2 * (i128)gv[s] - (i128)Ki * (i128)a.Sigma[c];
         if (!have || sc > best || (sc == best && c < bc)) {
           have = true;
           best = sc;
@@ -637,7 +643,7 @@ __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a,
     best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
     bc = s_c[0];
     i128 gain = 0;
-    bool mv = decide_move(a, i, d, Ki, have, best, bc, s_hd, &gain);
+    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
       if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
@@ -705,37 +711,196 @@ uint32_t next_pow2(uint64_t x) {
   return uint32_t(p);
 }
 
+
+
+__global__ void k_set_m2(Ctrl* ctrl, long long m2) { ctrl->m2v = m2; }
+
+constexpr uint32_t kGiantBlocks = 2 * 152;
+
+// Issue one local-moving iteration (all sub-steps) on h->stream.  With
+// `counts` (host-known list lengths) empty bins are skipped and grids are
+// sized to the work; without (graph capture) every bin is launched with a
+// fixed grid and reads its length on the device.
+int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*counts)[kBins],
+                    const GiantDecide& gd_base) {
+  const uint32_t k = a.k;
+  const int nxt = cur ^ 1;
+  // reset the iteration's sums and the next buffer's list lengths
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
+  a.fbits_next = h->fbits[nxt];
+  a.next_lists = h->lists[nxt];
+  a.next_buf = nxt;
+  for (uint32_t s = 0; s < k; ++s) {
+    // the degree bins of one class are independent: the larger ones run on
+    // auxiliary streams, concurrently with the rest
+    int nb = 0;
+    for (int b = 0; b < kBins; ++b) nb += (!counts || counts[s][b]) ? 1 : 0;
+    const bool any = nb > 0;
+    cudaEvent_t pa = nullptr, pb = nullptr;  // wall time of the decide phase (profiling)
+    if (any && (h->opt.flags & DFL_FLAG_PROFILE)) {
+      cudaEventCreate(&pa);
+      cudaEventCreate(&pb);
+      cudaEventRecord(pa, h->stream);
+    }
+    const bool forked = nb > 1;
+    if (forked) DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    bool joined[kBins - 1] = {false, false, false};
+    for (int b = kBins - 1; b >= 0; --b) {
+      const uint32_t c = counts ? counts[s][b] : 0u;
+      if (counts && !c) continue;
+      cudaStream_t st = h->stream;
+      if (forked && b > 0) {
+        st = h->aux[b - 1];
+        DFL_CUDA(h, cudaStreamWaitEvent(st, h->ev_fork, 0));
+        joined[b - 1] = true;
+      }
+      a.list = h->lists[cur] + h->segs.off[s * kBins + b];
+      a.count = &h->ctrl->count[cur][s][b];
+      LaunchScope ls(h, DFL_PROF_BIN0 + b, st);
+      if (b == 0) {
+        k_decide_warp<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 64) : 152 * 8, 256, 0, st>>>(a);
+      } else if (b == 1) {
+        k_decide_warp_hash<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 16) : 152 * 4, 256, 0, st>>>(a);
+      } else if (b == 2) {
+        k_decide_block<256><<<counts ? grid_for(c, 1, 152 * 3) : 152 * 3, 256,
+                              sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
+      } else {
+        GiantDecide gd = gd_base;
+        gd.nitems = &h->ctrl->giant_chunks[cur];
+        k_giant_prefix<<<1, 1024, 0, st>>>(a, gd);
+        DFL_TRY(check_launch(h, "giant prefix"));
+        k_decide_giant<<<kGiantBlocks, kGiantThreads, sizeof(uint32_t) * 2 * kGiantSlots, st>>>(a, gd);
+      }
+      DFL_TRY(check_launch(h, "decide"));
+    }
+    for (int b = 0; b < kBins - 1; ++b)
+      if (joined[b]) {
+        DFL_CUDA(h, cudaEventRecord(h->ev_join[b], h->aux[b]));
+        DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
+      }
+    if (pa && pb) {
+      cudaEventRecord(pb, h->stream);
+      h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
+      h->prof.launches[DFL_PROF_MOVE]++;
+    }
+    if (any) {
+      {
+        LaunchScope ls(h, DFL_PROF_COMMIT);
+        k_commit<<<152 * 2, 256, 0, h->stream>>>(h->mv_i, h->mv_c, h->mv_d, const_cast<uint32_t*>(a.C), a.K,
+                                                 const_cast<long long*>(a.Sigma), const_cast<int*>(a.size),
+                                                 h->ctrl);
+        DFL_TRY(check_launch(h, "commit"));
+      }
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+    }
+  }
+  // the processed frontier's bitmap becomes the next-next target
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
+  return DFL_OK;
+}
+
+// Everything an iteration graph bakes in; a different key means re-capture.
+struct GraphKey {
+  DecideArgs a;
+  GiantDecide gd;
+  int cur;
+  uint32_t flags;
+  void* stream;
+};
+
+int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd, int cur) {
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.a = a;
+  key.gd = gd;
+  key.cur = cur;
+  key.flags = h->opt.flags;
+  key.stream = h->stream;
+  Handle::IterGraph& g = h->igraph[cur];
+  if (g.exec && g.key.size() == sizeof(key) && std::memcmp(g.key.data(), &key, sizeof(key)) == 0)
+    return DFL_OK;
+  destroy_iteration_graph(h, cur);
+  const size_t ev0 = h->ev_pending.size();
+  const uint64_t l0 = h->launches;
+  uint64_t cl0[DFL_PROF_CLASSES];
+  for (int q = 0; q < DFL_PROF_CLASSES; ++q) cl0[q] = h->prof.launches[q];
+  DFL_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = issue_iteration(h, a, cur, nullptr, gd);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return set_error(h, DFL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g.exec = nullptr;
+    return set_error(h, DFL_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  // events recorded inside the graph are harvested after every replay
+  g.evs.assign(h->ev_pending.begin() + ev0, h->ev_pending.end());
+  h->ev_pending.resize(ev0);
+  g.kernels = h->launches - l0;
+  h->launches = l0;
+  for (int q = 0; q < DFL_PROF_CLASSES; ++q) {  // counted per replay instead
+    g.class_launches[q] = h->prof.launches[q] - cl0[q];
+    h->prof.launches[q] = cl0[q];
+  }
+  g.key.assign(reinterpret_cast<const char*>(&key), reinterpret_cast<const char*>(&key) + sizeof(key));
+  return DFL_OK;
+}
+
 }  // namespace
+
+void destroy_iteration_graph(Handle* h, int cur) {
+  Handle::IterGraph& g = h->igraph[cur];
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& ev : g.evs) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  g.evs.clear();
+  g.key.clear();
+  g.exec = nullptr;
+  g.kernels = 0;
+}
 
 int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial, uint64_t* ever) {
   const uint32_t k = h->opt.substeps;
   make_segs(h, k);
   const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
-  DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
-  unsigned long long skipped = h->hctrl->skipped;  // isolated frontier vertices
-  if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
-  if (initial) {
-    *initial = skipped;
-    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
-      for (int b = 0; b < kBins; ++b) *initial += h->hctrl->count[0][s][b];
-  }
+  // graph replay of the iterations needs stable buffers (the base graph) and
+  // a capturable (non-default) stream
+  const bool use_graph = ma.g.off == h->off && h->stream != nullptr &&
+                         !(h->opt.flags & DFL_FLAG_NO_GRAPH);
   unsigned int cur_count[kMaxSubsteps][kBins];
-  for (uint32_t s = 0; s < kMaxSubsteps; ++s)
-    for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
+  unsigned long long skipped = 0;
+  bool have_counts = false;
+  if (!use_graph) {
+    DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
+    if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
+    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+      for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
+    skipped = h->hctrl->skipped;
+    have_counts = true;
+  }
   // global tables for the largest bin: one slice of gslots keys + gslots
   // values per block, gslots >= 2 * (max degree of the current graph)
-  const uint32_t gblocks = 2 * 152;
   const uint32_t gslots = next_pow2(2ull * (ma.max_deg > kBinBlock ? ma.max_deg : kBinBlock));
-  if (ma.max_deg > kBinBlock && uint64_t(gblocks) * gslots > h->gtable_cap) {
+  if (ma.max_deg > kBinBlock && uint64_t(kGiantBlocks) * gslots > h->gtable_cap) {
     if (h->gtable) {
       cudaStreamSynchronize(h->stream);
       cudaFree(h->gtable);
       h->gtable = nullptr;
       h->gtable_cap = 0;
     }
-    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(gblocks) * gslots));
-    h->gtable_cap = uint64_t(gblocks) * gslots;
+    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(kGiantBlocks) * gslots));
+    h->gtable_cap = uint64_t(kGiantBlocks) * gslots;
   }
   static bool smem_set = false;
   if (!smem_set) {
@@ -788,104 +953,65 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   }
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->move_bytes, 0, sizeof(unsigned long long), h->stream));
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->ever_count, 0, sizeof(unsigned long long), h->stream));
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_set_m2<<<1, 1, 0, h->stream>>>(h->ctrl, ma.m2);
+    DFL_TRY(check_launch(h, "set m2"));
+  }
+  DecideArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = ma.g;
+  a.C = ma.C;
+  a.K = ma.K;
+  a.Sigma = ma.Sigma;
+  a.size = ma.size;
+  a.m2p = &h->ctrl->m2v;
+  a.seg = h->segs;
+  a.rbits = ma.use_range ? h->rbits : nullptr;
+  a.ever = ma.track_ever ? h->ever : nullptr;
+  a.mv_i = h->mv_i;
+  a.mv_c = h->mv_c;
+  a.mv_d = h->mv_d;
+  a.ctrl = h->ctrl;
+  a.k = k;
+  a.gtable = h->gtable;
+  a.gslots = gslots;
+  GiantDecide gd{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial, nullptr};
   int cur = 0;
   uint32_t it = 0;
   while (it < h->opt.max_iterations) {
     ++it;
     const int nxt = cur ^ 1;
-    // reset the iteration's sums and the next buffer's list lengths
-    DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
-    DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
-    DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
-    DecideArgs a;
-    a.g = ma.g;
-    a.C = ma.C;
-    a.K = ma.K;
-    a.Sigma = ma.Sigma;
-    a.size = ma.size;
-    a.m2 = ma.m2;
-    a.fbits_next = h->fbits[nxt];
-    a.next_lists = h->lists[nxt];
-    a.seg = h->segs;
-    a.next_buf = nxt;
-    a.rbits = ma.use_range ? h->rbits : nullptr;
-    a.ever = ma.track_ever ? h->ever : nullptr;
-    a.mv_i = h->mv_i;
-    a.mv_c = h->mv_c;
-    a.mv_d = h->mv_d;
-    a.ctrl = h->ctrl;
-    a.k = k;
-    a.gtable = h->gtable;
-    a.gslots = gslots;
-    for (uint32_t s = 0; s < k; ++s) {
-      // the degree bins of one class are independent: the largest ones run
-      // on auxiliary streams, concurrently with the rest
-      int nb = 0;
-      for (int b = 0; b < kBins; ++b) nb += cur_count[s][b] ? 1 : 0;
-      const bool any = nb > 0;
-      // wall time of the sub-step's decide phase (profiling only)
-      cudaEvent_t pa = nullptr, pb = nullptr;
-      if (any && (h->opt.flags & DFL_FLAG_PROFILE)) {
-        cudaEventCreate(&pa);
-        cudaEventCreate(&pb);
-        cudaEventRecord(pa, h->stream);
-      }
-      bool forked = false;
-      if (nb > 1) {
-        DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
-        forked = true;
-      }
-      bool joined[kBins - 1] = {false, false, false};
-      for (int b = kBins - 1; b >= 0; --b) {
-        uint32_t c = cur_count[s][b];
-        if (!c) continue;
-        cudaStream_t st = h->stream;
-        if (forked && b > 0) {
-          st = h->aux[b - 1];
-          DFL_CUDA(h, cudaStreamWaitEvent(st, h->ev_fork, 0));
-          joined[b - 1] = true;
-        }
-        a.list = h->lists[cur] + h->segs.off[s * kBins + b];
-        a.count = &h->ctrl->count[cur][s][b];
-        LaunchScope ls(h, DFL_PROF_BIN0 + b, st);
-        if (b == 0) {
-          k_decide_warp<<<grid_for(uint64_t(c) * 32, 256, 152 * 64), 256, 0, st>>>(a);
-        } else if (b == 1) {
-          k_decide_warp_hash<<<grid_for(uint64_t(c) * 32, 256, 152 * 16), 256, 0, st>>>(a);
-        } else if (b == 2) {
-          k_decide_block<256><<<grid_for(c, 1, 152 * 3), 256, sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
-        } else {
-          GiantDecide gd{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial,
-                         &h->ctrl->giant_chunks[cur]};
-          k_giant_prefix<<<1, 1024, 0, st>>>(a, gd);
-          DFL_TRY(check_launch(h, "giant prefix"));
-          k_decide_giant<<<gblocks, kGiantThreads, sizeof(uint32_t) * 2 * kGiantSlots, st>>>(a, gd);
-        }
-        DFL_TRY(check_launch(h, "decide"));
-      }
-      for (int b = 0; b < kBins - 1; ++b)
-        if (joined[b]) {
-          DFL_CUDA(h, cudaEventRecord(h->ev_join[b], h->aux[b]));
-          DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
-        }
-      if (pa && pb) {
-        cudaEventRecord(pb, h->stream);
-        h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
-        h->prof.launches[DFL_PROF_MOVE]++;
-      }
-      if (any) {
-        {
-          LaunchScope ls(h, DFL_PROF_COMMIT);
-          k_commit<<<152 * 2, 256, 0, h->stream>>>(h->mv_i, h->mv_c, h->mv_d, ma.C, ma.K, ma.Sigma,
-                                                   ma.size, h->ctrl);
-          DFL_TRY(check_launch(h, "commit"));
-        }
-        DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
-      }
+    if (use_graph) {
+      DFL_TRY(ensure_iteration_graph(h, a, gd, cur));
+      const Handle::IterGraph& g = h->igraph[cur];
+      DFL_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
+      h->launches += g.kernels;
+      for (int q = 0; q < DFL_PROF_CLASSES; ++q) h->prof.launches[q] += g.class_launches[q];
+    } else {
+      DFL_TRY(issue_iteration(h, a, cur, cur_count, gd));
     }
     DFL_TRY(read_ctrl(h));
     const Ctrl& c = *h->hctrl;
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
+    if (use_graph) {
+      for (const auto& ev : h->igraph[cur].evs) {  // harvest this replay's timings
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) h->prof.ms[ev.cls] += ms;
+      }
+      if (it == 1) {
+        skipped = c.skipped;
+        if (initial) {
+          *initial = skipped;
+          for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+            for (int b = 0; b < kBins; ++b) *initial += c.count[0][s][b];
+        }
+      }
+    } else if (it == 1 && initial) {
+      *initial = skipped;
+      for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+        for (int b = 0; b < kBins; ++b) *initial += cur_count[s][b];
+    }
     u128 S = ((u128)c.s_hi << 32) + (u128)c.s_lo;
     if (record_trace) {
       h->trace.push_back(c.processed + skipped);
@@ -893,9 +1019,9 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
       h->trace.push_back(uint64_t(S >> 64));
       h->trace.push_back(uint64_t(S));
     }
-    DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
-    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
-      for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
+    if (have_counts)
+      for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+        for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
     cur = nxt;
     skipped = 0;
     if (S <= threshold) break;  // locally converged

@@ -32,10 +32,20 @@ def orc():
     return oracle
 
 
-def pair(dfl, orc, g, substeps=4, tau_agg=0.8, **kw):
+_STREAMS = []
+
+
+def pair(dfl, orc, g, substeps=4, tau_agg=0.8, graph=True, **kw):
+    """GPU handle and oracle on the same graph.  The handle runs on a side
+    stream, which lets it replay its captured local-moving iteration; with
+    graph=False every kernel is launched from the host."""
+    import torch
     off, idx, w = synth.to_csr(g)
-    opt = dfl.default_options(substeps=substeps, tau_agg=tau_agg, **kw)
-    a = dfl.Dfl(g.n, off, idx, w, options=opt)
+    flags = kw.pop("flags", 0) | (0 if graph else 4)  # 4 = DFL_FLAG_NO_GRAPH
+    opt = dfl.default_options(substeps=substeps, tau_agg=tau_agg, flags=flags, **kw)
+    s = torch.cuda.Stream()
+    _STREAMS.append(s)
+    a = dfl.Dfl(g.n, off, idx, w, options=opt, stream=s)
     b = orc.Oracle(g.n, off, idx, w)
     b.set_options(substeps=substeps, tau_agg=tau_agg,
                   **{k: v for k, v in kw.items() if k in ("max_iterations", "max_passes")})
@@ -78,13 +88,14 @@ def test_static_sbm_10k(dfl, orc):
     same_graph(a, b)
 
 
+@pytest.mark.parametrize("graph", [True, False])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_sbm_batch_update(dfl, orc, mode):
+def test_sbm_batch_update(dfl, orc, mode, graph):
     """10,000-vertex SBM, static, then one 100-edge batch (80% insertions,
     20% deletions) updated with ND, DS or DF."""
     g = synth.sbm(10000, 50, 0.02, 0.0002, 1)
     dels, ins = synth.random_batch(g.n, g, 80, 20, 11)
-    a, b = pair(dfl, orc, g)
+    a, b = pair(dfl, orc, g, graph=graph)
     a.static()
     b.static()
     assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
@@ -98,11 +109,12 @@ def test_sbm_batch_update(dfl, orc, mode):
     same_state(a, b)
 
 
+@pytest.mark.parametrize("graph", [True, False])
 @pytest.mark.parametrize("substeps", [1, 2, 4, 8])
 @pytest.mark.parametrize("scale", [10, 13])
-def test_rmat_stream(dfl, orc, substeps, scale):
+def test_rmat_stream(dfl, orc, substeps, scale, graph):
     g = synth.rmat(scale, 8 << scale, 30 + scale)
-    a, b = pair(dfl, orc, g, substeps=substeps)
+    a, b = pair(dfl, orc, g, substeps=substeps, graph=graph)
     a.static()
     b.static()
     same_state(a, b)
@@ -141,7 +153,8 @@ def test_weighted_graph_partial_deletions(dfl, orc):
         same_state(a, b)
 
 
-def test_high_degree_bins(dfl, orc):
+@pytest.mark.parametrize("graph", [True, False])
+def test_high_degree_bins(dfl, orc, graph):
     """Hubs of degree ~300, ~5,000 and ~20,000 exercise the block kernels
     with shared-memory and global-memory tables."""
     rng = np.random.default_rng(8)
@@ -160,7 +173,7 @@ def test_high_degree_bins(dfl, orc):
     g = synth.EdgeList(n, (key >> np.uint64(32)).astype(np.uint32),
                        (key & np.uint64(0xFFFFFFFF)).astype(np.uint32),
                        np.ones(key.shape[0], np.uint32))
-    a, b = pair(dfl, orc, g)
+    a, b = pair(dfl, orc, g, graph=graph)
     a.static()
     b.static()
     same_state(a, b)
