@@ -21,6 +21,15 @@ int check_launch(Handle* h, const char* what) {
   return DFL_OK;
 }
 
+// Record a timing event; inside a stream capture it must become an event
+// record node of the graph (an external record), not a dependency marker.
+cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
+}
+
 LaunchScope::LaunchScope(Handle* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
   h->launches++;
   h->prof.launches[cls]++;
@@ -35,13 +44,13 @@ LaunchScope::LaunchScope(Handle* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls
       }
       (k ? b : a) = e;
     }
-    if (a) cudaEventRecord(a, s);
+    if (a) record_timing_event(a, s);
   }
 }
 
 LaunchScope::~LaunchScope() {
   if (a && b) {
-    cudaEventRecord(b, s);
+    record_timing_event(b, s);
     h->ev_pending.push_back(Handle::Ev{a, b, cls});
   } else {
     if (a) h->ev_free.push_back(a);

@@ -272,6 +272,7 @@ struct LaunchScope {
 };
 
 int check_launch(Handle* h, const char* what);
+cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device helpers

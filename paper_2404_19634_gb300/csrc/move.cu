@@ -742,7 +742,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     if (any && (h->opt.flags & DFL_FLAG_PROFILE)) {
       cudaEventCreate(&pa);
       cudaEventCreate(&pb);
-      cudaEventRecord(pa, h->stream);
+      record_timing_event(pa, h->stream);
     }
     const bool forked = nb > 1;
     if (forked) DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -781,7 +781,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
         DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
       }
     if (pa && pb) {
-      cudaEventRecord(pb, h->stream);
+      record_timing_event(pb, h->stream);
       h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
       h->prof.launches[DFL_PROF_MOVE]++;
     }

@@ -450,3 +450,22 @@ def test_giant_vertex_many_distinct_communities(dfl, orc):
         a.static()
         b.static()
         same_state(a, b)
+
+
+def test_profiled_graph_replay(dfl, orc):
+    """Profiling events inside the captured iteration graph are recorded and
+    harvested; results stay identical."""
+    g = synth.rmat(12, 8 << 12, 5)
+    a, b = pair(dfl, orc, g, flags=1)  # DFL_FLAG_PROFILE
+    a.static()
+    b.static()
+    stream = synth.BatchStream(g, 6)
+    for _ in range(3):
+        d, i = stream.next(200)
+        a.apply_batch(d, i)
+        b.apply_batch(d, i)
+        a.update(2)
+        b.update(2)
+        same_state(a, b)
+    prof = a.profile()
+    assert prof["move"]["ms"] > 0 and prof["move"]["bytes"] > 0 and prof["bin0"]["launches"] > 0
