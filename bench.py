@@ -339,6 +339,8 @@ def gpu_arm(args):
                        "static_move_gbs": round(static_gbs, 1) if static_gbs else None,
                        "df_ms_by_batch_fraction": extra or None,
                        "step_ms_median": round(statistics.median(step_ms), 4),
+                       "graph_captures": h.stats()["graph_captures"],
+                       "graph_capture_ms": round(h.stats()["graph_capture_ms"], 2),
                        "kernel_ms_per_step": kernel_share},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -110,6 +110,8 @@ typedef struct {
   uint64_t arc_pool;           /* arc slots allocated for the slack CSR */
   uint32_t max_degree;         /* largest vertex degree of G^t (upper bound) */
   uint32_t num_communities;    /* distinct labels of the last first-pass membership */
+  uint64_t graph_captures;     /* local-moving iteration graphs captured since creation */
+  double graph_capture_ms;     /* host time spent capturing and instantiating them */
 } dfl_stats_t;
 
 /* Per kernel class timing and algorithmic traffic (DFL_FLAG_PROFILE). */

@@ -93,7 +93,8 @@ class Stats(ct.Structure):
                 ("affected_initial", ct.c_uint64), ("affected_ever", ct.c_uint64),
                 ("kernel_launches", ct.c_uint64), ("num_arcs", ct.c_uint64),
                 ("arc_pool", ct.c_uint64), ("max_degree", ct.c_uint32),
-                ("num_communities", ct.c_uint32)]
+                ("num_communities", ct.c_uint32), ("graph_captures", ct.c_uint64),
+                ("graph_capture_ms", ct.c_double)]
 
 
 class Profile(ct.Structure):
@@ -316,7 +317,8 @@ class Dfl:
                 "affected_initial": s.affected_initial, "affected_ever": s.affected_ever,
                 "kernel_launches": s.kernel_launches, "num_arcs": s.num_arcs,
                 "arc_pool": s.arc_pool, "max_degree": s.max_degree,
-                "num_communities": s.num_communities}
+                "num_communities": s.num_communities, "graph_captures": s.graph_captures,
+                "graph_capture_ms": s.graph_capture_ms}
 
     def profile(self, reset: bool = False) -> dict:
         p = Profile()

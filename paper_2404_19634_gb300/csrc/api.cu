@@ -99,8 +99,8 @@ int alloc(Handle* h, T** p, uint64_t count) {
 }
 
 void free_all(Handle* h) {
-  destroy_iteration_graph(h, 0);
-  destroy_iteration_graph(h, 1);
+  for (auto& row : h->igraph)
+    for (auto& g : row) destroy_iteration_graph(g);
   void* ptrs[] = {h->off, h->deg, h->cap, h->srt, h->ntomb, h->b_newtomb, h->b_cum, h->b_rebuild, h->arcs, h->K, h->Sigma, h->csize, h->C, h->pend_key,
                   h->pend_w, h->Ctop, h->Cs, h->Ks, h->Ss, h->sizes, h->used, h->cnt, h->tdeg,
                   h->fillc, h->members, h->fbits[0], h->fbits[1], h->rbits, h->ever, h->lists[0],
@@ -108,6 +108,9 @@ void free_all(Handle* h) {
                   h->b_key2, h->b_w2, h->b_rowlist, h->b_pos, h->b_wnew, h->b_flag, h->b_delta,
                   h->b_newdeg, h->b_edges, h->scratch, h->tmp, h->gtable, h->ctrl,
                   h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial,
+                  h->h_keys, h->h_ndel, h->h_wdel, h->h_wins, h->h_slot, h->h_wnew, h->h_flag,
+                  h->h_delta, h->h_pairs, h->r_app, h->r_tomb, h->r_live, h->r_state, h->r_reg,
+                  h->h_rows, h->h_extra,
                   h->sg[0].off, h->sg[0].deg, h->sg[0].arcs, h->sg[1].off, h->sg[1].deg,
                   h->sg[1].arcs};
   for (void* p : ptrs)
@@ -411,6 +414,8 @@ int dfl_stats(dfl_handle* h, dfl_stats_t* s) {
   s->num_arcs = h->num_arcs;
   s->arc_pool = h->pool_cap;
   s->max_degree = h->max_deg;
+  s->graph_captures = h->graph_captures;
+  s->graph_capture_ms = h->graph_capture_ms;
   return DFL_OK;
 }
 

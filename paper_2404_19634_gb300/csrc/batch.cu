@@ -11,6 +11,9 @@
 
 namespace dfl {
 
+int apply_batch_sorted(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                       int mem_kind);
+
 namespace {
 
 // Slack-CSR row layout: arcs [0, srt) are sorted by neighbour, arcs
@@ -504,6 +507,348 @@ __global__ void k_ds_comm(uint32_t n, const uint32_t* __restrict__ C, const uint
   }
 }
 
+// ---------------------------------------------------------------------------
+// Hashed batch apply.  Arcs are grouped by (u, v) in an open-addressing table
+// (no sort); a new arc's tail position comes from a per-row counter (the tail
+// is unsorted, so the order does not matter); only rebuilt rows need their
+// new arcs sorted, which a block does in shared memory.  Per-vertex scratch
+// counters are zero at rest and reset for the touched rows at the end.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kExtraMax = 4096;   // new arcs of one rebuilt row sorted in shared memory
+constexpr unsigned long long kNoKey = ~0ull;
+
+struct HashApply {
+  unsigned long long* keys;   // (u << 32 | v), kNoKey = empty
+  uint32_t* ndel;             // deletions of the pair
+  uint32_t* wdel;             // their weight (0 = whole edge)
+  unsigned long long* wins;   // summed inserted weight
+  uint32_t* slot;             // row slot of the pair (found) or append rank
+  uint32_t* wnew;
+  uint32_t* flag;
+  long long* delta;
+  uint32_t* pairs;            // occupied table slots, in claim order
+  uint64_t mask;
+  // per-vertex scratch
+  uint32_t* r_app;            // appends of the row (then: rank counter)
+  int* r_tomb;                // tombstone change
+  int* r_live;                // live-arc change
+  uint32_t* r_state;          // 0 untouched, 1 touched, 2 rebuilt
+  uint32_t* r_reg;            // rebuilt row: offset of its new arcs in `extra`
+  uint32_t* rows;             // touched rows, in touch order
+  uint2* extra;               // new arcs of rebuilt rows
+};
+
+__device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Thread per edge: both arcs into the table; arcs also staged (key format of
+// the pending list) for the frontier marking of the next update.
+__global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
+                              KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
+                              uint32_t* __restrict__ w, Ctrl* ctrl) {
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < ne;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    dfl_edge x = e[q];
+    const bool ins = q >= nd;
+    if (x.u >= n || x.v >= n || x.u == x.v || (ins && x.w == 0)) {
+      atomicOr(&ctrl->err, kErrInvalid);
+      key[2 * q] = key[2 * q + 1] = 0;
+      w[2 * q] = w[2 * q + 1] = 0;
+      continue;
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      const uint32_t a = dir ? x.v : x.u, b = dir ? x.u : x.v;
+      key[2 * q + dir] = ((unsigned long long)a << (f.b + 1)) | ((unsigned long long)b << 1) |
+                         (ins ? 1ull : 0ull);
+      w[2 * q + dir] = x.w;
+      const unsigned long long k = ((unsigned long long)a << 32) | b;
+      uint64_t s = hash64(k) & t.mask;
+      for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+        unsigned long long prev = t.keys[s];
+        if (prev == kNoKey) {
+          prev = atomicCAS(&t.keys[s], kNoKey, k);
+          if (prev == kNoKey) {
+            t.pairs[atomicAdd(&ctrl->npairs, 1u)] = uint32_t(s);
+            prev = k;
+          }
+        }
+        if (prev == k) {
+          if (ins) {
+            atomicAdd(&t.wins[s], (unsigned long long)x.w);
+          } else {
+            atomicAdd(&t.ndel[s], 1u);
+            t.wdel[s] = x.w;  // several deletions of one pair are an error anyway
+          }
+          break;
+        }
+        s = (s + 1) & t.mask;
+      }
+    }
+  }
+}
+
+// Thread per pair: validate against the row, weights after the batch, and
+// per-row bookkeeping (append ranks, live and tombstone changes).
+__global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* __restrict__ off,
+                             const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
+                             const uint2* __restrict__ arcs, Ctrl* ctrl) {
+  const uint32_t np = ctrl->npairs;
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t s = t.pairs[p];
+    const unsigned long long k = t.keys[s];
+    const uint32_t u = uint32_t(k >> 32), v = uint32_t(k);
+    const uint32_t ndel = t.ndel[s], wdel = t.wdel[s];
+    const unsigned long long wins = t.wins[s];
+    if (ndel > 1) atomicOr(&ctrl->err, kErrInvalid);  // the same edge deleted twice
+    const uint2* row = arcs + off[u];
+    const uint32_t slot = find_slot(row, srt[u], deg[u], v);
+    const unsigned long long wold = slot != kEmpty ? row[slot].y : 0ull;
+    unsigned long long weff = 0;
+    if (ndel) {
+      if (wold == 0 || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);
+      else weff = wdel ? wdel : wold;
+    }
+    const unsigned long long wn = wold - weff + wins;
+    if (wn > 0xFFFFFFFFull) atomicOr(&ctrl->err, kErrOverflow);
+    uint32_t fl = kRunHead;
+    if (slot != kEmpty) fl |= kFound;
+    if (wold > 0) fl |= kLiveBefore;
+    if (wn > 0) fl |= kLiveAfter;
+    if (slot == kEmpty && wn > 0) fl |= kAppend;
+    const long long dl = (long long)wins - (long long)weff;
+    t.wnew[s] = uint32_t(wn);
+    t.flag[s] = fl;
+    t.delta[s] = dl;
+    t.slot[s] = (fl & kAppend) ? atomicAdd(&t.r_app[u], 1u) : slot;
+    if (dl) atomicAdd((unsigned long long*)&ctrl->m2_delta, (unsigned long long)dl);
+    const int live = (wn > 0 ? 1 : 0) - (wold > 0 ? 1 : 0);
+    if (live) {
+      atomicAdd(&t.r_live[u], live);
+      atomicAdd((unsigned long long*)&ctrl->arc_delta, (unsigned long long)(long long)live);
+    }
+    if ((fl & kFound) && wold > 0 && wn == 0) atomicAdd(&t.r_tomb[u], 1);
+    if ((fl & kFound) && wold == 0 && wn > 0) atomicAdd(&t.r_tomb[u], -1);
+    if (atomicCAS(&t.r_state[u], 0u, 1u) == 0u) t.rows[atomicAdd(&ctrl->rows, 1u)] = u;
+  }
+}
+
+// Thread per touched row: keep (append in place) or rebuild.
+__global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
+                            const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
+  const uint32_t nr = ctrl->rows;
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t u = t.rows[q];
+    const uint32_t d = deg[u], s = srt[u], app = t.r_app[u];
+    const long long tomb = (long long)ntomb[u] + t.r_tomb[u];
+    const long long live = (long long)d - ntomb[u] + t.r_live[u];
+    const uint32_t raw = d + app;
+    const uint32_t tomb_lim = raw / 4 > kTombMin ? raw / 4 : kTombMin;
+    const bool rebuild = raw > cap[u] || d - s + app > kTailMax || uint32_t(tomb) > tomb_lim;
+    if (rebuild) {
+      t.r_state[u] = 2u;
+      t.r_reg[u] = uint32_t(atomicAdd(&ctrl->extra_top, (unsigned long long)app));
+      atomicAdd(&ctrl->rebuild_rows, 1u);
+      atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(uint32_t(live)));
+      atomicAdd(&ctrl->scratch_need, (unsigned long long)s);
+      atomicMax(&ctrl->max_app, app);
+    }
+    atomicMax(&ctrl->max_deg, rebuild ? uint32_t(live) : raw);
+  }
+}
+
+// Thread per pair: in-place weight changes; new arcs to the row's tail, or to
+// the rebuilt row's region of `extra`.
+__global__ void k_hash_write(HashApply t, const unsigned long long* __restrict__ off,
+                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl) {
+  const uint32_t np = ctrl->npairs;
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t s = t.pairs[p];
+    const uint32_t fl = t.flag[s];
+    const unsigned long long k = t.keys[s];
+    const uint32_t u = uint32_t(k >> 32), v = uint32_t(k);
+    if (fl & kFound) {
+      arcs[off[u] + t.slot[s]].y = t.wnew[s];
+    } else if (fl & kAppend) {
+      if (t.r_state[u] == 2u) t.extra[t.r_reg[u] + t.slot[s]] = make_uint2(v, t.wnew[s]);
+      else arcs[off[u] + deg[u] + t.slot[s]] = make_uint2(v, t.wnew[s]);
+    }
+  }
+}
+
+constexpr int kHRebuildThreads = 256;
+
+// Block per rebuilt row: merge of the live sorted prefix (compacted into
+// scratch), the live tail and the row's new arcs (both sorted in shared
+// memory) into a new slot of 1.5x the live degree.
+__global__ void __launch_bounds__(kHRebuildThreads)
+k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __restrict__ deg,
+               uint32_t* __restrict__ cap, uint32_t* __restrict__ srt, uint32_t* __restrict__ ntomb,
+               uint2* __restrict__ arcs, uint2* __restrict__ scratch, unsigned long long pool_base,
+               unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
+  __shared__ uint2 tail[kTailMax];
+  __shared__ uint2 stail[kTailMax];
+  __shared__ uint2 sn[kExtraMax];
+  __shared__ unsigned long long s_sbase, s_dst;
+  __shared__ uint32_t s_nt, s_warp[kHRebuildThreads / 32], s_total;
+  const uint32_t nr = ctrl->rows;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  for (uint32_t r = blockIdx.x; r < nr; r += gridDim.x) {
+    const uint32_t u = t.rows[r];
+    if (t.r_state[u] != 2u) continue;
+    const uint2* old = arcs + off[u];
+    const uint32_t d = deg[u], s = srt[u], nnew = t.r_app[u];
+    const uint32_t live = uint32_t((long long)d - ntomb[u] + t.r_live[u]);
+    const uint32_t nc = grow_cap(live);
+    if (threadIdx.x == 0) {
+      s_sbase = atomicAdd(&ctrl->scratch_top, (unsigned long long)s);
+      s_dst = pool_base + atomicAdd(&ctrl->pool_top, (unsigned long long)nc);
+      s_nt = 0;
+      if (s_sbase + s > scratch_cap || s_dst + nc > pool_cap || nnew > kExtraMax)
+        atomicOr(&ctrl->err, kErrInternal);
+    }
+    __syncthreads();
+    const unsigned long long sbase = s_sbase, dst = s_dst;
+    if (sbase + s > scratch_cap || dst + nc > pool_cap || nnew > kExtraMax) {
+      __syncthreads();
+      continue;
+    }
+    uint2* A = scratch + sbase;
+    uint32_t L = 0;
+    for (uint32_t c0 = 0; c0 < s; c0 += blockDim.x) {
+      uint32_t k = c0 + threadIdx.x;
+      uint2 a = k < s ? old[k] : make_uint2(0, 0);
+      bool lv = k < s && a.y > 0;
+      unsigned m = __ballot_sync(0xFFFFFFFFu, lv);
+      if (lane == 0) s_warp[wib] = __popc(m);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (uint32_t x = 0; x < blockDim.x / 32; ++x) {
+          uint32_t tt = s_warp[x];
+          s_warp[x] = run;
+          run += tt;
+        }
+        s_total = run;
+      }
+      __syncthreads();
+      if (lv) A[L + s_warp[wib] + __popc(m & ((1u << lane) - 1u))] = a;
+      L += s_total;
+      __syncthreads();
+    }
+    for (uint32_t k = s + threadIdx.x; k < d; k += blockDim.x) {
+      uint2 a = old[k];
+      if (a.y > 0) tail[atomicAdd(&s_nt, 1u)] = a;
+    }
+    // new arcs into shared memory, padded to a power of two for a bitonic sort
+    uint32_t np2 = 1;
+    while (np2 < nnew) np2 <<= 1;
+    for (uint32_t k = threadIdx.x; k < np2; k += blockDim.x)
+      sn[k] = k < nnew ? t.extra[t.r_reg[u] + k] : make_uint2(0xFFFFFFFFu, 0u);
+    __syncthreads();
+    const uint32_t nt = s_nt;
+    for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
+      uint32_t rk = 0;
+      for (uint32_t x = 0; x < nt; ++x) rk += tail[x].x < tail[k].x;
+      stail[rk] = tail[k];
+    }
+    for (uint32_t kk = 2; kk <= np2; kk <<= 1)
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+          uint32_t ixj = i ^ j;
+          if (ixj > i) {
+            bool up = (i & kk) == 0;
+            uint2 x = sn[i], y = sn[ixj];
+            if ((x.x > y.x) == up) {
+              sn[i] = y;
+              sn[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    __syncthreads();
+    uint2* out = arcs + dst;
+    for (uint32_t k = threadIdx.x; k < L; k += blockDim.x) {
+      uint2 a = A[k];
+      out[k + count_below(stail, nt, a.x) + count_below(sn, nnew, a.x)] = a;
+    }
+    for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
+      uint2 a = stail[k];
+      out[k + count_below(A, L, a.x) + count_below(sn, nnew, a.x)] = a;
+    }
+    for (uint32_t k = threadIdx.x; k < nnew; k += blockDim.x) {
+      uint2 a = sn[k];
+      out[k + count_below(A, L, a.x) + count_below(stail, nt, a.x)] = a;
+    }
+    if (threadIdx.x == 0) {
+      if (L + nt + nnew != live) atomicOr(&ctrl->err, kErrInternal);
+      off[u] = dst;
+      deg[u] = live;
+      srt[u] = live;
+      cap[u] = nc;
+      ntomb[u] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Thread per touched row: metadata of kept rows, then reset the scratch.
+__global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb,
+                              Ctrl* ctrl) {
+  const uint32_t nr = ctrl->rows;
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t u = t.rows[q];
+    if (t.r_state[u] != 2u) {
+      deg[u] += t.r_app[u];
+      ntomb[u] = uint32_t((long long)ntomb[u] + t.r_tomb[u]);
+    }
+    t.r_app[u] = 0;
+    t.r_tomb[u] = 0;
+    t.r_live[u] = 0;
+    t.r_state[u] = 0;
+    t.r_reg[u] = 0;
+  }
+}
+
+// Alg. 7 per pair: K[u] and Sigma[C^{t-1}[u]] change by the net weight.
+__global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
+                               long long* __restrict__ Sigma, Ctrl* ctrl) {
+  const uint32_t np = ctrl->npairs;
+  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t s = t.pairs[p];
+    const long long dl = t.delta[s];
+    if (!dl) continue;
+    const uint32_t u = uint32_t(t.keys[s] >> 32);
+    atomicAdd((unsigned long long*)&K[u], (unsigned long long)dl);
+    atomicAdd((unsigned long long*)&Sigma[C[u]], (unsigned long long)dl);
+  }
+}
+
+// Reset the per-vertex scratch of the touched rows after a failed validation.
+__global__ void k_hash_reset(HashApply t, Ctrl* ctrl) {
+  const uint32_t nr = ctrl->rows;
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t u = t.rows[q];
+    t.r_app[u] = 0;
+    t.r_tomb[u] = 0;
+    t.r_live[u] = 0;
+    t.r_state[u] = 0;
+    t.r_reg[u] = 0;
+  }
+}
+
 int read_ctrl(Handle* h) {
   DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
   DFL_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -555,11 +900,206 @@ KeyFmt key_fmt(const Handle* h) {
   return f;
 }
 
+
+
+int ensure_hash_buffers(Handle* h, uint64_t na) {
+  uint64_t cap = 1024;
+  while (cap < 2 * na) cap <<= 1;
+  if (cap > h->h_cap) {
+    cudaStreamSynchronize(h->stream);
+    void* old[] = {h->h_keys, h->h_ndel, h->h_wdel, h->h_wins, h->h_slot, h->h_wnew,
+                   h->h_flag, h->h_delta, h->h_pairs};
+    for (void* q : old) cudaFree(q);
+    h->h_cap = 0;
+    DFL_CUDA(h, cudaMalloc(&h->h_keys, sizeof(unsigned long long) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_ndel, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_wdel, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_wins, sizeof(unsigned long long) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_slot, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_wnew, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_flag, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_delta, sizeof(long long) * cap));
+    DFL_CUDA(h, cudaMalloc(&h->h_pairs, sizeof(uint32_t) * cap));
+    h->h_cap = cap;
+  }
+  if (!h->r_app) {
+    const uint64_t n = h->n ? h->n : 1;
+    DFL_CUDA(h, cudaMalloc(&h->r_app, sizeof(uint32_t) * n));
+    DFL_CUDA(h, cudaMalloc(&h->r_tomb, sizeof(int) * n));
+    DFL_CUDA(h, cudaMalloc(&h->r_live, sizeof(int) * n));
+    DFL_CUDA(h, cudaMalloc(&h->r_state, sizeof(uint32_t) * n));
+    DFL_CUDA(h, cudaMalloc(&h->r_reg, sizeof(uint32_t) * n));
+    DFL_CUDA(h, cudaMemsetAsync(h->r_app, 0, sizeof(uint32_t) * n, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->r_tomb, 0, sizeof(int) * n, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->r_live, 0, sizeof(int) * n, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->r_state, 0, sizeof(uint32_t) * n, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->r_reg, 0, sizeof(uint32_t) * n, h->stream));
+  }
+  if (na > h->h_rows_cap) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->h_rows);
+    cudaFree(h->h_extra);
+    h->h_rows = nullptr;
+    h->h_extra = nullptr;
+    h->h_rows_cap = 0;
+    uint64_t want = na + na / 2 + 256;
+    DFL_CUDA(h, cudaMalloc(&h->h_rows, sizeof(uint32_t) * want));
+    DFL_CUDA(h, cudaMalloc(&h->h_extra, sizeof(uint2) * want));
+    h->h_rows_cap = want;
+  }
+  return DFL_OK;
+}
+
+HashApply hash_args(const Handle* h) {
+  HashApply t;
+  t.keys = h->h_keys;
+  t.ndel = h->h_ndel;
+  t.wdel = h->h_wdel;
+  t.wins = h->h_wins;
+  t.slot = h->h_slot;
+  t.wnew = h->h_wnew;
+  t.flag = h->h_flag;
+  t.delta = h->h_delta;
+  t.pairs = h->h_pairs;
+  t.mask = h->h_cap - 1;
+  t.r_app = h->r_app;
+  t.r_tomb = h->r_tomb;
+  t.r_live = h->r_live;
+  t.r_state = h->r_state;
+  t.r_reg = h->r_reg;
+  t.rows = h->h_rows;
+  t.extra = h->h_extra;
+  return t;
+}
+
+int hash_reset(Handle* h, const HashApply& t) {
+  LaunchScope ls(h, DFL_PROF_APPLY);
+  k_hash_reset<<<grid_for(h->h_rows_cap, 256), 256, 0, h->stream>>>(t, h->ctrl);
+  DFL_TRY(check_launch(h, "hash reset"));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
 }  // namespace
 
+// Batch apply (Section 3.4 and Alg. 7): validate, then change the graph, K,
+// Sigma and 2m, and append the batch to the pending list.
 int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
                 int mem_kind) {
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_apply_batch before dfl_static");
+  const uint64_t ne = nd + ni;
+  if (ne == 0) return DFL_OK;
+  const uint64_t na = 2 * ne;
+  if (ne > h->b_edges_cap) {
+    uint64_t cap = 0;
+    DFL_TRY(grow(h, &h->b_edges, ne, &cap, h->b_edges_cap));
+    h->b_edges_cap = cap;
+  }
+  DFL_TRY(ensure_batch_scratch(h, na));
+  DFL_TRY(ensure_hash_buffers(h, na));
+  cudaMemcpyKind kind = mem_kind == DFL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, kind, h->stream));
+  if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, kind, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  const uint64_t cap = h->h_cap;
+  const uint64_t used = cap < 4 * na ? cap : 4 * na;  // probes stay near the hashed slots
+  (void)used;
+  DFL_CUDA(h, cudaMemsetAsync(h->h_keys, 0xFF, sizeof(unsigned long long) * cap, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->h_ndel, 0, sizeof(uint32_t) * cap, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->h_wins, 0, sizeof(unsigned long long) * cap, h->stream));
+  const KeyFmt f = key_fmt(h);
+  const HashApply t = hash_args(h);
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_insert<<<grid_for(ne, 256), 256, 0, h->stream>>>(h->b_edges, nd, ne, h->n, f, t, h->b_key,
+                                                            h->b_w, h->ctrl);
+    DFL_TRY(check_launch(h, "hash insert"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_pairs<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->n, h->off, h->deg, h->srt, h->arcs,
+                                                           h->ctrl);
+    DFL_TRY(check_launch(h, "hash pairs"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_rows<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->deg, h->cap, h->srt, h->ntomb, h->ctrl);
+    DFL_TRY(check_launch(h, "hash rows"));
+  }
+  DFL_TRY(read_ctrl(h));
+  const Ctrl c = *h->hctrl;
+  int err = DFL_OK;
+  if (c.err & kErrInvalid) err = set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
+  else if (c.err & kErrNotFound) err = set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
+  else if (c.err & kErrOverflow) err = set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
+  else if (c.err) err = set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
+  else if (h->m2 + c.m2_delta >= (1ll << 32)) err = set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+  if (err) {
+    DFL_TRY(hash_reset(h, t));
+    return err;
+  }
+  if (c.max_app > kExtraMax) {  // a rebuilt row gains too many arcs to sort in shared memory
+    DFL_TRY(hash_reset(h, t));
+    return apply_batch_sorted(h, del, nd, ins, ni, mem_kind);
+  }
+  // --- mutation starts here ---
+  if (h->pool_top + c.reloc_need > h->pool_cap) {
+    uint64_t c2 = 0;
+    uint64_t need = h->pool_top + c.reloc_need;
+    need = need + need / 4 + 1024;
+    DFL_TRY(grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top));
+    h->pool_cap = c2;
+  }
+  if (c.scratch_need > h->scratch_cap) {
+    uint64_t c2 = 0;
+    DFL_TRY(grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap));
+    h->scratch_cap = c2;
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_write<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->off, h->deg, h->arcs, h->ctrl);
+    DFL_TRY(check_launch(h, "hash write"));
+  }
+  if (c.rebuild_rows) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_rebuild<<<grid_for(c.rows, 1, 152 * 8), kHRebuildThreads, 0, h->stream>>>(
+        t, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->scratch, h->pool_top, h->pool_cap,
+        h->scratch_cap, h->ctrl);
+    DFL_TRY(check_launch(h, "hash rebuild"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_weights<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->C, h->K, h->Sigma, h->ctrl);
+    DFL_TRY(check_launch(h, "hash weights"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_hash_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(t, h->deg, h->ntomb, h->ctrl);
+    DFL_TRY(check_launch(h, "hash finish"));
+  }
+  if (h->pend_count + na > h->pend_cap) {
+    uint64_t c2 = 0, need = h->pend_count + na;
+    DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
+    uint64_t c3 = 0;
+    DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
+    h->pend_cap = c2 < c3 ? c2 : c3;
+  }
+  DFL_CUDA(h, cudaMemcpyAsync(h->pend_key + h->pend_count, h->b_key, sizeof(unsigned long long) * na,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  DFL_CUDA(h, cudaMemcpyAsync(h->pend_w + h->pend_count, h->b_w, sizeof(uint32_t) * na,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  h->pend_count += na;
+  h->m2 += c.m2_delta;
+  h->pool_top += c.reloc_need;
+  h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
+  if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
+  return DFL_OK;
+}
+
+// Sort-based batch apply: used when a rebuilt row receives more new arcs
+// in one batch than the hashed path sorts in shared memory.
+int apply_batch_sorted(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                       int mem_kind) {
   const uint64_t ne = nd + ni;
   if (ne == 0) return DFL_OK;
   const uint64_t na = 2 * ne;

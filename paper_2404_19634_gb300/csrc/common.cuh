@@ -72,6 +72,9 @@ struct Ctrl {
   unsigned long long ever_count;     // vertices newly added to the first-pass processed set
   unsigned int giant_chunks[2];      // chunk work items of the largest bin (per buffer parity)
   long long m2v;                     // 2m of the current local-moving call
+  unsigned int npairs;               // distinct (u, v) pairs of the batch (hashed apply)
+  unsigned int max_app;              // most new arcs of one rebuilt row
+  unsigned long long extra_top;      // new arcs of rebuilt rows
   unsigned long long pool_top;       // first free arc slot of the pool
   unsigned long long scratch_top;
   // misc reductions
@@ -190,6 +193,26 @@ struct Handle {
   uint64_t b_edges_cap = 0;
   uint2* scratch = nullptr;        // merge scratch
   uint64_t scratch_cap = 0;
+  // hashed apply: pair table (capacity h_cap, a power of two), per-vertex
+  // scratch counters (zero at rest), touched rows, new arcs of rebuilt rows
+  unsigned long long* h_keys = nullptr;
+  uint32_t* h_ndel = nullptr;
+  uint32_t* h_wdel = nullptr;
+  unsigned long long* h_wins = nullptr;
+  uint32_t* h_slot = nullptr;
+  uint32_t* h_wnew = nullptr;
+  uint32_t* h_flag = nullptr;
+  long long* h_delta = nullptr;
+  uint32_t* h_pairs = nullptr;
+  uint64_t h_cap = 0;
+  uint32_t* r_app = nullptr;
+  int* r_tomb = nullptr;
+  int* r_live = nullptr;
+  uint32_t* r_state = nullptr;
+  uint32_t* r_reg = nullptr;
+  uint32_t* h_rows = nullptr;
+  uint2* h_extra = nullptr;
+  uint64_t h_rows_cap = 0;
 
   // generic scratch
   void* tmp = nullptr;
@@ -233,8 +256,13 @@ struct Handle {
     std::vector<Ev> evs;
     uint64_t kernels = 0;
     uint64_t class_launches[DFL_PROF_CLASSES] = {0};
+    uint64_t last_use = 0;
   };
-  IterGraph igraph[2];
+  static constexpr int kGraphCache = 4;  // graphs kept per parity (DF, ND/static, DS, ...)
+  IterGraph igraph[2][kGraphCache];
+  uint64_t graph_use = 0;                 // LRU clock
+  uint64_t graph_captures = 0;
+  double graph_capture_ms = 0;
   std::vector<cudaEvent_t> ev_free;
   dfl_profile_t prof;
 };
@@ -393,7 +421,7 @@ struct MoveArgs {
   bool use_range;
   bool track_ever;
 };
-void destroy_iteration_graph(Handle* h, int cur);
+void destroy_iteration_graph(Handle::IterGraph& g);
 int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial = nullptr, uint64_t* ever = nullptr);
 

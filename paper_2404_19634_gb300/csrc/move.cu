@@ -12,6 +12,7 @@
 // neighbours (in the affected range) are marked for the next iteration
 // (Section 4.1: a mover makes its neighbours affected).  The commit kernel then
 // applies the class's moves to C', Sigma' and the sizes.
+#include <chrono>
 #include <cstring>
 
 #include "common.cuh"
@@ -810,7 +811,10 @@ struct GraphKey {
   void* stream;
 };
 
-int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd, int cur) {
+// The cached graph for this iteration's key (captured on a miss, evicting
+// the least recently used entry of this parity).
+int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd, int cur,
+                           Handle::IterGraph** out) {
   GraphKey key;
   std::memset(&key, 0, sizeof(key));
   key.a = a;
@@ -818,10 +822,18 @@ int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd
   key.cur = cur;
   key.flags = h->opt.flags;
   key.stream = h->stream;
-  Handle::IterGraph& g = h->igraph[cur];
-  if (g.exec && g.key.size() == sizeof(key) && std::memcmp(g.key.data(), &key, sizeof(key)) == 0)
-    return DFL_OK;
-  destroy_iteration_graph(h, cur);
+  Handle::IterGraph* slot = nullptr;
+  for (auto& e : h->igraph[cur])
+    if (e.exec && e.key.size() == sizeof(key) && std::memcmp(e.key.data(), &key, sizeof(key)) == 0) {
+      e.last_use = ++h->graph_use;
+      *out = &e;
+      return DFL_OK;
+    }
+  for (auto& e : h->igraph[cur])
+    if (!slot || !e.exec || (slot->exec && e.last_use < slot->last_use)) slot = &e;
+  Handle::IterGraph& g = *slot;
+  destroy_iteration_graph(g);
+  const auto t0 = std::chrono::steady_clock::now();
   const size_t ev0 = h->ev_pending.size();
   const uint64_t l0 = h->launches;
   uint64_t cl0[DFL_PROF_CLASSES];
@@ -851,13 +863,17 @@ int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd
     h->prof.launches[q] = cl0[q];
   }
   g.key.assign(reinterpret_cast<const char*>(&key), reinterpret_cast<const char*>(&key) + sizeof(key));
+  g.last_use = ++h->graph_use;
+  h->graph_captures++;
+  h->graph_capture_ms +=
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = &g;
   return DFL_OK;
 }
 
 }  // namespace
 
-void destroy_iteration_graph(Handle* h, int cur) {
-  Handle::IterGraph& g = h->igraph[cur];
+void destroy_iteration_graph(Handle::IterGraph& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& ev : g.evs) {
     cudaEventDestroy(ev.a);
@@ -979,12 +995,15 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   GiantDecide gd{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial, nullptr};
   int cur = 0;
   uint32_t it = 0;
+  Handle::IterGraph* graph_used[2] = {nullptr, nullptr};
   while (it < h->opt.max_iterations) {
     ++it;
     const int nxt = cur ^ 1;
     if (use_graph) {
-      DFL_TRY(ensure_iteration_graph(h, a, gd, cur));
-      const Handle::IterGraph& g = h->igraph[cur];
+      Handle::IterGraph* gp = nullptr;
+      DFL_TRY(ensure_iteration_graph(h, a, gd, cur, &gp));
+      const Handle::IterGraph& g = *gp;
+      graph_used[cur] = gp;
       DFL_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
       h->launches += g.kernels;
       for (int q = 0; q < DFL_PROF_CLASSES; ++q) h->prof.launches[q] += g.class_launches[q];
@@ -995,7 +1014,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     const Ctrl& c = *h->hctrl;
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
     if (use_graph) {
-      for (const auto& ev : h->igraph[cur].evs) {  // harvest this replay's timings
+      for (const auto& ev : graph_used[cur]->evs) {  // harvest this replay's timings
         float ms = 0;
         if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) h->prof.ms[ev.cls] += ms;
       }

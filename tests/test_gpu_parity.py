@@ -398,14 +398,17 @@ def test_long_stream_tombstones_and_rebuilds(dfl, orc):
             same_state(a, b)
 
 
-def test_one_row_gets_thousands_of_edges(dfl, orc):
+@pytest.mark.parametrize("count", [3500, 5000])
+def test_one_row_gets_thousands_of_edges(dfl, orc, count):
+    """3,500 new arcs of one row are sorted in shared memory by the rebuild;
+    5,000 exceed that and take the sort-based batch apply."""
     g = synth.sbm(6000, 30, 0.01, 0.001, 41)
     a, b = pair(dfl, orc, g)
     a.static()
     b.static()
     rng = np.random.default_rng(2)
-    nb = rng.choice(np.arange(1, g.n), 3500, replace=False)
-    ins = np.stack([np.zeros(3500, np.int64), nb, rng.integers(1, 5, 3500)], 1).astype(np.uint32)
+    nb = rng.choice(np.arange(1, g.n), count, replace=False)
+    ins = np.stack([np.zeros(count, np.int64), nb, rng.integers(1, 5, count)], 1).astype(np.uint32)
     off, idx, w = synth.to_csr(g)
     row0 = idx[int(off[0]):int(off[1])]
     dels = np.array([[0, int(x), 0] for x in row0[:3]], np.uint32).reshape(-1, 3)
