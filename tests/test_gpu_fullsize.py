@@ -1,0 +1,52 @@
+"""Full-size parity on the benchmark workload: R-MAT with 2^22 vertices and
+33,554,432 edges, static Louvain, then DF updates of 1e-3 and 1e-5 x |E| edge
+batches, in the launch configuration the benchmark times (side stream, graph
+replay).  The oracle runs the same steps; membership, K, Sigma, 2m, modularity
+and the first-pass trace must match exactly.  About two minutes (most of it
+in the CPU oracle)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def test_rmat22_static_and_df_batches_match_oracle():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    import paper_2404_19634_gb300 as dfl
+    dfl.build()
+    oracle.build()
+    g = synth.rmat(22, 33_554_432, 2)
+    off, idx, w = synth.to_csr(g)
+    s = torch.cuda.Stream()
+    a = dfl.Dfl(g.n, off, idx, w, stream=s)
+    b = oracle.Oracle(g.n, off, idx, w)
+    a.static()
+    b.static()
+    stream = synth.BatchStream(g, 200)
+
+    def check():
+        assert np.array_equal(a.membership(), b.membership())
+        Ka, Sa, ma = a.weights()
+        Kb, Sb, mb = b.weights()
+        assert ma == mb and np.array_equal(Ka, Kb) and np.array_equal(Sa, Sb)
+        qa, na, da = a.modularity()
+        qb, nb, db = b.modularity()
+        assert (na, da) == (nb, db) and abs(qa - qb) <= 1e-12
+        assert a.trace() == b.trace()
+        sa, sb = a.stats(), b.stats()
+        assert sa["iterations"] == sb["iterations"]
+        assert sa["affected_ever"] == sb["affected_ever"]
+
+    check()
+    for size in (33_554, 335, 33_554):
+        d, i = stream.next(size)
+        assert a.apply_batch(d, i) == 0 and b.apply_batch(d, i) == 0
+        a.update(dfl.DF)
+        b.update(oracle.DF)
+        check()
+    assert a.num_arcs() == int(b.graph()[0][-1])
