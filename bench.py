@@ -10,6 +10,13 @@ device when the timed region starts; between timed steps L2 is flushed.
 
 Prints one JSON line (see the keys below).  --impl reference times the CPU
 oracle on the same workload instead.
+
+--serve measures the serving form instead: 8 resident R-MAT graphs (2^18 to
+2^23 vertices, edge factor 8) receive update requests as a Poisson stream of
+2000 requests/s with batch sizes log-uniform in [10, 1e6] edges (80%
+insertions, 20% deletions of existing edges), served three ways on fresh
+copies of the same graphs: one request at a time (serial DF), concurrently
+per graph without coalescing, and concurrently with coalescing.
 """
 from __future__ import annotations
 
@@ -37,6 +44,10 @@ BATCH_SEED = 200
 BATCH_FRAC = 1e-3
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
+SERVE_SCALES = [18, 19, 19, 20, 21, 22, 22, 23]
+SERVE_RATE = 2000.0
+SERVE_SIZES = (10, 1_000_000)
+SERVE_METRIC = "served updates/s with p50/p99 latency (8 resident R-MAT graphs, Poisson 2000 req/s)"
 
 
 def parse():
@@ -51,6 +62,9 @@ def parse():
     p.add_argument("--no-sizes", action="store_true")
     p.add_argument("--profile-only", action="store_true",
                    help="a few steps for a profiler (no clocks, no CPU baseline)")
+    p.add_argument("--serve", action="store_true", help="measure the serving form")
+    p.add_argument("--serve-seconds", type=float, default=0.5,
+                   help="length of the Poisson arrival window")
     return p.parse_args()
 
 
@@ -353,8 +367,92 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def _serve_graph(k):
+    g = synth.rmat(SERVE_SCALES[k], 8 << SERVE_SCALES[k], 300 + k)
+    return g, (g.n, *synth.to_csr(g))
+
+
+def serve_arm(args):
+    import torch
+
+    import paper_2404_19634_gb300 as dfl
+    from paper_2404_19634_gb300 import serve
+
+    torch.cuda.set_device(0)
+    dfl.build()
+    t_gen = time.perf_counter()
+    # the graphs are generated in parallel host processes (spawned, so that
+    # no child inherits a CUDA context)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(SERVE_SCALES), os.cpu_count() or 1)) as pool:
+        made = pool.map(_serve_graph, range(len(SERVE_SCALES)))
+    graphs = [g for g, _ in made]
+    csrs = [c for _, c in made]
+    del made
+    pools = [synth.EdgePool(g, 400 + k) for k, g in enumerate(graphs)]
+    warm = [(0.0, g, 1000) for _ in range(max(1, args.warmup)) for g in range(len(graphs))]
+    sched = synth.poisson_requests(len(graphs), SERVE_RATE, args.serve_seconds, *SERVE_SIZES, seed=500)
+    reqs = serve.make_requests(pools, warm + sched)
+    wreq, treq = reqs[:len(warm)], reqs[len(warm):]
+    gen_s = time.perf_counter() - t_gen
+    edges = [int(r.dels.shape[0] + r.ins.shape[0]) for r in treq]
+
+    def run(mode):
+        srv = serve.Server.from_graphs(csrs, mem_cap=150 << 30)
+        srv.replay(wreq, [(r.graph, [r.rid]) for r in wreq])
+        torch.cuda.synchronize()
+        l0 = sum(h.stats()["kernel_launches"] for h in srv.handles)
+        with Clocks(0) as clk:
+            if mode == "serial":
+                res = srv.serve_serial(treq)
+            else:
+                res = srv.serve(treq, coalesce=(mode == "coalesce"))
+            torch.cuda.synchronize()
+        launches = sum(h.stats()["kernel_launches"] for h in srv.handles) - l0
+        final = [h.modularity() for h in srv.handles]
+        srv.close()
+        out = res.summary()
+        out["gpu_launches"] = launches
+        return res, out, final, clk.summary()
+
+    ser, ser_sum, ser_final, _ = run("serial")
+    ovl, ovl_sum, ovl_final, _ = run("overlap")
+    coa, coa_sum, coa_final, clocks = run("coalesce")
+    ovl_sum["identical_to_serial"] = all((a.num, a.den) == (b.num, b.den)
+                                         for a, b in zip(ovl.records, ser.records))
+    coa_sum["final_q_minus_serial"] = [round(a[0] - b[0], 9) for a, b in zip(coa_final, ser_final)]
+    coa_sum["max_requests_per_update"] = max(len(ids) for _, ids in coa.groups)
+    mean_edges = float(np.mean(edges)) if edges else 0.0
+    line = {
+        "metric": SERVE_METRIC, "value": coa_sum["requests_per_s"], "unit": "updates/s",
+        "n_gpus": 1, "steps": len(treq), "warmup": len(wreq),
+        "ms_per_step": 1e3 * coa_sum["wall_s"] / max(1, len(treq)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "8 R-MAT graphs (a=.57 b=.19 c=.19) of 2^18,2^19,2^19,2^20,2^21,2^22,"
+                               "2^22,2^23 vertices, 8 edges per vertex; Poisson requests",
+                   "rate_per_s": SERVE_RATE, "arrival_window_s": args.serve_seconds,
+                   "batch_edges": "log-uniform [10, 1e6], 80% insertions / 20% deletions",
+                   "requests": len(treq), "mean_batch_edges": round(mean_edges, 1),
+                   "warmup": f"{len(wreq)} requests of 1000 edges, served serially, untimed",
+                   "mem_cap_bytes": 150 << 30, "generation_s": round(gen_s, 1),
+                   "l2": "not flushed (the 8 graphs total 1.7e8 edges, far above L2)"},
+        "serial": ser_sum, "overlap": ovl_sum, "coalesce": coa_sum,
+        "speedup_vs_serial": {"updates_per_s": coa_sum["requests_per_s"] / ser_sum["requests_per_s"],
+                              "p50": ser_sum["p50_ms"] / coa_sum["p50_ms"],
+                              "p99": ser_sum["p99_ms"] / coa_sum["p99_ms"]},
+        "e2e": {"value": coa_sum["requests_per_s"], "unit": "updates/s",
+                "h2d_bytes_per_step": 12 * mean_edges, "d2h_bytes_per_step": 32},
+        "gpu_launches": coa_sum["gpu_launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serve:
+        serve_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

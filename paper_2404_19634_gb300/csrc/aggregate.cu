@@ -14,6 +14,7 @@
 // block in shared memory and merged into the community's global table, which
 // is then emitted slot-parallel.  Within a warp, arcs are pre-aggregated per
 // neighbour community (match + reduce) before touching a table.
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -431,12 +432,14 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     DFL_CUDA(h, cudaMalloc(&sg.arcs, sizeof(uint2) * want));
     sg.arc_cap = want;
   }
-  static bool smem_set = false;
-  if (!smem_set) {
-    DFL_CUDA(h, cudaFuncSetAttribute(k_agg_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 2 * kAggBlockSlots)));
-    smem_set = true;
-  }
+  // once per process (handles may be driven from several host threads)
+  static std::once_flag smem_once;
+  static cudaError_t smem_rc = cudaSuccess;
+  std::call_once(smem_once, [] {
+    smem_rc = cudaFuncSetAttribute(k_agg_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(sizeof(uint32_t) * 2 * kAggBlockSlots));
+  });
+  DFL_CUDA(h, smem_rc);
   AggArgs a;
   a.g = g;
   a.Cp = Cp;

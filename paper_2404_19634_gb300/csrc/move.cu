@@ -14,6 +14,7 @@
 // applies the class's moves to C', Sigma' and the sizes.
 #include <chrono>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -918,14 +919,17 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(kGiantBlocks) * gslots));
     h->gtable_cap = uint64_t(kGiantBlocks) * gslots;
   }
-  static bool smem_set = false;
-  if (!smem_set) {
-    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 2 * kBlockSlots)));
-    DFL_CUDA(h, cudaFuncSetAttribute(k_decide_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 2 * kGiantSlots)));
-    smem_set = true;
-  }
+  // once per process (handles may be driven from several host threads)
+  static std::once_flag smem_once;
+  static cudaError_t smem_rc = cudaSuccess;
+  std::call_once(smem_once, [] {
+    smem_rc = cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(sizeof(uint32_t) * 2 * kBlockSlots));
+    if (smem_rc == cudaSuccess)
+      smem_rc = cudaFuncSetAttribute(k_decide_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * 2 * kGiantSlots));
+  });
+  DFL_CUDA(h, smem_rc);
   // chunked bin-3 buffers: per list item offsets/counters (sized by the
   // largest bin-3 list: at most arcs / 4097 vertices) and partial sums
   {

@@ -334,3 +334,73 @@ def graph_stats(g: EdgeList) -> dict:
 
 def log_uniform_int(rng, lo: float, hi: float) -> int:
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+class EdgePool:
+    """The edges a graph holds as a request stream evolves it, as unit-weight
+    entries: each base edge and each inserted edge is one entry (a pair
+    inserted twice has two).  A deletion removes a uniformly chosen entry and
+    one unit of weight, so every generated deletion is valid; two entries of
+    the same pair drawn for one batch become one deletion of weight 2.
+    Insertions join uniform vertex pairs with weight 1."""
+
+    def __init__(self, edges: EdgeList, seed: int):
+        self.n = edges.n
+        self.rng = np.random.default_rng(seed)
+        cap = max(1024, edges.m * 2)
+        self.u = np.zeros(cap, np.int64)
+        self.v = np.zeros(cap, np.int64)
+        self.u[:edges.m] = edges.u
+        self.v[:edges.m] = edges.v
+        self.size = edges.m
+
+    def _grow(self, extra):
+        if self.size + extra > self.u.shape[0]:
+            cap = max(self.u.shape[0] * 2, self.size + extra)
+            self.u = np.resize(self.u, cap)
+            self.v = np.resize(self.v, cap)
+
+    def next(self, size: int, frac_ins: float = 0.8):
+        n_ins = int(round(size * frac_ins))
+        n_del = min(size - n_ins, self.size)
+        idx = np.unique(self.rng.integers(0, self.size, n_del)) if n_del else np.zeros(0, np.int64)
+        lo = np.minimum(self.u[idx], self.v[idx])
+        hi = np.maximum(self.u[idx], self.v[idx])
+        key, cnt = np.unique((lo << 32) | hi, return_counts=True)
+        dels = np.stack([key >> 32, key & 0xFFFFFFFF, cnt], 1).astype(np.uint32)
+        # remove the drawn entries: the surviving entries of the last len(idx)
+        # slots move into the holes below the new end
+        k = idx.shape[0]
+        end = self.size - k
+        holes = idx[idx < end]
+        tail = np.arange(end, self.size)
+        keep = tail[~np.isin(tail, idx, assume_unique=True)]
+        self.u[holes] = self.u[keep]
+        self.v[holes] = self.v[keep]
+        self.size = end
+        a = self.rng.integers(0, self.n, n_ins)
+        b = self.rng.integers(0, self.n - 1, n_ins)
+        b = b + (b >= a)
+        self._grow(n_ins)
+        self.u[self.size:self.size + n_ins] = a
+        self.v[self.size:self.size + n_ins] = b
+        self.size += n_ins
+        ins = np.stack([a, b, np.ones(n_ins, np.int64)], 1).astype(np.uint32)
+        return dels.reshape(-1, 3), ins.reshape(-1, 3)
+
+
+def poisson_requests(num_graphs: int, rate: float, duration: float, size_lo: int, size_hi: int,
+                     seed: int):
+    """Arrival times (seconds) of a Poisson stream of `rate` requests per
+    second over `duration`, each for a uniformly chosen graph, with a batch
+    size log-uniform in [size_lo, size_hi] edges."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        g = int(rng.integers(0, num_graphs))
+        size = int(round(math.exp(rng.uniform(math.log(size_lo), math.log(size_hi)))))
+        out.append((t, g, size))
+    return out

@@ -1,0 +1,110 @@
+"""Host logic of the serving loop (admission, coalescing, ordering), with
+stand-in handles on the CPU: each records the batches it was given and
+sleeps inside update() so that graphs' work overlaps in time."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2404_19634_gb300 import serve
+
+
+class FakeHandle:
+    def __init__(self, g, delay=0.004):
+        self.g = g
+        self.delay = delay
+        self.pending = []
+        self.history = []  # request sizes per update, in order
+        self.lock = threading.Lock()
+        self.active = 0
+
+    def apply_batch(self, dels, ins):
+        self.pending.append(int(dels.shape[0] + ins.shape[0]))
+
+    def update(self, mode):
+        with self.lock:
+            self.active += 1
+            assert self.active == 1, "one update at a time per graph"
+        time.sleep(self.delay)
+        self.history.append(tuple(self.pending))
+        self.pending = []
+        with self.lock:
+            self.active -= 1
+
+    def modularity(self):
+        # a value that depends on the whole grouping history of this graph
+        num = hash(tuple(self.history)) & 0xFFFFFFFF
+        return num / 2**32, num, 2**32
+
+    def membership(self):
+        return np.array([len(self.history)], np.uint32)
+
+
+def requests(num_graphs=4, count=120, seed=3):
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for rid in range(count):
+        t += rng.exponential(1 / 5000)
+        g = int(rng.integers(0, num_graphs))
+        k = int(rng.integers(1, 50))
+        out.append(serve.Request(rid, g, t, np.zeros((k // 5, 3), np.uint32),
+                                 np.zeros((k - k // 5, 3), np.uint32)))
+    return out
+
+
+def check_groups(reqs, res, coalesce=True):
+    seen = []
+    for g, ids in res.groups:
+        assert all(reqs[i].graph == g for i in ids)
+        seen += ids
+        if not coalesce:
+            assert len(ids) == 1
+    assert sorted(seen) == [r.rid for r in reqs], "every request served exactly once"
+    for g in {r.graph for r in reqs}:
+        order = [i for gg, ids in res.groups if gg == g for i in ids]
+        assert order == sorted(order), "a graph's requests are applied in arrival order"
+    for rec in res.records:
+        assert rec.finish >= rec.start >= rec.arrival - 1e-3
+
+
+def test_coalescing_overlap_and_replay():
+    reqs = requests()
+    srv = serve.Server([FakeHandle(g) for g in range(4)])
+    res = srv.serve(reqs, coalesce=True)
+    check_groups(reqs, res)
+    assert len(res.groups) < len(reqs), "queued requests were coalesced"
+    assert srv.peak["busy"] > 1, "graphs' updates overlapped"
+    # the same grouping replayed one update at a time gives the same results
+    again = serve.Server([FakeHandle(g, 0.0) for g in range(4)]).replay(reqs, res.groups)
+    assert [(r.num, r.den, r.group) for r in again.records] == \
+           [(r.num, r.den, r.group) for r in res.records]
+    s = res.summary()
+    assert s["requests"] == len(reqs) and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_no_coalescing_matches_serial():
+    reqs = requests(count=60)
+    a = serve.Server([FakeHandle(g) for g in range(4)]).serve(reqs, coalesce=False)
+    check_groups(reqs, a, coalesce=False)
+    b = serve.Server([FakeHandle(g, 0.0) for g in range(4)]).serve_serial(reqs)
+    assert [(r.num, r.den) for r in a.records] == [(r.num, r.den) for r in b.records]
+
+
+def test_slots_and_memory_cap():
+    reqs = requests(count=80)
+    one = max(serve.batch_bytes(r) for r in reqs)
+    srv = serve.Server([FakeHandle(g) for g in range(4)], resident_bytes=1000,
+                       mem_cap=1000 + 2 * one, slots=2)
+    res = srv.serve(reqs, coalesce=True)
+    check_groups(reqs, res)
+    assert srv.peak["busy"] <= 2
+    assert srv.peak["mem"] <= 2 * one
+
+
+def test_oversized_request_runs_alone():
+    reqs = requests(count=20)
+    srv = serve.Server([FakeHandle(g) for g in range(4)], resident_bytes=0, mem_cap=1)
+    res = srv.serve(reqs, coalesce=True)
+    check_groups(reqs, res)
+    assert srv.peak["busy"] == 1
+    assert all(len(ids) == 1 for _, ids in res.groups)
