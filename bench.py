@@ -17,6 +17,13 @@ oracle on the same workload instead.
 insertions, 20% deletions of existing edges), served three ways on fresh
 copies of the same graphs: one request at a time (serial DF), concurrently
 per graph without coalescing, and concurrently with coalescing.
+
+--group measures the batched form instead: 64 planted-partition graphs
+(10^4 to 10^6 vertices, log-uniform; 20 to 2000 blocks; mixing 0.1 to 0.5;
+weights 1 to 16; 8 edges per vertex), each step one batch of 1e-4 x |E| per
+graph (80% insertions with weights 1 to 16, 20% deletions), applied and
+updated with DF for all graphs by one group handle, against the same
+batches through one handle per graph, one graph after another.
 """
 from __future__ import annotations
 
@@ -48,6 +55,9 @@ SERVE_SCALES = [18, 19, 19, 20, 21, 22, 22, 23]
 SERVE_RATE = 2000.0
 SERVE_SIZES = (10, 1_000_000)
 SERVE_METRIC = "served updates/s with p50/p99 latency (8 resident R-MAT graphs, Poisson 2000 req/s)"
+GROUP_GRAPHS = 64
+GROUP_SEED = 4
+GROUP_METRIC = "ms per step: DF update of 64 graphs, each with a 1e-4|E| batch (batched group launch)"
 
 
 def parse():
@@ -65,6 +75,9 @@ def parse():
     p.add_argument("--serve", action="store_true", help="measure the serving form")
     p.add_argument("--serve-seconds", type=float, default=0.5,
                    help="length of the Poisson arrival window")
+    p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
+    p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
+    p.add_argument("--group-max-n", type=float, default=1e6)
     return p.parse_args()
 
 
@@ -367,6 +380,145 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def _group_graph(args):
+    k, count, n_hi = args
+    n, blocks, mu, seed = synth.planted_group_params(count, 1e4, n_hi, GROUP_SEED)[k]
+    g = synth.planted_partition(n, blocks, mu, 16.0, 16, seed)
+    return g, (g.n, *synth.to_csr(g)), {"n": n, "blocks": blocks, "mu": round(mu, 4)}
+
+
+def group_arm(args):
+    import torch
+
+    import paper_2404_19634_gb300 as dfl
+
+    G = args.group_graphs
+    t_gen = time.perf_counter()
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        made = pool.map(_group_graph, [(k, G, args.group_max_n) for k in range(G)])
+    gen_s = time.perf_counter() - t_gen
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dfl.build()
+    graphs = [g for g, _, _ in made]
+    csrs = [c for _, c, _ in made]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    nsteps = args.warmup + args.steps
+    bstreams = [synth.BatchStream(g, 500 + k) for k, g in enumerate(graphs)]
+    batches = [[bs.next(max(1, int(round(1e-4 * g.m))), w_max=16) for bs, g in zip(bstreams, graphs)]
+               for _ in range(nsteps)]
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+    # one group handle: batches of all graphs in one device array each
+    grp = dfl.DflGroup(csrs, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grp.static()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    group_static_ms = e0.elapsed_time(e1)
+    gbatches = []
+    for step in batches:
+        d = np.concatenate([b[0] for b in step])
+        i = np.concatenate([b[1] for b in step])
+        doff = np.concatenate([[0], np.cumsum([b[0].shape[0] for b in step])]).astype(np.uint64)
+        ioff = np.concatenate([[0], np.cumsum([b[1].shape[0] for b in step])]).astype(np.uint64)
+        gbatches.append(((to_dev(d), doff), (to_dev(i), ioff)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def time_steps(run_step, first, count):
+        ms = []
+        for k in range(first, first + count):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run_step(k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    def group_step(k):
+        grp.apply_batches(*gbatches[k])
+        grp.update(dfl.DF)
+
+    time_steps(group_step, 0, args.warmup)
+    l0 = grp.stats()["kernel_launches"]
+    with Clocks(0) as clocks:
+        group_ms = time_steps(group_step, args.warmup, args.steps)
+    group_launches = grp.stats()["kernel_launches"] - l0
+    group_final = [grp.graph_modularity(g)[1:] for g in range(G)]
+    passes = [grp.graph_stats(g)["passes"] for g in range(G)]
+
+    # the same graphs and batches, one handle per graph, one after another
+    hs = [dfl.Dfl(n, off, idx, w, stream=stream) for n, off, idx, w in csrs]
+    t0 = time.perf_counter()
+    for h in hs:
+        h.static()
+    torch.cuda.synchronize()
+    serial_static_ms = 1e3 * (time.perf_counter() - t0)
+    sbatches = [[(to_dev(d), to_dev(i)) for d, i in step] for step in batches]
+
+    def serial_step(k):
+        for h, (d, i) in zip(hs, sbatches[k]):
+            h.apply_batch(d, i)
+            h.update(dfl.DF)
+
+    time_steps(serial_step, 0, args.warmup)
+    serial_ms = time_steps(serial_step, args.warmup, args.steps)
+    serial_final = [h.modularity()[1:] for h in hs]
+    identical = serial_final == group_final
+    same_membership = all(np.array_equal(grp.graph_membership(g), hs[g].membership()) for g in range(G))
+    for h in hs:
+        h.close()
+
+    # end to end: host batches in, every graph's membership out, each step
+    e2e = None
+    if not args.profile_only:
+        host = []
+        for _ in range(args.steps):
+            step = [bs.next(max(1, int(round(1e-4 * g.m))), w_max=16) for bs, g in zip(bstreams, graphs)]
+            host.append(([b[0] for b in step], [b[1] for b in step]))
+        out = [np.zeros(g.n, np.uint32) for g in graphs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, i in host:
+            grp.apply_batches(d, i)
+            grp.update(dfl.DF)
+            for g in range(G):
+                grp.graph_membership(g, out[g])
+        torch.cuda.synchronize()
+        e2e = {"value": 1e3 * (time.perf_counter() - t0) / args.steps, "unit": "ms",
+               "h2d_bytes_per_step": int(np.mean([12 * sum(x.shape[0] for x in d + i) for d, i in host])),
+               "d2h_bytes_per_step": 4 * sum(g.n for g in graphs)}
+    grp.close()
+    value = statistics.mean(group_ms)
+    line = {
+        "metric": GROUP_METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{G} planted-partition graphs, n log-uniform [1e4, {args.group_max_n:g}], "
+                               "blocks [20, 2000], mu [0.1, 0.5], weights 1-16, 8 edges per vertex; "
+                               "DF batches of 1e-4|E| per graph (80/20)",
+                   "vertices": sum(g.n for g in graphs), "edges": sum(g.m for g in graphs),
+                   "batch_edges_per_step": sum(d.shape[0] + i.shape[0] for d, i in batches[0]),
+                   "l2": "flushed between timed steps (256 MB write)", "generation_s": round(gen_s, 1),
+                   "group_static_ms": round(group_static_ms, 2),
+                   "serial_static_ms": round(serial_static_ms, 2),
+                   "passes_min_max": [min(passes), max(passes)]},
+        "serial_ms_per_step": statistics.mean(serial_ms),
+        "speedup_vs_serial": statistics.mean(serial_ms) / value,
+        "identical_to_serial": bool(identical and same_membership),
+        "e2e": e2e,
+        "gpu_launches": int(group_launches),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _serve_graph(k):
     g = synth.rmat(SERVE_SCALES[k], 8 << SERVE_SCALES[k], 300 + k)
     return g, (g.n, *synth.to_csr(g))
@@ -452,6 +604,9 @@ def main():
     args = parse()
     if args.serve:
         serve_arm(args)
+        return
+    if args.group:
+        group_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args)

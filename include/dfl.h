@@ -238,6 +238,90 @@ int dfl_move_iteration(dfl_handle* h, uint8_t* F, const uint8_t* R, uint8_t* mov
 int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets,
                   uint32_t* indices, uint64_t* weights);
 
+/* ---- Kernel tuning ------------------------------------------------------ */
+
+/* Launch-shape choices of the local-moving step.  They change which kernel
+ * decides a vertex and where its community table lives, never the result:
+ * any valid tuning gives the same membership, K, Sigma and modularity.
+ *   degree <= bin_warp:       one warp, table in registers (match/reduce)
+ *   degree <= bin_warp_hash:  one warp, open-addressing table in shared memory
+ *   degree <= bin_block:      one block of block_threads, shared-memory table
+ *                             (global-memory slice when it overflows)
+ *   larger:                   split into 4096-arc chunks, one block each,
+ *                             partial sums merged by the vertex's last block
+ * Valid ranges: bin_warp <= 32, bin_warp <= bin_warp_hash <= 256,
+ * bin_warp_hash <= bin_block, block_threads in {128, 256, 512}.
+ * Defaults: 32, 256, 4096, 256. */
+typedef struct {
+  uint32_t bin_warp;
+  uint32_t bin_warp_hash;
+  uint32_t bin_block;
+  uint32_t block_threads;
+} dfl_tuning;
+
+int dfl_get_tuning(const dfl_handle* h, dfl_tuning* t);
+int dfl_set_tuning(dfl_handle* h, const dfl_tuning* t); /* DFL_ERR_INVALID if out of range */
+
+/* Autotuner: marks the initial frontier that dfl_update(mode) would use for
+ * the pending batch (every vertex for DFL_ND), then times one local-moving
+ * iteration's decide phase over it (CUDA events, median of `reps`) for
+ * candidate tunings by coordinate descent over block_threads, bin_block,
+ * bin_warp_hash and bin_warp, starting from the current tuning.  Decisions
+ * are computed but not applied, so the graph, membership and pending batch
+ * are unchanged; the fastest tuning is set on the handle and written to
+ * *chosen (may be NULL).  *ms (may be NULL) receives its median time. */
+int dfl_autotune(dfl_handle* h, int mode, uint32_t reps, dfl_tuning* chosen, double* ms);
+
+/* ---- Groups: many independent graphs in one handle --------------------- */
+
+/* A group holds G independent graphs in one handle, laid out as their
+ * disjoint union (graph g's vertices are a contiguous range), so that every
+ * step of an update -- batch apply, marking, each local-moving sub-step,
+ * aggregation -- is one launch over all graphs.  Each graph keeps its own
+ * 2m, tolerance test, iteration and pass counts and aggregation decision
+ * (Alg. 4-5 per graph): every graph gets exactly the membership, K, Sigma
+ * and modularity that a handle of its own would, with labels in [0, n_g).
+ * A graph that converges stops being processed while the others continue.
+ * Each graph's 2m must stay below 2^32; the group's total need not.
+ *
+ * dfl_group_create: G graphs, graph g given as symmetric CSR (the
+ * dfl_create rules) offsets[g] (n[g]+1 entries), indices[g], weights[g],
+ * all in HOST memory.  The sum of n[g] must be below 2^31.  The returned
+ * handle works with dfl_destroy, dfl_set_options, dfl_set_stream,
+ * dfl_profile, dfl_get/set_tuning, dfl_autotune and dfl_membership (labels
+ * of the union, graph g's in [start_g, start_g + n_g)); dfl_static,
+ * dfl_apply_batch, dfl_update and dfl_modularity return DFL_ERR_STATE on it. */
+int dfl_group_create(dfl_handle** out, uint32_t num_graphs, const uint32_t* n,
+                     const uint64_t* const* offsets, const uint32_t* const* indices,
+                     const uint32_t* const* weights, const dfl_options* opt, void* cuda_stream);
+
+/* Static Louvain of every graph of the group. */
+int dfl_group_static(dfl_handle* h);
+
+/* One batch per graph: graph g's deletions are del[del_off[g] .. del_off[g+1])
+ * and its insertions ins[ins_off[g] .. ins_off[g+1]), with vertex ids local
+ * to graph g (del_off and ins_off have num_graphs + 1 entries, in HOST
+ * memory; del and ins in memory of kind mem_kind).  The batches are applied
+ * together (dfl_apply_batch rules per graph); on any error nothing changes.
+ * DFL_ERR_OVERFLOW also if a graph's 2m plus twice its inserted weight would
+ * reach 2^32. */
+int dfl_group_apply_batch(dfl_handle* h, const dfl_edge* del, const uint64_t* del_off,
+                          const dfl_edge* ins, const uint64_t* ins_off, int mem_kind);
+
+/* Update every graph for its pending batch (mode as in dfl_update). */
+int dfl_group_update(dfl_handle* h, int mode);
+
+/* Membership of graph g (n_g labels in [0, n_g)). */
+int dfl_group_membership(dfl_handle* h, uint32_t g, uint32_t* out, int mem_kind);
+
+/* Modularity of graph g (as dfl_modularity). */
+int dfl_group_modularity(dfl_handle* h, uint32_t g, double* q, int64_t* parts);
+
+/* Statistics of graph g for the last dfl_group_static / dfl_group_update
+ * (passes, iterations, num_communities; the launch, arc and capture
+ * counters are the group's). */
+int dfl_group_stats(dfl_handle* h, uint32_t g, dfl_stats_t* s);
+
 /* ---- Allocation-free entry point --------------------------------------- */
 
 /* Largest vertex count accepted by dfl_modularity_csr_noalloc. */

@@ -101,6 +101,14 @@ class Profile(ct.Structure):
     _fields_ = [("launches", ct.c_uint64 * 10), ("ms", ct.c_double * 10), ("bytes", ct.c_uint64 * 10)]
 
 
+class Tuning(ct.Structure):
+    _fields_ = [("bin_warp", ct.c_uint32), ("bin_warp_hash", ct.c_uint32),
+                ("bin_block", ct.c_uint32), ("block_threads", ct.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 # Every function the header declares, with its argument types.
@@ -129,6 +137,18 @@ _SIGS = {
     "dfl_louvain_from": (ct.c_int, [_P, _P, _P, ct.c_int]),
     "dfl_move_iteration": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
     "dfl_aggregate": (ct.c_int, [_P, ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint64), _P, _P, _P]),
+    "dfl_get_tuning": (ct.c_int, [_P, ct.POINTER(Tuning)]),
+    "dfl_set_tuning": (ct.c_int, [_P, ct.POINTER(Tuning)]),
+    "dfl_autotune": (ct.c_int, [_P, ct.c_int, ct.c_uint32, ct.POINTER(Tuning),
+                                ct.POINTER(ct.c_double)]),
+    "dfl_group_create": (ct.c_int, [ct.POINTER(_P), ct.c_uint32, _P, _P, _P, _P,
+                                    ct.POINTER(Options), _P]),
+    "dfl_group_static": (ct.c_int, [_P]),
+    "dfl_group_apply_batch": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
+    "dfl_group_update": (ct.c_int, [_P, ct.c_int]),
+    "dfl_group_membership": (ct.c_int, [_P, ct.c_uint32, _P, ct.c_int]),
+    "dfl_group_modularity": (ct.c_int, [_P, ct.c_uint32, ct.POINTER(ct.c_double), _P]),
+    "dfl_group_stats": (ct.c_int, [_P, ct.c_uint32, ct.POINTER(Stats)]),
     "dfl_modularity_csr_noalloc": (ct.c_int, [ct.c_uint32, _P, _P, _P, _P, ct.POINTER(ct.c_double),
                                               _P, _P]),
 }
@@ -253,6 +273,26 @@ class Dfl:
     def set_options(self, options: Options):
         self._check(self._lib.dfl_set_options(self._h, ct.byref(options)))
 
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(self._lib.dfl_get_tuning(self._h, ct.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        self._check(self._lib.dfl_get_tuning(self._h, ct.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(self._lib.dfl_set_tuning(self._h, ct.byref(t)))
+
+    def autotune(self, mode: int = DF, reps: int = 3):
+        """Pick the fastest launch shapes for the pending batch's frontier;
+        returns (tuning dict, median decide ms)."""
+        t = Tuning()
+        ms = ct.c_double()
+        self._check(self._lib.dfl_autotune(self._h, mode, reps, ct.byref(t), ct.byref(ms)))
+        return t.as_dict(), ms.value
+
     def set_stream(self, stream):
         self._check(self._lib.dfl_set_stream(self._h, _stream_ptr(stream)))
 
@@ -374,6 +414,88 @@ class Dfl:
                                             idx.ctypes.data_as(ct.c_void_p),
                                             w.ctypes.data_as(ct.c_void_p)))
         return off, idx[: na.value], w[: na.value]
+
+
+class DflGroup(Dfl):
+    """Many independent graphs in one handle (dfl_group_*): one launch per
+    step covers every graph, each graph gets the result a Dfl of its own
+    would.  graphs: list of (n, offsets, indices, weights) host CSR arrays."""
+
+    def __init__(self, graphs, options: Options | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        G = len(graphs)
+        self.sizes = [int(g[0]) for g in graphs]
+        self._keep = []
+        ns = np.array(self.sizes, np.uint32)
+        ptrs = {k: (ct.c_void_p * G)() for k in ("off", "idx", "w")}
+        for g, (n, off, idx, w) in enumerate(graphs):
+            a = np.ascontiguousarray(off, np.uint64)
+            b = np.ascontiguousarray(idx, np.uint32)
+            c = np.ascontiguousarray(w, np.uint32)
+            self._keep += [a, b, c]
+            ptrs["off"][g] = a.ctypes.data
+            ptrs["idx"][g] = b.ctypes.data
+            ptrs["w"][g] = c.ctypes.data
+        h = ct.c_void_p()
+        rc = lib.dfl_group_create(ct.byref(h), G, ns.ctypes.data_as(ct.c_void_p),
+                                  ct.cast(ptrs["off"], ct.c_void_p), ct.cast(ptrs["idx"], ct.c_void_p),
+                                  ct.cast(ptrs["w"], ct.c_void_p),
+                                  ct.byref(options) if options is not None else None, _stream_ptr(stream))
+        self._keep = []
+        if rc != 0:
+            raise DflError(rc, "dfl_group_create")
+        self._h = h
+        self.n = int(sum(self.sizes))
+        self.ngraphs = G
+
+    def static(self):
+        self._check(self._lib.dfl_group_static(self._h))
+
+    def apply_batches(self, dels, ins, check: bool = True) -> int:
+        """dels/ins: per graph (k, 3) uint32 arrays with local vertex ids
+        (host), or a pair (CUDA int32 tensor of all edges, offsets)."""
+        if isinstance(dels, tuple):
+            (d, doff), (i, ioff) = dels, ins
+            dp, mk, k0 = _buf(d, np.uint32)
+            ip, _, k1 = _buf(i, np.uint32)
+        else:
+            doff = np.concatenate([[0], np.cumsum([x.shape[0] for x in dels])]).astype(np.uint64)
+            ioff = np.concatenate([[0], np.cumsum([x.shape[0] for x in ins])]).astype(np.uint64)
+            d = np.concatenate([np.asarray(x, np.uint32).reshape(-1, 3) for x in dels]) if dels else np.zeros((0, 3), np.uint32)
+            i = np.concatenate([np.asarray(x, np.uint32).reshape(-1, 3) for x in ins]) if ins else np.zeros((0, 3), np.uint32)
+            dp, mk, k0 = _buf(d, np.uint32)
+            ip, _, k1 = _buf(i, np.uint32)
+        doff = np.ascontiguousarray(doff, np.uint64)
+        ioff = np.ascontiguousarray(ioff, np.uint64)
+        rc = self._lib.dfl_group_apply_batch(self._h, dp, doff.ctypes.data_as(ct.c_void_p), ip,
+                                             ioff.ctypes.data_as(ct.c_void_p), mk)
+        if check:
+            self._check(rc)
+        return rc
+
+    def update(self, mode: int):
+        self._check(self._lib.dfl_group_update(self._h, mode))
+
+    def graph_membership(self, g: int, out=None):
+        if out is None:
+            out = np.zeros(self.sizes[g], np.uint32)
+        p, mk, _ = _buf(out, np.uint32)
+        self._check(self._lib.dfl_group_membership(self._h, g, p, mk))
+        return out
+
+    def graph_modularity(self, g: int):
+        q = ct.c_double()
+        parts = np.zeros(4, np.int64)
+        self._check(self._lib.dfl_group_modularity(self._h, g, ct.byref(q),
+                                                   parts.ctypes.data_as(ct.c_void_p)))
+        return q.value, _i128(int(parts[0]), int(parts[1])), _i128(int(parts[2]), int(parts[3]))
+
+    def graph_stats(self, g: int) -> dict:
+        s = Stats()
+        self._check(self._lib.dfl_group_stats(self._h, g, ct.byref(s)))
+        return {"passes": s.passes, "iterations": list(s.iterations)[: s.passes],
+                "num_communities": s.num_communities}
 
 
 def __getattr__(name):

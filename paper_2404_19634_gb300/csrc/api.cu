@@ -112,10 +112,13 @@ void free_all(Handle* h) {
                   h->h_delta, h->h_pairs, h->r_app, h->r_tomb, h->r_live, h->r_state, h->r_reg,
                   h->h_rows, h->h_extra,
                   h->sg[0].off, h->sg[0].deg, h->sg[0].arcs, h->sg[1].off, h->sg[1].deg,
-                  h->sg[1].arcs};
+                  h->sg[1].arcs, h->d_goff0, h->d_goff, h->d_gnext, h->d_gm2, h->d_gdone,
+                  h->d_gflag, h->d_gS, h->d_gsum, h->Cfin, h->gb_edges, h->d_eoff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
+  if (h->h_gdone) cudaFreeHost(h->h_gdone);
+  if (h->h_gS) cudaFreeHost(h->h_gS);
   for (int k = 0; k < kBins - 1; ++k) {
     if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
     if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
@@ -202,22 +205,19 @@ void dfl_default_options(dfl_options* o) {
   o->flags = 0;
 }
 
-int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint32_t* indices,
-               const uint32_t* weights, uint64_t nnz, int mem_kind, const dfl_options* opt,
-               void* cuda_stream) {
-  using namespace dfl;
-  if (!out || !offsets || (nnz && (!indices || !weights))) return DFL_ERR_INVALID;
-  if (n >= (1u << 31)) return DFL_ERR_INVALID;
-  if (mem_kind != DFL_MEM_HOST && mem_kind != DFL_MEM_DEVICE) return DFL_ERR_INVALID;
-  *out = nullptr;
-  dfl_handle* h = new (std::nothrow) dfl_handle();
-  if (!h) return DFL_ERR_NOMEM;
+}  // extern "C"
+
+namespace dfl {
+namespace {
+
+// Everything of dfl_create after the handle exists (a group sets its graph
+// ranges first).  On failure the caller frees the handle.
+int create_common(Handle* h, uint32_t n, const uint64_t* offsets, const uint32_t* indices,
+                  const uint32_t* weights, uint64_t nnz, int mem_kind, const dfl_options* opt,
+                  void* cuda_stream) {
   dfl_default_options(&h->opt);
   if (opt) {
-    if (check_options(opt)) {
-      delete h;
-      return DFL_ERR_INVALID;
-    }
+    if (check_options(opt)) return DFL_ERR_INVALID;
     h->opt = *opt;
   }
   std::memset(&h->stats, 0, sizeof(h->stats));
@@ -295,6 +295,61 @@ int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint
   }
   if (!rc) rc = weighted_degrees(h);
   if (!rc) rc = (cudaStreamSynchronize(h->stream) == cudaSuccess) ? DFL_OK : DFL_ERR_CUDA;
+  return rc;
+}
+
+// Group membership of graph g: labels moved to [0, n_g).
+__global__ void k_local_labels(uint32_t v0, uint32_t cnt, const uint32_t* __restrict__ C,
+                               uint32_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < cnt;
+       i += uint64_t(gridDim.x) * blockDim.x)
+    out[i] = C[v0 + i] - v0;
+}
+
+// A group batch in union ids: edge e of the staged array belongs to the
+// graph whose range of eoff holds e; ids are checked against that graph's
+// size and shifted to its range; inserted weight is summed per graph.
+__global__ void k_group_edges(dfl_edge* __restrict__ e, uint64_t cnt, const uint64_t* __restrict__ eoff,
+                              uint32_t ng, const uint32_t* __restrict__ goff0, bool ins,
+                              unsigned long long* __restrict__ insw, Ctrl* ctrl) {
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < cnt;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t pos = eoff[0] + t;
+    uint32_t lo = 0, hi = ng;  // largest g with eoff[g] <= pos
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (eoff[mid] <= pos) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t g = lo, base = goff0[g], size = goff0[g + 1] - base;
+    dfl_edge x = e[t];
+    if (x.u >= size || x.v >= size) {
+      atomicOr(&ctrl->err, kErrInvalid);
+      continue;
+    }
+    x.u += base;
+    x.v += base;
+    e[t] = x;
+    if (ins) atomicAdd(insw + g, (unsigned long long)x.w);
+  }
+}
+
+}  // namespace
+}  // namespace dfl
+
+extern "C" {
+
+int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint32_t* indices,
+               const uint32_t* weights, uint64_t nnz, int mem_kind, const dfl_options* opt,
+               void* cuda_stream) {
+  using namespace dfl;
+  if (!out || !offsets || (nnz && (!indices || !weights))) return DFL_ERR_INVALID;
+  if (n >= (1u << 31)) return DFL_ERR_INVALID;
+  if (mem_kind != DFL_MEM_HOST && mem_kind != DFL_MEM_DEVICE) return DFL_ERR_INVALID;
+  *out = nullptr;
+  dfl_handle* h = new (std::nothrow) dfl_handle();
+  if (!h) return DFL_ERR_NOMEM;
+  int rc = create_common(h, n, offsets, indices, weights, nnz, mem_kind, opt, cuda_stream);
   if (rc) {
     free_all(h);
     delete h;
@@ -327,6 +382,7 @@ int dfl_set_stream(dfl_handle* h, void* s) {
 int dfl_static(dfl_handle* h) {
   using namespace dfl;
   if (!h) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   DFL_TRY(weighted_degrees(h));
   DFL_TRY(iota_u32(h, h->C, h->n));
   DFL_TRY(copy_i64(h, h->Sigma, h->K, h->n));
@@ -345,12 +401,14 @@ int dfl_apply_batch(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const df
                     uint64_t n_ins, int mem_kind) {
   if (!h || (n_del && !del) || (n_ins && !ins)) return DFL_ERR_INVALID;
   if (mem_kind != DFL_MEM_HOST && mem_kind != DFL_MEM_DEVICE) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   return dfl::apply_batch(h, del, n_del, ins, n_ins, mem_kind);
 }
 
 int dfl_update(dfl_handle* h, int mode) {
   using namespace dfl;
   if (!h) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_update before dfl_static");
   if (mode != DFL_ND && mode != DFL_DS && mode != DFL_DF)
     return set_error(h, DFL_ERR_INVALID, "unknown mode");
@@ -374,6 +432,7 @@ int dfl_membership(const dfl_handle* hc, uint32_t* out, int mem_kind) {
 int dfl_modularity(dfl_handle* h, double* q, int64_t* parts) {
   using namespace dfl;
   if (!h || !q) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
   i128 num = 0, den = 0;
   DFL_TRY(modularity_parts(h, &num, &den));
@@ -449,6 +508,7 @@ const char* dfl_last_error(const dfl_handle* h) { return h ? h->err.c_str() : "n
 int dfl_set_membership(dfl_handle* h, const uint32_t* C, int mem_kind) {
   using namespace dfl;
   if (!h || !C) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   DFL_TRY(copy_in(h, h->Cs, C, sizeof(uint32_t) * h->n, mem_kind));
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
   {
@@ -470,6 +530,7 @@ int dfl_set_membership(dfl_handle* h, const uint32_t* C, int mem_kind) {
 int dfl_mark(dfl_handle* h, int mode, uint8_t* F, uint8_t* R, int mem_kind) {
   using namespace dfl;
   if (!h || !F || !R) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
   if (mode != DFL_ND && mode != DFL_DS && mode != DFL_DF) return set_error(h, DFL_ERR_INVALID, "mode");
   bool all = false, use_range = false;
@@ -497,6 +558,7 @@ int dfl_mark(dfl_handle* h, int mode, uint8_t* F, uint8_t* R, int mem_kind) {
 int dfl_louvain_from(dfl_handle* h, const uint8_t* F0, const uint8_t* R0, int mem_kind) {
   using namespace dfl;
   if (!h || !F0 || !R0) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
   uint64_t initial = 0;
   DFL_TRY(frontier_from_bytes(h, F0, R0, mem_kind, &initial));
@@ -509,6 +571,7 @@ int dfl_move_iteration(dfl_handle* h, uint8_t* F, const uint8_t* R, uint8_t* mov
                        int mem_kind) {
   using namespace dfl;
   if (!h || !F || !R || !moved || !dq) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
   uint64_t initial = 0;
   DFL_TRY(frontier_from_bytes(h, F, R, mem_kind, &initial));
@@ -569,6 +632,7 @@ int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets, 
                   uint64_t* weights) {
   using namespace dfl;
   if (!h || !nv || !na) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
   uint32_t ncomm = 0;
   DFL_TRY(count_communities(h, h->C, h->n, &ncomm));
@@ -607,6 +671,239 @@ int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets, 
     }
     offsets[c + 1] = k;
   }
+  return DFL_OK;
+}
+
+int dfl_get_tuning(const dfl_handle* h, dfl_tuning* t) {
+  if (!h || !t) return DFL_ERR_INVALID;
+  *t = h->tune;
+  return DFL_OK;
+}
+
+int dfl_set_tuning(dfl_handle* h, const dfl_tuning* t) {
+  if (!h || !t) return DFL_ERR_INVALID;
+  if (dfl::check_tuning(*t)) return dfl::set_error(h, DFL_ERR_INVALID, "tuning out of range");
+  h->tune = *t;
+  return DFL_OK;
+}
+
+int dfl_autotune(dfl_handle* h, int mode, uint32_t reps, dfl_tuning* chosen, double* ms) {
+  using namespace dfl;
+  if (!h) return DFL_ERR_INVALID;
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
+  if (mode != DFL_ND && mode != DFL_DS && mode != DFL_DF)
+    return set_error(h, DFL_ERR_INVALID, "unknown mode");
+  double t = 0;
+  DFL_TRY(autotune(h, mode, reps, &t));
+  if (chosen) *chosen = h->tune;
+  if (ms) *ms = t;
+  return DFL_OK;
+}
+
+int dfl_group_create(dfl_handle** out, uint32_t num_graphs, const uint32_t* n,
+                     const uint64_t* const* offsets, const uint32_t* const* indices,
+                     const uint32_t* const* weights, const dfl_options* opt, void* cuda_stream) {
+  using namespace dfl;
+  if (!out || !num_graphs || !n || !offsets || !indices || !weights) return DFL_ERR_INVALID;
+  *out = nullptr;
+  const uint32_t G = num_graphs;
+  // the disjoint union on the host: graph g's vertices start at goff0[g]
+  std::vector<uint32_t> goff0(G + 1, 0);
+  uint64_t total = 0, nnz = 0;
+  for (uint32_t g = 0; g < G; ++g) {
+    if (!offsets[g] || (offsets[g][n[g]] && (!indices[g] || !weights[g]))) return DFL_ERR_INVALID;
+    total += n[g];
+    if (total >= (1ull << 31)) return DFL_ERR_INVALID;
+    goff0[g + 1] = uint32_t(total);
+    nnz += offsets[g][n[g]];
+  }
+  std::vector<uint64_t> off(total + 1);
+  std::vector<uint32_t> idx(nnz ? nnz : 1), w(nnz ? nnz : 1);
+  uint64_t e = 0;
+  for (uint32_t g = 0; g < G; ++g) {
+    const uint64_t* o = offsets[g];
+    const uint64_t base = o[0];
+    for (uint32_t i = 0; i < n[g]; ++i) off[goff0[g] + i] = e + (o[i] - base);
+    const uint64_t cnt = o[n[g]] - base;
+    for (uint64_t k = 0; k < cnt; ++k) {
+      idx[e + k] = indices[g][base + k] + goff0[g];
+      w[e + k] = weights[g][base + k];
+    }
+    e += cnt;
+  }
+  off[total] = e;
+  dfl_handle* h = new (std::nothrow) dfl_handle();
+  if (!h) return DFL_ERR_NOMEM;
+  h->ngraphs = G;
+  h->goff0 = goff0;
+  h->gm2.assign(G, 0);
+  h->gfin.assign(G, 0);
+  dfl_stats_t z;
+  std::memset(&z, 0, sizeof(z));
+  h->gstats.assign(G, z);
+  int rc = create_common(h, uint32_t(total), off.data(), idx.data(), w.data(), e, DFL_MEM_HOST, opt,
+                         cuda_stream);
+  auto A = [&](auto** p, uint64_t cnt) {
+    if (!rc) rc = alloc(h, p, cnt);
+  };
+  A(&h->d_goff0, G + 1);
+  A(&h->d_goff, G + 1);
+  A(&h->d_gnext, G + 1);
+  A(&h->d_gm2, G);
+  A(&h->d_gdone, G);
+  A(&h->d_gflag, G);
+  A(&h->d_gS, 2 * uint64_t(G));
+  A(&h->d_gsum, 3 * uint64_t(G));
+  A(&h->d_eoff, 2 * (uint64_t(G) + 1));
+  A(&h->Cfin, total);
+  if (!rc && (cudaMallocHost(&h->h_gdone, G) != cudaSuccess ||
+              cudaMallocHost(&h->h_gS, sizeof(unsigned long long) * 2 * G) != cudaSuccess))
+    rc = set_error(h, DFL_ERR_NOMEM, "pinned group buffers");
+  if (!rc) rc = copy_in(h, h->d_goff0, goff0.data(), sizeof(uint32_t) * (G + 1), DFL_MEM_HOST);
+  if (!rc) rc = copy_in(h, h->d_goff, goff0.data(), sizeof(uint32_t) * (G + 1), DFL_MEM_HOST);
+  if (!rc) rc = group_m2(h);
+  if (rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return DFL_OK;
+}
+
+int dfl_group_static(dfl_handle* h) {
+  using namespace dfl;
+  if (!h) return DFL_ERR_INVALID;
+  if (!h->ngraphs) return set_error(h, DFL_ERR_STATE, "not a group handle");
+  DFL_TRY(weighted_degrees(h));
+  DFL_TRY(group_m2(h));
+  DFL_TRY(iota_u32(h, h->C, h->n));
+  DFL_TRY(copy_i64(h, h->Sigma, h->K, h->n));
+  DFL_TRY(fill_i32(h, h->csize, 1, h->n));
+  h->pend_count = 0;
+  h->have_communities = true;
+  DFL_TRY(group_set_level(h, h->d_goff0));  // classes of the base graphs' vertices
+  make_segs(h, h->opt.substeps);
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[0], 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_TRY(lists_all(h, h->n, h->deg, 0, h->opt.substeps));
+  return louvain_group(h, true, false, h->n);
+}
+
+int dfl_group_apply_batch(dfl_handle* h, const dfl_edge* del, const uint64_t* del_off,
+                          const dfl_edge* ins, const uint64_t* ins_off, int mem_kind) {
+  using namespace dfl;
+  if (!h || !del_off || !ins_off) return DFL_ERR_INVALID;
+  if (mem_kind != DFL_MEM_HOST && mem_kind != DFL_MEM_DEVICE) return DFL_ERR_INVALID;
+  if (!h->ngraphs) return set_error(h, DFL_ERR_STATE, "not a group handle");
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_group_apply_batch before dfl_group_static");
+  const uint32_t G = h->ngraphs;
+  for (uint32_t g = 0; g < G; ++g)
+    if (del_off[g + 1] < del_off[g] || ins_off[g + 1] < ins_off[g])
+      return set_error(h, DFL_ERR_INVALID, "batch offsets must not decrease");
+  const uint64_t nd = del_off[G] - del_off[0], ni = ins_off[G] - ins_off[0];
+  if ((nd && !del) || (ni && !ins)) return DFL_ERR_INVALID;
+  // stage both lists on the device, in union ids
+  if (nd + ni > h->gb_cap) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->gb_edges);
+    h->gb_edges = nullptr;
+    h->gb_cap = 0;
+    const uint64_t want = (nd + ni) + (nd + ni) / 4 + 1024;
+    DFL_CUDA(h, cudaMalloc(&h->gb_edges, sizeof(dfl_edge) * want));
+    h->gb_cap = want;
+  }
+  dfl_edge* sd = h->gb_edges;
+  dfl_edge* si = h->gb_edges + nd;
+  DFL_TRY(copy_in(h, sd, del + del_off[0], sizeof(dfl_edge) * nd, mem_kind));
+  DFL_TRY(copy_in(h, si, ins + ins_off[0], sizeof(dfl_edge) * ni, mem_kind));
+  DFL_TRY(copy_in(h, h->d_eoff, del_off, sizeof(uint64_t) * (G + 1), DFL_MEM_HOST));
+  DFL_TRY(copy_in(h, h->d_eoff + G + 1, ins_off, sizeof(uint64_t) * (G + 1), DFL_MEM_HOST));
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->d_gsum, 0, sizeof(unsigned long long) * G, h->stream));
+  if (nd) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_group_edges<<<grid_for(nd, 256), 256, 0, h->stream>>>(sd, nd, h->d_eoff, G, h->d_goff0, false,
+                                                            h->d_gsum, h->ctrl);
+    DFL_TRY(check_launch(h, "group batch"));
+  }
+  if (ni) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_group_edges<<<grid_for(ni, 256), 256, 0, h->stream>>>(si, ni, h->d_eoff + G + 1, G, h->d_goff0,
+                                                            true, h->d_gsum, h->ctrl);
+    DFL_TRY(check_launch(h, "group batch"));
+  }
+  std::vector<unsigned long long> insw(G);
+  DFL_CUDA(h, cudaMemcpyAsync(insw.data(), h->d_gsum, sizeof(unsigned long long) * G,
+                              cudaMemcpyDeviceToHost, h->stream));
+  DFL_TRY(read_ctrl(h));
+  if (h->hctrl->err) return set_error(h, DFL_ERR_INVALID, "vertex id >= the graph's size");
+  for (uint32_t g = 0; g < G; ++g)
+    if ((unsigned long long)h->gm2[g] + 2 * insw[g] >= (1ull << 32))
+      return set_error(h, DFL_ERR_OVERFLOW, "a graph's 2m could reach 2^32");
+  DFL_TRY(apply_batch(h, sd, nd, si, ni, DFL_MEM_DEVICE));
+  return group_m2(h);
+}
+
+int dfl_group_update(dfl_handle* h, int mode) {
+  using namespace dfl;
+  if (!h) return DFL_ERR_INVALID;
+  if (!h->ngraphs) return set_error(h, DFL_ERR_STATE, "not a group handle");
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_group_update before dfl_group_static");
+  if (mode != DFL_ND && mode != DFL_DS && mode != DFL_DF)
+    return set_error(h, DFL_ERR_INVALID, "unknown mode");
+  bool all = false, use_range = false;
+  uint64_t initial = 0;
+  DFL_TRY(group_set_level(h, h->d_goff0));  // classes of the base graphs' vertices
+  DFL_TRY(mark(h, mode, &all, &use_range, &initial));
+  int rc = louvain_group(h, all, use_range, initial);
+  h->pend_count = 0;
+  return rc;
+}
+
+int dfl_group_membership(dfl_handle* h, uint32_t g, uint32_t* out, int mem_kind) {
+  using namespace dfl;
+  if (!h || !out) return DFL_ERR_INVALID;
+  if (!h->ngraphs || g >= h->ngraphs) return set_error(h, DFL_ERR_INVALID, "no such graph");
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
+  const uint32_t v0 = h->goff0[g], cnt = h->goff0[g + 1] - v0;
+  if (!cnt) return DFL_OK;
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_local_labels<<<grid_for(cnt, 256), 256, 0, h->stream>>>(v0, cnt, h->C, h->Cs);
+    DFL_TRY(check_launch(h, "group labels"));
+  }
+  DFL_TRY(copy_out(h, out, h->Cs, sizeof(uint32_t) * cnt, mem_kind));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+int dfl_group_modularity(dfl_handle* h, uint32_t g, double* q, int64_t* parts) {
+  using namespace dfl;
+  if (!h || !q) return DFL_ERR_INVALID;
+  if (!h->ngraphs || g >= h->ngraphs) return set_error(h, DFL_ERR_INVALID, "no such graph");
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "no communities yet");
+  i128 num = 0, den = 0;
+  DFL_TRY(group_modularity(h, g, &num, &den));
+  *q = den == 0 ? 0.0 : double(num) / double(den);
+  if (parts) {
+    parts[0] = int64_t(uint64_t((u128)num >> 64));
+    parts[1] = int64_t(uint64_t((u128)num));
+    parts[2] = int64_t(uint64_t((u128)den >> 64));
+    parts[3] = int64_t(uint64_t((u128)den));
+  }
+  return DFL_OK;
+}
+
+int dfl_group_stats(dfl_handle* h, uint32_t g, dfl_stats_t* s) {
+  if (!h || !s) return DFL_ERR_INVALID;
+  if (!h->ngraphs || g >= h->ngraphs) return dfl::set_error(h, DFL_ERR_INVALID, "no such graph");
+  DFL_TRY(dfl_stats(h, s));
+  const dfl_stats_t& q = h->gstats[g];
+  s->passes = q.passes;
+  for (int p = 0; p < 16; ++p) s->iterations[p] = q.iterations[p];
+  s->num_communities = q.num_communities;
   return DFL_OK;
 }
 

@@ -400,7 +400,7 @@ __global__ void k_mark_df(const unsigned long long* __restrict__ key, uint64_t n
       bool same = C[u] == C[v];
       if (ins != same && bit_set(fbits, u)) {
         valid = true;
-        lk = substep_class(u, k) * kBins + degree_bin(deg[u]);
+        lk = vertex_class(u, k, seg) * kBins + degree_bin(deg[u], seg);
       }
     }
     append_vertex(u, valid, lk, lists, seg, ctrl, 0);
@@ -444,13 +444,15 @@ __global__ void k_ds_keys(const unsigned long long* __restrict__ key, const uint
 // Per source u (sorted keys u << 32 | c): H[c] = summed inserted weight;
 // best c by 2m*H[c] - K_u*Sigma_c, ties to the smallest c.
 __global__ void k_ds_best(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
-                          uint64_t na, long long m2, const long long* __restrict__ K,
+                          uint64_t na, long long m2_one, uint32_t ngraphs, const uint32_t* __restrict__ goff,
+                          const long long* __restrict__ gm2, const long long* __restrict__ K,
                           const long long* __restrict__ Sigma, uint32_t* dV, uint32_t* dE,
                           uint32_t* dC) {
   for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < na;
        p += uint64_t(gridDim.x) * blockDim.x) {
     uint32_t u = uint32_t(key[p] >> 32);
     if (p > 0 && uint32_t(key[p - 1] >> 32) == u) continue;
+    const long long m2 = ngraphs ? gm2[graph_of(goff, ngraphs, u)] : m2_one;  // u's graph's 2m
     bool have = false;
     i128 best_s = 0;
     uint32_t best = 0;
@@ -1033,7 +1035,8 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
   else if (c.err & kErrNotFound) err = set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
   else if (c.err & kErrOverflow) err = set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
   else if (c.err) err = set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
-  else if (h->m2 + c.m2_delta >= (1ll << 32)) err = set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+  else if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
+    err = set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
   if (err) {
     DFL_TRY(hash_reset(h, t));
     return err;
@@ -1141,7 +1144,8 @@ int apply_batch_sorted(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_ed
   if (c.err & kErrNotFound) return set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
   if (c.err & kErrOverflow) return set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
   if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
-  if (h->m2 + c.m2_delta >= (1ll << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+  if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
+    return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
   // --- mutation starts here ---
   if (h->pool_top + c.reloc_need > h->pool_cap) {
     uint64_t c2 = 0;
@@ -1255,7 +1259,8 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
     if (nk) {
       DFL_TRY(sort_pairs(h, h->b_key, h->b_w, h->b_key2, h->b_w2, nk, 32 + h->key_shift));
       LaunchScope ls(h, DFL_PROF_MARK);
-      k_ds_best<<<grid_for(nk, 256), 256, 0, h->stream>>>(h->b_key, h->b_w, nk, h->m2, h->K, h->Sigma,
+      k_ds_best<<<grid_for(nk, 256), 256, 0, h->stream>>>(h->b_key, h->b_w, nk, h->m2, h->ngraphs,
+                                                          h->d_goff0, h->d_gm2, h->K, h->Sigma,
                                                           h->dsV, h->dsE, h->dsC);
       DFL_TRY(check_launch(h, "ds best"));
     }

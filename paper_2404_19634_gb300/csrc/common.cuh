@@ -107,6 +107,11 @@ struct SuperGraph {
 struct Segs {
   uint32_t off[kMaxSubsteps * kBins];
   uint32_t cap[kMaxSubsteps * kBins];
+  uint32_t hi[kBins - 1];  // largest degree of bins 0..2 (tuning; bin 3 takes the rest)
+  // group: a vertex's sub-step class comes from its id within its own graph
+  // (first vertex of each graph at the current level, device memory)
+  const uint32_t* goff;
+  uint32_t ng;
 };
 
 struct Handle {
@@ -265,6 +270,30 @@ struct Handle {
   double graph_capture_ms = 0;
   std::vector<cudaEvent_t> ev_free;
   dfl_profile_t prof;
+
+  // launch-shape tuning of local-moving (never changes results)
+  dfl_tuning tune{kBinWarp, kBinWarpHash, kBinBlock, 256};
+
+  // group: ngraphs > 0 independent graphs held as one disjoint union
+  uint32_t ngraphs = 0;
+  std::vector<uint32_t> goff0;         // first vertex of each graph (ngraphs + 1)
+  std::vector<long long> gm2;          // 2m of each graph
+  std::vector<uint8_t> gfin;           // graph finished the current Louvain run
+  std::vector<dfl_stats_t> gstats;
+  uint32_t* d_goff0 = nullptr;         // device copy of goff0
+  uint32_t* d_goff = nullptr;          // first vertex of each graph at the current level
+  uint32_t* d_gnext = nullptr;         // the next level's offsets (gathered scan)
+  long long* d_gm2 = nullptr;
+  uint8_t* d_gdone = nullptr;          // graph skipped by local-moving
+  uint8_t* d_gflag = nullptr;          // graphs to finalize
+  unsigned long long* d_gS = nullptr;  // per graph S limbs (lo, hi) of the iteration
+  unsigned long long* d_gsum = nullptr;  // per graph reduction slots (3 each)
+  uint8_t* h_gdone = nullptr;          // pinned host mirrors
+  unsigned long long* h_gS = nullptr;
+  uint32_t* Cfin = nullptr;            // final labels of the graphs (union ids)
+  dfl_edge* gb_edges = nullptr;        // staged group batch (union ids)
+  uint64_t gb_cap = 0;
+  uint64_t* d_eoff = nullptr;          // per graph edge offsets of a group batch (2 x (ngraphs + 1))
 };
 
 // ---------------------------------------------------------------------------
@@ -309,8 +338,25 @@ __host__ __device__ __forceinline__ uint32_t substep_class(uint32_t i, uint32_t 
   return uint32_t((uint64_t(i * 0x9E3779B1u) * k) >> 32);
 }
 
-__host__ __device__ __forceinline__ uint32_t degree_bin(uint32_t d) {
-  return d <= kBinWarp ? 0u : d <= kBinWarpHash ? 1u : d <= kBinBlock ? 2u : 3u;
+__host__ __device__ __forceinline__ uint32_t graph_of(const uint32_t* goff, uint32_t ng, uint32_t v) {
+  uint32_t lo = 0, hi = ng;  // largest g with goff[g] <= v
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (goff[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Sub-step class of vertex v of the current graph (a group's vertices by
+// their id within their own graph, so each graph gets its own schedule).
+__device__ __forceinline__ uint32_t vertex_class(uint32_t v, uint32_t k, const Segs& s) {
+  if (s.ng) v -= s.goff[graph_of(s.goff, s.ng, v)];
+  return substep_class(v, k);
+}
+
+__host__ __device__ __forceinline__ uint32_t degree_bin(uint32_t d, const Segs& s) {
+  return d <= s.hi[0] ? 0u : d <= s.hi[1] ? 1u : d <= s.hi[2] ? 2u : 3u;
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -412,6 +458,7 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial);
 // move.cu
 struct MoveArgs {
   GraphView g;
+  uint32_t* graph_iters = nullptr;  // group: iterations each graph ran (host, ngraphs)
   uint32_t* C;
   const long long* K;
   long long* Sigma;
@@ -424,6 +471,7 @@ struct MoveArgs {
 void destroy_iteration_graph(Handle::IterGraph& g);
 int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial = nullptr, uint64_t* ever = nullptr);
+int time_decide(Handle* h, const MoveArgs& a, uint32_t reps, std::vector<float>* ms);
 
 // aggregate.cu
 int count_communities(Handle* h, const uint32_t* Cp, uint32_t nv, uint32_t* ncomm);
@@ -431,6 +479,18 @@ int renumber(Handle* h, uint32_t* Cp, uint32_t nv, bool first_level);
 int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm, int dst,
               long long* Knew);
 int louvain(Handle* h, bool all, bool use_range, uint64_t initial);
+
+// group.cu
+int louvain_group(Handle* h, bool all, bool use_range, uint64_t initial);
+int group_m2(Handle* h);  // 2m of every graph from K (checks each < 2^32)
+int group_modularity(Handle* h, uint32_t g, i128* num, i128* den);
+int group_upload_flags(Handle* h, uint8_t* dev, const uint8_t* host);
+int group_set_level(Handle* h, const uint32_t* dev_off);
+
+// tune.cu
+int check_tuning(const dfl_tuning& t);
+int autotune(Handle* h, int mode, uint32_t reps, double* best_ms);
+
 
 inline GraphView base_view(const Handle* h) {
   return GraphView{h->off, h->deg, h->arcs, h->n};

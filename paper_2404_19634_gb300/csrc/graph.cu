@@ -174,7 +174,8 @@ int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx
   }
   DFL_TRY(read_ctrl(h));
   if (h->hctrl->err) return set_error(h, DFL_ERR_INVALID, "input CSR is not a valid symmetric graph");
-  if (h->hctrl->red_a >= (1ull << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m >= 2^32");
+  // (a group checks the 2m of each of its graphs instead)
+  if (!h->ngraphs && h->hctrl->red_a >= (1ull << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m >= 2^32");
   h->max_deg = h->hctrl->max_deg;
   h->num_arcs = nnz;
   // slack capacities and offsets

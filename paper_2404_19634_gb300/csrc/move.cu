@@ -44,7 +44,26 @@ struct DecideArgs {
   uint32_t k;
   uint2* gtable;          // bin 3: per-block global tables
   uint32_t gslots;        // slots per block (power of two)
+  // group of graphs (ngraphs > 0): the vertex's graph gives its 2m, whether
+  // it is still processed, and where its movers' dQ sum goes
+  uint32_t ngraphs;
+  const uint32_t* goff;   // first vertex of each graph at this level
+  const long long* gm2;
+  const uint8_t* gdone;
+  unsigned long long* gS;
 };
+
+// Group lookup for vertex i: false if its graph is no longer processed;
+// otherwise its graph and 2m.
+__device__ __forceinline__ bool group_active(const DecideArgs& a, uint32_t i, long long* m2,
+                                             uint32_t* gi) {
+  if (!a.ngraphs) return true;
+  const uint32_t g = graph_of(a.goff, a.ngraphs, i);
+  if (a.gdone[g]) return false;
+  *gi = g;
+  *m2 = a.gm2[g];
+  return true;
+}
 
 // Outcome of one vertex's decision, identical on every lane / thread.
 __device__ __forceinline__ bool decide_move(const DecideArgs& a, long long m2, uint32_t i, uint32_t d,
@@ -59,12 +78,19 @@ __device__ __forceinline__ bool decide_move(const DecideArgs& a, long long m2, u
 }
 
 __device__ __forceinline__ void record_move(const DecideArgs& a, uint32_t i, uint32_t c, uint32_t d,
-                                            i128 gain) {
+                                            i128 gain, uint32_t gi) {
   uint32_t slot = atomicAdd(&a.ctrl->movers, 1u);
   a.mv_i[slot] = i;
   a.mv_c[slot] = c;
   a.mv_d[slot] = d;
   add_s(a.ctrl, (u128)gain);
+  if (a.ngraphs) {
+    const u128 v = (u128)gain;
+    const unsigned long long lo = (unsigned long long)(v & 0xFFFFFFFFull);
+    const unsigned long long hi = (unsigned long long)(v >> 32);
+    if (lo) atomicAdd(a.gS + 2 * gi, lo);
+    if (hi) atomicAdd(a.gS + 2 * gi + 1, hi);
+  }
 }
 
 // Mark neighbour j of a mover for the next iteration (warp-collective).
@@ -73,7 +99,7 @@ __device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool 
   uint32_t key = 0;
   if (valid && (!a.rbits || bit_test(a.rbits, j)) && bit_set(a.fbits_next, j)) {
     fresh = true;
-    key = substep_class(j, a.k) * kBins + degree_bin(a.g.deg[j]);
+    key = vertex_class(j, a.k, a.seg) * kBins + degree_bin(a.g.deg[j], a.seg);
   }
   append_vertex(j, fresh, key, a.next_lists, a.seg, a.ctrl, a.next_buf);
 }
@@ -83,7 +109,7 @@ __device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool 
 // community with match/reduce in registers.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
-  const long long m2 = *a.m2p;
+  const long long m2_one = *a.m2p;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -91,6 +117,9 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
   unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t i = a.list[t];
+    long long m2 = m2_one;
+    uint32_t gi = 0;
+    if (!group_active(a, i, &m2, &gi)) continue;
     if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
@@ -117,7 +146,7 @@ __global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
     bool mv = decide_move(a, m2, i, d, Ki, have, score, bc, Hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * __popc(cm);
     if (mv) {
-      if (lane == 0) record_move(a, i, bc, d, gain);
+      if (lane == 0) record_move(a, i, bc, d, gain, gi);
       mark_next(a, arc.x, valid);
       bytes += 16 + 4ull * dg;
     }
@@ -187,7 +216,7 @@ constexpr uint32_t kWarpSlots = 512;
 constexpr int kWarpHashWarps = 8;
 
 __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
-  const long long m2 = *a.m2p;
+  const long long m2_one = *a.m2p;
   __shared__ uint32_t skeys[kWarpHashWarps][kWarpSlots];
   __shared__ uint32_t svals[kWarpHashWarps][kWarpSlots];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
@@ -199,6 +228,9 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
   unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t i = a.list[t];
+    long long m2 = m2_one;
+    uint32_t gi = 0;
+    if (!group_active(a, i, &m2, &gi)) continue;
     if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
@@ -246,7 +278,7 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
     bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * ncand;
     if (mv) {
-      if (lane == 0) record_move(a, i, bc, d, gain);
+      if (lane == 0) record_move(a, i, bc, d, gain, gi);
       for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
         uint32_t k = k0 + lane;
         uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
@@ -274,7 +306,7 @@ constexpr uint32_t kBlockSlots = 2 * kBinBlock;  // 8192 keys + 8192 values = 64
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
-  const long long m2 = *a.m2p;
+  const long long m2_one = *a.m2p;
   extern __shared__ uint32_t dyn[];
   __shared__ unsigned long long s_hd;
   __shared__ uint32_t s_ncand;
@@ -287,6 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const uint32_t i = a.list[t];
+    long long m2 = m2_one;
+    uint32_t gi = 0;
+    if (!group_active(a, i, &m2, &gi)) continue;
     if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
     ++processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
@@ -380,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
     bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
-      if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
+      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi);
       for (uint32_t k0 = wib * 32; k0 < dg; k0 += kThreads) {
         uint32_t k = k0 + lane;
         uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
@@ -436,6 +471,7 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
   for (uint32_t t0 = 0; t0 < cnt; t0 += blockDim.x) {
     uint32_t t = t0 + threadIdx.x;
     unsigned long long d = t < cnt ? a.g.deg[a.list[t]] : 0ull;
+    if (d && a.ngraphs && a.gdone[graph_of(a.goff, a.ngraphs, a.list[t])]) d = 0;  // skipped
     uint32_t ch = uint32_t((d + kGiantChunk - 1) / kGiantChunk);
     unsigned long long xd = d;
     uint32_t xc = ch;
@@ -480,7 +516,7 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
 }
 
 __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a, GiantDecide gd) {
-  const long long m2 = *a.m2p;
+  const long long m2_one = *a.m2p;
   extern __shared__ uint32_t dyn[];
   uint32_t* keys = dyn;
   uint32_t* vals = dyn + kGiantSlots;
@@ -502,6 +538,9 @@ __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a,
     const uint32_t chunk = item - gd.cpre[t];
     const uint32_t nch = gd.cpre[t + 1] - gd.cpre[t];
     const uint32_t i = a.list[t];
+    long long m2 = m2_one;
+    uint32_t gi = 0;
+    group_active(a, i, &m2, &gi);  // its graph is active: the prefix gave it chunks
     if (chunk == 0) {
       if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
       ++processed;
@@ -648,7 +687,7 @@ __global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a,
     bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
     bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
-      if (threadIdx.x == 0) record_move(a, i, bc, d, gain);
+      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi);
       for (uint32_t q0 = wib * 32; q0 < dg; q0 += kGiantThreads) {
         uint32_t q = q0 + lane;
         uint2 arc = q < dg ? a.g.arcs[o + q] : make_uint2(i, 0u);
@@ -724,13 +763,15 @@ constexpr uint32_t kGiantBlocks = 2 * 152;
 // sized to the work; without (graph capture) every bin is launched with a
 // fixed grid and reads its length on the device.
 int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*counts)[kBins],
-                    const GiantDecide& gd_base) {
+                    const GiantDecide& gd_base, bool decide_only = false) {
   const uint32_t k = a.k;
   const int nxt = cur ^ 1;
   // reset the iteration's sums and the next buffer's list lengths
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
+  if (a.ngraphs)
+    DFL_CUDA(h, cudaMemsetAsync(a.gS, 0, sizeof(unsigned long long) * 2 * a.ngraphs, h->stream));
   a.fbits_next = h->fbits[nxt];
   a.next_lists = h->lists[nxt];
   a.next_buf = nxt;
@@ -766,8 +807,13 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       } else if (b == 1) {
         k_decide_warp_hash<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 16) : 152 * 4, 256, 0, st>>>(a);
       } else if (b == 2) {
-        k_decide_block<256><<<counts ? grid_for(c, 1, 152 * 3) : 152 * 3, 256,
-                              sizeof(uint32_t) * 2 * kBlockSlots, st>>>(a);
+        const size_t smem = sizeof(uint32_t) * 2 * kBlockSlots;
+        const uint32_t bt = h->tune.block_threads;
+        const uint32_t per_sm = bt == 128 ? 3 : bt == 256 ? 3 : 2;  // 64 KB table each
+        const uint32_t grid = counts ? grid_for(c, 1, 152 * per_sm) : 152 * per_sm;
+        if (bt == 128) k_decide_block<128><<<grid, 128, smem, st>>>(a);
+        else if (bt == 512) k_decide_block<512><<<grid, 512, smem, st>>>(a);
+        else k_decide_block<256><<<grid, 256, smem, st>>>(a);
       } else {
         GiantDecide gd = gd_base;
         gd.nitems = &h->ctrl->giant_chunks[cur];
@@ -787,7 +833,9 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
       h->prof.launches[DFL_PROF_MOVE]++;
     }
-    if (any) {
+    if (any && decide_only) {
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+    } else if (any) {
       {
         LaunchScope ls(h, DFL_PROF_COMMIT);
         k_commit<<<152 * 2, 256, 0, h->stream>>>(h->mv_i, h->mv_c, h->mv_d, const_cast<uint32_t*>(a.C), a.K,
@@ -810,6 +858,7 @@ struct GraphKey {
   int cur;
   uint32_t flags;
   void* stream;
+  uint32_t block_threads;
 };
 
 // The cached graph for this iteration's key (captured on a miss, evicting
@@ -823,6 +872,7 @@ int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd
   key.cur = cur;
   key.flags = h->opt.flags;
   key.stream = h->stream;
+  key.block_threads = h->tune.block_threads;
   Handle::IterGraph* slot = nullptr;
   for (auto& e : h->igraph[cur])
     if (e.exec && e.key.size() == sizeof(key) && std::memcmp(e.key.data(), &key, sizeof(key)) == 0) {
@@ -886,27 +936,14 @@ void destroy_iteration_graph(Handle::IterGraph& g) {
   g.kernels = 0;
 }
 
-int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
-               bool record_trace, uint64_t* initial, uint64_t* ever) {
+namespace {
+
+// Buffers, streams and kernel attributes one local-moving run needs, and its
+// decide arguments.
+int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gdo) {
   const uint32_t k = h->opt.substeps;
   make_segs(h, k);
-  const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
-  // graph replay of the iterations needs stable buffers (the base graph) and
-  // a capturable (non-default) stream
-  const bool use_graph = ma.g.off == h->off && h->stream != nullptr &&
-                         !(h->opt.flags & DFL_FLAG_NO_GRAPH);
-  unsigned int cur_count[kMaxSubsteps][kBins];
-  unsigned long long skipped = 0;
-  bool have_counts = false;
-  if (!use_graph) {
-    DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
-    if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
-    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
-      for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
-    skipped = h->hctrl->skipped;
-    have_counts = true;
-  }
-  // global tables for the largest bin: one slice of gslots keys + gslots
+  // global tables for the largest bins: one slice of gslots keys + gslots
   // values per block, gslots >= 2 * (max degree of the current graph)
   const uint32_t gslots = next_pow2(2ull * (ma.max_deg > kBinBlock ? ma.max_deg : kBinBlock));
   if (ma.max_deg > kBinBlock && uint64_t(kGiantBlocks) * gslots > h->gtable_cap) {
@@ -923,17 +960,21 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   static std::once_flag smem_once;
   static cudaError_t smem_rc = cudaSuccess;
   std::call_once(smem_once, [] {
-    smem_rc = cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(sizeof(uint32_t) * 2 * kBlockSlots));
+    const int tb = int(sizeof(uint32_t) * 2 * kBlockSlots);
+    smem_rc = cudaFuncSetAttribute(k_decide_block<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if (smem_rc == cudaSuccess)
+      smem_rc = cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if (smem_rc == cudaSuccess)
+      smem_rc = cudaFuncSetAttribute(k_decide_block<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
     if (smem_rc == cudaSuccess)
       smem_rc = cudaFuncSetAttribute(k_decide_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(sizeof(uint32_t) * 2 * kGiantSlots));
   });
   DFL_CUDA(h, smem_rc);
   // chunked bin-3 buffers: per list item offsets/counters (sized by the
-  // largest bin-3 list: at most arcs / 4097 vertices) and partial sums
+  // largest bin-3 list: at most arcs / (bin_block + 1) vertices) and partial sums
   {
-    uint64_t items = h->pool_top / (kBinBlock + 1) + 64;
+    uint64_t items = h->pool_top / (uint64_t(h->tune.bin_block) + 1) + 64;
     uint64_t parts = h->pool_top + 64;
     for (int q = 0; q < 2; ++q) parts = parts > h->sg[q].arc_cap ? parts : h->sg[q].arc_cap;
     if (items > h->g_items_cap) {
@@ -954,7 +995,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
       DFL_CUDA(h, cudaMemsetAsync(h->g_pcount, 0, sizeof(uint32_t) * want, h->stream));
       h->g_items_cap = want;
     }
-    if (ma.max_deg > kBinBlock && parts > h->g_partial_cap) {
+    if (ma.max_deg > h->tune.bin_block && parts > h->g_partial_cap) {
       cudaStreamSynchronize(h->stream);
       cudaFree(h->g_partial);
       h->g_partial = nullptr;
@@ -978,7 +1019,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     k_set_m2<<<1, 1, 0, h->stream>>>(h->ctrl, ma.m2);
     DFL_TRY(check_launch(h, "set m2"));
   }
-  DecideArgs a;
+  DecideArgs& a = *out;
   std::memset(&a, 0, sizeof(a));
   a.g = ma.g;
   a.C = ma.C;
@@ -996,11 +1037,58 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   a.k = k;
   a.gtable = h->gtable;
   a.gslots = gslots;
-  GiantDecide gd{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial, nullptr};
+  if (h->ngraphs) {
+    a.ngraphs = h->ngraphs;
+    a.goff = h->d_goff;
+    a.gm2 = h->d_gm2;
+    a.gdone = h->d_gdone;
+    a.gS = h->d_gS;
+  }
+  *gdo = GiantDecide{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial, nullptr};
+  return DFL_OK;
+}
+
+}  // namespace
+
+int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
+               bool record_trace, uint64_t* initial, uint64_t* ever) {
+  const uint32_t G = h->ngraphs;
+  const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
+  // a group tests each graph against its own threshold; graphs that have
+  // finished (h->gfin) or converge stop being processed
+  std::vector<u128> gthr(G);
+  std::vector<uint8_t> gactive(G);
+  uint32_t nactive = 0;
+  for (uint32_t g = 0; g < G; ++g) {
+    gthr[g] = tolerance_threshold(h->opt, h->gm2[g], pass);
+    gactive[g] = !h->gfin[g];
+    nactive += gactive[g];
+    h->h_gdone[g] = !gactive[g];
+    if (ma.graph_iters) ma.graph_iters[g] = 0;
+  }
+  if (G) DFL_TRY(group_upload_flags(h, h->d_gdone, h->h_gdone));
+  // graph replay of the iterations needs stable buffers (the base graph) and
+  // a capturable (non-default) stream
+  const bool use_graph = ma.g.off == h->off && h->stream != nullptr &&
+                         !(h->opt.flags & DFL_FLAG_NO_GRAPH);
+  unsigned int cur_count[kMaxSubsteps][kBins];
+  unsigned long long skipped = 0;
+  bool have_counts = false;
+  if (!use_graph) {
+    DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
+    if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
+    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+      for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
+    skipped = h->hctrl->skipped;
+    have_counts = true;
+  }
+  DecideArgs a;
+  GiantDecide gd;
+  DFL_TRY(prepare_move(h, ma, &a, &gd));
   int cur = 0;
   uint32_t it = 0;
   Handle::IterGraph* graph_used[2] = {nullptr, nullptr};
-  while (it < h->opt.max_iterations) {
+  while (it < h->opt.max_iterations && (!G || nactive)) {
     ++it;
     const int nxt = cur ^ 1;
     if (use_graph) {
@@ -1014,6 +1102,9 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     } else {
       DFL_TRY(issue_iteration(h, a, cur, cur_count, gd));
     }
+    if (G)
+      DFL_CUDA(h, cudaMemcpyAsync(h->h_gS, h->d_gS, sizeof(unsigned long long) * 2 * G,
+                                  cudaMemcpyDeviceToHost, h->stream));
     DFL_TRY(read_ctrl(h));
     const Ctrl& c = *h->hctrl;
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
@@ -1047,7 +1138,23 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
         for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
     cur = nxt;
     skipped = 0;
-    if (S <= threshold) break;  // locally converged
+    if (!G) {
+      if (S <= threshold) break;  // locally converged
+      continue;
+    }
+    bool changed = false;
+    for (uint32_t g = 0; g < G; ++g) {
+      if (!gactive[g]) continue;
+      if (ma.graph_iters) ma.graph_iters[g] = it;
+      const u128 Sg = ((u128)h->h_gS[2 * g + 1] << 32) + (u128)h->h_gS[2 * g];
+      if (Sg <= gthr[g]) {  // this graph converged: skip its vertices from now on
+        gactive[g] = 0;
+        h->h_gdone[g] = 1;
+        --nactive;
+        changed = true;
+      }
+    }
+    if (changed && nactive) DFL_TRY(group_upload_flags(h, h->d_gdone, h->h_gdone));
   }
   h->prof.bytes[DFL_PROF_MOVE] += h->hctrl->move_bytes;
   if (ever) *ever = h->hctrl->ever_count;
@@ -1055,6 +1162,44 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
   *iterations = it;
   return DFL_OK;
+}
+
+// Decide phase of one local-moving iteration over the frontier in list
+// buffer 0, without applying the moves: `reps` timed runs (the autotuner).
+int time_decide(Handle* h, const MoveArgs& ma, uint32_t reps, std::vector<float>* ms) {
+  DFL_TRY(read_ctrl(h));
+  unsigned int counts[kMaxSubsteps][kBins];
+  for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+    for (int b = 0; b < kBins; ++b) counts[s][b] = h->hctrl->count[0][s][b];
+  if (h->ngraphs) {
+    for (uint32_t g = 0; g < h->ngraphs; ++g) h->h_gdone[g] = 0;
+    DFL_TRY(group_upload_flags(h, h->d_gdone, h->h_gdone));
+  }
+  DecideArgs a;
+  GiantDecide gd;
+  DFL_TRY(prepare_move(h, ma, &a, &gd));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DFL_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(h, DFL_ERR_CUDA, "event");
+  }
+  int rc = DFL_OK;
+  ms->clear();
+  for (uint32_t r = 0; r < reps && !rc; ++r) {
+    if (cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream) != cudaSuccess)
+      rc = set_error(h, DFL_ERR_CUDA, "memset");
+    if (!rc) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? DFL_OK : DFL_ERR_CUDA;
+    if (!rc) rc = issue_iteration(h, a, 0, counts, gd, true);
+    if (!rc) rc = cudaEventRecord(e1, h->stream) == cudaSuccess ? DFL_OK : DFL_ERR_CUDA;
+    if (!rc) rc = read_ctrl(h);
+    if (!rc && h->hctrl->err) rc = set_error(h, DFL_ERR_CUDA, "internal error in local-moving");
+    float t = 0;
+    if (!rc && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms->push_back(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 }  // namespace dfl

@@ -261,7 +261,7 @@ __global__ void k_lists_all(uint32_t nv, const uint32_t* __restrict__ deg, uint3
     unsigned idle = __ballot_sync(0xFFFFFFFFu, i < nv && d == 0);
     if ((threadIdx.x & 31u) == 0 && idle) atomicAdd(&ctrl->skipped, (unsigned long long)__popc(idle));
     uint32_t key = 0;
-    if (valid) key = substep_class(uint32_t(i), k) * kBins + degree_bin(d);
+    if (valid) key = vertex_class(uint32_t(i), k, seg) * kBins + degree_bin(d, seg);
     append_vertex(uint32_t(i), valid, key, lists, seg, ctrl, buf);
   }
 }
@@ -277,7 +277,7 @@ __global__ void k_lists_bits(const uint32_t* __restrict__ bits, uint32_t words, 
       uint32_t v = uint32_t(w * 32 + b);
       bool valid = ((word >> b) & 1u) && v < nv;
       uint32_t key = 0;
-      if (valid) key = substep_class(v, k) * kBins + degree_bin(deg[v]);
+      if (valid) key = vertex_class(v, k, seg) * kBins + degree_bin(deg[v], seg);
       append_vertex(v, valid, key, lists, seg, ctrl, buf);
     }
   }
@@ -317,9 +317,21 @@ __global__ void k_popcount(const uint32_t* bits, uint32_t words, unsigned long l
 // one segment of a buffer, and a super-vertex graph has ids in [0, nv) with
 // nv <= n).
 void make_segs(Handle* h, uint32_t k) {
+  h->segs.hi[0] = h->tune.bin_warp;
+  h->segs.hi[1] = h->tune.bin_warp_hash;
+  h->segs.hi[2] = h->tune.bin_block;
+  h->segs.goff = h->ngraphs ? h->d_goff : nullptr;
+  h->segs.ng = h->ngraphs;
   if (h->segs_k == k) return;
+  // a segment holds every vertex of its class; a group's classes come from
+  // ids within each graph, and later levels only have fewer vertices per graph
   uint64_t counts[kMaxSubsteps] = {0};
-  for (uint32_t i = 0; i < h->n; ++i) counts[substep_class(i, k)]++;
+  if (h->ngraphs) {
+    for (uint32_t g = 0; g < h->ngraphs; ++g)
+      for (uint32_t i = 0; i < h->goff0[g + 1] - h->goff0[g]; ++i) counts[substep_class(i, k)]++;
+  } else {
+    for (uint32_t i = 0; i < h->n; ++i) counts[substep_class(i, k)]++;
+  }
   uint64_t off = 0;
   for (uint32_t c = 0; c < kMaxSubsteps; ++c)
     for (int b = 0; b < kBins; ++b) {

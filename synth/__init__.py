@@ -233,7 +233,8 @@ class BatchStream:
         self.order = self.rng.permutation(edges.m)
         self.pos = 0
 
-    def next(self, size: int, frac_ins: float = 0.8):
+    def next(self, size: int, frac_ins: float = 0.8, w_max: int = 1):
+        """Insertion weights are 1, or uniform in 1..w_max when w_max > 1."""
         n_ins = int(round(size * frac_ins))
         n_del = size - n_ins
         if self.pos + n_del > self.order.shape[0]:
@@ -245,7 +246,8 @@ class BatchStream:
         a = self.rng.integers(0, self.n, n_ins)
         b = self.rng.integers(0, self.n - 1, n_ins)
         b = b + (b >= a)
-        ins = np.stack([a, b, np.ones(n_ins, np.int64)], 1).astype(np.uint32)
+        w = self.rng.integers(1, w_max + 1, n_ins) if w_max > 1 else np.ones(n_ins, np.int64)
+        ins = np.stack([a, b, w], 1).astype(np.uint32)
         return dels.reshape(-1, 3), ins.reshape(-1, 3)
 
 
@@ -403,4 +405,31 @@ def poisson_requests(num_graphs: int, rate: float, duration: float, size_lo: int
         g = int(rng.integers(0, num_graphs))
         size = int(round(math.exp(rng.uniform(math.log(size_lo), math.log(size_hi)))))
         out.append((t, g, size))
+    return out
+
+
+def planted_group_params(count: int, n_lo: float, n_hi: float, seed: int):
+    """Per graph (n, blocks, mu, seed) of `planted_group`, drawn in order:
+    n log-uniform in [n_lo, n_hi], blocks log-uniform in [20, 2000] (at most
+    n / 32, so blocks keep room for their internal edges), mu uniform in
+    [0.1, 0.5]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = log_uniform_int(rng, n_lo, n_hi)
+        blocks = max(2, min(log_uniform_int(rng, 20, 2000), n // 32))
+        mu = float(rng.uniform(0.1, 0.5))
+        out.append((n, blocks, mu, int(rng.integers(1 << 31))))
+    return out
+
+
+def planted_group(count: int, n_lo: float, n_hi: float, seed: int, mean_degree: float = 16.0,
+                  w_max: int = 16):
+    """Independent planted-partition graphs of uneven size (parameters from
+    `planted_group_params`), weights uniform in 1..w_max.  Returns a list of
+    (EdgeList, {"n", "blocks", "mu"})."""
+    out = []
+    for n, blocks, mu, gseed in planted_group_params(count, n_lo, n_hi, seed):
+        g = planted_partition(n, blocks, mu, mean_degree, w_max, gseed)
+        out.append((g, {"n": n, "blocks": blocks, "mu": round(mu, 4)}))
     return out
