@@ -105,7 +105,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -222,10 +222,12 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     # static Louvain (the paper's comparator), timed on its own
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("static")
     e0.record(stream)
     h.static()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     static_ms = e0.elapsed_time(e1)
     static_stats = h.stats()
     static_prof = h.profile(reset=True)
@@ -254,6 +256,7 @@ def gpu_arm(args):
     evs = []
     clocks = Clocks(local)
     with clocks:
+        torch.cuda.nvtx.range_push("df_steps")  # lets a profiler select the timed steps
         for k in range(args.warmup, nsteps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -262,6 +265,7 @@ def gpu_arm(args):
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -359,7 +363,7 @@ def gpu_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale} |E|={g.m} DF batches of {size} (1e-3|E|)",
-                       "graph": "R-MAT a=.57 b=.19 c=.19, 2^22 vertices, 33,554,432 edges, unit weights",
+                       "graph": f"R-MAT a=.57 b=.19 c=.19, 2^{args.scale} vertices, {g.m:,} edges, unit weights",
                        "batch_edges": size, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "static_ms": round(static_ms, 3), "static_passes": static_stats["iterations"],
@@ -448,7 +452,9 @@ def group_arm(args):
     time_steps(group_step, 0, args.warmup)
     l0 = grp.stats()["kernel_launches"]
     with Clocks(0) as clocks:
+        torch.cuda.nvtx.range_push("group_steps")
         group_ms = time_steps(group_step, args.warmup, args.steps)
+        torch.cuda.nvtx.range_pop()
     group_launches = grp.stats()["kernel_launches"] - l0
     group_final = [grp.graph_modularity(g)[1:] for g in range(G)]
     passes = [grp.graph_stats(g)["passes"] for g in range(G)]

@@ -82,9 +82,11 @@ enum {
 enum {
   DFL_FLAG_PROFILE = 1u, /* time every kernel class with CUDA events (dfl_profile) */
   DFL_FLAG_TRACE = 2u,   /* reserved */
-  DFL_FLAG_NO_GRAPH = 4u /* launch every kernel from the host instead of replaying the captured
-                            local-moving iteration (a CUDA graph, used on the first pass when the
-                            handle's stream is not the legacy default stream) */
+  DFL_FLAG_NO_GRAPH = 4u, /* launch every kernel from the host instead of replaying the captured
+                             local-moving iteration (a CUDA graph, used on the first pass when the
+                             handle's stream is not the legacy default stream) */
+  DFL_FLAG_SERIAL_BINS = 8u /* run the degree bins of a sub-step one after another on the handle's
+                               stream instead of concurrently (for measuring each bin alone) */
 };
 
 /* Algorithm options; defaults from Section 5.1.2 of the paper. */

@@ -107,13 +107,14 @@ void free_all(Handle* h) {
                   h->lists[1], h->mv_i, h->mv_c, h->mv_d, h->dsV, h->dsE, h->dsC, h->b_key, h->b_w,
                   h->b_key2, h->b_w2, h->b_rowlist, h->b_pos, h->b_wnew, h->b_flag, h->b_delta,
                   h->b_newdeg, h->b_edges, h->scratch, h->tmp, h->gtable, h->ctrl,
-                  h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial,
+                  h->g_toff, h->g_loff, h->g_cpre, h->g_ndist, h->g_done, h->g_hd, h->g_res,
+                  h->g_tkeys, h->g_tvals, h->g_tlist,
                   h->h_keys, h->h_ndel, h->h_wdel, h->h_wins, h->h_slot, h->h_wnew, h->h_flag,
                   h->h_delta, h->h_pairs, h->r_app, h->r_tomb, h->r_live, h->r_state, h->r_reg,
                   h->h_rows, h->h_extra,
                   h->sg[0].off, h->sg[0].deg, h->sg[0].arcs, h->sg[1].off, h->sg[1].deg,
                   h->sg[1].arcs, h->d_goff0, h->d_goff, h->d_gnext, h->d_gm2, h->d_gdone,
-                  h->d_gflag, h->d_gS, h->d_gsum, h->Cfin, h->gb_edges, h->d_eoff};
+                  h->d_gflag, h->d_gS, h->d_gsum, h->Cfin, h->gb_edges, h->d_eoff, h->bigmv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);

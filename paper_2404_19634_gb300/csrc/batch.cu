@@ -34,7 +34,7 @@ constexpr uint32_t kAppend = 16u;     // a new slot is needed
 constexpr uint32_t kRebuild = 32u;    // (every run of the row) the row is rebuilt
 
 __host__ __device__ inline uint32_t grow_cap(uint32_t d) {
-  uint64_t c = uint64_t(d) + d / 2 + 4;
+  uint64_t c = uint64_t(d) + d / 2 + 8;
   c = (c + 1) & ~uint64_t(1);
   return c > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(c);
 }
@@ -551,46 +551,75 @@ __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
 
 // Thread per edge: both arcs into the table; arcs also staged (key format of
 // the pending list) for the frontier marking of the next update.
+// Claim `n` consecutive entries of a shared counter for the lanes with `want`
+// set (one atomic per warp); returns this lane's entry.  Every lane of the
+// warp must call it.
+__device__ __forceinline__ uint32_t warp_claim(unsigned int* counter, bool want) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+  if (!m) return 0;
+  const uint32_t lane = threadIdx.x & 31u, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(counter, uint32_t(__popc(m)));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ long long warp_sum64(long long x) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
 __global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
                               KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
                               uint32_t* __restrict__ w, Ctrl* ctrl) {
-  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < ne;
-       q += uint64_t(gridDim.x) * blockDim.x) {
-    dfl_edge x = e[q];
+  // warp-uniform loop: the claims of new table slots are made per warp
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t q0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); q0 < ne; q0 += stride) {
+    const uint64_t q = q0 + lane;
+    bool valid = q < ne;
+    dfl_edge x = valid ? e[q] : dfl_edge{0, 0, 0};
     const bool ins = q >= nd;
-    if (x.u >= n || x.v >= n || x.u == x.v || (ins && x.w == 0)) {
+    if (valid && (x.u >= n || x.v >= n || x.u == x.v || (ins && x.w == 0))) {
       atomicOr(&ctrl->err, kErrInvalid);
       key[2 * q] = key[2 * q + 1] = 0;
       w[2 * q] = w[2 * q + 1] = 0;
-      continue;
+      valid = false;
     }
     for (int dir = 0; dir < 2; ++dir) {
-      const uint32_t a = dir ? x.v : x.u, b = dir ? x.u : x.v;
-      key[2 * q + dir] = ((unsigned long long)a << (f.b + 1)) | ((unsigned long long)b << 1) |
-                         (ins ? 1ull : 0ull);
-      w[2 * q + dir] = x.w;
-      const unsigned long long k = ((unsigned long long)a << 32) | b;
-      uint64_t s = hash64(k) & t.mask;
-      for (uint64_t probe = 0; probe <= t.mask; ++probe) {
-        unsigned long long prev = t.keys[s];
-        if (prev == kNoKey) {
-          prev = atomicCAS(&t.keys[s], kNoKey, k);
+      bool claimed = false;
+      uint32_t cs = 0;
+      if (valid) {
+        const uint32_t a = dir ? x.v : x.u, b = dir ? x.u : x.v;
+        key[2 * q + dir] = ((unsigned long long)a << (f.b + 1)) | ((unsigned long long)b << 1) |
+                           (ins ? 1ull : 0ull);
+        w[2 * q + dir] = x.w;
+        const unsigned long long k = ((unsigned long long)a << 32) | b;
+        uint64_t s = hash64(k) & t.mask;
+        for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+          unsigned long long prev = t.keys[s];
           if (prev == kNoKey) {
-            t.pairs[atomicAdd(&ctrl->npairs, 1u)] = uint32_t(s);
-            prev = k;
+            prev = atomicCAS(&t.keys[s], kNoKey, k);
+            if (prev == kNoKey) {
+              claimed = true;
+              cs = uint32_t(s);
+              prev = k;
+            }
           }
-        }
-        if (prev == k) {
-          if (ins) {
-            atomicAdd(&t.wins[s], (unsigned long long)x.w);
-          } else {
-            atomicAdd(&t.ndel[s], 1u);
-            t.wdel[s] = x.w;  // several deletions of one pair are an error anyway
+          if (prev == k) {
+            if (ins) {
+              atomicAdd(&t.wins[s], (unsigned long long)x.w);
+            } else {
+              atomicAdd(&t.ndel[s], 1u);
+              t.wdel[s] = x.w;  // several deletions of one pair are an error anyway
+            }
+            break;
           }
-          break;
+          s = (s + 1) & t.mask;
         }
-        s = (s + 1) & t.mask;
       }
+      const uint32_t at = warp_claim(&ctrl->npairs, claimed);
+      if (claimed) t.pairs[at] = cs;
     }
   }
 }
@@ -601,43 +630,60 @@ __global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* 
                              const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
                              const uint2* __restrict__ arcs, Ctrl* ctrl) {
   const uint32_t np = ctrl->npairs;
-  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
-       p += uint64_t(gridDim.x) * blockDim.x) {
-    const uint32_t s = t.pairs[p];
-    const unsigned long long k = t.keys[s];
-    const uint32_t u = uint32_t(k >> 32), v = uint32_t(k);
-    const uint32_t ndel = t.ndel[s], wdel = t.wdel[s];
-    const unsigned long long wins = t.wins[s];
-    if (ndel > 1) atomicOr(&ctrl->err, kErrInvalid);  // the same edge deleted twice
-    const uint2* row = arcs + off[u];
-    const uint32_t slot = find_slot(row, srt[u], deg[u], v);
-    const unsigned long long wold = slot != kEmpty ? row[slot].y : 0ull;
-    unsigned long long weff = 0;
-    if (ndel) {
-      if (wold == 0 || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);
-      else weff = wdel ? wdel : wold;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  // warp-uniform loop: 2m and arc-count changes are summed, new rows claimed, per warp
+  for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
+    const uint64_t p = p0 + lane;
+    long long dm2 = 0, darcs = 0;
+    bool new_row = false;
+    uint32_t row_u = 0;
+    if (p < np) {
+      const uint32_t s = t.pairs[p];
+      const unsigned long long k = t.keys[s];
+      const uint32_t u = uint32_t(k >> 32), v = uint32_t(k);
+      const uint32_t ndel = t.ndel[s], wdel = t.wdel[s];
+      const unsigned long long wins = t.wins[s];
+      if (ndel > 1) atomicOr(&ctrl->err, kErrInvalid);  // the same edge deleted twice
+      const uint2* row = arcs + off[u];
+      const uint32_t slot = find_slot(row, srt[u], deg[u], v);
+      const unsigned long long wold = slot != kEmpty ? row[slot].y : 0ull;
+      unsigned long long weff = 0;
+      if (ndel) {
+        if (wold == 0 || wdel > wold) atomicOr(&ctrl->err, kErrNotFound);
+        else weff = wdel ? wdel : wold;
+      }
+      const unsigned long long wn = wold - weff + wins;
+      if (wn > 0xFFFFFFFFull) atomicOr(&ctrl->err, kErrOverflow);
+      uint32_t fl = kRunHead;
+      if (slot != kEmpty) fl |= kFound;
+      if (wold > 0) fl |= kLiveBefore;
+      if (wn > 0) fl |= kLiveAfter;
+      if (slot == kEmpty && wn > 0) fl |= kAppend;
+      const long long dl = (long long)wins - (long long)weff;
+      t.wnew[s] = uint32_t(wn);
+      t.flag[s] = fl;
+      t.delta[s] = dl;
+      t.slot[s] = (fl & kAppend) ? atomicAdd(&t.r_app[u], 1u) : slot;
+      dm2 = dl;
+      const int live = (wn > 0 ? 1 : 0) - (wold > 0 ? 1 : 0);
+      if (live) {
+        atomicAdd(&t.r_live[u], live);
+        darcs = live;
+      }
+      if ((fl & kFound) && wold > 0 && wn == 0) atomicAdd(&t.r_tomb[u], 1);
+      if ((fl & kFound) && wold == 0 && wn > 0) atomicAdd(&t.r_tomb[u], -1);
+      new_row = atomicCAS(&t.r_state[u], 0u, 1u) == 0u;
+      row_u = u;
     }
-    const unsigned long long wn = wold - weff + wins;
-    if (wn > 0xFFFFFFFFull) atomicOr(&ctrl->err, kErrOverflow);
-    uint32_t fl = kRunHead;
-    if (slot != kEmpty) fl |= kFound;
-    if (wold > 0) fl |= kLiveBefore;
-    if (wn > 0) fl |= kLiveAfter;
-    if (slot == kEmpty && wn > 0) fl |= kAppend;
-    const long long dl = (long long)wins - (long long)weff;
-    t.wnew[s] = uint32_t(wn);
-    t.flag[s] = fl;
-    t.delta[s] = dl;
-    t.slot[s] = (fl & kAppend) ? atomicAdd(&t.r_app[u], 1u) : slot;
-    if (dl) atomicAdd((unsigned long long*)&ctrl->m2_delta, (unsigned long long)dl);
-    const int live = (wn > 0 ? 1 : 0) - (wold > 0 ? 1 : 0);
-    if (live) {
-      atomicAdd(&t.r_live[u], live);
-      atomicAdd((unsigned long long*)&ctrl->arc_delta, (unsigned long long)(long long)live);
+    const uint32_t at = warp_claim(&ctrl->rows, new_row);
+    if (new_row) t.rows[at] = row_u;
+    dm2 = warp_sum64(dm2);
+    darcs = warp_sum64(darcs);
+    if (lane == 0) {
+      if (dm2) atomicAdd((unsigned long long*)&ctrl->m2_delta, (unsigned long long)dm2);
+      if (darcs) atomicAdd((unsigned long long*)&ctrl->arc_delta, (unsigned long long)darcs);
     }
-    if ((fl & kFound) && wold > 0 && wn == 0) atomicAdd(&t.r_tomb[u], 1);
-    if ((fl & kFound) && wold == 0 && wn > 0) atomicAdd(&t.r_tomb[u], -1);
-    if (atomicCAS(&t.r_state[u], 0u, 1u) == 0u) t.rows[atomicAdd(&ctrl->rows, 1u)] = u;
   }
 }
 
@@ -645,24 +691,30 @@ __global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* 
 __global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
                             const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
   const uint32_t nr = ctrl->rows;
-  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
-       q += uint64_t(gridDim.x) * blockDim.x) {
-    const uint32_t u = t.rows[q];
-    const uint32_t d = deg[u], s = srt[u], app = t.r_app[u];
-    const long long tomb = (long long)ntomb[u] + t.r_tomb[u];
-    const long long live = (long long)d - ntomb[u] + t.r_live[u];
-    const uint32_t raw = d + app;
-    const uint32_t tomb_lim = raw / 4 > kTombMin ? raw / 4 : kTombMin;
-    const bool rebuild = raw > cap[u] || d - s + app > kTailMax || uint32_t(tomb) > tomb_lim;
-    if (rebuild) {
-      t.r_state[u] = 2u;
-      t.r_reg[u] = uint32_t(atomicAdd(&ctrl->extra_top, (unsigned long long)app));
-      atomicAdd(&ctrl->rebuild_rows, 1u);
-      atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(uint32_t(live)));
-      atomicAdd(&ctrl->scratch_need, (unsigned long long)s);
-      atomicMax(&ctrl->max_app, app);
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t q0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); q0 < nr; q0 += stride) {
+    const uint64_t q = q0 + (threadIdx.x & 31u);
+    uint32_t dmax = 0;
+    if (q < nr) {
+      const uint32_t u = t.rows[q];
+      const uint32_t d = deg[u], s = srt[u], app = t.r_app[u];
+      const long long tomb = (long long)ntomb[u] + t.r_tomb[u];
+      const long long live = (long long)d - ntomb[u] + t.r_live[u];
+      const uint32_t raw = d + app;
+      const uint32_t tomb_lim = raw / 4 > kTombMin ? raw / 4 : kTombMin;
+      const bool rebuild = raw > cap[u] || d - s + app > kTailMax || uint32_t(tomb) > tomb_lim;
+      if (rebuild) {
+        t.r_state[u] = 2u;
+        t.r_reg[u] = uint32_t(atomicAdd(&ctrl->extra_top, (unsigned long long)app));
+        atomicAdd(&ctrl->rebuild_rows, 1u);
+        atomicAdd(&ctrl->reloc_need, (unsigned long long)grow_cap(uint32_t(live)));
+        atomicAdd(&ctrl->scratch_need, (unsigned long long)s);
+        atomicMax(&ctrl->max_app, app);
+      }
+      dmax = rebuild ? uint32_t(live) : raw;
     }
-    atomicMax(&ctrl->max_deg, rebuild ? uint32_t(live) : raw);
+    dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);  // one update per warp
+    if ((threadIdx.x & 31u) == 0 && dmax) atomicMax(&ctrl->max_deg, dmax);
   }
 }
 

@@ -57,7 +57,9 @@ struct Ctrl {
   unsigned long long moved;          // movers in the iteration
   unsigned long long move_bytes;     // algorithmic bytes of the decide kernels
   unsigned int movers;               // movers of the current sub-step (list length)
+  unsigned int big_movers;           // ... of them listed for k_commit to mark the neighbours of
   unsigned int err;                  // kErr* bits
+  unsigned int pad_err;
   unsigned int count[2][kMaxSubsteps][kBins];  // frontier list lengths [buffer][class][bin]
   // batch apply
   unsigned long long reloc_need;     // arc slots needed for relocated rows
@@ -224,15 +226,26 @@ struct Handle {
   uint64_t tmp_cap = 0;
   uint2* gtable = nullptr;         // global hash tables of the largest bin
   uint64_t gtable_cap = 0;
-  // chunked decisions of the largest bin: per list item partial-sum region
-  // offset, chunk prefix, finished chunks and partial count; partial sums
-  unsigned long long* g_poff = nullptr;
+  uint32_t* bigmv = nullptr;       // high-degree movers of a sub-step (marked by k_mark_big)
+  uint64_t bigmv_cap = 0;
+  // decisions of the largest bin: per list position its table and list
+  // offsets, chunk prefix, occupied-slot count, finished part blocks and
+  // weight to the own community (the last two zero at rest); per part
+  // results; the global tables (empty at rest) and occupied-slot lists
+  unsigned long long* g_toff = nullptr;
+  unsigned long long* g_loff = nullptr;
   uint32_t* g_cpre = nullptr;
+  uint32_t* g_ndist = nullptr;
   uint32_t* g_done = nullptr;
-  uint32_t* g_pcount = nullptr;
+  unsigned long long* g_hd = nullptr;
   uint64_t g_items_cap = 0;
-  uint2* g_partial = nullptr;
-  uint64_t g_partial_cap = 0;
+  void* g_res = nullptr;
+  uint64_t g_res_cap = 0;
+  uint32_t* g_tkeys = nullptr;
+  uint32_t* g_tvals = nullptr;
+  uint64_t g_tab_cap = 0;
+  uint32_t* g_tlist = nullptr;
+  uint64_t g_lst_cap = 0;
 
   // auxiliary streams for the concurrent degree bins of a sub-step
   cudaStream_t aux[kBins - 1] = {nullptr, nullptr, nullptr};
@@ -393,14 +406,6 @@ __device__ __forceinline__ bool bit_set(uint32_t* bits, uint32_t i) {
   return (atomicOr(bits + (i >> 5), m) & m) == 0;
 }
 
-// Add a non-negative 128-bit value to the (s_hi, s_lo) limb pair.
-__device__ __forceinline__ void add_s(Ctrl* ctrl, u128 v) {
-  unsigned long long lo = (unsigned long long)(v & 0xFFFFFFFFull);
-  unsigned long long hi = (unsigned long long)(v >> 32);
-  if (lo) atomicAdd(&ctrl->s_lo, lo);
-  if (hi) atomicAdd(&ctrl->s_hi, hi);
-}
-
 // Append vertex v (if valid) to frontier list `key` = class * kBins + bin of
 // buffer `buf`; one atomic per distinct key in the warp.  Every lane of the
 // warp must call this (with valid = false where it has nothing).
@@ -437,6 +442,9 @@ int fill_i32(Handle* h, int* p, int v, uint64_t n);
 int copy_i64(Handle* h, long long* dst, const long long* src, uint64_t n);
 int lists_from_bits(Handle* h, const uint32_t* bits, uint32_t nv, const uint32_t* deg, int buf,
                     uint32_t substeps);
+__global__ void k_lists_bits(const uint32_t* __restrict__ bits, uint32_t words, uint32_t nv,
+                             const uint32_t* __restrict__ deg, uint32_t* lists, Segs seg, Ctrl* ctrl,
+                             int buf, uint32_t k);
 int lists_all(Handle* h, uint32_t nv, const uint32_t* deg, int buf, uint32_t substeps);
 int bits_to_bytes(Handle* h, const uint32_t* bits, uint8_t* out, uint32_t n);
 int bytes_to_bits(Handle* h, const uint8_t* in, uint32_t* bits, uint32_t n);

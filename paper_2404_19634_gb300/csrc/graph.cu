@@ -8,10 +8,11 @@ namespace dfl {
 
 namespace {
 
-// Capacity of a row of degree d in the slack CSR: 25% headroom plus two
-// slots, rounded up to an even count so every row starts 16-byte aligned.
+// Capacity of a row of degree d in the slack CSR: 25% headroom plus eight
+// slots (so low-degree rows absorb a few insertions before a rebuild),
+// rounded up to an even count so every row starts 16-byte aligned.
 __host__ __device__ inline uint32_t slack_cap(uint32_t d) {
-  uint64_t c = uint64_t(d) + d / 4 + 2;
+  uint64_t c = uint64_t(d) + d / 4 + 8;
   c = (c + 1) & ~uint64_t(1);
   return c > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(c);
 }

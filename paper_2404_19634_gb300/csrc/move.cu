@@ -44,6 +44,7 @@ struct DecideArgs {
   uint32_t k;
   uint2* gtable;          // bin 3: per-block global tables
   uint32_t gslots;        // slots per block (power of two)
+  uint32_t* bigmv;        // movers of degree > kMarkInline (neighbours marked by k_commit)
   // group of graphs (ngraphs > 0): the vertex's graph gives its 2m, whether
   // it is still processed, and where its movers' dQ sum goes
   uint32_t ngraphs;
@@ -77,13 +78,20 @@ __device__ __forceinline__ bool decide_move(const DecideArgs& a, long long m2, u
   return true;
 }
 
+// A decide kernel's counters: summed in registers by the thread that owns a
+// vertex's outcome, then once per block (flush_sums).
+struct MoveSums {
+  unsigned long long bytes = 0, processed = 0, ever = 0, s_lo = 0, s_hi = 0;
+};
+
 __device__ __forceinline__ void record_move(const DecideArgs& a, uint32_t i, uint32_t c, uint32_t d,
-                                            i128 gain, uint32_t gi) {
+                                            i128 gain, uint32_t gi, MoveSums& sums) {
   uint32_t slot = atomicAdd(&a.ctrl->movers, 1u);
   a.mv_i[slot] = i;
   a.mv_c[slot] = c;
   a.mv_d[slot] = d;
-  add_s(a.ctrl, (u128)gain);
+  sums.s_lo += (unsigned long long)((u128)gain & 0xFFFFFFFFull);
+  sums.s_hi += (unsigned long long)((u128)gain >> 32);
   if (a.ngraphs) {
     const u128 v = (u128)gain;
     const unsigned long long lo = (unsigned long long)(v & 0xFFFFFFFFull);
@@ -93,69 +101,137 @@ __device__ __forceinline__ void record_move(const DecideArgs& a, uint32_t i, uin
   }
 }
 
-// Mark neighbour j of a mover for the next iteration (warp-collective).
-__device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool valid) {
-  bool fresh = false;
-  uint32_t key = 0;
-  if (valid && (!a.rbits || bit_test(a.rbits, j)) && bit_set(a.fbits_next, j)) {
-    fresh = true;
-    key = vertex_class(j, a.k, a.seg) * kBins + degree_bin(a.g.deg[j], a.seg);
+// Block-wide sums of the counters held by `holder` threads, one global
+// atomic each per block.  Every thread of the block must call it.
+__device__ __forceinline__ void flush_sums(const DecideArgs& a, const MoveSums& v, bool holder) {
+  __shared__ unsigned long long sh[5];
+  if (threadIdx.x < 5) sh[threadIdx.x] = 0;
+  __syncthreads();
+  if (holder) {
+    if (v.bytes) atomicAdd(&sh[0], v.bytes);
+    if (v.processed) atomicAdd(&sh[1], v.processed);
+    if (v.ever) atomicAdd(&sh[2], v.ever);
+    if (v.s_lo) atomicAdd(&sh[3], v.s_lo);
+    if (v.s_hi) atomicAdd(&sh[4], v.s_hi);
   }
-  append_vertex(j, fresh, key, a.next_lists, a.seg, a.ctrl, a.next_buf);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (sh[0]) atomicAdd(&a.ctrl->move_bytes, sh[0]);
+    if (sh[1]) atomicAdd(&a.ctrl->processed, sh[1]);
+    if (sh[2]) atomicAdd(&a.ctrl->ever_count, sh[2]);
+    if (sh[3]) atomicAdd(&a.ctrl->s_lo, sh[3]);
+    if (sh[4]) atomicAdd(&a.ctrl->s_hi, sh[4]);
+  }
+}
+
+// A mover of more than kMarkInline arcs does not mark its neighbours itself
+// (one block would walk them all while the rest of the GPU idles): it is
+// listed, and k_commit spreads every listed mover's arcs over all blocks.
+constexpr uint32_t kMarkInline = 512;
+constexpr uint32_t kMarkChunk = 1024;
+
+// Mark neighbour j of a mover for the next iteration: its bit in the next
+// frontier's bitmap (the lists are built from the bitmap once, at the end of
+// the iteration).  The bit is read first, so a vertex marked by many movers
+// takes one atomic.
+__device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool valid) {
+  if (valid && (!a.rbits || bit_test(a.rbits, j)) && !bit_test(a.fbits_next, j)) bit_set(a.fbits_next, j);
 }
 
 // ---------------------------------------------------------------------------
-// Bin 0: deg <= 32, one warp per vertex, one arc per lane, aggregation by
-// community with match/reduce in registers.
+// Bin 0: small degrees (at most W <= 32 arcs), W lanes per vertex, so one
+// warp decides 32 / W vertices at once, one arc per lane; aggregation by
+// community with match/reduce in registers inside each W-lane segment.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_decide_warp(DecideArgs a) {
-  const long long m2_one = *a.m2p;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t cnt = *a.count;
-  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
-  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
-  for (uint64_t t = warp; t < cnt; t += nwarps) {
-    const uint32_t i = a.list[t];
-    long long m2 = m2_one;
-    uint32_t gi = 0;
-    if (!group_active(a, i, &m2, &gi)) continue;
-    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
-    ++processed;
-    if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
-    const uint32_t d = a.C[i];
-    const long long Ki = a.K[i];
-    const unsigned long long o = a.g.off[i];
-    const uint32_t dg = a.g.deg[i];
-    uint2 arc = lane < dg ? a.g.arcs[o + lane] : make_uint2(i, 0u);
-    bool valid = lane < dg && arc.x != i && arc.y != 0;  // weight 0 = deleted arc
-    uint32_t c = valid ? a.C[arc.x] : kEmpty;
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
-    uint32_t hsum = __reduce_add_sync(peers, valid ? arc.y : 0u);
-    bool leader = valid && lane == uint32_t(__ffs(peers) - 1);
-    unsigned dm = __ballot_sync(0xFFFFFFFFu, leader && c == d);
-    unsigned long long Hd = dm ? __shfl_sync(0xFFFFFFFFu, hsum, __ffs(dm) - 1) : 0u;
-    bool cand = leader && c != d;
-    unsigned cm = __ballot_sync(0xFFFFFFFFu, cand);
-    i128 score = 0;
-    if (cand) score = (i128)m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
-    bool have = cand;
-    uint32_t bc = c;
-    warp_argmax(have, score, bc);
-    i128 gain = 0;
-    bool mv = decide_move(a, m2, i, d, Ki, have, score, bc, Hd, &gain);
-    bytes += 24 + 12ull * dg + 12ull * __popc(cm);
-    if (mv) {
-      if (lane == 0) record_move(a, i, bc, d, gain, gi);
-      mark_next(a, arc.x, valid);
-      bytes += 16 + 4ull * dg;
+
+// Argmax of (score, -c) over the aligned W-lane segment of each lane.
+template <int W>
+__device__ __forceinline__ void segment_argmax(bool& have, i128& score, uint32_t& c) {
+#pragma unroll
+  for (int s = W / 2; s >= 1; s >>= 1) {
+    unsigned long long lo = (unsigned long long)(u128)score;
+    unsigned long long hi = (unsigned long long)((u128)score >> 64);
+    unsigned long long olo = __shfl_xor_sync(0xFFFFFFFFu, lo, s);
+    unsigned long long ohi = __shfl_xor_sync(0xFFFFFFFFu, hi, s);
+    uint32_t oc = __shfl_xor_sync(0xFFFFFFFFu, c, s);
+    bool oh = __shfl_xor_sync(0xFFFFFFFFu, have ? 1 : 0, s) != 0;
+    i128 os = (i128)(((u128)ohi << 64) | (u128)olo);
+    if (oh && (!have || os > score || (os == score && oc < c))) {
+      have = true;
+      score = os;
+      c = oc;
     }
   }
-  if (lane == 0) {
-    atomicAdd(&a.ctrl->move_bytes, bytes);
-    if (processed) atomicAdd(&a.ctrl->processed, processed);
-    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
+}
+
+// One vertex per W-lane segment (`active` false: the segment idles).  Every
+// lane of the warp must call it.  Returns the segment's move decision.
+template <int W>
+__device__ __forceinline__ bool decide_segment(const DecideArgs& a, bool active, uint32_t i, long long m2,
+                                               uint32_t gi, MoveSums& sums) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t seg = lane / W, sl = lane % W;
+  const unsigned segmask = W == 32 ? 0xFFFFFFFFu : (((1u << W) - 1u) << (seg * W));
+  const uint32_t d = active ? a.C[i] : 0u;
+  const long long Ki = active ? a.K[i] : 0;
+  const unsigned long long o = active ? a.g.off[i] : 0ull;
+  const uint32_t dg = active ? a.g.deg[i] : 0u;
+  uint2 arc = sl < dg ? a.g.arcs[o + sl] : make_uint2(i, 0u);
+  const bool valid = sl < dg && arc.x != i && arc.y != 0;  // weight 0 = deleted arc
+  const uint32_t c = valid ? a.C[arc.x] : kEmpty;
+  // group equal communities of one segment (the segment number in the key)
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, ((unsigned long long)seg << 32) | c);
+  const uint32_t hsum = __reduce_add_sync(peers, valid ? arc.y : 0u);
+  const bool leader = valid && lane == uint32_t(__ffs(peers) - 1);
+  const unsigned dm = __ballot_sync(0xFFFFFFFFu, leader && c == d) & segmask;
+  // every lane shuffles (from its segment's holder of d, or from itself)
+  const uint32_t hd_src = dm ? uint32_t(__ffs(dm) - 1) : lane;
+  const uint32_t hd_val = __shfl_sync(0xFFFFFFFFu, hsum, hd_src);
+  const unsigned long long Hd = dm ? hd_val : 0u;
+  const bool cand = leader && c != d;
+  const unsigned cm = __ballot_sync(0xFFFFFFFFu, cand) & segmask;
+  i128 score = 0;
+  if (cand) score = (i128)m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
+  bool have = cand;
+  uint32_t bc = c;
+  segment_argmax<W>(have, score, bc);
+  i128 gain = 0;
+  const bool mv = active && decide_move(a, m2, i, d, Ki, have, score, bc, Hd, &gain);
+  if (active && sl == 0) sums.bytes += 24 + 12ull * dg + 12ull * __popc(cm);
+  if (mv) {
+    if (sl == 0) {
+      record_move(a, i, bc, d, gain, gi, sums);
+      sums.bytes += 16 + 4ull * dg;
+    }
   }
+  mark_next(a, arc.x, mv && valid);
+  return mv;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 5) k_decide_warp(DecideArgs a) {
+  constexpr uint32_t kSegs = 32 / W;
+  const long long m2_one = *a.m2p;
+  const uint32_t lane = threadIdx.x & 31u, seg = lane / W, sl = lane % W;
+  const uint32_t cnt = *a.count;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  MoveSums sums;
+  for (uint64_t t0 = warp * kSegs; t0 < cnt; t0 += nwarps * kSegs) {
+    const uint64_t t = t0 + seg;
+    bool active = t < cnt;
+    const uint32_t i = active ? a.list[t] : 0u;
+    long long m2 = m2_one;
+    uint32_t gi = 0;
+    if (active && !group_active(a, i, &m2, &gi)) active = false;
+    if (active && sl == 0) {
+      if (a.ever && bit_set(a.ever, i)) ++sums.ever;
+      ++sums.processed;
+    }
+    if (active && a.rbits && !bit_test(a.rbits, i)) active = false;  // processed, not in range
+    decide_segment<W>(a, active, i, m2, gi, sums);
+  }
+  flush_sums(a, sums, sl == 0);
 }
 
 // Open-addressing insert (linear probing) of weight w under key c; gives up
@@ -209,6 +285,47 @@ __device__ __forceinline__ bool scan_row(const DecideArgs& a, uint32_t i, unsign
   return ok;
 }
 
+// Best candidate of table slots start, start + step, ... below `slots`: U
+// slots' keys and values, then their Sigma gathers, are issued before any is
+// used, so a thread waits once per U occupied slots.  Returns (per thread)
+// the weight to d if this thread met d's slot, and counts candidates.
+template <int U>
+__device__ __forceinline__ unsigned long long table_argmax(const DecideArgs& a, const uint32_t* keys,
+                                                           const uint32_t* vals, uint32_t slots,
+                                                           uint32_t start, uint32_t step, uint32_t d,
+                                                           long long m2, long long Ki, bool& have,
+                                                           i128& best, uint32_t& bc, uint32_t& ncand) {
+  unsigned long long hd = 0;
+  for (uint32_t s0 = start; s0 < slots; s0 += step * U) {
+    uint32_t c[U], w[U];
+    long long sg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t sl = s0 + u * step;
+      c[u] = sl < slots ? keys[sl] : kEmpty;
+      w[u] = sl < slots ? vals[sl] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) sg[u] = (c[u] != kEmpty && c[u] != d) ? a.Sigma[c[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c[u] == kEmpty) continue;
+      if (c[u] == d) {
+        hd = w[u];
+        continue;
+      }
+      ++ncand;
+      const i128 sc = (i128)m2 * (i128)w[u] - (i128)Ki * (i128)sg[u];
+      if (!have || sc > best || (sc == best && c[u] < bc)) {
+        have = true;
+        best = sc;
+        bc = c[u];
+      }
+    }
+  }
+  return hd;
+}
+
 // ---------------------------------------------------------------------------
 // Bin 1: 32 < deg <= 256, one warp per vertex with a shared table.
 // ---------------------------------------------------------------------------
@@ -225,19 +342,23 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
+  MoveSums sums;
   for (uint64_t t = warp; t < cnt; t += nwarps) {
     const uint32_t i = a.list[t];
     long long m2 = m2_one;
     uint32_t gi = 0;
     if (!group_active(a, i, &m2, &gi)) continue;
-    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++fresh_ever;
-    ++processed;
+    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++sums.ever;
+    ++sums.processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
+    const uint32_t dg = a.g.deg[i];
+    if (dg <= 32) {  // (when bin 0 takes fewer than 32 arcs) registers, not a table
+      decide_segment<32>(a, true, i, m2, gi, sums);
+      continue;
+    }
     const uint32_t d = a.C[i];
     const long long Ki = a.K[i];
     const unsigned long long o = a.g.off[i];
-    const uint32_t dg = a.g.deg[i];
     uint32_t slots = 64;
     while (slots < 2 * dg && slots < kWarpSlots) slots <<= 1;
     const uint32_t mask = slots - 1;
@@ -246,29 +367,14 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
       vals[s] = 0;
     }
     __syncwarp();
-    bool ok = scan_row<4>(a, i, o, dg, 0, 32, keys, vals, mask, slots);
+    bool ok = scan_row<8>(a, i, o, dg, 0, 32, keys, vals, mask, slots);
     if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
     __syncwarp();
     bool have = false;
     i128 best = 0;
     uint32_t bc = 0;
-    unsigned long long Hd = 0;
     uint32_t ncand = 0;
-    for (uint32_t s = lane; s < slots; s += 32) {
-      uint32_t c = keys[s];
-      if (c == kEmpty) continue;
-      if (c == d) {
-        Hd = vals[s];
-        continue;
-      }
-      ++ncand;
-      i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
-      if (!have || sc > best || (sc == best && c < bc)) {
-        have = true;
-        best = sc;
-        bc = c;
-      }
-    }
+    unsigned long long Hd = table_argmax<4>(a, keys, vals, slots, lane, 32, d, m2, Ki, have, best, bc, ncand);
     for (int x = 16; x; x >>= 1) {
       Hd += __shfl_xor_sync(0xFFFFFFFFu, Hd, x);
       ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
@@ -276,23 +382,19 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
     warp_argmax(have, best, bc);
     i128 gain = 0;
     bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
-    bytes += 24 + 12ull * dg + 12ull * ncand;
+    sums.bytes += 24 + 12ull * dg + 12ull * ncand;
     if (mv) {
-      if (lane == 0) record_move(a, i, bc, d, gain, gi);
+      if (lane == 0) record_move(a, i, bc, d, gain, gi, sums);
       for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
         uint32_t k = k0 + lane;
         uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
         mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
       }
-      bytes += 16 + 4ull * dg;
+      sums.bytes += 16 + 4ull * dg;
     }
     __syncwarp();
   }
-  if (lane == 0) {
-    atomicAdd(&a.ctrl->move_bytes, bytes);
-    if (processed) atomicAdd(&a.ctrl->processed, processed);
-    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
-  }
+  flush_sums(a, sums, lane == 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,14 +418,14 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   __shared__ int s_ok;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kThreads / 32;
   const uint32_t cnt = *a.count;
-  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
+  MoveSums sums;
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const uint32_t i = a.list[t];
     long long m2 = m2_one;
     uint32_t gi = 0;
     if (!group_active(a, i, &m2, &gi)) continue;
-    if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
-    ++processed;
+    if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++sums.ever;
+    ++sums.processed;
     if (a.rbits && !bit_test(a.rbits, i)) continue;
     const uint32_t d = a.C[i];
     const long long Ki = a.K[i];
@@ -355,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
       // a table of >= 2 * deg slots cannot overflow: probe it to the end;
       // a smaller shared table (bin 3) gives up early and falls back
       const uint32_t limit = (global || slots >= 2 * dg) ? slots : 64;
-      bool ok = scan_row<4>(a, i, o, dg, wib * 32, kThreads, keys, vals, mask, limit);
+      bool ok = scan_row<8>(a, i, o, dg, wib * 32, kThreads, keys, vals, mask, limit);
       if (!ok) s_ok = 0;
       __syncthreads();
       const bool done = s_ok;
@@ -370,20 +472,10 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
     i128 best = 0;
     uint32_t bc = 0;
     uint32_t ncand = 0;
-    for (uint32_t s = threadIdx.x; s < slots; s += kThreads) {
-      uint32_t c = keys[s];
-      if (c == kEmpty) continue;
-      if (c == d) {
-        s_hd = vals[s];  // exactly one slot holds d
-        continue;
-      }
-      ++ncand;
-      i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
-      if (!have || sc > best || (sc == best && c < bc)) {
-        have = true;
-        best = sc;
-        bc = c;
-      }
+    {
+      const unsigned long long hd = table_argmax<4>(a, keys, vals, slots, threadIdx.x, kThreads, d, m2, Ki,
+                                                     have, best, bc, ncand);
+      if (hd) s_hd = hd;  // exactly one slot holds d
     }
     for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
     warp_argmax(have, best, bc);
@@ -413,99 +505,143 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
     bc = s_c[0];
     i128 gain = 0;
     bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
-    bytes += 24 + 12ull * dg + 12ull * s_ncand;
+    sums.bytes += 24 + 12ull * dg + 12ull * s_ncand;
     if (mv) {
-      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi);
-      for (uint32_t k0 = wib * 32; k0 < dg; k0 += kThreads) {
-        uint32_t k = k0 + lane;
-        uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
-        mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
+      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi, sums);
+      if (dg > kMarkInline) {
+        if (threadIdx.x == 0) a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;
+      } else {
+        for (uint32_t k0 = wib * 32; k0 < dg; k0 += kThreads) {
+          uint32_t k = k0 + lane;
+          uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+          mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
+        }
       }
-      bytes += 16 + 4ull * dg;
+      sums.bytes += 16 + 4ull * dg;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    atomicAdd(&a.ctrl->move_bytes, bytes);
-    if (processed) atomicAdd(&a.ctrl->processed, processed);
-    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
-  }
+  flush_sums(a, sums, threadIdx.x == 0);
 }
 
 // ---------------------------------------------------------------------------
-// Bin 3 (deg > 4096): a vertex is split into chunks of kGiantChunk arcs, one
-// block per chunk.  A chunk block aggregates its arcs in shared memory and
-// writes the distinct (community, weight) partial sums to the vertex's region
-// of g_partial; the last chunk block of the vertex merges the partial sums
-// (in hash-partitioned passes that each fit the shared table) and decides.
-// If a pass still overflows, the last block redoes the vertex alone with a
-// global table slice.
+// Bin 3 (the largest degrees): three kernels, every step parallel and
+// proportional to the vertex's arcs or its distinct neighbour communities.
+//   k_giant_prefix  lays out, per listed vertex, its chunks of kGiantChunk
+//                   arcs, a global open-addressing table of a power of two
+//                   >= 2 x degree slots (empty at rest) and a list of the
+//                   table's occupied slots (capacity = degree);
+//   k_giant_accum   one block per chunk: the chunk's arcs are aggregated by
+//                   community in shared memory, then every distinct (community,
+//                   weight) is added into the vertex's table; a new key's slot
+//                   is appended to the vertex's occupied list;
+//   k_giant_decide  one block per kGiantPart occupied slots of a vertex: those
+//                   entries are read and cleared, the part's best candidate is
+//                   kept (and the weight to the own community, when met); the
+//                   vertex's last part block reduces the parts and decides.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kGiantChunk = 4096;
-constexpr uint32_t kGiantSlots = 2 * kGiantChunk;  // 8192 keys + values = 64 KB
+constexpr uint32_t kGiantChunk = 1024;             // short per-block work: latency, not bandwidth, bounds it
+constexpr uint32_t kGiantSlots = 2 * kGiantChunk;  // shared chunk table: 2048 keys + values = 16 KB
+constexpr int kAccumThreads = 128;
+constexpr uint32_t kGiantPart = 2048;               // occupied slots per decide block
 constexpr int kGiantThreads = 256;
+constexpr uint32_t kGiantListSmem = 2048;          // chunk prefix cached in shared memory
 
-struct GiantDecide {
-  unsigned long long* poff;
-  uint32_t* cpre;
-  uint32_t* done;
-  uint32_t* pcount;
-  uint2* partial;
-  unsigned int* nitems;
+struct GiantRes {
+  unsigned long long lo, hi;  // best score of the part
+  uint32_t c;
+  uint32_t have;
 };
 
-// One block: exclusive prefix over the bin-3 list of deg (partial regions)
-// and of the chunk counts (work items).
+struct GiantDecide {
+  unsigned long long* toff;   // per list position: first slot of its table
+  unsigned long long* loff;   // ... first entry of its occupied-slot list
+  uint32_t* cpre;             // exclusive prefix of chunk counts (+ total)
+  uint32_t* ndist;            // occupied slots of its table (zeroed by k_giant_prefix)
+  uint32_t* done;             // part blocks finished (zero at rest)
+  unsigned long long* hd;     // weight to the own community (zero at rest)
+  GiantRes* res;              // per part
+  uint32_t* tkeys;            // tables (kEmpty at rest)
+  uint32_t* tvals;            // (0 at rest)
+  uint32_t* tlist;            // occupied-slot lists
+  unsigned int* nitems;       // chunk total
+};
+
+__device__ __forceinline__ uint32_t giant_deg(const DecideArgs& a, uint32_t t) {
+  const uint32_t v = a.list[t];
+  uint32_t d = a.g.deg[v];
+  if (d && a.ngraphs && a.gdone[graph_of(a.goff, a.ngraphs, v)]) d = 0;  // finished graph: skipped
+  return d;
+}
+
+// Table of a vertex of degree d: a power of two >= 2d (at least 64 slots).
+__device__ __forceinline__ uint64_t giant_table_slots(uint32_t d) {
+  if (!d) return 0;
+  uint64_t p = 64;
+  while (p < 2 * uint64_t(d)) p <<= 1;
+  return p;
+}
+
+// One block: exclusive prefixes over the bin-3 list of chunks, table slots
+// and list capacities.
 __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd) {
-  __shared__ unsigned long long s_d[32];
+  __shared__ unsigned long long s_t[32], s_l[32];
   __shared__ uint32_t s_c[32];
-  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_tbase, s_lbase;
   __shared__ uint32_t s_cbase;
   const uint32_t cnt = *a.count;
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    s_base = 0;
+    s_tbase = s_lbase = 0;
     s_cbase = 0;
   }
   __syncthreads();
   for (uint32_t t0 = 0; t0 < cnt; t0 += blockDim.x) {
-    uint32_t t = t0 + threadIdx.x;
-    unsigned long long d = t < cnt ? a.g.deg[a.list[t]] : 0ull;
-    if (d && a.ngraphs && a.gdone[graph_of(a.goff, a.ngraphs, a.list[t])]) d = 0;  // skipped
-    uint32_t ch = uint32_t((d + kGiantChunk - 1) / kGiantChunk);
-    unsigned long long xd = d;
+    const uint32_t t = t0 + threadIdx.x;
+    const uint32_t d = t < cnt ? giant_deg(a, t) : 0u;
+    const uint32_t ch = (d + kGiantChunk - 1) / kGiantChunk;
+    const unsigned long long ts = giant_table_slots(d);
+    unsigned long long xt = ts, xl = d;
     uint32_t xc = ch;
     for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long yd = __shfl_up_sync(0xFFFFFFFFu, xd, o);
+      unsigned long long yt = __shfl_up_sync(0xFFFFFFFFu, xt, o);
+      unsigned long long yl = __shfl_up_sync(0xFFFFFFFFu, xl, o);
       uint32_t yc = __shfl_up_sync(0xFFFFFFFFu, xc, o);
       if (lane >= (uint32_t)o) {
-        xd += yd;
+        xt += yt;
+        xl += yl;
         xc += yc;
       }
     }
     if (lane == 31) {
-      s_d[w] = xd;
+      s_t[w] = xt;
+      s_l[w] = xl;
       s_c[w] = xc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long rd = s_base;
+      unsigned long long rt = s_tbase, rl = s_lbase;
       uint32_t rc = s_cbase;
       for (uint32_t k = 0; k < blockDim.x / 32; ++k) {
-        unsigned long long td = s_d[k];
-        uint32_t tc = s_c[k];
-        s_d[k] = rd;
+        const unsigned long long tt = s_t[k], tl = s_l[k];
+        const uint32_t tc = s_c[k];
+        s_t[k] = rt;
+        s_l[k] = rl;
         s_c[k] = rc;
-        rd += td;
+        rt += tt;
+        rl += tl;
         rc += tc;
       }
-      s_base = rd;
+      s_tbase = rt;
+      s_lbase = rl;
       s_cbase = rc;
     }
     __syncthreads();
     if (t < cnt) {
-      gd.poff[t] = s_d[w] + xd - d;
+      gd.toff[t] = s_t[w] + xt - ts;
+      gd.loff[t] = s_l[w] + xl - d;
       gd.cpre[t] = s_c[w] + xc - ch;
+      gd.ndist[t] = 0;  // counted by k_giant_accum, read by every k_giant_decide block
     }
     __syncthreads();
   }
@@ -515,215 +651,405 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
   }
 }
 
-__global__ void __launch_bounds__(kGiantThreads, 2) k_decide_giant(DecideArgs a, GiantDecide gd) {
+// Reduce (have, score, c) of every thread of the block to thread 0 (larger
+// score wins, ties to the smaller c); every thread calls it.
+__device__ __forceinline__ void block_argmax(bool& have, i128& best, uint32_t& bc) {
+  __shared__ unsigned long long s_lo[kGiantThreads / 32], s_hi[kGiantThreads / 32];
+  __shared__ uint32_t s_c[kGiantThreads / 32];
+  __shared__ int s_have[kGiantThreads / 32];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x / 32;
+  warp_argmax(have, best, bc);
+  __syncthreads();
+  if (lane == 0) {
+    s_lo[wib] = (unsigned long long)(u128)best;
+    s_hi[wib] = (unsigned long long)((u128)best >> 64);
+    s_c[wib] = bc;
+    s_have[wib] = have;
+  }
+  __syncthreads();
+  if (wib == 0) {
+    have = lane < nw && s_have[lane];
+    best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
+    bc = lane < nw ? s_c[lane] : 0;
+    warp_argmax(have, best, bc);
+  }
+}
+
+// Entries [e0, e1) of vertex t's occupied list: read and clear them, keep the
+// best candidate of this thread (and the weight to d, in hd[t]); returns the
+// number of candidates this thread saw.  Four entries' loads are in flight
+// at a time (slot, then key and weight, then Sigma).
+__device__ __forceinline__ uint32_t giant_scan_entries(const DecideArgs& a, const GiantDecide& gd, uint32_t t,
+                                                       uint32_t e0, uint32_t e1, uint32_t d, long long m2,
+                                                       long long Ki, bool& have, i128& best, uint32_t& bc) {
+  constexpr int U = 4;
+  uint32_t* gk = gd.tkeys + gd.toff[t];
+  uint32_t* gv = gd.tvals + gd.toff[t];
+  const uint32_t* gl = gd.tlist + gd.loff[t];
+  uint32_t ncand = 0;
+  for (uint32_t b = e0 + threadIdx.x; b < e1; b += blockDim.x * U) {
+    uint32_t slot[U], c[U], h[U];
+    long long sg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = b + u * blockDim.x;
+      slot[u] = e < e1 ? __ldcg(gl + e) : kEmpty;  // written by other blocks of this kernel
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = slot[u] != kEmpty ? __ldcg(gk + slot[u]) : kEmpty;
+      h[u] = slot[u] != kEmpty ? __ldcg(gv + slot[u]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) sg[u] = (c[u] != kEmpty && c[u] != d) ? a.Sigma[c[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (slot[u] == kEmpty) continue;
+      gk[slot[u]] = kEmpty;
+      gv[slot[u]] = 0;
+      if (c[u] == d) {
+        gd.hd[t] = h[u];  // exactly one entry of the table holds d
+        continue;
+      }
+      ++ncand;
+      const i128 sc = (i128)m2 * (i128)h[u] - (i128)Ki * (i128)sg[u];
+      if (!have || sc > best || (sc == best && c[u] < bc)) {
+        have = true;
+        best = sc;
+        bc = c[u];
+      }
+    }
+  }
+  return ncand;
+}
+
+constexpr uint32_t kSmallDecide = 4096;  // occupied slots the last chunk block decides alone
+
+__global__ void __launch_bounds__(kAccumThreads, 8) k_giant_accum(DecideArgs a, GiantDecide gd) {
+  __shared__ uint32_t keys[kGiantSlots];
+  __shared__ uint32_t vals[kGiantSlots];
+  __shared__ uint32_t s_pre[kGiantListSmem];
+  __shared__ int s_last;
+  __shared__ uint32_t s_ncand, s_ne;
+  __shared__ uint32_t s_ek[kGiantChunk], s_ev[kGiantChunk];  // distinct communities of a chunk
   const long long m2_one = *a.m2p;
-  extern __shared__ uint32_t dyn[];
-  uint32_t* keys = dyn;
-  uint32_t* vals = dyn + kGiantSlots;
-  __shared__ int s_last, s_ok, s_have[kGiantThreads / 32];
-  __shared__ unsigned long long s_hd, s_lo[kGiantThreads / 32], s_hi[kGiantThreads / 32];
-  __shared__ uint32_t s_c[kGiantThreads / 32], s_ncand;
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kGiantThreads / 32;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_ncand = 0;
   const uint32_t cnt = *a.count;
   const uint32_t nitems = *gd.nitems;
-  unsigned long long bytes = 0, processed = 0, fresh_ever = 0;
+  // the chunk prefix, cached in shared memory when it fits
+  const uint32_t* cp = gd.cpre;
+  if (cnt + 1 <= kGiantListSmem) {
+    for (uint32_t k = threadIdx.x; k <= cnt; k += blockDim.x) s_pre[k] = gd.cpre[k];
+    __syncthreads();
+    cp = s_pre;
+  }
+  MoveSums sums;
   for (uint32_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     uint32_t lo = 0, hi = cnt;  // list position owning this chunk
     while (hi - lo > 1) {
       uint32_t mid = (lo + hi) >> 1;
-      if (gd.cpre[mid] <= item) lo = mid;
+      if (cp[mid] <= item) lo = mid;
       else hi = mid;
     }
     const uint32_t t = lo;
-    const uint32_t chunk = item - gd.cpre[t];
-    const uint32_t nch = gd.cpre[t + 1] - gd.cpre[t];
+    const uint32_t chunk = item - cp[t];
     const uint32_t i = a.list[t];
-    long long m2 = m2_one;
-    uint32_t gi = 0;
-    group_active(a, i, &m2, &gi);  // its graph is active: the prefix gave it chunks
     if (chunk == 0) {
-      if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++fresh_ever;
-      ++processed;
+      if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++sums.ever;
+      ++sums.processed;
     }
     if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
     const unsigned long long o = a.g.off[i];
     const uint32_t dg = a.g.deg[i];
     const uint32_t k0 = chunk * kGiantChunk;
     const uint32_t k1 = min(dg, k0 + kGiantChunk);
-    // 1. this chunk's partial sums
-    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
+    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kAccumThreads) {
       keys[s] = kEmpty;
       vals[s] = 0;
     }
     __syncthreads();
     // a table of 2x the chunk's arcs cannot overflow
-    scan_row<4>(a, i, o, k1, k0 + wib * 32, kGiantThreads, keys, vals, kGiantSlots - 1, kGiantSlots);
+    scan_row<8>(a, i, o, k1, k0 + wib * 32, kAccumThreads, keys, vals, kGiantSlots - 1, kGiantSlots);
     __syncthreads();
-    for (uint32_t s0 = wib * 32; s0 < kGiantSlots; s0 += kGiantThreads) {
-      uint32_t s = s0 + lane;
-      uint32_t key = keys[s];
-      unsigned m = __ballot_sync(0xFFFFFFFFu, key != kEmpty);
+    // the chunk's distinct communities: compacted in shared memory, then
+    // added into the vertex's global table, four per thread in flight; new
+    // keys' slots go onto its occupied list (one counter update per warp)
+    if (threadIdx.x == 0) s_ne = 0;
+    __syncthreads();
+    for (uint32_t s0 = wib * 32; s0 < kGiantSlots; s0 += kAccumThreads) {
+      const uint32_t c = keys[s0 + lane];
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, c != kEmpty);
+      if (!m) continue;
       uint32_t base = 0;
-      if (lane == 0 && m) base = atomicAdd(&gd.pcount[t], __popc(m));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (key != kEmpty) gd.partial[gd.poff[t] + base + __popc(m & ((1u << lane) - 1u))] = make_uint2(key, vals[s]);
+      if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&s_ne, uint32_t(__popc(m)));
+      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+      if (c != kEmpty) {
+        const uint32_t r = base + __popc(m & ((1u << lane) - 1u));
+        s_ek[r] = c;
+        s_ev[r] = vals[s0 + lane];
+      }
     }
+    __syncthreads();
+    const uint32_t ne = s_ne;
+    const uint32_t tmask = uint32_t(giant_table_slots(dg) - 1);
+    uint32_t* gk = gd.tkeys + gd.toff[t];
+    uint32_t* gv = gd.tvals + gd.toff[t];
+    uint32_t* gl = gd.tlist + gd.loff[t];
+    constexpr int U = 4;
+    for (uint32_t b0 = wib * 32 * U; b0 < ne; b0 += kAccumThreads * U) {  // warp-uniform
+      uint32_t c[U], slot[U], prev[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t e = b0 + u * 32 + lane;
+        c[u] = e < ne ? s_ek[e] : kEmpty;
+        slot[u] = hash32(c[u]) & tmask;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) prev[u] = c[u] != kEmpty ? atomicCAS(&gk[slot[u]], kEmpty, c[u]) : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t e = b0 + u * 32 + lane;
+        bool created = false;
+        if (c[u] != kEmpty) {
+          // load <= 1/2: the probe ends within the table
+          for (uint32_t probe = 0; prev[u] != kEmpty && prev[u] != c[u] && probe < tmask; ++probe) {
+            slot[u] = (slot[u] + 1) & tmask;
+            prev[u] = atomicCAS(&gk[slot[u]], kEmpty, c[u]);
+          }
+          if (prev[u] != kEmpty && prev[u] != c[u]) {
+            atomicOr(&a.ctrl->err, kErrInternal);  // (cannot happen: the table is never full)
+          } else {
+            created = prev[u] == kEmpty;
+            atomicAdd(&gv[slot[u]], s_ev[e]);
+          }
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, created);
+        if (m) {
+          uint32_t base = 0;
+          if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&gd.ndist[t], uint32_t(__popc(m)));
+          base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+          if (created) gl[base + __popc(m & ((1u << lane) - 1u))] = slot[u];
+        }
+      }
+    }
+    // the vertex's last chunk block decides it when its table holds few
+    // communities; k_giant_decide takes the rest
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&gd.done[t], 1u) == nch - 1;
+    if (threadIdx.x == 0) s_last = atomicAdd(&gd.done[t], 1u) == cp[t + 1] - cp[t] - 1;
     __syncthreads();
-    if (!s_last) continue;
-    __threadfence();
-    // 2. last block of the vertex: merge the partial sums and decide
-    const uint32_t d = a.C[i];
-    const long long Ki = a.K[i];
-    const uint32_t np = __ldcg(gd.pcount + t);
-    const uint32_t passes = (np + kGiantChunk - 1) / kGiantChunk > 0 ? (np + kGiantChunk - 1) / kGiantChunk : 1;
-    bool have = false;
-    i128 best = 0;
-    uint32_t bc = 0;
-    uint32_t ncand = 0;
-    unsigned long long hd_local = 0;
-    if (threadIdx.x == 0) {
-      s_ok = 1;
-      s_hd = 0;
-      s_ncand = 0;
-    }
-    for (uint32_t pass = 0; pass < passes; ++pass) {
-      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
-        keys[s] = kEmpty;
-        vals[s] = 0;
-      }
-      __syncthreads();
-      bool ok = true;
-      for (uint32_t e = threadIdx.x; e < np; e += kGiantThreads) {
-        uint2 pe = __ldcg(gd.partial + gd.poff[t] + e);  // written by other blocks: bypass L1
-        if (passes == 1 || hash32(pe.x ^ 0x5bd1e995u) % passes == pass)
-          ok &= table_add(keys, vals, kGiantSlots - 1, pe.x, pe.y, kGiantSlots);
-      }
-      if (!ok) s_ok = 0;
-      __syncthreads();
-      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kGiantThreads) {
-        uint32_t c = keys[s];
-        if (c == kEmpty) continue;
-        if (c == d) {
-          hd_local = vals[s];
-          continue;
-        }
-        ++ncand;
-        i128 sc = (i128)m2 * (i128)vals[s] - (i128)Ki * (i128)a.Sigma[c];
-        if (!have || sc > best || (sc == best && c < bc)) {
-          have = true;
-          best = sc;
-          bc = c;
+    if (s_last) {
+      __threadfence();
+      const uint32_t nd = __ldcg(gd.ndist + t);
+      if (threadIdx.x == 0) gd.done[t] = 0;  // k_giant_decide counts its part blocks from 0
+      if (nd <= kSmallDecide) {
+        long long m2 = m2_one;
+        uint32_t gi = 0;
+        group_active(a, i, &m2, &gi);
+        const uint32_t d = a.C[i];
+        const long long Ki = a.K[i];
+        bool have = false;
+        i128 best = 0;
+        uint32_t bc = 0;
+        uint32_t ncand = giant_scan_entries(a, gd, t, 0, nd, d, m2, Ki, have, best, bc);
+        for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+        if (lane == 0 && ncand) atomicAdd(&s_ncand, ncand);
+        __threadfence();
+        __syncthreads();
+        block_argmax(have, best, bc);
+        if (threadIdx.x == 0) {
+          const unsigned long long Hd = __ldcg(gd.hd + t);
+          gd.hd[t] = 0;
+          i128 gain = 0;
+          const bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
+          sums.bytes += 24 + 12ull * dg + 12ull * s_ncand;
+          s_ncand = 0;
+          if (mv) {
+            record_move(a, i, bc, d, gain, gi, sums);
+            a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;  // neighbours marked by k_commit
+            sums.bytes += 16 + 4ull * dg;
+          }
         }
       }
-      __syncthreads();
-    }
-    const bool overflow = !s_ok;
-    __syncthreads();
-    if (overflow) {
-      // rare: redo the whole vertex with this block's global table slice
-      have = false;
-      ncand = 0;
-      hd_local = 0;
-      uint32_t* gk = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
-      uint32_t* gv = gk + a.gslots;
-      uint32_t slots = a.gslots;
-      for (uint32_t s = threadIdx.x; s < slots; s += kGiantThreads) {
-        gk[s] = kEmpty;
-        gv[s] = 0;
-      }
-      __syncthreads();
-      scan_row<4>(a, i, o, dg, wib * 32, kGiantThreads, gk, gv, slots - 1, slots);
-      __syncthreads();
-      for (uint32_t s = threadIdx.x; s < slots; s += kGiantThreads) {
-        uint32_t c = gk[s];
-        if (c == kEmpty) continue;
-        if (c == d) {
-          hd_local = gv[s];
-          continue;
-        }
-        ++ncand;
-        i128 sc = (i128)m2 * (i128)gv[s] - (i128)Ki * (i128)a.Sigma[c];
-        if (!have || sc > best || (sc == best && c < bc)) {
-          have = true;
-          best = sc;
-          bc = c;
-        }
-      }
-    }
-    for (int x = 16; x; x >>= 1) {
-      ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
-      hd_local += __shfl_xor_sync(0xFFFFFFFFu, hd_local, x);
-    }
-    warp_argmax(have, best, bc);
-    if (lane == 0) {
-      s_lo[wib] = (unsigned long long)(u128)best;
-      s_hi[wib] = (unsigned long long)((u128)best >> 64);
-      s_c[wib] = bc;
-      s_have[wib] = have;
-      if (ncand) atomicAdd(&s_ncand, ncand);
-      if (hd_local) atomicAdd(&s_hd, hd_local);
-    }
-    __syncthreads();
-    if (wib == 0) {
-      have = lane < nw && s_have[lane];
-      best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
-      bc = lane < nw ? s_c[lane] : 0;
-      warp_argmax(have, best, bc);
-      if (lane == 0) {
-        s_lo[0] = (unsigned long long)(u128)best;
-        s_hi[0] = (unsigned long long)((u128)best >> 64);
-        s_c[0] = bc;
-        s_have[0] = have;
-      }
-    }
-    __syncthreads();
-    have = s_have[0];
-    best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
-    bc = s_c[0];
-    i128 gain = 0;
-    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
-    bytes += 24 + 12ull * dg + 12ull * s_ncand;
-    if (mv) {
-      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi);
-      for (uint32_t q0 = wib * 32; q0 < dg; q0 += kGiantThreads) {
-        uint32_t q = q0 + lane;
-        uint2 arc = q < dg ? a.g.arcs[o + q] : make_uint2(i, 0u);
-        mark_next(a, arc.x, q < dg && arc.x != i && arc.y != 0);
-      }
-      bytes += 16 + 4ull * dg;
-    }
-    if (threadIdx.x == 0) {  // ready for the next use of this list position
-      gd.done[t] = 0;
-      gd.pcount[t] = 0;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    atomicAdd(&a.ctrl->move_bytes, bytes);
-    if (processed) atomicAdd(&a.ctrl->processed, processed);
-    if (fresh_ever) atomicAdd(&a.ctrl->ever_count, fresh_ever);
-  }
+  flush_sums(a, sums, threadIdx.x == 0);
 }
 
-// Apply the moves of one sub-step.
-__global__ void k_commit(const uint32_t* __restrict__ mv_i, const uint32_t* __restrict__ mv_c,
-                         const uint32_t* __restrict__ mv_d, uint32_t* __restrict__ C,
-                         const long long* __restrict__ K, long long* __restrict__ Sigma,
-                         int* __restrict__ size, Ctrl* ctrl) {
-  const uint32_t m = ctrl->movers;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && m) atomicAdd(&ctrl->moved, (unsigned long long)m);
-  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < m;
-       t += uint64_t(gridDim.x) * blockDim.x) {
-    uint32_t i = mv_i[t], c = mv_c[t], d = mv_d[t];
-    long long ki = K[i];
-    C[i] = c;
-    atomicAdd((unsigned long long*)&Sigma[d], (unsigned long long)(-ki));
-    atomicAdd((unsigned long long*)&Sigma[c], (unsigned long long)ki);
-    atomicSub(&size[d], 1);
-    atomicAdd(&size[c], 1);
+__global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, GiantDecide gd) {
+  const long long m2_one = *a.m2p;
+  __shared__ uint32_t s_ipre[kGiantThreads + 1];  // part prefix of one tile of the list
+  __shared__ uint32_t s_ncand;
+  __shared__ int s_last;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  const uint32_t cnt = *a.count;
+  MoveSums sums;
+  // sweep the list in tiles of blockDim.x positions; part items of a tile
+  // are numbered from `ibase` and dealt round-robin over the blocks
+  uint32_t ibase = 0;
+  for (uint32_t t0 = 0; t0 < cnt; t0 += kGiantThreads) {
+    {
+      const uint32_t t = t0 + threadIdx.x;
+      const uint32_t nd = t < cnt ? gd.ndist[t] : 0u;
+      const uint32_t np = nd > kSmallDecide ? (nd + kGiantPart - 1) / kGiantPart : 0u;  // else decided
+      uint32_t x = np;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+      }
+      __shared__ uint32_t s_w[kGiantThreads / 32];
+      if (lane == 31) s_w[wib] = x;
+      __syncthreads();
+      uint32_t wbase = 0;
+      for (uint32_t k = 0; k < wib; ++k) wbase += s_w[k];
+      s_ipre[threadIdx.x + 1] = wbase + x;
+      if (threadIdx.x == 0) s_ipre[0] = 0;
+      __syncthreads();
+    }
+    const uint32_t tile_items = s_ipre[kGiantThreads];
+    const uint32_t first = (blockIdx.x + gridDim.x - ibase % gridDim.x) % gridDim.x;
+    for (uint32_t it = first; it < tile_items; it += gridDim.x) {
+      uint32_t lo = 0, hi = kGiantThreads;  // tile position owning part item `it`
+      while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (s_ipre[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t t = t0 + lo;
+      const uint32_t part = it - s_ipre[lo];
+      const uint32_t nparts = s_ipre[lo + 1] - s_ipre[lo];
+      const uint32_t ridx = ibase + s_ipre[lo];  // results of this vertex start here
+      const uint32_t nd = gd.ndist[t];
+      const uint32_t i = a.list[t];
+      long long m2 = m2_one;
+      uint32_t gi = 0;
+      group_active(a, i, &m2, &gi);  // its graph is active: it has entries
+      const uint32_t d = a.C[i];
+      const long long Ki = a.K[i];
+      if (threadIdx.x == 0) s_ncand = 0;
+      // 1. this part's entries: best candidate, weight to d; then clear them
+      bool have = false;
+      i128 best = 0;
+      uint32_t bc = 0;
+      uint32_t ncand = giant_scan_entries(a, gd, t, part * kGiantPart, min(nd, (part + 1) * kGiantPart), d, m2,
+                                          Ki, have, best, bc);
+      for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+      __syncthreads();  // s_ncand reset seen
+      if (lane == 0 && ncand) atomicAdd(&s_ncand, ncand);
+      block_argmax(have, best, bc);
+      __threadfence();  // hd[t] (from whichever thread met d) ...
+      __syncthreads();  // ... before thread 0's done count
+      if (threadIdx.x == 0) {
+        GiantRes r;
+        r.lo = (unsigned long long)(u128)best;
+        r.hi = (unsigned long long)((u128)best >> 64);
+        r.c = bc;
+        r.have = have ? 1u : 0u;
+        gd.res[ridx + part] = r;
+        sums.bytes += 12ull * s_ncand;
+        __threadfence();
+        s_last = atomicAdd(&gd.done[t], 1u) == nparts - 1;
+      }
+      __syncthreads();
+      if (s_last) {
+        // 2. last part block of the vertex: reduce the parts and decide
+        __threadfence();
+        have = false;
+        best = 0;
+        bc = 0;
+        for (uint32_t k = threadIdx.x; k < nparts; k += kGiantThreads) {
+          const GiantRes* src = gd.res + ridx + k;
+          const unsigned long long rlo = __ldcg(&src->lo), rhi = __ldcg(&src->hi);
+          const uint32_t rc = __ldcg(&src->c), rh = __ldcg(&src->have);
+          const i128 sc = (i128)(((u128)rhi << 64) | (u128)rlo);
+          if (rh && (!have || sc > best || (sc == best && rc < bc))) {
+            have = true;
+            best = sc;
+            bc = rc;
+          }
+        }
+        block_argmax(have, best, bc);
+        if (threadIdx.x == 0) {
+          const unsigned long long Hd = __ldcg(gd.hd + t);
+          gd.hd[t] = 0;  // zero at rest for the next use of this list position
+          gd.done[t] = 0;
+          const uint32_t dg = a.g.deg[i];
+          i128 gain = 0;
+          const bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
+          sums.bytes += 24 + 12ull * dg;
+          if (mv) {
+            record_move(a, i, bc, d, gain, gi, sums);
+            a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;  // neighbours marked by k_commit
+            sums.bytes += 16 + 4ull * dg;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    ibase += tile_items;
+    __syncthreads();  // s_ipre is rewritten for the next tile
+  }
+  flush_sums(a, sums, threadIdx.x == 0);
+}
+
+// Apply the moves of one sub-step, then mark the next frontier around the
+// listed high-degree movers: their arcs in kMarkChunk pieces spread over the
+// blocks (each block walks the short mover list to find its pieces).
+__global__ void __launch_bounds__(256) k_commit(DecideArgs a) {
+  const uint32_t m = a.ctrl->movers;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && m) atomicAdd(&a.ctrl->moved, (unsigned long long)m);
+  uint32_t* C = const_cast<uint32_t*>(a.C);
+  long long* Sigma = const_cast<long long*>(a.Sigma);
+  int* size = const_cast<int*>(a.size);
+  // warp-uniform loop; movers of one warp joining (or leaving) the same
+  // community are summed first, so a popular community takes one update
+  // per warp instead of one per mover
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); t0 < m; t0 += stride) {
+    const uint64_t t = t0 + (threadIdx.x & 31u);
+    const bool ok = t < m;
+    const uint32_t i = ok ? a.mv_i[t] : 0u;
+    const uint32_t c = ok ? a.mv_c[t] : kEmpty, d = ok ? a.mv_d[t] : kEmpty;
+    const long long ki = ok ? a.K[i] : 0;
+    if (ok) C[i] = c;
+    for (int side = 0; side < 2; ++side) {
+      const uint32_t key = side ? d : c;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+      long long sk = 0;
+      int cnt = 0;
+      // sum over the peers (a few shuffles per distinct community)
+      for (unsigned rest = peers; rest; rest &= rest - 1) {
+        const int src = __ffs(rest) - 1;
+        sk += __shfl_sync(peers, ki, src);
+        ++cnt;
+      }
+      if (ok && (threadIdx.x & 31u) == uint32_t(__ffs(peers) - 1)) {
+        atomicAdd((unsigned long long*)&Sigma[key], (unsigned long long)(side ? -sk : sk));
+        atomicAdd(&size[key], side ? -cnt : cnt);
+      }
+    }
+  }
+  const uint32_t count = a.ctrl->big_movers;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  uint64_t item0 = 0;
+  for (uint32_t q = 0; q < count; ++q) {
+    const uint32_t i = a.bigmv[q];
+    const uint32_t dg = a.g.deg[i];
+    const unsigned long long o = a.g.off[i];
+    const uint64_t nch = (dg + kMarkChunk - 1) / kMarkChunk;
+    // piece c of this mover is item item0 + c, handled by block (item0 + c) mod grid
+    uint64_t c = (blockIdx.x + gridDim.x - item0 % gridDim.x) % gridDim.x;
+    for (; c < nch; c += gridDim.x) {
+      const uint32_t k1 = min(dg, uint32_t((c + 1) * kMarkChunk));
+      for (uint32_t k0 = uint32_t(c * kMarkChunk) + wib * 32; k0 < k1; k0 += blockDim.x) {
+        const uint32_t k = k0 + lane;
+        uint2 arc = k < k1 ? a.g.arcs[o + k] : make_uint2(i, 0u);
+        mark_next(a, arc.x, k < k1 && arc.x != i && arc.y != 0);
+      }
+    }
+    item0 += nch;
   }
 }
 
@@ -756,7 +1082,9 @@ uint32_t next_pow2(uint64_t x) {
 
 __global__ void k_set_m2(Ctrl* ctrl, long long m2) { ctrl->m2v = m2; }
 
-constexpr uint32_t kGiantBlocks = 2 * 152;
+// largest grid of the block-per-vertex kernel; each of its blocks owns one
+// slice of the global overflow table
+constexpr uint32_t kBlockGridMax = 3 * 152;
 
 // Issue one local-moving iteration (all sub-steps) on h->stream.  With
 // `counts` (host-known list lengths) empty bins are skipped and grids are
@@ -768,7 +1096,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   const int nxt = cur ^ 1;
   // reset the iteration's sums and the next buffer's list lengths
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));  // + big_movers
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
   if (a.ngraphs)
     DFL_CUDA(h, cudaMemsetAsync(a.gS, 0, sizeof(unsigned long long) * 2 * a.ngraphs, h->stream));
@@ -787,7 +1115,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       cudaEventCreate(&pb);
       record_timing_event(pa, h->stream);
     }
-    const bool forked = nb > 1;
+    const bool forked = nb > 1 && !(h->opt.flags & DFL_FLAG_SERIAL_BINS);
     if (forked) DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
     bool joined[kBins - 1] = {false, false, false};
     for (int b = kBins - 1; b >= 0; --b) {
@@ -803,13 +1131,20 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       a.count = &h->ctrl->count[cur][s][b];
       LaunchScope ls(h, DFL_PROF_BIN0 + b, st);
       if (b == 0) {
-        k_decide_warp<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 64) : 152 * 8, 256, 0, st>>>(a);
+        // W lanes per vertex, W = the bin's degree limit rounded up to a power of two
+        const uint32_t lim = h->tune.bin_warp;
+        const uint32_t segs = lim <= 4 ? 8 : lim <= 8 ? 4 : lim <= 16 ? 2 : 1;
+        const uint32_t grid = counts ? grid_for((uint64_t(c) + segs - 1) / segs * 32, 256, 152 * 64) : 152 * 8;
+        if (segs == 8) k_decide_warp<4><<<grid, 256, 0, st>>>(a);
+        else if (segs == 4) k_decide_warp<8><<<grid, 256, 0, st>>>(a);
+        else if (segs == 2) k_decide_warp<16><<<grid, 256, 0, st>>>(a);
+        else k_decide_warp<32><<<grid, 256, 0, st>>>(a);
       } else if (b == 1) {
         k_decide_warp_hash<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 16) : 152 * 4, 256, 0, st>>>(a);
       } else if (b == 2) {
         const size_t smem = sizeof(uint32_t) * 2 * kBlockSlots;
         const uint32_t bt = h->tune.block_threads;
-        const uint32_t per_sm = bt == 128 ? 3 : bt == 256 ? 3 : 2;  // 64 KB table each
+        const uint32_t per_sm = bt == 512 ? 2 : 3;  // 64 KB table each; grid <= kBlockGridMax
         const uint32_t grid = counts ? grid_for(c, 1, 152 * per_sm) : 152 * per_sm;
         if (bt == 128) k_decide_block<128><<<grid, 128, smem, st>>>(a);
         else if (bt == 512) k_decide_block<512><<<grid, 512, smem, st>>>(a);
@@ -819,7 +1154,9 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
         gd.nitems = &h->ctrl->giant_chunks[cur];
         k_giant_prefix<<<1, 1024, 0, st>>>(a, gd);
         DFL_TRY(check_launch(h, "giant prefix"));
-        k_decide_giant<<<kGiantBlocks, kGiantThreads, sizeof(uint32_t) * 2 * kGiantSlots, st>>>(a, gd);
+        k_giant_accum<<<152 * 8, kAccumThreads, 0, st>>>(a, gd);
+        DFL_TRY(check_launch(h, "giant accumulate"));
+        k_giant_decide<<<152 * 4, kGiantThreads, 0, st>>>(a, gd);
       }
       DFL_TRY(check_launch(h, "decide"));
     }
@@ -834,17 +1171,23 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       h->prof.launches[DFL_PROF_MOVE]++;
     }
     if (any && decide_only) {
-      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
     } else if (any) {
       {
         LaunchScope ls(h, DFL_PROF_COMMIT);
-        k_commit<<<152 * 2, 256, 0, h->stream>>>(h->mv_i, h->mv_c, h->mv_d, const_cast<uint32_t*>(a.C), a.K,
-                                                 const_cast<long long*>(a.Sigma), const_cast<int*>(a.size),
-                                                 h->ctrl);
+        k_commit<<<152 * 2, 256, 0, h->stream>>>(a);
         DFL_TRY(check_launch(h, "commit"));
       }
-      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
     }
+  }
+  // the next frontier's lists, from its bitmap
+  {
+    const uint32_t words = (a.g.nv + 31) / 32;
+    LaunchScope ls(h, DFL_PROF_MARK);
+    k_lists_bits<<<grid_for(words, 256, 152 * 8), 256, 0, h->stream>>>(
+        a.fbits_next, words, a.g.nv, a.g.deg, a.next_lists, a.seg, h->ctrl, nxt, k);
+    DFL_TRY(check_launch(h, "next frontier lists"));
   }
   // the processed frontier's bitmap becomes the next-next target
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
@@ -943,18 +1286,21 @@ namespace {
 int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gdo) {
   const uint32_t k = h->opt.substeps;
   make_segs(h, k);
-  // global tables for the largest bins: one slice of gslots keys + gslots
-  // values per block, gslots >= 2 * (max degree of the current graph)
-  const uint32_t gslots = next_pow2(2ull * (ma.max_deg > kBinBlock ? ma.max_deg : kBinBlock));
-  if (ma.max_deg > kBinBlock && uint64_t(kGiantBlocks) * gslots > h->gtable_cap) {
+  // overflow tables of the block-per-vertex kernel, needed only when its bin
+  // takes degrees beyond what its shared table always holds: one slice of
+  // gslots keys + gslots values per block, gslots >= 2 * (largest degree it takes)
+  const uint32_t blk_max = ma.max_deg < h->tune.bin_block ? ma.max_deg : h->tune.bin_block;
+  const bool need_gtable = blk_max > kBinBlock;
+  const uint32_t gslots = next_pow2(2ull * (need_gtable ? blk_max : kBinBlock));
+  if (need_gtable && uint64_t(kBlockGridMax) * gslots > h->gtable_cap) {
     if (h->gtable) {
       cudaStreamSynchronize(h->stream);
       cudaFree(h->gtable);
       h->gtable = nullptr;
       h->gtable_cap = 0;
     }
-    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(kGiantBlocks) * gslots));
-    h->gtable_cap = uint64_t(kGiantBlocks) * gslots;
+    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(kBlockGridMax) * gslots));
+    h->gtable_cap = uint64_t(kBlockGridMax) * gslots;
   }
   // once per process (handles may be driven from several host threads)
   static std::once_flag smem_once;
@@ -966,49 +1312,79 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       smem_rc = cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
     if (smem_rc == cudaSuccess)
       smem_rc = cudaFuncSetAttribute(k_decide_block<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
-    if (smem_rc == cudaSuccess)
-      smem_rc = cudaFuncSetAttribute(k_decide_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(uint32_t) * 2 * kGiantSlots));
+
   });
   DFL_CUDA(h, smem_rc);
-  // chunked bin-3 buffers: per list item offsets/counters (sized by the
-  // largest bin-3 list: at most arcs / (bin_block + 1) vertices) and partial sums
+  // bin-3 buffers, sized by bounds: at most arcs / (bin_block + 1) listed
+  // vertices; tables of at most 4 x degree (>= 64) slots each; occupied
+  // lists of at most degree entries; at most arcs / kGiantPart + items parts
   {
-    uint64_t items = h->pool_top / (uint64_t(h->tune.bin_block) + 1) + 64;
-    uint64_t parts = h->pool_top + 64;
-    for (int q = 0; q < 2; ++q) parts = parts > h->sg[q].arc_cap ? parts : h->sg[q].arc_cap;
+    uint64_t arcs = h->num_arcs;
+    for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
+    const uint64_t items = arcs / (uint64_t(h->tune.bin_block) + 1) + 64;
+    const bool any = ma.max_deg > h->tune.bin_block;
+    const uint64_t tab = any ? 4 * arcs + 64 * items : 0;
+    const uint64_t lst = any ? arcs + 64 : 0;
+    const uint64_t res = any ? arcs / kGiantPart + items : 0;
+    auto regrow = [&](auto** p, uint64_t& cap, uint64_t need, size_t elem, int fill) -> int {
+      if (need <= cap) return DFL_OK;
+      cudaStreamSynchronize(h->stream);
+      cudaFree(*p);
+      *p = nullptr;
+      cap = 0;
+      const uint64_t want = need + need / 4;
+      DFL_CUDA(h, cudaMalloc(p, elem * want));
+      if (fill >= 0) DFL_CUDA(h, cudaMemsetAsync(*p, fill, elem * want, h->stream));
+      cap = want;
+      return DFL_OK;
+    };
     if (items > h->g_items_cap) {
-      cudaStreamSynchronize(h->stream);
-      cudaFree(h->g_poff);
-      cudaFree(h->g_cpre);
-      cudaFree(h->g_done);
-      cudaFree(h->g_pcount);
-      h->g_poff = nullptr;
-      h->g_cpre = h->g_done = h->g_pcount = nullptr;
-      h->g_items_cap = 0;
-      uint64_t want = items + items / 2;
-      DFL_CUDA(h, cudaMalloc(&h->g_poff, sizeof(unsigned long long) * want));
-      DFL_CUDA(h, cudaMalloc(&h->g_cpre, sizeof(uint32_t) * (want + 1)));
-      DFL_CUDA(h, cudaMalloc(&h->g_done, sizeof(uint32_t) * want));
-      DFL_CUDA(h, cudaMalloc(&h->g_pcount, sizeof(uint32_t) * want));
-      DFL_CUDA(h, cudaMemsetAsync(h->g_done, 0, sizeof(uint32_t) * want, h->stream));
-      DFL_CUDA(h, cudaMemsetAsync(h->g_pcount, 0, sizeof(uint32_t) * want, h->stream));
-      h->g_items_cap = want;
+      uint64_t c0 = h->g_items_cap, c1 = c0, c2 = c0, c3 = c0, c4 = c0, c5 = c0;
+      DFL_TRY(regrow(&h->g_toff, c0, items, sizeof(unsigned long long), -1));
+      DFL_TRY(regrow(&h->g_loff, c1, items, sizeof(unsigned long long), -1));
+      DFL_TRY(regrow(&h->g_cpre, c2, items + 1, sizeof(uint32_t), -1));
+      DFL_TRY(regrow(&h->g_ndist, c3, items, sizeof(uint32_t), 0));
+      DFL_TRY(regrow(&h->g_done, c4, items, sizeof(uint32_t), 0));
+      DFL_TRY(regrow(&h->g_hd, c5, items, sizeof(unsigned long long), 0));
+      h->g_items_cap = c0 < c2 ? c0 : c2 - 1;
     }
-    if (ma.max_deg > h->tune.bin_block && parts > h->g_partial_cap) {
+    {
+      uint64_t c = h->g_res_cap;
+      GiantRes* r = static_cast<GiantRes*>(h->g_res);
+      DFL_TRY(regrow(&r, c, res, sizeof(GiantRes), -1));
+      h->g_res = r;
+      h->g_res_cap = c;
+    }
+    if (tab > h->g_tab_cap) {
+      uint64_t c0 = h->g_tab_cap, c1 = c0;
+      DFL_TRY(regrow(&h->g_tkeys, c0, tab, sizeof(uint32_t), 0xFF));  // kEmpty
+      DFL_TRY(regrow(&h->g_tvals, c1, tab, sizeof(uint32_t), 0));
+      h->g_tab_cap = c0;
+    }
+    DFL_TRY(regrow(&h->g_tlist, h->g_lst_cap, lst, sizeof(uint32_t), -1));
+  }
+  {  // list of high-degree movers: at most one per vertex of degree > kMarkInline
+    uint64_t arcs = h->pool_top;
+    for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
+    const uint64_t need = arcs / (kMarkInline + 1) + 64;
+    if (need > h->bigmv_cap) {
       cudaStreamSynchronize(h->stream);
-      cudaFree(h->g_partial);
-      h->g_partial = nullptr;
-      h->g_partial_cap = 0;
-      uint64_t want = parts + parts / 4;
-      DFL_CUDA(h, cudaMalloc(&h->g_partial, sizeof(uint2) * want));
-      h->g_partial_cap = want;
+      cudaFree(h->bigmv);
+      h->bigmv = nullptr;
+      h->bigmv_cap = 0;
+      DFL_CUDA(h, cudaMalloc(&h->bigmv, sizeof(uint32_t) * (need + need / 2)));
+      h->bigmv_cap = need + need / 2;
     }
   }
   if (!h->ev_fork) {
     DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    // the largest degrees make the longest chains of a sub-step: their
+    // stream gets the highest priority, the block-per-vertex bin the next
+    int least = 0, greatest = 0;
+    DFL_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     for (int b = 0; b < kBins - 1; ++b) {
-      DFL_CUDA(h, cudaStreamCreateWithFlags(&h->aux[b], cudaStreamNonBlocking));
+      int prio = b == kBins - 2 ? greatest : b == kBins - 3 ? (greatest < least ? greatest + 1 : least) : least;
+      DFL_CUDA(h, cudaStreamCreateWithPriority(&h->aux[b], cudaStreamNonBlocking, prio));
       DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
     }
   }
@@ -1035,8 +1411,9 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
   a.mv_d = h->mv_d;
   a.ctrl = h->ctrl;
   a.k = k;
-  a.gtable = h->gtable;
+  a.gtable = need_gtable ? h->gtable : nullptr;
   a.gslots = gslots;
+  a.bigmv = h->bigmv;
   if (h->ngraphs) {
     a.ngraphs = h->ngraphs;
     a.goff = h->d_goff;
@@ -1044,7 +1421,8 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
     a.gdone = h->d_gdone;
     a.gS = h->d_gS;
   }
-  *gdo = GiantDecide{h->g_poff, h->g_cpre, h->g_done, h->g_pcount, h->g_partial, nullptr};
+  *gdo = GiantDecide{h->g_toff, h->g_loff, h->g_cpre, h->g_ndist, h->g_done, h->g_hd,
+                     static_cast<GiantRes*>(h->g_res), h->g_tkeys, h->g_tvals, h->g_tlist, nullptr};
   return DFL_OK;
 }
 

@@ -63,6 +63,8 @@ TUNINGS = [
     dict(bin_warp=0, bin_warp_hash=0, bin_block=0, block_threads=256),      # all chunked
     dict(bin_warp=0, bin_warp_hash=256, bin_block=256, block_threads=128),  # warp tables only
     dict(bin_warp=32, bin_warp_hash=32, bin_block=32, block_threads=512),
+    dict(bin_warp=4, bin_warp_hash=256, bin_block=4096, block_threads=256),  # 8 vertices a warp
+    dict(bin_warp=5, bin_warp_hash=40, bin_block=2048, block_threads=256),   # 4 a warp, odd limits
 ]
 
 
@@ -115,7 +117,7 @@ def test_autotune_keeps_state_and_results(dfl, orc, mode):
         C0 = a.membership()
         K0, S0, m0 = a.weights()
         tuning, ms = a.autotune(mode, reps=2)
-        assert ms > 0 and set(tuning) == set(TUNINGS[0])
+        assert ms > 0 and set(tuning) == set(TUNINGS[0])  # the same fields
         assert a.tuning() == tuning
         # the autotuner computed decisions but applied none of them
         K1, S1, m1 = a.weights()
