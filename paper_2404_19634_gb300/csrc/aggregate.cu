@@ -96,8 +96,8 @@ __device__ __forceinline__ bool agg_add(uint32_t* keys, uint32_t* vals, uint32_t
   return false;
 }
 
-// Warp-collective: add arcs [0, d) of one vertex (32 per step) to the table,
-// pre-aggregated per neighbour community; deleted arcs (weight 0) skipped.
+// Add arcs [0, d) of one vertex (warp-strided, two loads in flight per lane)
+// to the table by neighbour community; deleted arcs (weight 0) skipped.
 // Entries that do not fit are added to the fallback table if one is given.
 __device__ __forceinline__ bool agg_row(const AggArgs& a, unsigned long long o, uint32_t d,
                                         uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t limit,
@@ -113,13 +113,9 @@ __device__ __forceinline__ bool agg_row(const AggArgs& a, unsigned long long o, 
     for (int u = 0; u < 2; ++u) {
       uint32_t c = u ? c1 : c0;
       uint32_t w = u ? arc1.y : arc0.y;
-      unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
-      uint32_t hs = __reduce_add_sync(peers, c != kEmpty ? w : 0u);
-      if (c != kEmpty && lane == uint32_t(__ffs(peers) - 1)) {
-        if (!agg_add(keys, vals, mask, c, hs, limit)) {
-          if (fkeys) ok &= agg_add(fkeys, fvals, fmask, c, hs, fmask + 1);
-          else ok = false;
-        }
+      if (c != kEmpty && !agg_add(keys, vals, mask, c, w, limit)) {
+        if (fkeys) ok &= agg_add(fkeys, fvals, fmask, c, w, fmask + 1);
+        else ok = false;
       }
     }
   }

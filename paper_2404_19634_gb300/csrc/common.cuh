@@ -32,7 +32,8 @@ typedef unsigned __int128 u128;
 // ---------------------------------------------------------------------------
 constexpr int kWarp = 32;
 constexpr int kBins = 4;            // degree bins of the local-moving kernels
-constexpr uint32_t kBinWarp = 32;   // deg <= 32: one warp, registers only
+constexpr uint32_t kBinWarp = 32;   // deg <= 32: registers only (largest bin-0 limit)
+constexpr uint32_t kBinWarpDefault = 8;  // default bin-0 limit: 8 lanes per vertex, 4 vertices a warp
 constexpr uint32_t kBinWarpHash = 256;   // deg <= 256: one warp, shared-memory table
 constexpr uint32_t kBinBlock = 4096;     // deg <= 4096: one block, shared-memory table
                                           // larger: one block, global-memory table
@@ -285,7 +286,7 @@ struct Handle {
   dfl_profile_t prof;
 
   // launch-shape tuning of local-moving (never changes results)
-  dfl_tuning tune{kBinWarp, kBinWarpHash, kBinBlock, 256};
+  dfl_tuning tune{kBinWarpDefault, kBinWarpHash, kBinBlock, 256};
 
   // group: ngraphs > 0 independent graphs held as one disjoint union
   uint32_t ngraphs = 0;
@@ -407,23 +408,27 @@ __device__ __forceinline__ bool bit_set(uint32_t* bits, uint32_t i) {
 }
 
 // Append vertex v (if valid) to frontier list `key` = class * kBins + bin of
-// buffer `buf`; one atomic per distinct key in the warp.  Every lane of the
-// warp must call this (with valid = false where it has nothing).
+// buffer `buf`; one atomic per distinct key in the warp (the distinct keys
+// are visited one by one with ballots).  Every lane of the warp must call it.
 __device__ __forceinline__ void append_vertex(uint32_t v, bool valid, uint32_t key,
                                               uint32_t* lists, const Segs& seg, Ctrl* ctrl,
                                               int buf) {
-  unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
-  if (!act) return;
-  unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu);
-  if (!valid) return;
   const unsigned lane = threadIdx.x & 31u;
-  unsigned leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&ctrl->count[buf][key / kBins][key % kBins], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  uint32_t r = base + __popc(peers & ((1u << lane) - 1u));
-  if (r < seg.cap[key]) lists[seg.off[key] + r] = v;
-  else atomicOr(&ctrl->err, kErrInternal);
+  unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
+  while (act) {
+    const unsigned leader = __ffs(act) - 1;
+    const uint32_t kl = __shfl_sync(0xFFFFFFFFu, key, leader);
+    const unsigned grp = __ballot_sync(0xFFFFFFFFu, valid && key == kl);
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&ctrl->count[buf][kl / kBins][kl % kBins], __popc(grp));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if ((grp >> lane) & 1u) {
+      const uint32_t r = base + __popc(grp & ((1u << lane) - 1u));
+      if (r < seg.cap[kl]) lists[seg.off[kl] + r] = v;
+      else atomicOr(&ctrl->err, kErrInternal);
+    }
+    act &= ~grp;
+  }
 }
 
 // ---------------------------------------------------------------------------

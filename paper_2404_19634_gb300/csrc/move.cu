@@ -179,10 +179,22 @@ __device__ __forceinline__ bool decide_segment(const DecideArgs& a, bool active,
   uint2 arc = sl < dg ? a.g.arcs[o + sl] : make_uint2(i, 0u);
   const bool valid = sl < dg && arc.x != i && arc.y != 0;  // weight 0 = deleted arc
   const uint32_t c = valid ? a.C[arc.x] : kEmpty;
-  // group equal communities of one segment (the segment number in the key)
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, ((unsigned long long)seg << 32) | c);
-  const uint32_t hsum = __reduce_add_sync(peers, valid ? arc.y : 0u);
-  const bool leader = valid && lane == uint32_t(__ffs(peers) - 1);
+  // weight of this lane's community within the segment, and whether this is
+  // the community's first lane: W shuffles and compares (cheaper here than
+  // match/reduce over many groups)
+  uint32_t hsum = 0;
+  bool leader = valid;
+  const uint32_t wv = valid ? arc.y : 0u;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const uint32_t src = seg * W + k;
+    const uint32_t ck = __shfl_sync(0xFFFFFFFFu, c, src);
+    const uint32_t wk = __shfl_sync(0xFFFFFFFFu, wv, src);
+    if (valid && ck == c) {
+      hsum += wk;
+      if (uint32_t(k) < sl) leader = false;
+    }
+  }
   const unsigned dm = __ballot_sync(0xFFFFFFFFu, leader && c == d) & segmask;
   // every lane shuffles (from its segment's holder of d, or from itself)
   const uint32_t hd_src = dm ? uint32_t(__ffs(dm) - 1) : lane;
@@ -252,9 +264,10 @@ __device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32
 }
 
 // scanCommunities over arcs [k0, dg) of row o, lanes striding by `step`:
-// each 32-arc chunk is pre-aggregated per community inside the warp
-// (match + reduce), so only one table update per distinct community and
-// chunk is issued.  Loads of kUnroll chunks are issued before use.
+// every lane adds its arc's weight under its neighbour's community (shared
+// memory atomics; grouping equal communities inside the warp first with
+// match/reduce was measured slower on this GPU when a warp holds many
+// communities).  Loads of kUnroll chunks are issued before use.
 template <int kUnroll>
 __device__ __forceinline__ bool scan_row(const DecideArgs& a, uint32_t i, unsigned long long o,
                                          uint32_t dg, uint32_t k0, uint32_t step, uint32_t* keys,
@@ -275,12 +288,8 @@ __device__ __forceinline__ bool scan_row(const DecideArgs& a, uint32_t i, unsign
       c[u] = valid ? a.C[arc[u].x] : kEmpty;
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      unsigned peers = __match_any_sync(0xFFFFFFFFu, c[u]);
-      uint32_t hs = __reduce_add_sync(peers, c[u] != kEmpty ? arc[u].y : 0u);
-      if (c[u] != kEmpty && lane == uint32_t(__ffs(peers) - 1))
-        ok &= table_add(keys, vals, mask, c[u], hs, limit);
-    }
+    for (int u = 0; u < kUnroll; ++u)
+      if (c[u] != kEmpty) ok &= table_add(keys, vals, mask, c[u], arc[u].y, limit);
   }
   return ok;
 }
@@ -1014,18 +1023,23 @@ __global__ void __launch_bounds__(256) k_commit(DecideArgs a) {
     const uint32_t c = ok ? a.mv_c[t] : kEmpty, d = ok ? a.mv_d[t] : kEmpty;
     const long long ki = ok ? a.K[i] : 0;
     if (ok) C[i] = c;
+    const uint32_t lane = threadIdx.x & 31u;
     for (int side = 0; side < 2; ++side) {
       const uint32_t key = side ? d : c;
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
       long long sk = 0;
       int cnt = 0;
-      // sum over the peers (a few shuffles per distinct community)
-      for (unsigned rest = peers; rest; rest &= rest - 1) {
-        const int src = __ffs(rest) - 1;
-        sk += __shfl_sync(peers, ki, src);
-        ++cnt;
+      bool first = ok;
+      // sum over the lanes with the same community (32 shuffles)
+      for (int k = 0; k < 32; ++k) {
+        const uint32_t kk = __shfl_sync(0xFFFFFFFFu, key, k);
+        const long long kv = __shfl_sync(0xFFFFFFFFu, ki, k);
+        if (ok && kk == key) {
+          sk += kv;
+          ++cnt;
+          if (uint32_t(k) < lane) first = false;
+        }
       }
-      if (ok && (threadIdx.x & 31u) == uint32_t(__ffs(peers) - 1)) {
+      if (first) {
         atomicAdd((unsigned long long*)&Sigma[key], (unsigned long long)(side ? -sk : sk));
         atomicAdd(&size[key], side ? -cnt : cnt);
       }

@@ -249,20 +249,38 @@ __global__ void k_copy_i64(long long* d, const long long* s, uint64_t n) {
 // ---------------------------------------------------------------------------
 // Frontier lists
 // ---------------------------------------------------------------------------
-__global__ void k_lists_all(uint32_t nv, const uint32_t* __restrict__ deg, uint32_t* lists,
-                            Segs seg, Ctrl* ctrl, int buf, uint32_t k) {
-  uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x); i0 < nv; i0 += stride) {
-    uint64_t i = i0 + threadIdx.x;
+__global__ void __launch_bounds__(256) k_lists_all(uint32_t nv, const uint32_t* __restrict__ deg, uint32_t* lists,
+                                                   Segs seg, Ctrl* ctrl, int buf, uint32_t k) {
+  // every vertex with arcs, thread per vertex, counted per list key in shared
+  // memory and reserved once per block and key
+  __shared__ uint32_t s_cnt[kMaxSubsteps * kBins];
+  __shared__ uint32_t s_base[kMaxSubsteps * kBins];
+  const uint32_t nkeys = k * kBins;
+  for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x); i0 < nv; i0 += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
     // a vertex without arcs has no neighbour community: it is processed
     // (counted) but never queued
-    uint32_t d = i < nv ? deg[i] : 0u;
-    bool valid = i < nv && d > 0;
-    unsigned idle = __ballot_sync(0xFFFFFFFFu, i < nv && d == 0);
+    const uint32_t d = i < nv ? deg[i] : 0u;
+    const bool valid = i < nv && d > 0;
+    const unsigned idle = __ballot_sync(0xFFFFFFFFu, i < nv && d == 0);
     if ((threadIdx.x & 31u) == 0 && idle) atomicAdd(&ctrl->skipped, (unsigned long long)__popc(idle));
-    uint32_t key = 0;
-    if (valid) key = vertex_class(uint32_t(i), k, seg) * kBins + degree_bin(d, seg);
-    append_vertex(uint32_t(i), valid, key, lists, seg, ctrl, buf);
+    const uint32_t key = valid ? vertex_class(uint32_t(i), k, seg) * kBins + degree_bin(d, seg) : 0u;
+    if (threadIdx.x < nkeys) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    if (valid) atomicAdd(&s_cnt[key], 1u);
+    __syncthreads();
+    if (threadIdx.x < nkeys) {
+      const uint32_t c = s_cnt[threadIdx.x];
+      s_base[threadIdx.x] = c ? atomicAdd(&ctrl->count[buf][threadIdx.x / kBins][threadIdx.x % kBins], c) : 0u;
+      s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t r = s_base[key] + atomicAdd(&s_cnt[key], 1u);
+      if (r < seg.cap[key]) lists[seg.off[key] + r] = uint32_t(i);
+      else atomicOr(&ctrl->err, kErrInternal);
+    }
+    __syncthreads();
   }
 }
 
@@ -465,7 +483,7 @@ int lists_all(Handle* h, uint32_t nv, const uint32_t* deg, int buf, uint32_t k) 
   make_segs(h, k);
   const Segs& seg = h->segs;
   LaunchScope ls(h, DFL_PROF_MARK);
-  k_lists_all<<<grid_for(nv, 256), 256, 0, h->stream>>>(nv, deg, h->lists[buf], seg, h->ctrl, buf,
+  k_lists_all<<<grid_for(nv, 256, 152 * 8), 256, 0, h->stream>>>(nv, deg, h->lists[buf], seg, h->ctrl, buf,
                                                         k);
   return check_launch(h, "lists_all");
 }
