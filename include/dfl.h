@@ -245,15 +245,20 @@ int dfl_aggregate(dfl_handle* h, uint32_t* nv, uint64_t* na, uint64_t* offsets,
 /* Launch-shape choices of the local-moving step.  They change which kernel
  * decides a vertex and where its community table lives, never the result:
  * any valid tuning gives the same membership, K, Sigma and modularity.
- *   degree <= bin_warp:       one warp, table in registers (match/reduce)
- *   degree <= bin_warp_hash:  one warp, open-addressing table in shared memory
+ *   degree <= bin_warp:       W = bin_warp rounded up to a power of two (>= 4)
+ *                             lanes per vertex, 32/W vertices per warp,
+ *                             communities grouped in registers
+ *   degree <= bin_warp_hash:  one warp (registers up to 32 arcs, else an
+ *                             open-addressing table in shared memory)
  *   degree <= bin_block:      one block of block_threads, shared-memory table
  *                             (global-memory slice when it overflows)
- *   larger:                   split into 4096-arc chunks, one block each,
- *                             partial sums merged by the vertex's last block
+ *   larger:                   split into 1024-arc chunks, one block each,
+ *                             summed in a global table of the vertex; its
+ *                             last chunk block (or, for many distinct
+ *                             communities, a block per 2048 of them) decides
  * Valid ranges: bin_warp <= 32, bin_warp <= bin_warp_hash <= 256,
  * bin_warp_hash <= bin_block, block_threads in {128, 256, 512}.
- * Defaults: 32, 256, 4096, 256. */
+ * Defaults: 8, 256, 4096, 256. */
 typedef struct {
   uint32_t bin_warp;
   uint32_t bin_warp_hash;

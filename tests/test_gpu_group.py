@@ -56,6 +56,7 @@ def same(a, b):
     assert sa["passes"] == sb["passes"] and sa["iterations"] == sb["iterations"]
 
 
+DEFAULT_TUNING = dict(bin_warp=8, bin_warp_hash=256, bin_block=4096, block_threads=256)
 TUNINGS = [
     dict(bin_warp=32, bin_warp_hash=256, bin_block=4096, block_threads=256),
     dict(bin_warp=8, bin_warp_hash=64, bin_block=1024, block_threads=128),
@@ -99,7 +100,7 @@ def test_tuning_rejects_out_of_range(dfl):
         with pytest.raises(dfl.DflError) as e:
             a.set_tuning(**bad)
         assert e.value.code == -1
-    assert a.tuning() == TUNINGS[0]
+    assert a.tuning() == DEFAULT_TUNING
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
