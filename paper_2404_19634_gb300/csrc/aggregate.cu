@@ -79,6 +79,8 @@ struct AggArgs {
   Ctrl* ctrl;
   uint2* gtable;
   uint32_t gslots;
+  uint2* bigq;              // giant-community members of high degree: (member, giant index)
+  unsigned int* nbig;       // their count
 };
 
 __device__ __forceinline__ bool agg_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
@@ -126,6 +128,8 @@ constexpr uint32_t kAggWarpSlots = 512;
 constexpr int kAggWarps = 8;
 constexpr uint32_t kAggBlockSlots = 2 * kBinBlock;  // 8192 keys + values = 64 KB
 constexpr uint32_t kChunkMembers = 256;             // members per block of a giant community
+constexpr uint32_t kAggBigMember = 512;             // larger member rows go to k_agg_big ...
+constexpr uint32_t kAggPiece = 2048;                // ... in pieces of this many arcs
 constexpr uint32_t kGiantSlots = 4096;              // shared table of a giant-community block
 
 // Write the table's entries as the row of super-vertex c (ballot order).
@@ -295,8 +299,13 @@ __global__ void __launch_bounds__(256) k_agg_giant_accum(AggArgs a, GiantArgs gi
     }
     __syncthreads();
     for (uint32_t m = uint32_t(m0) + wib; m < m1; m += nw) {
-      uint32_t v = a.members[m];
-      ok &= agg_row(a, a.g.off[v], a.g.deg[v], keys, vals, kGiantSlots - 1, 32, gkeys, gvals, gs - 1);
+      const uint32_t v = a.members[m];
+      const uint32_t dv = a.g.deg[v];
+      if (dv > kAggBigMember) {  // spread over many blocks by k_agg_big
+        if ((threadIdx.x & 31u) == 0) a.bigq[atomicAdd(a.nbig, 1u)] = make_uint2(v, g);
+        continue;
+      }
+      ok &= agg_row(a, a.g.off[v], dv, keys, vals, kGiantSlots - 1, 32, gkeys, gvals, gs - 1);
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
@@ -304,6 +313,50 @@ __global__ void __launch_bounds__(256) k_agg_giant_accum(AggArgs a, GiantArgs gi
       if (k != kEmpty) ok &= agg_add(gkeys, gvals, gs - 1, k, vals[s], gs);
     }
     __syncthreads();
+  }
+  if (!ok) atomicOr(&a.ctrl->err, kErrInternal);
+}
+
+// The queued high-degree members of giant communities: their rows in pieces
+// of kAggPiece arcs dealt over the blocks (each block sweeps the short queue
+// to find its pieces); a piece is aggregated in shared memory and added to
+// the community's global table.
+__global__ void __launch_bounds__(256) k_agg_big(AggArgs a, GiantArgs gi) {
+  __shared__ uint32_t keys[kGiantSlots];
+  __shared__ uint32_t vals[kGiantSlots];
+  const uint32_t count = *a.nbig;
+  bool ok = true;
+  uint64_t item0 = 0;
+  for (uint32_t q = 0; q < count; ++q) {
+    const uint2 e = a.bigq[q];
+    const uint32_t v = e.x, g = e.y;
+    const uint32_t dv = a.g.deg[v];
+    const unsigned long long o = a.g.off[v];
+    const uint64_t npc = (dv + kAggPiece - 1) / kAggPiece;
+    const uint32_t gs = gi.gsize[g];
+    uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
+    uint32_t* gvals = gkeys + gs;
+    for (uint64_t pc = (blockIdx.x + gridDim.x - item0 % gridDim.x) % gridDim.x; pc < npc; pc += gridDim.x) {
+      const uint32_t k0 = uint32_t(pc * kAggPiece), k1 = min(dv, k0 + kAggPiece);
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+        keys[s] = kEmpty;
+        vals[s] = 0;
+      }
+      __syncthreads();
+      for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const uint2 arc = a.g.arcs[o + k];
+        if (!arc.y) continue;  // deleted arc
+        const uint32_t c = a.Cp[arc.x];
+        if (!agg_add(keys, vals, kGiantSlots - 1, c, arc.y, 32)) ok &= agg_add(gkeys, gvals, gs - 1, c, arc.y, gs);
+      }
+      __syncthreads();
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+        const uint32_t c = keys[s];
+        if (c != kEmpty) ok &= agg_add(gkeys, gvals, gs - 1, c, vals[s], gs);
+      }
+      __syncthreads();
+    }
+    item0 += npc;
   }
   if (!ok) atomicOr(&a.ctrl->err, kErrInternal);
 }
@@ -511,6 +564,22 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     DFL_CUDA(h, cudaMemcpyAsync(d_gsize, gsize.data(), sizeof(uint32_t) * ngiant, cudaMemcpyHostToDevice,
                                 h->stream));
     a.gtable = h->gtable;
+    {  // queue of high-degree members: at most one per vertex of degree > kAggBigMember
+      uint64_t arcs = h->num_arcs;
+      for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
+      const uint64_t need = arcs / (kAggBigMember + 1) + 64;
+      if (need > h->aggq_cap) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->aggq);
+        h->aggq = nullptr;
+        h->aggq_cap = 0;
+        DFL_CUDA(h, cudaMalloc(&h->aggq, sizeof(uint2) * need));
+        h->aggq_cap = need;
+      }
+    }
+    a.bigq = h->aggq;
+    a.nbig = &h->ctrl->red_u;
+    DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->red_u, 0, sizeof(unsigned int), h->stream));
     GiantArgs gi{d_giant, d_gtab, d_gsize, d_chunk0, ngiant, nitems};
     {
       LaunchScope ls(h, DFL_PROF_AGG);
@@ -521,6 +590,11 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
       LaunchScope ls(h, DFL_PROF_AGG);
       k_agg_giant_accum<<<grid_for(nitems, 1, 152 * 8), 256, 0, h->stream>>>(a, gi);
       DFL_TRY(check_launch(h, "giant accum"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_AGG);
+      k_agg_big<<<152 * 4, 256, 0, h->stream>>>(a, gi);
+      DFL_TRY(check_launch(h, "giant members"));
     }
     {
       LaunchScope ls(h, DFL_PROF_AGG);

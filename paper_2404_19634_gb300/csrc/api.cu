@@ -114,7 +114,8 @@ void free_all(Handle* h) {
                   h->h_rows, h->h_extra,
                   h->sg[0].off, h->sg[0].deg, h->sg[0].arcs, h->sg[1].off, h->sg[1].deg,
                   h->sg[1].arcs, h->d_goff0, h->d_goff, h->d_gnext, h->d_gm2, h->d_gdone,
-                  h->d_gflag, h->d_gS, h->d_gsum, h->Cfin, h->gb_edges, h->d_eoff, h->bigmv};
+                  h->d_gflag, h->d_gS, h->d_gsum, h->Cfin, h->gb_edges, h->d_eoff, h->bigmv,
+                  h->aggq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);

@@ -72,15 +72,44 @@ __global__ void k_expand(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t n
 // scan of the tail.  Returns kEmpty if absent.
 __device__ __forceinline__ uint32_t find_slot(const uint2* __restrict__ row, uint32_t srt, uint32_t deg,
                                               uint32_t v) {
+  // lower bound of v in the sorted prefix: nine-way splits with the eight
+  // probe loads in flight together (a hub row takes ~6 rounds, not ~20)
   uint32_t lo = 0, hi = srt;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (row[mid].x < v) lo = mid + 1;
-    else hi = mid;
+  while (hi - lo > 16) {
+    const uint32_t step = (hi - lo) / 9;
+    uint32_t key[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) key[j] = row[lo + (j + 1) * step].x;
+    uint32_t nlo = lo, nhi = hi;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t pos = lo + (j + 1) * step;
+      if (key[j] < v) nlo = pos + 1;
+      else if (pos < nhi) nhi = pos;
+    }
+    lo = nlo;
+    hi = nhi;
+  }
+  {
+    uint32_t key[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) key[j] = lo + j < hi ? row[lo + j].x : 0xFFFFFFFFu;
+    uint32_t lb = hi;
+#pragma unroll
+    for (int j = 15; j >= 0; --j)
+      if (lo + j < hi && key[j] >= v) lb = lo + j;
+    lo = lb;
   }
   if (lo < srt && row[lo].x == v) return lo;
-  for (uint32_t q = srt; q < deg; ++q)
-    if (row[q].x == v) return q;
+  // the unsorted tail (at most kTailMax arcs), eight loads in flight
+  for (uint32_t q0 = srt; q0 < deg; q0 += 8) {
+    uint32_t x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = q0 + u < deg ? row[q0 + u].x : ~v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (x[u] == v) return q0 + u;
+  }
   return kEmpty;
 }
 
@@ -878,14 +907,34 @@ __global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t*
 __global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
                                long long* __restrict__ Sigma, Ctrl* ctrl) {
   const uint32_t np = ctrl->npairs;
-  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
-       p += uint64_t(gridDim.x) * blockDim.x) {
-    const uint32_t s = t.pairs[p];
-    const long long dl = t.delta[s];
-    if (!dl) continue;
-    const uint32_t u = uint32_t(t.keys[s] >> 32);
-    atomicAdd((unsigned long long*)&K[u], (unsigned long long)dl);
-    atomicAdd((unsigned long long*)&Sigma[C[u]], (unsigned long long)dl);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  // warp-uniform loop: changes to one community's Sigma are summed in the
+  // warp first (a large community takes one update per warp, not per arc)
+  for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
+    const uint64_t p = p0 + lane;
+    long long dl = 0;
+    uint32_t c = kEmpty;
+    if (p < np) {
+      const uint32_t s = t.pairs[p];
+      dl = t.delta[s];
+      if (dl) {
+        const uint32_t u = uint32_t(t.keys[s] >> 32);
+        atomicAdd((unsigned long long*)&K[u], (unsigned long long)dl);
+        c = C[u];
+      }
+    }
+    long long sum = 0;
+    bool first = c != kEmpty;
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t ck = __shfl_sync(0xFFFFFFFFu, c, k);
+      const long long dk = __shfl_sync(0xFFFFFFFFu, dl, k);
+      if (c != kEmpty && ck == c) {
+        sum += dk;
+        if (uint32_t(k) < lane) first = false;
+      }
+    }
+    if (first && sum) atomicAdd((unsigned long long*)&Sigma[c], (unsigned long long)sum);
   }
 }
 

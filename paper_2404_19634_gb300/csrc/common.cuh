@@ -229,6 +229,8 @@ struct Handle {
   uint64_t gtable_cap = 0;
   uint32_t* bigmv = nullptr;       // high-degree movers of a sub-step (marked by k_mark_big)
   uint64_t bigmv_cap = 0;
+  uint2* aggq = nullptr;           // high-degree members of giant communities (aggregation)
+  uint64_t aggq_cap = 0;
   // decisions of the largest bin: per list position its table and list
   // offsets, chunk prefix, occupied-slot count, finished part blocks and
   // weight to the own community (the last two zero at rest); per part
