@@ -74,7 +74,7 @@ enum {
   DFL_ERR_OVERFLOW = -3,  /* an edge weight would exceed 2^32-1, or 2m would reach 2^32 */
   DFL_ERR_NOMEM = -4,     /* device or pinned host allocation failed */
   DFL_ERR_CUDA = -5,      /* a CUDA runtime call failed */
-  DFL_ERR_TIMEOUT = -6,   /* reserved for bounded device waits */
+  DFL_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (DFL_FLAG_PERSISTENT) */
   DFL_ERR_STATE = -7      /* call out of order, e.g. dfl_update before dfl_static */
 };
 
@@ -85,8 +85,12 @@ enum {
   DFL_FLAG_NO_GRAPH = 4u, /* launch every kernel from the host instead of replaying the captured
                              local-moving iteration (a CUDA graph, used on the first pass when the
                              handle's stream is not the legacy default stream) */
-  DFL_FLAG_SERIAL_BINS = 8u /* run the degree bins of a sub-step one after another on the handle's
-                               stream instead of concurrently (for measuring each bin alone) */
+  DFL_FLAG_SERIAL_BINS = 8u, /* run the degree bins of a sub-step one after another on the handle's
+                                stream instead of concurrently (for measuring each bin alone) */
+  DFL_FLAG_PERSISTENT = 16u   /* run each local-moving iteration as one cooperative launch whose
+                                 blocks meet at bounded grid barriers between sub-steps; a barrier
+                                 that waits about a second gives up and the call returns
+                                 DFL_ERR_TIMEOUT (the handle should then be destroyed) */
 };
 
 /* Algorithm options; defaults from Section 5.1.2 of the paper. */

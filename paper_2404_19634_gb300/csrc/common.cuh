@@ -46,6 +46,7 @@ enum : uint32_t {
   kErrNotFound = 2u,
   kErrOverflow = 4u,
   kErrInternal = 8u,  // a hash table overflowed or an index check failed
+  kErrTimeout = 16u,  // a bounded wait of the persistent iteration kernel gave up
 };
 
 // ---------------------------------------------------------------------------
@@ -74,6 +75,12 @@ struct Ctrl {
   unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
   unsigned long long ever_count;     // vertices newly added to the first-pass processed set
   unsigned int giant_chunks[2];      // chunk work items of the largest bin (per buffer parity)
+  // persistent iteration kernel: per sub-step parity, movers, listed
+  // high-degree movers, work units taken, vertices left to the part blocks;
+  // chunk items of each class; grid barrier
+  unsigned int it_movers[2], it_nbig[2], it_work[2], it_bignd[2];
+  unsigned int it_items[kMaxSubsteps];
+  unsigned int bar_count, bar_gen;
   long long m2v;                     // 2m of the current local-moving call
   unsigned int npairs;               // distinct (u, v) pairs of the batch (hashed apply)
   unsigned int max_app;              // most new arcs of one rebuilt row
@@ -430,6 +437,47 @@ __device__ __forceinline__ void append_vertex(uint32_t v, bool valid, uint32_t k
       else atomicOr(&ctrl->err, kErrInternal);
     }
     act &= ~grp;
+  }
+}
+
+// Frontier lists from a bitmap, one bitmap word per thread: a block counts
+// its vertices per list key in shared memory, reserves each key's range with
+// one global atomic, then writes (so a dense frontier does not funnel every
+// vertex through the few global list counters).
+__device__ __forceinline__ void lists_bits_body(const uint32_t* __restrict__ bits, uint32_t words,
+                                                uint32_t nv, const uint32_t* __restrict__ deg,
+                                                uint32_t* lists, const Segs& seg, Ctrl* ctrl, int buf,
+                                                uint32_t k) {
+  __shared__ uint32_t s_cnt[kMaxSubsteps * kBins];
+  __shared__ uint32_t s_base[kMaxSubsteps * kBins];
+  const uint32_t nkeys = k * kBins;
+  for (uint64_t w0 = blockIdx.x * uint64_t(blockDim.x); w0 < words; w0 += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t w = w0 + threadIdx.x;
+    const uint32_t word = w < words ? bits[w] : 0u;
+    if (!__syncthreads_or(word != 0u)) continue;  // block-uniform: no vertex in this tile
+    if (threadIdx.x < nkeys) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t x = word; x; x &= x - 1) {
+      const uint32_t v = uint32_t(w * 32 + __ffs(x) - 1);
+      if (v >= nv) break;
+      atomicAdd(&s_cnt[vertex_class(v, k, seg) * kBins + degree_bin(deg[v], seg)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < nkeys) {
+      const uint32_t c = s_cnt[threadIdx.x];
+      s_base[threadIdx.x] = c ? atomicAdd(&ctrl->count[buf][threadIdx.x / kBins][threadIdx.x % kBins], c) : 0u;
+      s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (uint32_t x = word; x; x &= x - 1) {
+      const uint32_t v = uint32_t(w * 32 + __ffs(x) - 1);
+      if (v >= nv) break;
+      const uint32_t key = vertex_class(v, k, seg) * kBins + degree_bin(deg[v], seg);
+      const uint32_t r = s_base[key] + atomicAdd(&s_cnt[key], 1u);
+      if (r < seg.cap[key]) lists[seg.off[key] + r] = v;
+      else atomicOr(&ctrl->err, kErrInternal);
+    }
+    __syncthreads();
   }
 }
 

@@ -45,6 +45,8 @@ struct DecideArgs {
   uint2* gtable;          // bin 3: per-block global tables
   uint32_t gslots;        // slots per block (power of two)
   uint32_t* bigmv;        // movers of degree > kMarkInline (neighbours marked by k_commit)
+  unsigned int* movers;   // movers of the sub-step (slot counter into mv_i/mv_c/mv_d)
+  unsigned int* nbig;     // ... of them in bigmv
   // group of graphs (ngraphs > 0): the vertex's graph gives its 2m, whether
   // it is still processed, and where its movers' dQ sum goes
   uint32_t ngraphs;
@@ -86,7 +88,7 @@ struct MoveSums {
 
 __device__ __forceinline__ void record_move(const DecideArgs& a, uint32_t i, uint32_t c, uint32_t d,
                                             i128 gain, uint32_t gi, MoveSums& sums) {
-  uint32_t slot = atomicAdd(&a.ctrl->movers, 1u);
+  uint32_t slot = atomicAdd(a.movers, 1u);
   a.mv_i[slot] = i;
   a.mv_c[slot] = c;
   a.mv_d[slot] = d;
@@ -335,19 +337,95 @@ __device__ __forceinline__ unsigned long long table_argmax(const DecideArgs& a, 
   return hd;
 }
 
+// Reduce (have, score, c) of every thread of the block to thread 0 (larger
+// score wins, ties to the smaller c); every thread calls it.
+constexpr uint32_t kMaxBlockWarps = 16;  // blocks of up to 512 threads
+
+__device__ __forceinline__ void block_argmax(bool& have, i128& best, uint32_t& bc) {
+  __shared__ unsigned long long s_lo[kMaxBlockWarps], s_hi[kMaxBlockWarps];
+  __shared__ uint32_t s_c[kMaxBlockWarps];
+  __shared__ int s_have[kMaxBlockWarps];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x / 32;
+  warp_argmax(have, best, bc);
+  __syncthreads();
+  if (lane == 0) {
+    s_lo[wib] = (unsigned long long)(u128)best;
+    s_hi[wib] = (unsigned long long)((u128)best >> 64);
+    s_c[wib] = bc;
+    s_have[wib] = have;
+  }
+  __syncthreads();
+  if (wib == 0) {
+    have = lane < nw && s_have[lane];
+    best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
+    bc = lane < nw ? s_c[lane] : 0;
+    warp_argmax(have, best, bc);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Bin 1: 32 < deg <= 256, one warp per vertex with a shared table.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kWarpSlots = 512;
 constexpr int kWarpHashWarps = 8;
 
+// One vertex of bin 1 by one warp (its degree up to kWarpSlots / 2): up to
+// 32 arcs by the register path, else a shared table of the warp.  Every lane
+// of the warp calls it.
+__device__ __forceinline__ void warp_table_vertex(const DecideArgs& a, uint32_t i, long long m2, uint32_t gi,
+                                                  uint32_t* keys, uint32_t* vals, MoveSums& sums) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t dg = a.g.deg[i];
+  if (dg <= 32) {  // (when bin 0 takes fewer than 32 arcs) registers, not a table
+    decide_segment<32>(a, true, i, m2, gi, sums);
+    return;
+  }
+  const uint32_t d = a.C[i];
+  const long long Ki = a.K[i];
+  const unsigned long long o = a.g.off[i];
+  uint32_t slots = 64;
+  while (slots < 2 * dg && slots < kWarpSlots) slots <<= 1;
+  const uint32_t mask = slots - 1;
+  for (uint32_t s = lane; s < slots; s += 32) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  __syncwarp();
+  bool ok = scan_row<8>(a, i, o, dg, 0, 32, keys, vals, mask, slots);
+  if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
+  __syncwarp();
+  bool have = false;
+  i128 best = 0;
+  uint32_t bc = 0;
+  uint32_t ncand = 0;
+  unsigned long long Hd = table_argmax<4>(a, keys, vals, slots, lane, 32, d, m2, Ki, have, best, bc, ncand);
+  for (int x = 16; x; x >>= 1) {
+    Hd += __shfl_xor_sync(0xFFFFFFFFu, Hd, x);
+    ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+  }
+  warp_argmax(have, best, bc);
+  i128 gain = 0;
+  bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
+  if (lane == 0) sums.bytes += 24 + 12ull * dg + 12ull * ncand;
+  if (mv) {
+    if (lane == 0) {
+      record_move(a, i, bc, d, gain, gi, sums);
+      sums.bytes += 16 + 4ull * dg;
+    }
+    for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
+      uint32_t k = k0 + lane;
+      uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+      mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
+    }
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
   const long long m2_one = *a.m2p;
   __shared__ uint32_t skeys[kWarpHashWarps][kWarpSlots];
   __shared__ uint32_t svals[kWarpHashWarps][kWarpSlots];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  uint32_t* keys = skeys[wib];
-  uint32_t* vals = svals[wib];
   const uint32_t cnt = *a.count;
   uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -357,51 +435,12 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
     long long m2 = m2_one;
     uint32_t gi = 0;
     if (!group_active(a, i, &m2, &gi)) continue;
-    if (a.ever && lane == 0 && bit_set(a.ever, i)) ++sums.ever;
-    ++sums.processed;
+    if (lane == 0) {
+      if (a.ever && bit_set(a.ever, i)) ++sums.ever;
+      ++sums.processed;
+    }
     if (a.rbits && !bit_test(a.rbits, i)) continue;
-    const uint32_t dg = a.g.deg[i];
-    if (dg <= 32) {  // (when bin 0 takes fewer than 32 arcs) registers, not a table
-      decide_segment<32>(a, true, i, m2, gi, sums);
-      continue;
-    }
-    const uint32_t d = a.C[i];
-    const long long Ki = a.K[i];
-    const unsigned long long o = a.g.off[i];
-    uint32_t slots = 64;
-    while (slots < 2 * dg && slots < kWarpSlots) slots <<= 1;
-    const uint32_t mask = slots - 1;
-    for (uint32_t s = lane; s < slots; s += 32) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncwarp();
-    bool ok = scan_row<8>(a, i, o, dg, 0, 32, keys, vals, mask, slots);
-    if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
-    __syncwarp();
-    bool have = false;
-    i128 best = 0;
-    uint32_t bc = 0;
-    uint32_t ncand = 0;
-    unsigned long long Hd = table_argmax<4>(a, keys, vals, slots, lane, 32, d, m2, Ki, have, best, bc, ncand);
-    for (int x = 16; x; x >>= 1) {
-      Hd += __shfl_xor_sync(0xFFFFFFFFu, Hd, x);
-      ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
-    }
-    warp_argmax(have, best, bc);
-    i128 gain = 0;
-    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
-    sums.bytes += 24 + 12ull * dg + 12ull * ncand;
-    if (mv) {
-      if (lane == 0) record_move(a, i, bc, d, gain, gi, sums);
-      for (uint32_t k0 = 0; k0 < dg; k0 += 32) {
-        uint32_t k = k0 + lane;
-        uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
-        mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
-      }
-      sums.bytes += 16 + 4ull * dg;
-    }
-    __syncwarp();
+    warp_table_vertex(a, i, m2, gi, skeys[wib], svals[wib], sums);
   }
   flush_sums(a, sums, lane == 0);
 }
@@ -415,17 +454,100 @@ __global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
 // ---------------------------------------------------------------------------
 constexpr uint32_t kBlockSlots = 2 * kBinBlock;  // 8192 keys + 8192 values = 64 KB
 
+// Shared scalars of the block-level bodies.
+struct BlockScratch {
+  unsigned long long hd;
+  uint32_t ncand, ne;
+  int ok, last;
+};
+
+// One vertex by the whole block (up to 512 threads): a shared table of
+// 2 x degree slots at `dyn` (at most kBlockSlots keys + values); a vertex of
+// larger degree whose distinct communities overflow it is redone in the
+// block's slice of the global table.  Every thread of the block calls it.
+__device__ __forceinline__ void block_vertex(const DecideArgs& a, uint32_t i, long long m2, uint32_t gi,
+                                             uint32_t* dyn, BlockScratch& sc, MoveSums& sums) {
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nthr = blockDim.x;
+  const uint32_t d = a.C[i];
+  const long long Ki = a.K[i];
+  const unsigned long long o = a.g.off[i];
+  const uint32_t dg = a.g.deg[i];
+  uint32_t slots = 1024;
+  while (slots < 2 * dg && slots < kBlockSlots) slots <<= 1;
+  uint32_t* keys = dyn;
+  uint32_t* vals = dyn + slots;
+  bool global = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (attempt == 1) {  // shared table overflowed: global slice of gslots
+      global = true;
+      slots = a.gslots;
+      keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
+      vals = keys + a.gslots;
+    }
+    const uint32_t mask = slots - 1;
+    for (uint32_t s = threadIdx.x; s < slots; s += nthr) {
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    if (threadIdx.x == 0) {
+      sc.hd = 0;
+      sc.ncand = 0;
+      sc.ok = 1;
+    }
+    __syncthreads();
+    // a table of >= 2 * deg slots cannot overflow: probe it to the end;
+    // a smaller shared table (bin 3) gives up early and falls back
+    const uint32_t limit = (global || slots >= 2 * dg) ? slots : 64;
+    bool ok = scan_row<8>(a, i, o, dg, wib * 32, nthr, keys, vals, mask, limit);
+    if (!ok) sc.ok = 0;
+    __syncthreads();
+    const bool done = sc.ok;
+    __syncthreads();  // everyone has read sc.ok before the retry resets it
+    if (done) break;
+    if (global || !a.gtable) {
+      if (threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
+      break;
+    }
+  }
+  bool have = false;
+  i128 best = 0;
+  uint32_t bc = 0;
+  uint32_t ncand = 0;
+  {
+    const unsigned long long hd = table_argmax<4>(a, keys, vals, slots, threadIdx.x, nthr, d, m2, Ki,
+                                                   have, best, bc, ncand);
+    if (hd) sc.hd = hd;  // exactly one slot holds d
+  }
+  for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+  if (lane == 0 && ncand) atomicAdd(&sc.ncand, ncand);
+  block_argmax(have, best, bc);
+  if (threadIdx.x == 0) {
+    i128 gain = 0;
+    const bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, sc.hd, &gain);
+    sums.bytes += 24 + 12ull * dg + 12ull * sc.ncand;
+    sc.last = mv;
+    if (mv) {
+      record_move(a, i, bc, d, gain, gi, sums);
+      sums.bytes += 16 + 4ull * dg;
+      if (dg > kMarkInline) a.bigmv[atomicAdd(a.nbig, 1u)] = i;
+    }
+  }
+  __syncthreads();
+  if (sc.last && dg <= kMarkInline) {
+    for (uint32_t k0 = wib * 32; k0 < dg; k0 += nthr) {
+      uint32_t k = k0 + lane;
+      uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
+      mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
+    }
+  }
+  __syncthreads();
+}
+
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   const long long m2_one = *a.m2p;
   extern __shared__ uint32_t dyn[];
-  __shared__ unsigned long long s_hd;
-  __shared__ uint32_t s_ncand;
-  __shared__ unsigned long long s_lo[kThreads / 32], s_hi[kThreads / 32];
-  __shared__ uint32_t s_c[kThreads / 32];
-  __shared__ int s_have[kThreads / 32];
-  __shared__ int s_ok;
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = kThreads / 32;
+  __shared__ BlockScratch sc;
   const uint32_t cnt = *a.count;
   MoveSums sums;
   for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
@@ -433,102 +555,12 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
     long long m2 = m2_one;
     uint32_t gi = 0;
     if (!group_active(a, i, &m2, &gi)) continue;
-    if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++sums.ever;
-    ++sums.processed;
+    if (threadIdx.x == 0) {
+      if (a.ever && bit_set(a.ever, i)) ++sums.ever;
+      ++sums.processed;
+    }
     if (a.rbits && !bit_test(a.rbits, i)) continue;
-    const uint32_t d = a.C[i];
-    const long long Ki = a.K[i];
-    const unsigned long long o = a.g.off[i];
-    const uint32_t dg = a.g.deg[i];
-    uint32_t slots = 1024;
-    while (slots < 2 * dg && slots < kBlockSlots) slots <<= 1;
-    uint32_t* keys = dyn;
-    uint32_t* vals = dyn + slots;
-    bool global = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      if (attempt == 1) {  // shared table overflowed: global slice of gslots
-        global = true;
-        slots = a.gslots;
-        keys = reinterpret_cast<uint32_t*>(a.gtable + uint64_t(blockIdx.x) * a.gslots);
-        vals = keys + a.gslots;
-      }
-      const uint32_t mask = slots - 1;
-      for (uint32_t s = threadIdx.x; s < slots; s += kThreads) {
-        keys[s] = kEmpty;
-        vals[s] = 0;
-      }
-      if (threadIdx.x == 0) {
-        s_hd = 0;
-        s_ncand = 0;
-        s_ok = 1;
-      }
-      __syncthreads();
-      // a table of >= 2 * deg slots cannot overflow: probe it to the end;
-      // a smaller shared table (bin 3) gives up early and falls back
-      const uint32_t limit = (global || slots >= 2 * dg) ? slots : 64;
-      bool ok = scan_row<8>(a, i, o, dg, wib * 32, kThreads, keys, vals, mask, limit);
-      if (!ok) s_ok = 0;
-      __syncthreads();
-      const bool done = s_ok;
-      __syncthreads();  // everyone has read s_ok before the retry resets it
-      if (done) break;
-      if (global || !a.gtable) {
-        if (threadIdx.x == 0) atomicOr(&a.ctrl->err, kErrInternal);
-        break;
-      }
-    }
-    bool have = false;
-    i128 best = 0;
-    uint32_t bc = 0;
-    uint32_t ncand = 0;
-    {
-      const unsigned long long hd = table_argmax<4>(a, keys, vals, slots, threadIdx.x, kThreads, d, m2, Ki,
-                                                     have, best, bc, ncand);
-      if (hd) s_hd = hd;  // exactly one slot holds d
-    }
-    for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
-    warp_argmax(have, best, bc);
-    if (lane == 0) {
-      s_lo[wib] = (unsigned long long)(u128)best;
-      s_hi[wib] = (unsigned long long)((u128)best >> 64);
-      s_c[wib] = bc;
-      s_have[wib] = have;
-      if (ncand) atomicAdd(&s_ncand, ncand);
-    }
-    __syncthreads();
-    if (wib == 0) {
-      have = lane < nw && s_have[lane];
-      best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
-      bc = lane < nw ? s_c[lane] : 0;
-      warp_argmax(have, best, bc);
-      if (lane == 0) {
-        s_lo[0] = (unsigned long long)(u128)best;
-        s_hi[0] = (unsigned long long)((u128)best >> 64);
-        s_c[0] = bc;
-        s_have[0] = have;
-      }
-    }
-    __syncthreads();
-    have = s_have[0];
-    best = (i128)(((u128)s_hi[0] << 64) | (u128)s_lo[0]);
-    bc = s_c[0];
-    i128 gain = 0;
-    bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, s_hd, &gain);
-    sums.bytes += 24 + 12ull * dg + 12ull * s_ncand;
-    if (mv) {
-      if (threadIdx.x == 0) record_move(a, i, bc, d, gain, gi, sums);
-      if (dg > kMarkInline) {
-        if (threadIdx.x == 0) a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;
-      } else {
-        for (uint32_t k0 = wib * 32; k0 < dg; k0 += kThreads) {
-          uint32_t k = k0 + lane;
-          uint2 arc = k < dg ? a.g.arcs[o + k] : make_uint2(i, 0u);
-          mark_next(a, arc.x, k < dg && arc.x != i && arc.y != 0);
-        }
-      }
-      sums.bytes += 16 + 4ull * dg;
-    }
-    __syncthreads();
+    block_vertex(a, i, m2, gi, dyn, sc, sums);
   }
   flush_sums(a, sums, threadIdx.x == 0);
 }
@@ -574,6 +606,7 @@ struct GiantDecide {
   uint32_t* tvals;            // (0 at rest)
   uint32_t* tlist;            // occupied-slot lists
   unsigned int* nitems;       // chunk total
+  unsigned int* nbignd;       // vertices left to the part blocks (counted)
 };
 
 __device__ __forceinline__ uint32_t giant_deg(const DecideArgs& a, uint32_t t) {
@@ -593,7 +626,7 @@ __device__ __forceinline__ uint64_t giant_table_slots(uint32_t d) {
 
 // One block: exclusive prefixes over the bin-3 list of chunks, table slots
 // and list capacities.
-__global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd) {
+__device__ __forceinline__ void giant_prefix_body(const DecideArgs& a, const GiantDecide& gd) {
   __shared__ unsigned long long s_t[32], s_l[32];
   __shared__ uint32_t s_c[32];
   __shared__ unsigned long long s_tbase, s_lbase;
@@ -660,28 +693,8 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
   }
 }
 
-// Reduce (have, score, c) of every thread of the block to thread 0 (larger
-// score wins, ties to the smaller c); every thread calls it.
-__device__ __forceinline__ void block_argmax(bool& have, i128& best, uint32_t& bc) {
-  __shared__ unsigned long long s_lo[kGiantThreads / 32], s_hi[kGiantThreads / 32];
-  __shared__ uint32_t s_c[kGiantThreads / 32];
-  __shared__ int s_have[kGiantThreads / 32];
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nw = blockDim.x / 32;
-  warp_argmax(have, best, bc);
-  __syncthreads();
-  if (lane == 0) {
-    s_lo[wib] = (unsigned long long)(u128)best;
-    s_hi[wib] = (unsigned long long)((u128)best >> 64);
-    s_c[wib] = bc;
-    s_have[wib] = have;
-  }
-  __syncthreads();
-  if (wib == 0) {
-    have = lane < nw && s_have[lane];
-    best = lane < nw ? (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]) : 0;
-    bc = lane < nw ? s_c[lane] : 0;
-    warp_argmax(have, best, bc);
-  }
+__global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd) {
+  giant_prefix_body(a, gd);
 }
 
 // Entries [e0, e1) of vertex t's occupied list: read and clear them, keep the
@@ -734,16 +747,148 @@ __device__ __forceinline__ uint32_t giant_scan_entries(const DecideArgs& a, cons
 
 constexpr uint32_t kSmallDecide = 4096;  // occupied slots the last chunk block decides alone
 
+// One chunk (arcs [chunk * kGiantChunk, +kGiantChunk)) of list position t
+// by the whole block: aggregated in the shared table (keys, vals:
+// kGiantSlots each), its distinct communities compacted (ek, ev: kGiantChunk
+// each) and added into the vertex's global table; the vertex's last chunk
+// block decides it when the table holds at most kSmallDecide communities.
+// `nch` is the vertex's chunk count.  Every thread of the block calls it.
+__device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDecide& gd, uint32_t t,
+                                            uint32_t chunk, uint32_t nch, long long m2_one, uint32_t* keys,
+                                            uint32_t* vals, uint32_t* ek, uint32_t* ev, BlockScratch& sc,
+                                            MoveSums& sums) {
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nthr = blockDim.x;
+  const uint32_t i = a.list[t];
+  if (chunk == 0 && threadIdx.x == 0) {
+    if (a.ever && bit_set(a.ever, i)) ++sums.ever;
+    ++sums.processed;
+  }
+  if (a.rbits && !bit_test(a.rbits, i)) return;  // processed, not in the affected range
+  const unsigned long long o = a.g.off[i];
+  const uint32_t dg = a.g.deg[i];
+  const uint32_t k0 = chunk * kGiantChunk;
+  const uint32_t k1 = min(dg, k0 + kGiantChunk);
+  for (uint32_t s = threadIdx.x; s < kGiantSlots; s += nthr) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (threadIdx.x == 0) sc.ne = 0;
+  __syncthreads();
+  // a table of 2x the chunk's arcs cannot overflow
+  scan_row<8>(a, i, o, k1, k0 + wib * 32, nthr, keys, vals, kGiantSlots - 1, kGiantSlots);
+  __syncthreads();
+  // the chunk's distinct communities: compacted in shared memory, then
+  // added into the vertex's global table, four per thread in flight; new
+  // keys' slots go onto its occupied list (one counter update per warp)
+  for (uint32_t s0 = wib * 32; s0 < kGiantSlots; s0 += nthr) {
+    const uint32_t c = keys[s0 + lane];
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, c != kEmpty);
+    if (!m) continue;
+    uint32_t base = 0;
+    if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&sc.ne, uint32_t(__popc(m)));
+    base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+    if (c != kEmpty) {
+      const uint32_t r = base + __popc(m & ((1u << lane) - 1u));
+      ek[r] = c;
+      ev[r] = vals[s0 + lane];
+    }
+  }
+  __syncthreads();
+  const uint32_t ne = sc.ne;
+  const uint32_t tmask = uint32_t(giant_table_slots(dg) - 1);
+  uint32_t* gk = gd.tkeys + gd.toff[t];
+  uint32_t* gv = gd.tvals + gd.toff[t];
+  uint32_t* gl = gd.tlist + gd.loff[t];
+  constexpr int U = 4;
+  for (uint32_t b0 = wib * 32 * U; b0 < ne; b0 += nthr * U) {  // warp-uniform
+    uint32_t c[U], slot[U], prev[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = b0 + u * 32 + lane;
+      c[u] = e < ne ? ek[e] : kEmpty;
+      slot[u] = hash32(c[u]) & tmask;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) prev[u] = c[u] != kEmpty ? atomicCAS(&gk[slot[u]], kEmpty, c[u]) : kEmpty;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = b0 + u * 32 + lane;
+      bool created = false;
+      if (c[u] != kEmpty) {
+        // load <= 1/2: the probe ends within the table
+        for (uint32_t probe = 0; prev[u] != kEmpty && prev[u] != c[u] && probe < tmask; ++probe) {
+          slot[u] = (slot[u] + 1) & tmask;
+          prev[u] = atomicCAS(&gk[slot[u]], kEmpty, c[u]);
+        }
+        if (prev[u] != kEmpty && prev[u] != c[u]) {
+          atomicOr(&a.ctrl->err, kErrInternal);  // (cannot happen: the table is never full)
+        } else {
+          created = prev[u] == kEmpty;
+          atomicAdd(&gv[slot[u]], ev[e]);
+        }
+      }
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, created);
+      if (m) {
+        uint32_t base = 0;
+        if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&gd.ndist[t], uint32_t(__popc(m)));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+        if (created) gl[base + __popc(m & ((1u << lane) - 1u))] = slot[u];
+      }
+    }
+  }
+  // the vertex's last chunk block decides it when its table holds few
+  // communities; the part blocks take the rest
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sc.last = atomicAdd(&gd.done[t], 1u) == nch - 1;
+  __syncthreads();
+  if (sc.last) {
+    __threadfence();
+    const uint32_t nd = __ldcg(gd.ndist + t);
+    if (threadIdx.x == 0) {
+      gd.done[t] = 0;  // the part blocks count from 0
+      sc.ncand = 0;
+    }
+    if (nd > kSmallDecide && gd.nbignd && threadIdx.x == 0) atomicAdd(gd.nbignd, 1u);
+    if (nd <= kSmallDecide) {
+      long long m2 = m2_one;
+      uint32_t gi = 0;
+      group_active(a, i, &m2, &gi);
+      const uint32_t d = a.C[i];
+      const long long Ki = a.K[i];
+      bool have = false;
+      i128 best = 0;
+      uint32_t bc = 0;
+      uint32_t ncand = giant_scan_entries(a, gd, t, 0, nd, d, m2, Ki, have, best, bc);
+      for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
+      __threadfence();
+      __syncthreads();
+      if (lane == 0 && ncand) atomicAdd(&sc.ncand, ncand);
+      block_argmax(have, best, bc);
+      if (threadIdx.x == 0) {
+        const unsigned long long Hd = __ldcg(gd.hd + t);
+        gd.hd[t] = 0;
+        i128 gain = 0;
+        const bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
+        sums.bytes += 24 + 12ull * dg + 12ull * sc.ncand;
+        if (mv) {
+          record_move(a, i, bc, d, gain, gi, sums);
+          a.bigmv[atomicAdd(a.nbig, 1u)] = i;  // neighbours marked by the commit
+          sums.bytes += 16 + 4ull * dg;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kAccumThreads, 8) k_giant_accum(DecideArgs a, GiantDecide gd) {
   __shared__ uint32_t keys[kGiantSlots];
   __shared__ uint32_t vals[kGiantSlots];
   __shared__ uint32_t s_pre[kGiantListSmem];
-  __shared__ int s_last;
-  __shared__ uint32_t s_ncand, s_ne;
   __shared__ uint32_t s_ek[kGiantChunk], s_ev[kGiantChunk];  // distinct communities of a chunk
+  __shared__ BlockScratch sc;
   const long long m2_one = *a.m2p;
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_ncand = 0;
   const uint32_t cnt = *a.count;
   const uint32_t nitems = *gd.nitems;
   // the chunk prefix, cached in shared memory when it fits
@@ -761,140 +906,22 @@ __global__ void __launch_bounds__(kAccumThreads, 8) k_giant_accum(DecideArgs a, 
       if (cp[mid] <= item) lo = mid;
       else hi = mid;
     }
-    const uint32_t t = lo;
-    const uint32_t chunk = item - cp[t];
-    const uint32_t i = a.list[t];
-    if (chunk == 0) {
-      if (a.ever && threadIdx.x == 0 && bit_set(a.ever, i)) ++sums.ever;
-      ++sums.processed;
-    }
-    if (a.rbits && !bit_test(a.rbits, i)) continue;  // processed, not in the affected range
-    const unsigned long long o = a.g.off[i];
-    const uint32_t dg = a.g.deg[i];
-    const uint32_t k0 = chunk * kGiantChunk;
-    const uint32_t k1 = min(dg, k0 + kGiantChunk);
-    for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kAccumThreads) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncthreads();
-    // a table of 2x the chunk's arcs cannot overflow
-    scan_row<8>(a, i, o, k1, k0 + wib * 32, kAccumThreads, keys, vals, kGiantSlots - 1, kGiantSlots);
-    __syncthreads();
-    // the chunk's distinct communities: compacted in shared memory, then
-    // added into the vertex's global table, four per thread in flight; new
-    // keys' slots go onto its occupied list (one counter update per warp)
-    if (threadIdx.x == 0) s_ne = 0;
-    __syncthreads();
-    for (uint32_t s0 = wib * 32; s0 < kGiantSlots; s0 += kAccumThreads) {
-      const uint32_t c = keys[s0 + lane];
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, c != kEmpty);
-      if (!m) continue;
-      uint32_t base = 0;
-      if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&s_ne, uint32_t(__popc(m)));
-      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
-      if (c != kEmpty) {
-        const uint32_t r = base + __popc(m & ((1u << lane) - 1u));
-        s_ek[r] = c;
-        s_ev[r] = vals[s0 + lane];
-      }
-    }
-    __syncthreads();
-    const uint32_t ne = s_ne;
-    const uint32_t tmask = uint32_t(giant_table_slots(dg) - 1);
-    uint32_t* gk = gd.tkeys + gd.toff[t];
-    uint32_t* gv = gd.tvals + gd.toff[t];
-    uint32_t* gl = gd.tlist + gd.loff[t];
-    constexpr int U = 4;
-    for (uint32_t b0 = wib * 32 * U; b0 < ne; b0 += kAccumThreads * U) {  // warp-uniform
-      uint32_t c[U], slot[U], prev[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t e = b0 + u * 32 + lane;
-        c[u] = e < ne ? s_ek[e] : kEmpty;
-        slot[u] = hash32(c[u]) & tmask;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) prev[u] = c[u] != kEmpty ? atomicCAS(&gk[slot[u]], kEmpty, c[u]) : kEmpty;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t e = b0 + u * 32 + lane;
-        bool created = false;
-        if (c[u] != kEmpty) {
-          // load <= 1/2: the probe ends within the table
-          for (uint32_t probe = 0; prev[u] != kEmpty && prev[u] != c[u] && probe < tmask; ++probe) {
-            slot[u] = (slot[u] + 1) & tmask;
-            prev[u] = atomicCAS(&gk[slot[u]], kEmpty, c[u]);
-          }
-          if (prev[u] != kEmpty && prev[u] != c[u]) {
-            atomicOr(&a.ctrl->err, kErrInternal);  // (cannot happen: the table is never full)
-          } else {
-            created = prev[u] == kEmpty;
-            atomicAdd(&gv[slot[u]], s_ev[e]);
-          }
-        }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, created);
-        if (m) {
-          uint32_t base = 0;
-          if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&gd.ndist[t], uint32_t(__popc(m)));
-          base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
-          if (created) gl[base + __popc(m & ((1u << lane) - 1u))] = slot[u];
-        }
-      }
-    }
-    // the vertex's last chunk block decides it when its table holds few
-    // communities; k_giant_decide takes the rest
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&gd.done[t], 1u) == cp[t + 1] - cp[t] - 1;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      const uint32_t nd = __ldcg(gd.ndist + t);
-      if (threadIdx.x == 0) gd.done[t] = 0;  // k_giant_decide counts its part blocks from 0
-      if (nd <= kSmallDecide) {
-        long long m2 = m2_one;
-        uint32_t gi = 0;
-        group_active(a, i, &m2, &gi);
-        const uint32_t d = a.C[i];
-        const long long Ki = a.K[i];
-        bool have = false;
-        i128 best = 0;
-        uint32_t bc = 0;
-        uint32_t ncand = giant_scan_entries(a, gd, t, 0, nd, d, m2, Ki, have, best, bc);
-        for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
-        if (lane == 0 && ncand) atomicAdd(&s_ncand, ncand);
-        __threadfence();
-        __syncthreads();
-        block_argmax(have, best, bc);
-        if (threadIdx.x == 0) {
-          const unsigned long long Hd = __ldcg(gd.hd + t);
-          gd.hd[t] = 0;
-          i128 gain = 0;
-          const bool mv = decide_move(a, m2, i, d, Ki, have, best, bc, Hd, &gain);
-          sums.bytes += 24 + 12ull * dg + 12ull * s_ncand;
-          s_ncand = 0;
-          if (mv) {
-            record_move(a, i, bc, d, gain, gi, sums);
-            a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;  // neighbours marked by k_commit
-            sums.bytes += 16 + 4ull * dg;
-          }
-        }
-      }
-    }
-    __syncthreads();
+    giant_chunk(a, gd, lo, item - cp[lo], cp[lo + 1] - cp[lo], m2_one, keys, vals, s_ek, s_ev, sc, sums);
   }
   flush_sums(a, sums, threadIdx.x == 0);
 }
 
-__global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, GiantDecide gd) {
-  const long long m2_one = *a.m2p;
+// Vertices whose tables hold more than kSmallDecide communities: kGiantPart
+// occupied slots per block (blocks of kGiantThreads threads), the vertex's
+// last part block reduces.  The block sweeps the list in tiles to number
+// the parts.  Every thread of the block calls it.
+__device__ __forceinline__ void giant_parts(const DecideArgs& a, const GiantDecide& gd, long long m2_one,
+                                            MoveSums& sums) {
   __shared__ uint32_t s_ipre[kGiantThreads + 1];  // part prefix of one tile of the list
   __shared__ uint32_t s_ncand;
   __shared__ int s_last;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint32_t cnt = *a.count;
-  MoveSums sums;
   // sweep the list in tiles of blockDim.x positions; part items of a tile
   // are numbered from `ibase` and dealt round-robin over the blocks
   uint32_t ibase = 0;
@@ -990,7 +1017,7 @@ __global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, Gi
           sums.bytes += 24 + 12ull * dg;
           if (mv) {
             record_move(a, i, bc, d, gain, gi, sums);
-            a.bigmv[atomicAdd(&a.ctrl->big_movers, 1u)] = i;  // neighbours marked by k_commit
+            a.bigmv[atomicAdd(a.nbig, 1u)] = i;  // neighbours marked by k_commit
             sums.bytes += 16 + 4ull * dg;
           }
         }
@@ -1000,14 +1027,24 @@ __global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, Gi
     ibase += tile_items;
     __syncthreads();  // s_ipre is rewritten for the next tile
   }
+}
+
+__global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, GiantDecide gd) {
+  MoveSums sums;
+  giant_parts(a, gd, *a.m2p, sums);
   flush_sums(a, sums, threadIdx.x == 0);
 }
 
+constexpr int kCommitThreads = 256;
+
 // Apply the moves of one sub-step, then mark the next frontier around the
 // listed high-degree movers: their arcs in kMarkChunk pieces spread over the
-// blocks (each block walks the short mover list to find its pieces).
-__global__ void __launch_bounds__(256) k_commit(DecideArgs a) {
-  const uint32_t m = a.ctrl->movers;
+// blocks.  The list is swept in tiles of one block's threads: a block-wide
+// prefix numbers the pieces of a tile, which are dealt round-robin over the
+// blocks, so a long list (the first iterations of a static run) costs every
+// block one parallel pass per tile instead of one dependent walk per mover.
+// Blocks of kCommitThreads threads.
+__device__ __forceinline__ void commit_body(const DecideArgs& a, uint32_t m, uint32_t count) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && m) atomicAdd(&a.ctrl->moved, (unsigned long long)m);
   uint32_t* C = const_cast<uint32_t*>(a.C);
   long long* Sigma = const_cast<long long*>(a.Sigma);
@@ -1045,26 +1082,53 @@ __global__ void __launch_bounds__(256) k_commit(DecideArgs a) {
       }
     }
   }
-  const uint32_t count = a.ctrl->big_movers;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  uint64_t item0 = 0;
-  for (uint32_t q = 0; q < count; ++q) {
-    const uint32_t i = a.bigmv[q];
-    const uint32_t dg = a.g.deg[i];
-    const unsigned long long o = a.g.off[i];
-    const uint64_t nch = (dg + kMarkChunk - 1) / kMarkChunk;
-    // piece c of this mover is item item0 + c, handled by block (item0 + c) mod grid
-    uint64_t c = (blockIdx.x + gridDim.x - item0 % gridDim.x) % gridDim.x;
-    for (; c < nch; c += gridDim.x) {
-      const uint32_t k1 = min(dg, uint32_t((c + 1) * kMarkChunk));
-      for (uint32_t k0 = uint32_t(c * kMarkChunk) + wib * 32; k0 < k1; k0 += blockDim.x) {
+  __shared__ uint32_t s_pre[kCommitThreads + 1];
+  __shared__ uint32_t s_w[kCommitThreads / 32];
+  uint64_t ibase = 0;  // pieces of the earlier tiles
+  for (uint32_t q0 = 0; q0 < count; q0 += kCommitThreads) {
+    const uint32_t q = q0 + threadIdx.x;
+    const uint32_t nch = q < count ? (a.g.deg[a.bigmv[q]] + kMarkChunk - 1) / kMarkChunk : 0u;
+    uint32_t x = nch;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= uint32_t(o)) x += y;
+    }
+    if (lane == 31) s_w[wib] = x;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (uint32_t k = 0; k < wib; ++k) wbase += s_w[k];
+    s_pre[threadIdx.x + 1] = wbase + x;
+    if (threadIdx.x == 0) s_pre[0] = 0;
+    __syncthreads();
+    const uint32_t tile_items = s_pre[kCommitThreads];
+    // piece `it` of the tile is item ibase + it, handled by block (ibase + it) mod grid
+    for (uint32_t it = uint32_t((blockIdx.x + gridDim.x - ibase % gridDim.x) % gridDim.x); it < tile_items;
+         it += gridDim.x) {
+      uint32_t lo = 0, hi = kCommitThreads;  // tile position owning piece `it`
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_pre[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t i = a.bigmv[q0 + lo];
+      const uint32_t c = it - s_pre[lo];
+      const uint32_t dg = a.g.deg[i];
+      const unsigned long long o = a.g.off[i];
+      const uint32_t k1 = min(dg, (c + 1) * kMarkChunk);
+      for (uint32_t k0 = c * kMarkChunk + wib * 32; k0 < k1; k0 += kCommitThreads) {
         const uint32_t k = k0 + lane;
-        uint2 arc = k < k1 ? a.g.arcs[o + k] : make_uint2(i, 0u);
+        const uint2 arc = k < k1 ? a.g.arcs[o + k] : make_uint2(i, 0u);
         mark_next(a, arc.x, k < k1 && arc.x != i && arc.y != 0);
       }
     }
-    item0 += nch;
+    ibase += tile_items;
+    __syncthreads();  // s_pre and s_w are rewritten by the next tile
   }
+}
+
+__global__ void __launch_bounds__(kCommitThreads) k_commit(DecideArgs a) {
+  commit_body(a, *a.movers, *a.nbig);
 }
 
 int read_ctrl(Handle* h) {
@@ -1093,6 +1157,232 @@ uint32_t next_pow2(uint64_t x) {
 }
 
 
+
+
+// ---------------------------------------------------------------------------
+// Persistent iteration kernel: one cooperative launch runs a whole
+// local-moving iteration.  Its blocks take work units of a sub-step from a
+// shared counter (largest-degree chunks first, then block, warp and
+// segment units), meet at grid barriers between deciding and committing,
+// and build the next frontier's lists at the end.  It replaces the per
+// sub-step launches, stream forks and joins of issue_iteration.
+// ---------------------------------------------------------------------------
+constexpr int kIterThreads = 256;
+constexpr uint32_t kIterDynWords = 2 * kBlockSlots + kGiantListSmem;  // tables + chunk prefix cache
+constexpr unsigned long long kBarrierPolls = 1ull << 22;             // x 256 ns: about a second
+// vertices per warp in one work unit of bins 1 and 0 (rounds of 1 and of
+// 32 / W vertices); larger units save counter updates on big frontiers but
+// measured slower on small DF frontiers, where they leave blocks idle
+constexpr uint32_t kIterRounds1 = 1;
+constexpr uint32_t kIterRounds0 = 1;
+
+struct IterArgs {
+  DecideArgs a;            // list/count/movers/nbig are set per bin and sub-step
+  GiantDecide gd;          // class 0's arrays; class s at + s * gstride
+  uint32_t gstride;
+  uint32_t k;
+  int cur;
+  uint32_t seg_lanes;      // W: lanes per bin-0 vertex
+  const uint32_t* lists_cur;
+  uint32_t* fbits_cur;     // cleared at the end (the processed frontier)
+  uint32_t words;
+};
+
+// Grid-wide barrier with a bounded wait: false if it gave up (the error bit
+// kErrTimeout is then set and the kernel must return).  Every thread calls it.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* genp = &ctrl->bar_gen;
+    const unsigned int gen = *genp;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
+      ctrl->bar_count = 0;
+      __threadfence();
+      atomicAdd(&ctrl->bar_gen, 1u);
+    } else {
+      unsigned long long polls = 0;
+      while (*genp == gen) {
+        if (++polls > kBarrierPolls || (*((volatile unsigned int*)&ctrl->err) & kErrTimeout)) {
+          ok = 0;
+          atomicOr(&ctrl->err, kErrTimeout);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  __threadfence();  // every thread: later reads see what other blocks wrote before the barrier
+  return s_ok;
+}
+
+__device__ __forceinline__ DecideArgs bin_args(const IterArgs& ia, uint32_t s, int b) {
+  DecideArgs a = ia.a;
+  a.list = ia.lists_cur + a.seg.off[s * kBins + b];
+  a.count = &a.ctrl->count[ia.cur][s][b];
+  a.movers = &a.ctrl->it_movers[s & 1];
+  a.nbig = &a.ctrl->it_nbig[s & 1];
+  return a;
+}
+
+__device__ __forceinline__ GiantDecide class_giant(const IterArgs& ia, uint32_t s) {
+  GiantDecide gd = ia.gd;
+  const uint64_t o = uint64_t(s) * ia.gstride;
+  gd.toff += o;
+  gd.loff += o;
+  gd.cpre += o;
+  gd.ndist += o;
+  gd.done += o;
+  gd.hd += o;
+  gd.nitems = &ia.a.ctrl->it_items[s];
+  gd.nbignd = &ia.a.ctrl->it_bignd[s & 1];
+  return gd;
+}
+
+// Every lane of the warp calls it: bin-0 vertices of one warp (32 / W of them).
+template <int W>
+__device__ __forceinline__ void iter_segments(const DecideArgs& a, uint64_t first, uint32_t cnt, long long m2_one,
+                                              MoveSums& sums) {
+  const uint32_t lane = threadIdx.x & 31u, seg = lane / W, sl = lane % W;
+  const uint64_t t = first + seg;
+  bool active = t < cnt;
+  const uint32_t i = active ? a.list[t] : 0u;
+  long long m2 = m2_one;
+  uint32_t gi = 0;
+  if (active && !group_active(a, i, &m2, &gi)) active = false;
+  if (active && sl == 0) {
+    if (a.ever && bit_set(a.ever, i)) ++sums.ever;
+    ++sums.processed;
+  }
+  if (active && a.rbits && !bit_test(a.rbits, i)) active = false;
+  decide_segment<W>(a, active, i, m2, gi, sums);
+}
+
+static_assert(kIterThreads == kGiantThreads && kIterThreads == kCommitThreads,
+              "the part blocks and the commit sweep their lists in tiles of one block");
+static_assert(kIterDynWords >= 2 * kBlockSlots && 8 * 2 * kWarpSlots <= 2 * kBlockSlots &&
+                  2 * kGiantSlots + 2 * kGiantChunk <= 2 * kBlockSlots,
+              "the dynamic tables hold every unit kind");
+
+__global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
+  extern __shared__ uint32_t dyn[];
+  __shared__ BlockScratch sc;
+  __shared__ uint32_t s_unit;
+  Ctrl* ctrl = ia.a.ctrl;
+  const long long m2_one = *ia.a.m2p;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  uint32_t* pre_cache = dyn + 2 * kBlockSlots;
+  MoveSums sums;
+  // 1. the largest-degree lists of every class: chunk, table and list layouts
+  if (blockIdx.x < ia.k) {
+    const DecideArgs a3 = bin_args(ia, blockIdx.x, 3);
+    giant_prefix_body(a3, class_giant(ia, blockIdx.x));
+  }
+  if (!grid_barrier(ctrl)) return;
+  for (uint32_t s = 0; s < ia.k; ++s) {
+    const uint32_t par = s & 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s >= 1) {  // the other parity's counters are idle now
+      ctrl->it_movers[par ^ 1] = 0;
+      ctrl->it_nbig[par ^ 1] = 0;
+      ctrl->it_work[par ^ 1] = 0;
+      ctrl->it_bignd[par ^ 1] = 0;
+    }
+    const DecideArgs a0 = bin_args(ia, s, 0), a1 = bin_args(ia, s, 1), a2 = bin_args(ia, s, 2),
+                     a3 = bin_args(ia, s, 3);
+    const GiantDecide gd = class_giant(ia, s);
+    const uint32_t n0 = *a0.count, n1 = *a1.count, n2 = *a2.count, n3 = *a3.count;
+    const uint32_t G = *gd.nitems;
+    // chunk prefix of the class, cached when it fits
+    const uint32_t* cp = gd.cpre;
+    if (n3 + 1 <= kGiantListSmem) {
+      for (uint32_t q = threadIdx.x; q <= n3; q += blockDim.x) pre_cache[q] = gd.cpre[q];
+      __syncthreads();
+      cp = pre_cache;
+    }
+    const uint32_t per_warp0 = 32 / ia.seg_lanes;
+    const uint64_t U0 = (uint64_t(n0) + per_warp0 * 8 * kIterRounds0 - 1) / (per_warp0 * 8 * kIterRounds0);
+    const uint64_t U1 = (uint64_t(n1) + 8 * kIterRounds1 - 1) / (8 * kIterRounds1);
+    const uint64_t total = uint64_t(G) + n2 + U1 + U0;
+    // 2. decide: work units from the shared counter
+    for (;;) {
+      if (threadIdx.x == 0) s_unit = atomicAdd(&ctrl->it_work[par], 1u);
+      __syncthreads();
+      const uint64_t u = s_unit;
+      __syncthreads();
+      if (u >= total) break;
+      if (u < G) {
+        uint32_t lo = 0, hi = n3;  // list position owning chunk u
+        while (hi - lo > 1) {
+          uint32_t mid = (lo + hi) >> 1;
+          if (cp[mid] <= u) lo = mid;
+          else hi = mid;
+        }
+        giant_chunk(a3, gd, lo, uint32_t(u) - cp[lo], cp[lo + 1] - cp[lo], m2_one, dyn, dyn + kGiantSlots,
+                    dyn + 2 * kGiantSlots, dyn + 2 * kGiantSlots + kGiantChunk, sc, sums);
+      } else if (u < uint64_t(G) + n2) {
+        const uint32_t i = a2.list[u - G];
+        long long m2 = m2_one;
+        uint32_t gi = 0;
+        if (!group_active(a2, i, &m2, &gi)) continue;
+        if (threadIdx.x == 0) {
+          if (a2.ever && bit_set(a2.ever, i)) ++sums.ever;
+          ++sums.processed;
+        }
+        if (a2.rbits && !bit_test(a2.rbits, i)) continue;
+        block_vertex(a2, i, m2, gi, dyn, sc, sums);
+      } else if (u < uint64_t(G) + n2 + U1) {
+        // one bin-1 vertex per warp and round, in the warp's own table
+        for (uint32_t r = 0; r < kIterRounds1; ++r) {
+          const uint64_t t = ((u - G - n2) * kIterRounds1 + r) * 8 + wib;
+          if (t >= n1) break;
+          const uint32_t i = a1.list[t];
+          long long m2 = m2_one;
+          uint32_t gi = 0;
+          if (!group_active(a1, i, &m2, &gi)) continue;
+          if (lane == 0) {
+            if (a1.ever && bit_set(a1.ever, i)) ++sums.ever;
+            ++sums.processed;
+          }
+          if (!a1.rbits || bit_test(a1.rbits, i))
+            warp_table_vertex(a1, i, m2, gi, dyn + wib * 2 * kWarpSlots, dyn + wib * 2 * kWarpSlots + kWarpSlots,
+                              sums);
+        }
+      } else {
+        for (uint32_t r = 0; r < kIterRounds0; ++r) {
+          const uint64_t first =
+              ((u - G - n2 - U1) * kIterRounds0 + r) * (per_warp0 * 8) + uint64_t(wib) * per_warp0;
+          if (first >= n0) break;  // warp-uniform
+          switch (ia.seg_lanes) {
+            case 4: iter_segments<4>(a0, first, n0, m2_one, sums); break;
+            case 8: iter_segments<8>(a0, first, n0, m2_one, sums); break;
+            case 16: iter_segments<16>(a0, first, n0, m2_one, sums); break;
+            default: iter_segments<32>(a0, first, n0, m2_one, sums); break;
+          }
+        }
+      }
+    }
+    if (!grid_barrier(ctrl)) return;
+    // 3. vertices with many distinct communities: spread over part blocks
+    if (*((volatile unsigned int*)&ctrl->it_bignd[par])) {
+      giant_parts(a3, gd, m2_one, sums);
+      if (!grid_barrier(ctrl)) return;
+    }
+    // 4. commit the sub-step's moves (and mark around high-degree movers)
+    commit_body(a0, *((volatile unsigned int*)a0.movers), *((volatile unsigned int*)a0.nbig));
+    if (!grid_barrier(ctrl)) return;
+  }
+  // 5. the next frontier's lists; clear the processed frontier's bitmap
+  lists_bits_body(ia.a.fbits_next, ia.words, ia.a.g.nv, ia.a.g.deg, ia.a.next_lists, ia.a.seg, ctrl,
+                  ia.a.next_buf, ia.k);
+  for (uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; w < ia.words;
+       w += uint64_t(gridDim.x) * blockDim.x)
+    ia.fbits_cur[w] = 0;
+  flush_sums(ia.a, sums, true);  // every thread holds counts (segment and warp leaders, block leaders)
+}
 
 __global__ void k_set_m2(Ctrl* ctrl, long long m2) { ctrl->m2v = m2; }
 
@@ -1189,7 +1479,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     } else if (any) {
       {
         LaunchScope ls(h, DFL_PROF_COMMIT);
-        k_commit<<<152 * 2, 256, 0, h->stream>>>(a);
+        k_commit<<<152 * 2, kCommitThreads, 0, h->stream>>>(a);
         DFL_TRY(check_launch(h, "commit"));
       }
       DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
@@ -1205,6 +1495,64 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   }
   // the processed frontier's bitmap becomes the next-next target
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
+  return DFL_OK;
+}
+
+// Blocks of the cooperative iteration kernel that are resident at once
+// (0: it cannot run); queried once per process.
+uint32_t persistent_grid() {
+  static std::once_flag once;
+  static uint32_t grid = 0;
+  std::call_once(once, [] {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return;
+    if (cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(uint32_t) * kIterDynWords)) != cudaSuccess)
+      return;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, kIterThreads,
+                                                      sizeof(uint32_t) * kIterDynWords) != cudaSuccess)
+      return;
+    uint64_t g = uint64_t(sms) * uint64_t(per_sm);
+    // each block may own a slice of the block kernel's overflow table
+    grid = uint32_t(g < kBlockGridMax ? g : kBlockGridMax);
+  });
+  return grid;
+}
+
+// One local-moving iteration as a single cooperative launch of k_iterate.
+int issue_persistent(Handle* h, const DecideArgs& a_base, int cur, const GiantDecide& gd, uint32_t grid) {
+  const int nxt = cur ^ 1;
+  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0,
+                              offsetof(Ctrl, bar_gen) + sizeof(unsigned int) - offsetof(Ctrl, it_movers),
+                              h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
+  if (a_base.ngraphs)
+    DFL_CUDA(h, cudaMemsetAsync(a_base.gS, 0, sizeof(unsigned long long) * 2 * a_base.ngraphs, h->stream));
+  IterArgs ia;
+  std::memset(&ia, 0, sizeof(ia));
+  ia.a = a_base;
+  ia.a.fbits_next = h->fbits[nxt];
+  ia.a.next_lists = h->lists[nxt];
+  ia.a.next_buf = nxt;
+  ia.gd = gd;
+  ia.gstride = uint32_t(h->g_items_cap / kMaxSubsteps);
+  ia.k = a_base.k;
+  ia.cur = cur;
+  const uint32_t lim = h->tune.bin_warp;
+  ia.seg_lanes = lim <= 4 ? 4 : lim <= 8 ? 8 : lim <= 16 ? 16 : 32;
+  ia.lists_cur = h->lists[cur];
+  ia.fbits_cur = h->fbits[cur];
+  ia.words = h->words;
+  void* args[] = {&ia};
+  {
+    LaunchScope ls(h, DFL_PROF_MOVE);
+    DFL_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_iterate, dim3(grid), dim3(kIterThreads), args,
+                                            sizeof(uint32_t) * kIterDynWords, h->stream));
+  }
   return DFL_OK;
 }
 
@@ -1326,6 +1674,9 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       smem_rc = cudaFuncSetAttribute(k_decide_block<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
     if (smem_rc == cudaSuccess)
       smem_rc = cudaFuncSetAttribute(k_decide_block<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if (smem_rc == cudaSuccess)
+      smem_rc = cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(uint32_t) * kIterDynWords));
 
   });
   DFL_CUDA(h, smem_rc);
@@ -1335,7 +1686,9 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
   {
     uint64_t arcs = h->num_arcs;
     for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
-    const uint64_t items = arcs / (uint64_t(h->tune.bin_block) + 1) + 64;
+    // (one region per sub-step class: the persistent kernel lays out all
+    // classes at the start of an iteration)
+    const uint64_t items = (arcs / (uint64_t(h->tune.bin_block) + 1) + 64 + 1) * kMaxSubsteps;
     const bool any = ma.max_deg > h->tune.bin_block;
     const uint64_t tab = any ? 4 * arcs + 64 * items : 0;
     const uint64_t lst = any ? arcs + 64 : 0;
@@ -1428,6 +1781,8 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
   a.gtable = need_gtable ? h->gtable : nullptr;
   a.gslots = gslots;
   a.bigmv = h->bigmv;
+  a.movers = &h->ctrl->movers;
+  a.nbig = &h->ctrl->big_movers;
   if (h->ngraphs) {
     a.ngraphs = h->ngraphs;
     a.goff = h->d_goff;
@@ -1436,7 +1791,8 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
     a.gS = h->d_gS;
   }
   *gdo = GiantDecide{h->g_toff, h->g_loff, h->g_cpre, h->g_ndist, h->g_done, h->g_hd,
-                     static_cast<GiantRes*>(h->g_res), h->g_tkeys, h->g_tvals, h->g_tlist, nullptr};
+                     static_cast<GiantRes*>(h->g_res), h->g_tkeys, h->g_tvals, h->g_tlist, nullptr,
+                     nullptr};
   return DFL_OK;
 }
 
@@ -1461,12 +1817,14 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   if (G) DFL_TRY(group_upload_flags(h, h->d_gdone, h->h_gdone));
   // graph replay of the iterations needs stable buffers (the base graph) and
   // a capturable (non-default) stream
-  const bool use_graph = ma.g.off == h->off && h->stream != nullptr &&
+  const uint32_t pgrid = (h->opt.flags & DFL_FLAG_PERSISTENT) ? persistent_grid() : 0u;
+  const bool use_persistent = pgrid >= kMaxSubsteps;
+  const bool use_graph = !use_persistent && ma.g.off == h->off && h->stream != nullptr &&
                          !(h->opt.flags & DFL_FLAG_NO_GRAPH);
   unsigned int cur_count[kMaxSubsteps][kBins];
   unsigned long long skipped = 0;
   bool have_counts = false;
-  if (!use_graph) {
+  if (!use_graph && !use_persistent) {
     DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
     if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
     for (uint32_t s = 0; s < kMaxSubsteps; ++s)
@@ -1491,6 +1849,8 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
       DFL_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
       h->launches += g.kernels;
       for (int q = 0; q < DFL_PROF_CLASSES; ++q) h->prof.launches[q] += g.class_launches[q];
+    } else if (use_persistent) {
+      DFL_TRY(issue_persistent(h, a, cur, gd, pgrid));
     } else {
       DFL_TRY(issue_iteration(h, a, cur, cur_count, gd));
     }
@@ -1499,8 +1859,18 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
                                   cudaMemcpyDeviceToHost, h->stream));
     DFL_TRY(read_ctrl(h));
     const Ctrl& c = *h->hctrl;
+    if (c.err & kErrTimeout) return set_error(h, DFL_ERR_TIMEOUT, "grid barrier of the iteration kernel gave up");
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
-    if (use_graph) {
+    if (use_persistent) {
+      if (it == 1) {
+        skipped = c.skipped;
+        if (initial) {
+          *initial = skipped;
+          for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+            for (int b = 0; b < kBins; ++b) *initial += c.count[0][s][b];
+        }
+      }
+    } else if (use_graph) {
       for (const auto& ev : graph_used[cur]->evs) {  // harvest this replay's timings
         float ms = 0;
         if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) h->prof.ms[ev.cls] += ms;

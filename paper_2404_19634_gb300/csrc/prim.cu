@@ -313,45 +313,11 @@ __global__ void k_popcount(const uint32_t* bits, uint32_t words, unsigned long l
 
 }  // namespace
 
-// Frontier lists from a bitmap, one bitmap word per thread: a block counts
-// its vertices per list key in shared memory, reserves each key's range with
-// one global atomic, then writes (so a dense frontier does not funnel every
-// vertex through the few global list counters).
 __global__ void __launch_bounds__(256) k_lists_bits(const uint32_t* __restrict__ bits, uint32_t words,
                                                     uint32_t nv, const uint32_t* __restrict__ deg,
                                                     uint32_t* lists, Segs seg, Ctrl* ctrl, int buf,
                                                     uint32_t k) {
-  __shared__ uint32_t s_cnt[kMaxSubsteps * kBins];
-  __shared__ uint32_t s_base[kMaxSubsteps * kBins];
-  const uint32_t nkeys = k * kBins;
-  for (uint64_t w0 = blockIdx.x * uint64_t(blockDim.x); w0 < words; w0 += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t w = w0 + threadIdx.x;
-    const uint32_t word = w < words ? bits[w] : 0u;
-    if (!__syncthreads_or(word != 0u)) continue;  // block-uniform: no vertex in this tile
-    if (threadIdx.x < nkeys) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    for (uint32_t x = word; x; x &= x - 1) {
-      const uint32_t v = uint32_t(w * 32 + __ffs(x) - 1);
-      if (v >= nv) break;
-      atomicAdd(&s_cnt[vertex_class(v, k, seg) * kBins + degree_bin(deg[v], seg)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < nkeys) {
-      const uint32_t c = s_cnt[threadIdx.x];
-      s_base[threadIdx.x] = c ? atomicAdd(&ctrl->count[buf][threadIdx.x / kBins][threadIdx.x % kBins], c) : 0u;
-      s_cnt[threadIdx.x] = 0;
-    }
-    __syncthreads();
-    for (uint32_t x = word; x; x &= x - 1) {
-      const uint32_t v = uint32_t(w * 32 + __ffs(x) - 1);
-      if (v >= nv) break;
-      const uint32_t key = vertex_class(v, k, seg) * kBins + degree_bin(deg[v], seg);
-      const uint32_t r = s_base[key] + atomicAdd(&s_cnt[key], 1u);
-      if (r < seg.cap[key]) lists[seg.off[key] + r] = v;
-      else atomicOr(&ctrl->err, kErrInternal);
-    }
-    __syncthreads();
-  }
+  lists_bits_body(bits, words, nv, deg, lists, seg, ctrl, buf, k);
 }
 
 // Segment layout for k sub-step classes: class s gets kBins segments, each
