@@ -49,6 +49,13 @@ EDGES = 33_554_432
 GRAPH_SEED = 2
 BATCH_SEED = 200
 BATCH_FRAC = 1e-3
+# DRAM bytes (read + write) of the decide kernels of one sub-step's decide
+# phase on the default workload (R-MAT 2^22, 1e-3|E| batches), from a
+# single-pass ncu capture of the timed DF steps: cold (ncu's default, caches
+# flushed before each launch) and warm (--cache-control none).  They belong
+# to the decide kernels as they stand; other workloads report null.
+DECIDE_TRAFFIC_COLD = 53.44e6
+DECIDE_TRAFFIC_WARM = 19.50e6
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
 SERVE_SCALES = [18, 19, 19, 20, 21, 22, 22, 23]
@@ -76,6 +83,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=0.5,
                    help="length of the Poisson arrival window")
     p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
+    p.add_argument("--persistent", action="store_true",
+                   help="run each local-moving iteration as one cooperative launch (DFL_FLAG_PERSISTENT)")
     p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
     p.add_argument("--group-max-n", type=float, default=1e6)
     return p.parse_args()
@@ -217,7 +226,8 @@ def gpu_arm(args):
     # (a CUDA graph) only on a non-default stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    opt = dfl.default_options(flags=dfl.FLAG_PROFILE)
+    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
+    opt = dfl.default_options(flags=dfl.FLAG_PROFILE | pflag)
     h = dfl.Dfl(g.n, off, idx, w, options=opt, stream=stream)
     torch.cuda.synchronize()
     # static Louvain (the paper's comparator), timed on its own
@@ -284,8 +294,12 @@ def gpu_arm(args):
     peak, peak_kind = peaks()
     mv = prof["move"]
     achieved = (mv["bytes"] / 1e9) / (mv["ms"] / 1e3) if mv["ms"] > 0 else 0.0
+    default_workload = args.scale == SCALE and args.edges == EDGES
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "local-move decide",
+                "frac": achieved / peak,
+                "traffic": DECIDE_TRAFFIC_COLD if default_workload else None,
+                "traffic_warm": DECIDE_TRAFFIC_WARM if default_workload else None,
+                "kernel": "local-move decide",
                 "peak_kind": peak_kind, "bytes_per_step": mv["bytes"] / args.steps,
                 "kernel_ms_per_step": mv["ms"] / args.steps,
                 "launches_per_step": mv["launches"] / args.steps}
@@ -334,7 +348,7 @@ def gpu_arm(args):
         e2e_batches = [bstream.next(size) for _ in range(args.steps)]
         pin_d = [torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory() for d, _ in e2e_batches]
         pin_i = [torch.from_numpy(np.ascontiguousarray(i).view(np.int32)).pin_memory() for _, i in e2e_batches]
-        h.set_options(dfl.default_options())
+        h.set_options(dfl.default_options(flags=pflag))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
@@ -366,6 +380,7 @@ def gpu_arm(args):
                        "graph": f"R-MAT a=.57 b=.19 c=.19, 2^{args.scale} vertices, {g.m:,} edges, unit weights",
                        "batch_edges": size, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
                        "static_ms": round(static_ms, 3), "static_passes": static_stats["iterations"],
                        "static_move_gbs": round(static_gbs, 1) if static_gbs else None,
                        "df_ms_by_batch_fraction": extra or None,
@@ -416,7 +431,8 @@ def group_arm(args):
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
 
     # one group handle: batches of all graphs in one device array each
-    grp = dfl.DflGroup(csrs, stream=stream)
+    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
+    grp = dfl.DflGroup(csrs, options=dfl.default_options(flags=pflag), stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -460,7 +476,8 @@ def group_arm(args):
     passes = [grp.graph_stats(g)["passes"] for g in range(G)]
 
     # the same graphs and batches, one handle per graph, one after another
-    hs = [dfl.Dfl(n, off, idx, w, stream=stream) for n, off, idx, w in csrs]
+    hs = [dfl.Dfl(n, off, idx, w, options=dfl.default_options(flags=pflag), stream=stream)
+          for n, off, idx, w in csrs]
     t0 = time.perf_counter()
     for h in hs:
         h.static()
@@ -512,6 +529,7 @@ def group_arm(args):
                    "vertices": sum(g.n for g in graphs), "edges": sum(g.m for g in graphs),
                    "batch_edges_per_step": sum(d.shape[0] + i.shape[0] for d, i in batches[0]),
                    "l2": "flushed between timed steps (256 MB write)", "generation_s": round(gen_s, 1),
+                   "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
                    "group_static_ms": round(group_static_ms, 2),
                    "serial_static_ms": round(serial_static_ms, 2),
                    "passes_min_max": [min(passes), max(passes)]},

@@ -28,6 +28,9 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 ND, DS, DF = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_PROFILE = 1
+FLAG_NO_GRAPH = 4
+FLAG_SERIAL_BINS = 8
+FLAG_PERSISTENT = 16
 PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other", "bin0", "bin1", "bin2",
               "bin3"]
 PROF_APPLY, PROF_MARK, PROF_MOVE, PROF_COMMIT, PROF_AGG, PROF_OTHER = range(6)

@@ -318,45 +318,75 @@ __global__ void __launch_bounds__(256) k_agg_giant_accum(AggArgs a, GiantArgs gi
 }
 
 // The queued high-degree members of giant communities: their rows in pieces
-// of kAggPiece arcs dealt over the blocks (each block sweeps the short queue
-// to find its pieces); a piece is aggregated in shared memory and added to
-// the community's global table.
-__global__ void __launch_bounds__(256) k_agg_big(AggArgs a, GiantArgs gi) {
+// of kAggPiece arcs dealt over the blocks; a piece is aggregated in shared
+// memory and added to the community's global table.  The queue is swept in
+// tiles of one block's threads (a block-wide prefix numbers the pieces of a
+// tile, dealt round-robin), so a long queue costs each block one parallel
+// pass per tile rather than a dependent walk over every entry.
+constexpr int kAggBigThreads = 256;
+
+__global__ void __launch_bounds__(kAggBigThreads) k_agg_big(AggArgs a, GiantArgs gi) {
   __shared__ uint32_t keys[kGiantSlots];
   __shared__ uint32_t vals[kGiantSlots];
+  __shared__ uint32_t s_pre[kAggBigThreads + 1];
+  __shared__ uint32_t s_w[kAggBigThreads / 32];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint32_t count = *a.nbig;
   bool ok = true;
-  uint64_t item0 = 0;
-  for (uint32_t q = 0; q < count; ++q) {
-    const uint2 e = a.bigq[q];
-    const uint32_t v = e.x, g = e.y;
-    const uint32_t dv = a.g.deg[v];
-    const unsigned long long o = a.g.off[v];
-    const uint64_t npc = (dv + kAggPiece - 1) / kAggPiece;
-    const uint32_t gs = gi.gsize[g];
-    uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
-    uint32_t* gvals = gkeys + gs;
-    for (uint64_t pc = (blockIdx.x + gridDim.x - item0 % gridDim.x) % gridDim.x; pc < npc; pc += gridDim.x) {
-      const uint32_t k0 = uint32_t(pc * kAggPiece), k1 = min(dv, k0 + kAggPiece);
-      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+  uint64_t ibase = 0;  // pieces of the earlier tiles
+  for (uint32_t q0 = 0; q0 < count; q0 += kAggBigThreads) {
+    const uint32_t q = q0 + threadIdx.x;
+    const uint32_t npc = q < count ? (a.g.deg[a.bigq[q].x] + kAggPiece - 1) / kAggPiece : 0u;
+    uint32_t x = npc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= uint32_t(o)) x += y;
+    }
+    if (lane == 31) s_w[wib] = x;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (uint32_t k = 0; k < wib; ++k) wbase += s_w[k];
+    s_pre[threadIdx.x + 1] = wbase + x;
+    if (threadIdx.x == 0) s_pre[0] = 0;
+    __syncthreads();
+    const uint32_t tile_items = s_pre[kAggBigThreads];
+    // piece `it` of the tile is item ibase + it, handled by block (ibase + it) mod grid
+    for (uint32_t it = uint32_t((blockIdx.x + gridDim.x - ibase % gridDim.x) % gridDim.x); it < tile_items;
+         it += gridDim.x) {
+      uint32_t lo = 0, hi = kAggBigThreads;  // tile position owning piece `it`
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_pre[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      const uint2 e = a.bigq[q0 + lo];
+      const uint32_t v = e.x, g = e.y;
+      const uint32_t dv = a.g.deg[v];
+      const unsigned long long o = a.g.off[v];
+      const uint32_t gs = gi.gsize[g];
+      uint32_t* gkeys = reinterpret_cast<uint32_t*>(a.gtable + gi.gtab[g]);
+      uint32_t* gvals = gkeys + gs;
+      const uint32_t k0 = (it - s_pre[lo]) * kAggPiece, k1 = min(dv, k0 + kAggPiece);
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kAggBigThreads) {
         keys[s] = kEmpty;
         vals[s] = 0;
       }
       __syncthreads();
-      for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      for (uint32_t k = k0 + threadIdx.x; k < k1; k += kAggBigThreads) {
         const uint2 arc = a.g.arcs[o + k];
         if (!arc.y) continue;  // deleted arc
         const uint32_t c = a.Cp[arc.x];
         if (!agg_add(keys, vals, kGiantSlots - 1, c, arc.y, 32)) ok &= agg_add(gkeys, gvals, gs - 1, c, arc.y, gs);
       }
       __syncthreads();
-      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += blockDim.x) {
+      for (uint32_t s = threadIdx.x; s < kGiantSlots; s += kAggBigThreads) {
         const uint32_t c = keys[s];
         if (c != kEmpty) ok &= agg_add(gkeys, gvals, gs - 1, c, vals[s], gs);
       }
       __syncthreads();
     }
-    item0 += npc;
+    ibase += tile_items;
+    __syncthreads();  // s_pre and s_w are rewritten by the next tile
   }
   if (!ok) atomicOr(&a.ctrl->err, kErrInternal);
 }
@@ -593,7 +623,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     }
     {
       LaunchScope ls(h, DFL_PROF_AGG);
-      k_agg_big<<<152 * 4, 256, 0, h->stream>>>(a, gi);
+      k_agg_big<<<152 * 4, kAggBigThreads, 0, h->stream>>>(a, gi);
       DFL_TRY(check_launch(h, "giant members"));
     }
     {

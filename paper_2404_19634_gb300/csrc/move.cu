@@ -1168,7 +1168,8 @@ uint32_t next_pow2(uint64_t x) {
 // sub-step launches, stream forks and joins of issue_iteration.
 // ---------------------------------------------------------------------------
 constexpr int kIterThreads = 256;
-constexpr uint32_t kIterDynWords = 2 * kBlockSlots + kGiantListSmem;  // tables + chunk prefix cache
+constexpr uint32_t kIterPreCache = kGiantListSmem;                   // chunk prefix cached in shared memory
+constexpr uint32_t kIterDynWords = 2 * kBlockSlots + kIterPreCache;  // tables + chunk prefix cache
 constexpr unsigned long long kBarrierPolls = 1ull << 22;             // x 256 ns: about a second
 // vertices per warp in one work unit of bins 1 and 0 (rounds of 1 and of
 // 32 / W vertices); larger units save counter updates on big frontiers but
@@ -1268,6 +1269,8 @@ static_assert(kIterDynWords >= 2 * kBlockSlots && 8 * 2 * kWarpSlots <= 2 * kBlo
                   2 * kGiantSlots + 2 * kGiantChunk <= 2 * kBlockSlots,
               "the dynamic tables hold every unit kind");
 
+// two blocks per SM: 128 registers a thread (three blocks, at 80 registers,
+// spilled and measured slower)
 __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
   extern __shared__ uint32_t dyn[];
   __shared__ BlockScratch sc;
@@ -1298,7 +1301,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
     const uint32_t G = *gd.nitems;
     // chunk prefix of the class, cached when it fits
     const uint32_t* cp = gd.cpre;
-    if (n3 + 1 <= kGiantListSmem) {
+    if (n3 + 1 <= kIterPreCache) {
       for (uint32_t q = threadIdx.x; q <= n3; q += blockDim.x) pre_cache[q] = gd.cpre[q];
       __syncthreads();
       cp = pre_cache;
