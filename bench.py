@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=0.5,
                    help="length of the Poisson arrival window")
     p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
+    p.add_argument("--temporal", action="store_true",
+                   help="measure DF on the temporal stream (sliding-window batches)")
     p.add_argument("--persistent", action="store_true",
                    help="run each local-moving iteration as one cooperative launch (DFL_FLAG_PERSISTENT)")
     p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
@@ -543,6 +545,93 @@ def group_arm(args):
     print(json.dumps(line), flush=True)
 
 
+TEMPORAL_N = 2_000_000
+TEMPORAL_STEPS = 30_000_000
+TEMPORAL_METRIC = "ms/batch DF update, temporal PA stream (2M vertices, 30M interactions), sliding window"
+
+
+def temporal_arm(args):
+    """The temporal workload: base = the first 90% of the stream (weight =
+    multiplicity, tau_agg = 1), then consecutive sliding-window batches of
+    1e-5 and 1e-4 x interactions (insert the next ones, expire as many of the
+    oldest), each applied and updated with DF."""
+    import torch
+
+    import paper_2404_19634_gb300 as dfl
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dfl.build()
+    t0 = time.perf_counter()
+    src, dst = synth.temporal_pa_stream_vec(TEMPORAL_N, TEMPORAL_STEPS, 0.3, 3)
+    base_end = TEMPORAL_STEPS * 9 // 10
+    g = synth.temporal_edges(src[:base_end], dst[:base_end], TEMPORAL_N)
+    off, idx, w = synth.to_csr(g)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
+    h = dfl.Dfl(g.n, off, idx, w, options=dfl.default_options(tau_agg=1.0, flags=pflag), stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.static()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    static_ms = e0.elapsed_time(e1)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    start, end = 0, base_end
+    by_size = {}
+    launches = 0
+    clocks = Clocks(0)
+    for frac in (1e-5, 1e-4):
+        size = int(round(frac * TEMPORAL_STEPS))
+        batches = []
+        for _ in range(args.warmup + args.steps):
+            batches.append(synth.window_batch(src, dst, start, end, size))
+            start += size
+            end += size
+        dbatches = [(to_dev(d), to_dev(i)) for d, i in batches]
+        ms = []
+        for k, (d, i) in enumerate(dbatches):
+            timed = k >= args.warmup
+            if k == args.warmup:
+                l0 = h.stats()["kernel_launches"]
+                if frac == 1e-4:
+                    clocks.__enter__()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.apply_batch(d, i)
+            h.update(dfl.DF)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if timed:
+                ms.append(a.elapsed_time(b))
+        launches += h.stats()["kernel_launches"] - l0
+        by_size[f"{frac:g}"] = {"batch_interactions": size, "ms_mean": round(statistics.mean(ms), 4),
+                                "ms_median": round(statistics.median(ms), 4)}
+    clocks.__exit__(None, None, None)
+    h.close()
+    value = by_size["0.0001"]["ms_mean"]
+    line = {
+        "metric": TEMPORAL_METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"temporal PA stream, {TEMPORAL_N:,} vertices, {TEMPORAL_STEPS:,} interactions "
+                               "(30% repeats), base = first 90%, window batches of 1e-4 x interactions",
+                   "base_edges": g.m, "tau_agg": 1.0, "generation_s": round(gen_s, 1),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
+                   "static_ms": round(static_ms, 2), "df_by_batch_fraction": by_size},
+        "e2e": None,
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _serve_graph(k):
     g = synth.rmat(SERVE_SCALES[k], 8 << SERVE_SCALES[k], 300 + k)
     return g, (g.n, *synth.to_csr(g))
@@ -631,6 +720,9 @@ def main():
         return
     if args.group:
         group_arm(args)
+        return
+    if args.temporal:
+        temporal_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -315,9 +315,82 @@ def temporal_pa_stream(n: int, steps: int, p_repeat: float, seed: int):
     return src, dst
 
 
+def _temporal_draws(n: int, steps: int, p_repeat: float, seed: int, vertex_weight: int | None):
+    """The random choices of temporal_pa_stream_vec, one entry per step:
+    (direct source, repeat flag, repeated step, urn position of the target,
+    vertices arrived, vertex weight in the urn)."""
+    rng = np.random.default_rng(seed)
+    T = int(steps)
+    gap = max(1, T // n)
+    delta = int(vertex_weight) if vertex_weight else max(1, (2 * T) // n)
+    t = np.arange(T, dtype=np.int64)
+    arrived = np.minimum(n, t // gap + 2)
+    newest = t // gap + 1                      # vertex arriving at step t (if any)
+    is_arrival = (t % gap == 0) & (newest < n)
+    src_direct = np.where(is_arrival, newest, (rng.random(T) * arrived).astype(np.int64))
+    repeat = (rng.random(T) < p_repeat) & ~is_arrival & (t > 0)
+    s_rep = (rng.random(T) * t).astype(np.int64)          # earlier step repeated (t >= 1)
+    r = (rng.random(T) * (delta * arrived + 2 * t)).astype(np.int64)  # urn position of the target
+    return src_direct, repeat, s_rep, r, arrived, delta
+
+
+def temporal_pa_stream_vec(n: int, steps: int, p_repeat: float, seed: int, vertex_weight: int | None = None):
+    """Temporal preferential-attachment interaction stream for large sizes
+    (tens of millions of steps), generated with array operations.
+
+    Vertices 0 and 1 arrive at step 0 and vertex k >= 2 at step
+    (k - 1) * gap, gap = max(1, steps // n).  At each step t:
+      - on vertex k's arrival step the newcomer k is the source and draws a
+        target; at t = 0 the source is vertex 1;
+      - otherwise, with probability p_repeat, an earlier interaction chosen
+        uniformly among steps [0, t) repeats (its source and target);
+      - otherwise a uniformly chosen arrived vertex is the source and draws
+        a target.
+    A target is drawn uniformly from the urn holding each arrived vertex
+    `vertex_weight` times (default: the mean number of interactions per
+    vertex, 2 * steps / n) plus both endpoints of every earlier step, i.e.
+    with probability proportional to (interactions so far + vertex_weight).
+    With weight 1 and arrivals rare against interactions the urn condenses:
+    the first vertices end up holding a fixed fraction of all interactions;
+    a weight near the mean degree gives a heavy tail instead (largest
+    degree about 32,000 interactions at 2 million vertices and 30 million
+    steps).  An urn entry that is the endpoint of an earlier step is a
+    pointer to that step's value; pointers always lead to earlier steps, so
+    all values are resolved by pointer jumping.  A draw that lands on the
+    source itself yields a self pair, which the stream keeps and the graph
+    builders drop.  Returns (src, dst) uint32 arrays of length `steps`, in
+    time order."""
+    T = int(steps)
+    src_direct, repeat, s_rep, r, arrived, delta = _temporal_draws(n, T, p_repeat, seed, vertex_weight)
+    # slots 2t (source of step t) and 2t + 1 (target): a direct vertex id
+    # (ptr < 0) or a pointer to an earlier slot
+    ptr = np.full(2 * T, -1, np.int64)
+    val = np.zeros(2 * T, np.int64)
+    val[0::2] = src_direct
+    ptr[0::2] = np.where(repeat, 2 * s_rep, -1)
+    on_vertex = r < delta * arrived
+    ptr[1::2] = np.where(repeat, 2 * s_rep + 1, np.where(on_vertex, -1, r - delta * arrived))
+    val[1::2] = np.where(on_vertex, r // delta, 0)
+    del src_direct, repeat, s_rep, r, arrived, on_vertex
+    todo = np.flatnonzero(ptr >= 0)
+    while todo.size:
+        p = ptr[todo]
+        pp = ptr[p]                            # read before this round's writes
+        ready = pp < 0
+        done_idx = todo[ready]
+        val[done_idx] = val[p[ready]]
+        ptr[done_idx] = -1
+        wait = todo[~ready]
+        ptr[wait] = pp[~ready]                 # jump
+        todo = wait
+    return val[0::2].astype(np.uint32), val[1::2].astype(np.uint32)
+
+
 def temporal_edges(src: np.ndarray, dst: np.ndarray, n: int) -> EdgeList:
     """Collapse a temporal interaction list into an undirected weighted graph
-    (weight = multiplicity of the pair)."""
+    (weight = multiplicity of the pair); self pairs are dropped."""
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
     lo = np.minimum(src, dst).astype(np.uint64)
     hi = np.maximum(src, dst).astype(np.uint64)
     key = (lo << np.uint64(32)) | hi
@@ -325,6 +398,24 @@ def temporal_edges(src: np.ndarray, dst: np.ndarray, n: int) -> EdgeList:
     u = (uk >> np.uint64(32)).astype(np.uint32)
     v = (uk & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     return EdgeList(n, u, v, cnt.astype(np.uint32))
+
+
+def window_batch(src: np.ndarray, dst: np.ndarray, start: int, end: int, size: int):
+    """One sliding-window batch of a temporal stream whose window holds
+    interactions [start, end): insert interactions [end, end + size) with
+    weight 1 each, expire the `size` oldest, [start, start + size), as
+    deletions of one unit per interaction grouped by pair.  Self pairs are
+    dropped on both sides.  Returns (deletions, insertions) as (k, 3) uint32
+    arrays of (u, v, w)."""
+    ins = np.stack([src[end:end + size], dst[end:end + size], np.ones(size, np.uint32)], 1)
+    ins = ins[ins[:, 0] != ins[:, 1]]
+    s, d = src[start:start + size], dst[start:start + size]
+    keep = s != d
+    lo, hi = np.minimum(s[keep], d[keep]), np.maximum(s[keep], d[keep])
+    key, cnt = np.unique((lo.astype(np.uint64) << np.uint64(32)) | hi, return_counts=True)
+    dels = np.stack([(key >> np.uint64(32)).astype(np.uint32), (key & np.uint64(0xFFFFFFFF)).astype(np.uint32),
+                     cnt.astype(np.uint32)], 1)
+    return dels, ins
 
 
 def graph_stats(g: EdgeList) -> dict:

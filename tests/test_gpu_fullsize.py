@@ -50,3 +50,52 @@ def test_rmat22_static_and_df_batches_match_oracle():
         b.update(oracle.DF)
         check()
     assert a.num_arcs() == int(b.graph()[0][-1])
+
+
+def test_temporal_stream_2m_vertices_matches_oracle():
+    """Temporal workload at full size: 2,000,000 vertices, 30,000,000
+    preferential-attachment interactions with 30% repeats; the first 90% form
+    the base graph (multiplicity = weight, tau_agg = 1 as for the paper's
+    temporal graphs), then batches of 1e-5 and 1e-4 x 30M insertions with as
+    many expiries of the oldest interactions, each updated with DF."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    import paper_2404_19634_gb300 as dfl
+    dfl.build()
+    oracle.build()
+    n, steps = 2_000_000, 30_000_000
+    src, dst = synth.temporal_pa_stream_vec(n, steps, 0.3, 3)
+    base_end = steps * 9 // 10
+    g = synth.temporal_edges(src[:base_end], dst[:base_end], n)
+    off, idx, w = synth.to_csr(g)
+    s = torch.cuda.Stream()
+    a = dfl.Dfl(g.n, off, idx, w, options=dfl.default_options(tau_agg=1.0), stream=s)
+    b = oracle.Oracle(g.n, off, idx, w)
+    b.set_options(tau_agg=1.0)
+    a.static()
+    b.static()
+
+    def check():
+        assert np.array_equal(a.membership(), b.membership())
+        Ka, Sa, ma = a.weights()
+        Kb, Sb, mb = b.weights()
+        assert ma == mb and np.array_equal(Ka, Kb) and np.array_equal(Sa, Sb)
+        qa, na, da = a.modularity()
+        qb, nb, db = b.modularity()
+        assert (na, da) == (nb, db) and abs(qa - qb) <= 1e-12
+        assert a.trace() == b.trace()
+        assert a.stats()["iterations"] == b.stats()["iterations"]
+
+    check()
+    start, end = 0, base_end
+    for size in (300, 3000, 300, 3000):
+        dels, ins = synth.window_batch(src, dst, start, end, size)
+        start += size
+        end += size
+        assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+        a.update(dfl.DF)
+        b.update(oracle.DF)
+        check()
+    assert a.num_arcs() == int(b.graph()[0][-1])
