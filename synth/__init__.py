@@ -514,6 +514,16 @@ def planted_group_params(count: int, n_lo: float, n_hi: float, seed: int):
     return out
 
 
+def planted_group_member(k: int, count: int, n_lo: float, n_hi: float, seed: int, mean_degree: float = 16.0,
+                         w_max: int = 16):
+    """Graph k of `planted_group(count, n_lo, n_hi, seed)` alone, with its
+    CSR: (EdgeList, (n, offsets, indices, weights)).  A module-level function,
+    so that worker processes can build the graphs of a group in parallel."""
+    n, blocks, mu, gseed = planted_group_params(count, n_lo, n_hi, seed)[k]
+    g = planted_partition(n, blocks, mu, mean_degree, w_max, gseed)
+    return g, (g.n, *to_csr(g))
+
+
 def planted_group(count: int, n_lo: float, n_hi: float, seed: int, mean_degree: float = 16.0,
                   w_max: int = 16):
     """Independent planted-partition graphs of uneven size (parameters from

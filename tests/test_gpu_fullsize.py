@@ -99,3 +99,50 @@ def test_temporal_stream_2m_vertices_matches_oracle():
         b.update(oracle.DF)
         check()
     assert a.num_arcs() == int(b.graph()[0][-1])
+
+
+def test_group_64_graphs_sampled_against_oracle():
+    """The batched workload at full size: 64 planted-partition graphs (n
+    log-uniform in [1e4, 1e6], 15.7 M vertices in total) in one group, static
+    Louvain, then one DF step with a 1e-4 x |E_g| batch per graph.  The oracle
+    runs four of the graphs alone (the smallest, the largest and two between);
+    each must match exactly, including its pass and iteration counts."""
+    import multiprocessing as mp
+    import os
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    import paper_2404_19634_gb300 as dfl
+    dfl.build()
+    oracle.build()
+    G = 64
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        made = pool.starmap(synth.planted_group_member, [(k, G, 1e4, 1e6, 4) for k in range(G)])
+    graphs = [g for g, _ in made]
+    csrs = [c for _, c in made]
+    s = torch.cuda.Stream()
+    grp = dfl.DflGroup(csrs, stream=s)
+    grp.static()
+    streams = [synth.BatchStream(g, 500 + k) for k, g in enumerate(graphs)]
+    batches = [st.next(max(1, int(round(1e-4 * g.m))), w_max=16) for st, g in zip(streams, graphs)]
+    grp.apply_batches([b[0] for b in batches], [b[1] for b in batches])
+    grp.update(dfl.DF)
+    K, S, _ = grp.weights()
+    starts = np.concatenate([[0], np.cumsum([g.n for g in graphs])])
+    order = np.argsort([g.n for g in graphs])
+    for k in (order[0], order[G // 3], order[2 * G // 3], order[-1]):
+        n, off, idx, w = csrs[k]
+        o = oracle.Oracle(n, off, idx, w)
+        o.static()
+        assert o.apply_batch(*batches[k]) == 0
+        o.update(oracle.DF)
+        assert np.array_equal(grp.graph_membership(k), o.membership()), f"graph {k}: membership"
+        Ko, So, _ = o.weights()
+        assert np.array_equal(K[starts[k]:starts[k + 1]], Ko) and np.array_equal(S[starts[k]:starts[k + 1]], So)
+        q, num, den = grp.graph_modularity(k)
+        qo, numo, deno = o.modularity()
+        assert (num, den) == (numo, deno) and abs(q - qo) <= 1e-12
+        so, sg = o.stats(), grp.graph_stats(k)
+        assert sg["passes"] == so["passes"] and sg["iterations"] == so["iterations"]
