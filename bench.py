@@ -85,11 +85,21 @@ def parse():
     p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
     p.add_argument("--temporal", action="store_true",
                    help="measure DF on the temporal stream (sliding-window batches)")
-    p.add_argument("--persistent", action="store_true",
-                   help="run each local-moving iteration as one cooperative launch (DFL_FLAG_PERSISTENT)")
+    p.add_argument("--launch", default="host", choices=["host", "graph", "persistent"],
+                   help="how a local-moving iteration is launched: kernels from the host (default), "
+                        "a replayed CUDA graph (DFL_FLAG_GRAPH) or one cooperative kernel "
+                        "(DFL_FLAG_PERSISTENT)")
     p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
     p.add_argument("--group-max-n", type=float, default=1e6)
     return p.parse_args()
+
+
+LAUNCH_DESC = {"host": "per-bin kernels launched from the host", "graph": "per-bin kernels, graph replay",
+               "persistent": "one cooperative kernel per iteration"}
+
+
+def launch_flag(dfl, args):
+    return {"host": 0, "graph": dfl.FLAG_GRAPH, "persistent": dfl.FLAG_PERSISTENT}[args.launch]
 
 
 def peaks():
@@ -224,12 +234,13 @@ def gpu_arm(args):
     dfl.build()
     g, off, idx, w = make_workload(args, rank)
     size = batch_size(g, BATCH_FRAC)
-    # a side stream: the library replays its captured local-moving iteration
-    # (a CUDA graph) only on a non-default stream
+    # a side stream (graph replay, when chosen, needs a non-default stream)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
-    opt = dfl.default_options(flags=dfl.FLAG_PROFILE | pflag)
+    pflag = launch_flag(dfl, args)
+    # the timed runs time only the decide phase (two events per sub-step):
+    # the roofline's kernel duration
+    opt = dfl.default_options(flags=dfl.FLAG_PROFILE_MOVE | pflag)
     h = dfl.Dfl(g.n, off, idx, w, options=opt, stream=stream)
     torch.cuda.synchronize()
     # static Louvain (the paper's comparator), timed on its own
@@ -305,7 +316,7 @@ def gpu_arm(args):
                 "peak_kind": peak_kind, "bytes_per_step": mv["bytes"] / args.steps,
                 "kernel_ms_per_step": mv["ms"] / args.steps,
                 "launches_per_step": mv["launches"] / args.steps}
-    kernel_share = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()}
+    kernel_share = None
 
     extra = {}
     if not args.profile_only and not args.no_sizes and rank == 0:
@@ -341,6 +352,17 @@ def gpu_arm(args):
         extra["nd_move_gbs"] = round((nd_prof["bytes"] / 1e9) / (nd_prof["ms"] / 1e3), 1) if nd_prof["ms"] else None
     static_move = static_prof["move"]
     static_gbs = (static_move["bytes"] / 1e9) / (static_move["ms"] / 1e3) if static_move["ms"] else None
+    # every kernel class timed (more events, so separate from the timed steps)
+    if rank == 0:
+        h.set_options(dfl.default_options(flags=dfl.FLAG_PROFILE | pflag))
+        h.profile(reset=True)
+        nprof = 5
+        for _ in range(nprof):
+            d, i = bstream.next(size)
+            h.apply_batch(to_dev(d), to_dev(i))
+            h.update(dfl.DF)
+        torch.cuda.synchronize()
+        kernel_share = {k: round(v["ms"] / nprof, 4) for k, v in h.profile(reset=True).items()}
 
     # end to end through the public API with host buffers: pinned host batch in,
     # membership (4 bytes per vertex) out, every step
@@ -382,14 +404,14 @@ def gpu_arm(args):
                        "graph": f"R-MAT a=.57 b=.19 c=.19, 2^{args.scale} vertices, {g.m:,} edges, unit weights",
                        "batch_edges": size, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
+                       "iteration_launch": LAUNCH_DESC[args.launch],
                        "static_ms": round(static_ms, 3), "static_passes": static_stats["iterations"],
                        "static_move_gbs": round(static_gbs, 1) if static_gbs else None,
                        "df_ms_by_batch_fraction": extra or None,
                        "step_ms_median": round(statistics.median(step_ms), 4),
                        "graph_captures": h.stats()["graph_captures"],
                        "graph_capture_ms": round(h.stats()["graph_capture_ms"], 2),
-                       "kernel_ms_per_step": kernel_share},
+                       "kernel_ms_per_step_profiled": kernel_share},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -433,7 +455,7 @@ def group_arm(args):
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
 
     # one group handle: batches of all graphs in one device array each
-    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
+    pflag = launch_flag(dfl, args)
     grp = dfl.DflGroup(csrs, options=dfl.default_options(flags=pflag), stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -531,7 +553,7 @@ def group_arm(args):
                    "vertices": sum(g.n for g in graphs), "edges": sum(g.m for g in graphs),
                    "batch_edges_per_step": sum(d.shape[0] + i.shape[0] for d, i in batches[0]),
                    "l2": "flushed between timed steps (256 MB write)", "generation_s": round(gen_s, 1),
-                   "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
+                   "iteration_launch": LAUNCH_DESC[args.launch],
                    "group_static_ms": round(group_static_ms, 2),
                    "serial_static_ms": round(serial_static_ms, 2),
                    "passes_min_max": [min(passes), max(passes)]},
@@ -570,7 +592,7 @@ def temporal_arm(args):
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    pflag = dfl.FLAG_PERSISTENT if args.persistent else 0
+    pflag = launch_flag(dfl, args)
     h = dfl.Dfl(g.n, off, idx, w, options=dfl.default_options(tau_agg=1.0, flags=pflag), stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -623,7 +645,7 @@ def temporal_arm(args):
                                "(30% repeats), base = first 90%, window batches of 1e-4 x interactions",
                    "base_edges": g.m, "tau_agg": 1.0, "generation_s": round(gen_s, 1),
                    "l2": "flushed between timed steps (256 MB write)",
-                   "iteration_launch": "persistent" if args.persistent else "per-bin kernels, graph replay",
+                   "iteration_launch": LAUNCH_DESC[args.launch],
                    "static_ms": round(static_ms, 2), "df_by_batch_fraction": by_size},
         "e2e": None,
         "gpu_launches": int(launches),

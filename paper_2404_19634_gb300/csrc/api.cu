@@ -30,20 +30,23 @@ cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
   return cudaEventRecord(e, s);
 }
 
+cudaEvent_t take_event(Handle* h) {
+  cudaEvent_t e = nullptr;
+  if (!h->ev_free.empty()) {
+    e = h->ev_free.back();
+    h->ev_free.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    e = nullptr;
+  }
+  return e;
+}
+
 LaunchScope::LaunchScope(Handle* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
   h->launches++;
   h->prof.launches[cls]++;
-  if (h->opt.flags & DFL_FLAG_PROFILE) {
-    for (int k = 0; k < 2; ++k) {
-      cudaEvent_t e = nullptr;
-      if (!h->ev_free.empty()) {
-        e = h->ev_free.back();
-        h->ev_free.pop_back();
-      } else if (cudaEventCreate(&e) != cudaSuccess) {
-        e = nullptr;
-      }
-      (k ? b : a) = e;
-    }
+  if ((h->opt.flags & DFL_FLAG_PROFILE) || ((h->opt.flags & DFL_FLAG_PROFILE_MOVE) && cls == DFL_PROF_MOVE)) {
+    a = take_event(h);
+    b = take_event(h);
     if (a) record_timing_event(a, s);
   }
 }

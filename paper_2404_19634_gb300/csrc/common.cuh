@@ -353,6 +353,7 @@ struct LaunchScope {
 
 int check_launch(Handle* h, const char* what);
 cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s);
+cudaEvent_t take_event(Handle* h);  // a timing event from the handle's pool (nullptr if none)
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -267,9 +267,13 @@ __device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32
 
 // scanCommunities over arcs [k0, dg) of row o, lanes striding by `step`:
 // every lane adds its arc's weight under its neighbour's community (shared
-// memory atomics; grouping equal communities inside the warp first with
-// match/reduce was measured slower on this GPU when a warp holds many
-// communities).  Loads of kUnroll chunks are issued before use.
+// memory atomics).  Grouping equal communities inside the warp first was
+// measured slower on this GPU both ways tried: match/reduce when a warp
+// holds many communities, and ballot/shuffle rounds that sum the lanes of
+// the first pending lane's community (even for hubs whose thousands of arcs
+// lead to a few dozen communities, the DF decide phase on R-MAT 2^22 went
+// from 0.219 to 0.246-0.296 ms with 2-8 such rounds).  Loads of kUnroll
+// chunks are issued before use.
 template <int kUnroll>
 __device__ __forceinline__ bool scan_row(const DecideArgs& a, uint32_t i, unsigned long long o,
                                          uint32_t dg, uint32_t k0, uint32_t step, uint32_t* keys,
@@ -1417,10 +1421,10 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     for (int b = 0; b < kBins; ++b) nb += (!counts || counts[s][b]) ? 1 : 0;
     const bool any = nb > 0;
     cudaEvent_t pa = nullptr, pb = nullptr;  // wall time of the decide phase (profiling)
-    if (any && (h->opt.flags & DFL_FLAG_PROFILE)) {
-      cudaEventCreate(&pa);
-      cudaEventCreate(&pb);
-      record_timing_event(pa, h->stream);
+    if (any && (h->opt.flags & (DFL_FLAG_PROFILE | DFL_FLAG_PROFILE_MOVE))) {
+      pa = take_event(h);
+      pb = take_event(h);
+      if (pa) record_timing_event(pa, h->stream);
     }
     const bool forked = nb > 1 && !(h->opt.flags & DFL_FLAG_SERIAL_BINS);
     if (forked) DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -1476,6 +1480,9 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       record_timing_event(pb, h->stream);
       h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
       h->prof.launches[DFL_PROF_MOVE]++;
+    } else {
+      if (pa) h->ev_free.push_back(pa);
+      if (pb) h->ev_free.push_back(pb);
     }
     if (any && decide_only) {
       DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
@@ -1823,7 +1830,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   const uint32_t pgrid = (h->opt.flags & DFL_FLAG_PERSISTENT) ? persistent_grid() : 0u;
   const bool use_persistent = pgrid >= kMaxSubsteps;
   const bool use_graph = !use_persistent && ma.g.off == h->off && h->stream != nullptr &&
-                         !(h->opt.flags & DFL_FLAG_NO_GRAPH);
+                         (h->opt.flags & DFL_FLAG_GRAPH) && !(h->opt.flags & DFL_FLAG_NO_GRAPH);
   unsigned int cur_count[kMaxSubsteps][kBins];
   unsigned long long skipped = 0;
   bool have_counts = false;

@@ -1,7 +1,7 @@
 """Full-size parity on the benchmark workload: R-MAT with 2^22 vertices and
 33,554,432 edges, static Louvain, then DF updates of 1e-3 and 1e-5 x |E| edge
-batches, in the launch configuration the benchmark times (side stream, graph
-replay).  The oracle runs the same steps; membership, K, Sigma, 2m, modularity
+batches, in the launch configuration the benchmark times (side stream, host
+launches).  The oracle runs the same steps; membership, K, Sigma, 2m, modularity
 and the first-pass trace must match exactly.  About two minutes (most of it
 in the CPU oracle)."""
 import numpy as np

@@ -74,7 +74,7 @@ TUNINGS = [
 def test_tuning_same_results(dfl, orc, tuning, graph):
     g = synth.rmat(13, 8 << 13, 41)
     off, idx, w = synth.to_csr(g)
-    opt = dfl.default_options(flags=0 if graph else 4)
+    opt = dfl.default_options(flags=32 if graph else 4)
     a = dfl.Dfl(g.n, off, idx, w, options=opt, stream=_stream())
     a.set_tuning(**TUNINGS[tuning])
     assert a.tuning() == TUNINGS[tuning]
@@ -178,7 +178,7 @@ def same_group(grp, orcs):
 @pytest.mark.parametrize("graph", [True, False])
 def test_group_matches_each_graph_alone(dfl, orc, graph):
     gs = group_graphs()
-    grp, orcs = group_pair(dfl, orc, gs, flags=0 if graph else 4)
+    grp, orcs = group_pair(dfl, orc, gs, flags=32 if graph else 4)
     grp.static()
     for o in orcs:
         o.static()

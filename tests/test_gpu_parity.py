@@ -37,11 +37,12 @@ _STREAMS = []
 
 def pair(dfl, orc, g, substeps=4, tau_agg=0.8, graph=True, **kw):
     """GPU handle and oracle on the same graph.  The handle runs on a side
-    stream, which lets it replay its captured local-moving iteration; with
-    graph=False every kernel is launched from the host."""
+    stream; with graph=True it replays its captured local-moving iteration
+    (DFL_FLAG_GRAPH), with graph=False every kernel is launched from the
+    host (the default)."""
     import torch
     off, idx, w = synth.to_csr(g)
-    flags = kw.pop("flags", 0) | (0 if graph else 4)  # 4 = DFL_FLAG_NO_GRAPH
+    flags = kw.pop("flags", 0) | (32 if graph else 4)  # DFL_FLAG_GRAPH / DFL_FLAG_NO_GRAPH
     opt = dfl.default_options(substeps=substeps, tau_agg=tau_agg, flags=flags, **kw)
     s = torch.cuda.Stream()
     _STREAMS.append(s)
@@ -472,3 +473,25 @@ def test_profiled_graph_replay(dfl, orc):
         same_state(a, b)
     prof = a.profile()
     assert prof["move"]["ms"] > 0 and prof["move"]["bytes"] > 0 and prof["bin0"]["launches"] > 0
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_decide_phase_profile_only(dfl, orc, graph):
+    """DFL_FLAG_PROFILE_MOVE times the decide phase alone: the move class
+    gets time and bytes, no other class is timed; results stay identical."""
+    g = synth.rmat(12, 8 << 12, 7)
+    a, b = pair(dfl, orc, g, graph=graph, flags=64)  # DFL_FLAG_PROFILE_MOVE
+    a.static()
+    b.static()
+    a.profile(reset=True)
+    stream = synth.BatchStream(g, 8)
+    for _ in range(3):
+        d, i = stream.next(300)
+        a.apply_batch(d, i)
+        b.apply_batch(d, i)
+        a.update(2)
+        b.update(2)
+        same_state(a, b)
+    prof = a.profile()
+    assert prof["move"]["ms"] > 0 and prof["move"]["bytes"] > 0 and prof["move"]["launches"] > 0
+    assert all(v["ms"] == 0 for k, v in prof.items() if k != "move")
