@@ -85,21 +85,24 @@ def parse():
     p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
     p.add_argument("--temporal", action="store_true",
                    help="measure DF on the temporal stream (sliding-window batches)")
-    p.add_argument("--launch", default="host", choices=["host", "graph", "persistent"],
-                   help="how a local-moving iteration is launched: kernels from the host (default), "
-                        "a replayed CUDA graph (DFL_FLAG_GRAPH) or one cooperative kernel "
-                        "(DFL_FLAG_PERSISTENT)")
+    p.add_argument("--launch", default="auto", choices=["auto", "host", "graph", "persistent"],
+                   help="how a local-moving iteration is launched: the library's choice (default: "
+                        "graph replay, host launches for updates below 256 batch edges), kernels "
+                        "from the host (DFL_FLAG_NO_GRAPH), always a replayed CUDA graph "
+                        "(DFL_FLAG_GRAPH) or one cooperative kernel (DFL_FLAG_PERSISTENT)")
     p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
     p.add_argument("--group-max-n", type=float, default=1e6)
     return p.parse_args()
 
 
-LAUNCH_DESC = {"host": "per-bin kernels launched from the host", "graph": "per-bin kernels, graph replay",
+LAUNCH_DESC = {"auto": "per-bin kernels, graph replay (host launches below 256 batch edges)",
+               "host": "per-bin kernels launched from the host", "graph": "per-bin kernels, graph replay",
                "persistent": "one cooperative kernel per iteration"}
 
 
 def launch_flag(dfl, args):
-    return {"host": 0, "graph": dfl.FLAG_GRAPH, "persistent": dfl.FLAG_PERSISTENT}[args.launch]
+    return {"auto": 0, "host": dfl.FLAG_NO_GRAPH, "graph": dfl.FLAG_GRAPH,
+            "persistent": dfl.FLAG_PERSISTENT}[args.launch]
 
 
 def peaks():
@@ -553,7 +556,7 @@ def group_arm(args):
                    "vertices": sum(g.n for g in graphs), "edges": sum(g.m for g in graphs),
                    "batch_edges_per_step": sum(d.shape[0] + i.shape[0] for d, i in batches[0]),
                    "l2": "flushed between timed steps (256 MB write)", "generation_s": round(gen_s, 1),
-                   "iteration_launch": LAUNCH_DESC[args.launch],
+                   "iteration_launch": LAUNCH_DESC["host" if args.launch == "auto" else args.launch],
                    "group_static_ms": round(group_static_ms, 2),
                    "serial_static_ms": round(serial_static_ms, 2),
                    "passes_min_max": [min(passes), max(passes)]},

@@ -82,20 +82,19 @@ enum {
 enum {
   DFL_FLAG_PROFILE = 1u, /* time every kernel class with CUDA events (dfl_profile) */
   DFL_FLAG_TRACE = 2u,   /* reserved */
-  DFL_FLAG_NO_GRAPH = 4u, /* launch every kernel from the host (the default; overrides
-                             DFL_FLAG_GRAPH) */
+  DFL_FLAG_NO_GRAPH = 4u, /* launch every kernel from the host (overrides DFL_FLAG_GRAPH) */
   DFL_FLAG_SERIAL_BINS = 8u, /* run the degree bins of a sub-step one after another on the handle's
                                 stream instead of concurrently (for measuring each bin alone) */
   DFL_FLAG_PERSISTENT = 16u,  /* run each local-moving iteration as one cooperative launch whose
                                  blocks meet at bounded grid barriers between sub-steps; a barrier
                                  that waits about a second gives up and the call returns
                                  DFL_ERR_TIMEOUT (the handle should then be destroyed) */
-  DFL_FLAG_GRAPH = 32u,       /* replay each first-pass local-moving iteration as a captured CUDA
-                                 graph (needs a handle stream other than the legacy default
-                                 stream).  By default the host launches an iteration's kernels
-                                 with the list lengths it read: empty bins are skipped and grids
-                                 fit the work, which measured faster than replaying a graph that
-                                 launches every bin */
+  DFL_FLAG_GRAPH = 32u,       /* always replay each first-pass local-moving iteration as a
+                                 captured CUDA graph (needs a handle stream other than the legacy
+                                 default stream).  Without this flag or DFL_FLAG_NO_GRAPH, replay
+                                 is used except for group handles and for DF/DS updates of fewer
+                                 than 256 batch edges, which launch from the host with the list
+                                 lengths read (empty bins skipped, grids fit to the work) */
   DFL_FLAG_PROFILE_MOVE = 64u /* time only the decide phase of each sub-step (two CUDA events per
                                  sub-step, the DFL_PROF_MOVE class of dfl_profile): the cheap
                                  subset of DFL_FLAG_PROFILE */

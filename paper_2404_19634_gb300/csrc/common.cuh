@@ -74,7 +74,6 @@ struct Ctrl {
   unsigned int pad2;
   unsigned long long skipped;        // frontier vertices without arcs (processed, not queued)
   unsigned long long ever_count;     // vertices newly added to the first-pass processed set
-  unsigned int giant_chunks[2];      // chunk work items of the largest bin (per buffer parity)
   // persistent iteration kernel: per sub-step parity, movers, listed
   // high-degree movers, work units taken, vertices left to the part blocks;
   // chunk items of each class; grid barrier
@@ -531,7 +530,15 @@ struct MoveArgs {
   uint32_t max_deg;  // upper bound of the degrees of g
   bool use_range;
   bool track_ever;
+  bool prefer_host = false;  // launch from the host unless DFL_FLAG_GRAPH asks for replay
 };
+// Below this many pending batch arcs a DF or DS update launches its
+// iterations from the host even when graph replay is allowed: a frontier of
+// a few vertices leaves most bins empty, and skipping them beats replaying
+// a graph that launches every bin (R-MAT 2^22: 0.19 vs 0.23 ms at 3 edges,
+// while replay won from about 300 edges up).  Groups prefer host launches
+// too (64 graphs: 0.600 vs 0.607 ms per DF step, static 267 vs 296 ms).
+constexpr uint64_t kGraphMinArcs = 512;
 void destroy_iteration_graph(Handle::IterGraph& g);
 int local_move(Handle* h, const MoveArgs& a, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial = nullptr, uint64_t* ever = nullptr);

@@ -225,6 +225,7 @@ int louvain_group(Handle* h, bool all, bool use_range, uint64_t initial) {
     a.max_deg = maxdeg;
     a.use_range = use_range && pass == 0;
     a.track_ever = pass == 0 && !all;
+    a.prefer_host = true;
     a.graph_iters = git.data();
     uint32_t it = 0;
     uint64_t init0 = 0, ever0 = 0;

@@ -572,10 +572,11 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
 // ---------------------------------------------------------------------------
 // Bin 3 (the largest degrees): three kernels, every step parallel and
 // proportional to the vertex's arcs or its distinct neighbour communities.
-//   k_giant_prefix  lays out, per listed vertex, its chunks of kGiantChunk
-//                   arcs, a global open-addressing table of a power of two
-//                   >= 2 x degree slots (empty at rest) and a list of the
-//                   table's occupied slots (capacity = degree);
+//   k_giant_prefix  at the start of an iteration, for every sub-step class
+//                   (one block each), lays out per listed vertex its chunks
+//                   of kGiantChunk arcs, a global open-addressing table of a
+//                   power of two >= 2 x degree slots (empty at rest) and a
+//                   list of the table's occupied slots (capacity = degree);
 //   k_giant_accum   one block per chunk: the chunk's arcs are aggregated by
 //                   community in shared memory, then every distinct (community,
 //                   weight) is added into the vertex's table; a new key's slot
@@ -697,8 +698,30 @@ __device__ __forceinline__ void giant_prefix_body(const DecideArgs& a, const Gia
   }
 }
 
-__global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd) {
-  giant_prefix_body(a, gd);
+// Class s's region of the bin-3 arrays: every sub-step class has its own
+// layout (at s * gstride), so all of an iteration's layouts are made at once.
+__host__ __device__ __forceinline__ GiantDecide giant_class(GiantDecide gd, uint32_t s, uint64_t gstride,
+                                                          Ctrl* ctrl) {
+  const uint64_t o = uint64_t(s) * gstride;
+  gd.toff += o;
+  gd.loff += o;
+  gd.cpre += o;
+  gd.ndist += o;
+  gd.done += o;
+  gd.hd += o;
+  gd.nitems = &ctrl->it_items[s];
+  return gd;
+}
+
+// The bin-3 layouts of every sub-step class (block s: class s), at the start
+// of an iteration, when all classes' lists are final; each sub-step's chain
+// of largest-degree kernels then starts with its chunks.
+__global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd, uint64_t gstride,
+                                                       const uint32_t* lists, int cur) {
+  const uint32_t s = blockIdx.x;
+  a.list = lists + a.seg.off[s * kBins + 3];
+  a.count = &a.ctrl->count[cur][s][3];
+  giant_prefix_body(a, giant_class(gd, s, gstride, a.ctrl));
 }
 
 // Entries [e0, e1) of vertex t's occupied list: read and clear them, keep the
@@ -1235,15 +1258,7 @@ __device__ __forceinline__ DecideArgs bin_args(const IterArgs& ia, uint32_t s, i
 }
 
 __device__ __forceinline__ GiantDecide class_giant(const IterArgs& ia, uint32_t s) {
-  GiantDecide gd = ia.gd;
-  const uint64_t o = uint64_t(s) * ia.gstride;
-  gd.toff += o;
-  gd.loff += o;
-  gd.cpre += o;
-  gd.ndist += o;
-  gd.done += o;
-  gd.hd += o;
-  gd.nitems = &ia.a.ctrl->it_items[s];
+  GiantDecide gd = giant_class(ia.gd, s, ia.gstride, ia.a.ctrl);
   gd.nbignd = &ia.a.ctrl->it_bignd[s & 1];
   return gd;
 }
@@ -1414,6 +1429,14 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   a.fbits_next = h->fbits[nxt];
   a.next_lists = h->lists[nxt];
   a.next_buf = nxt;
+  const uint64_t gstride = h->g_items_cap / kMaxSubsteps;
+  bool any3 = !counts;
+  for (uint32_t s = 0; counts && s < k; ++s) any3 |= counts[s][3] != 0;
+  if (any3) {  // the largest-degree layouts of all classes, once
+    LaunchScope ls(h, DFL_PROF_BIN3);
+    k_giant_prefix<<<k, 1024, 0, h->stream>>>(a, gd_base, gstride, h->lists[cur], cur);
+    DFL_TRY(check_launch(h, "giant prefix"));
+  }
   for (uint32_t s = 0; s < k; ++s) {
     // the degree bins of one class are independent: the larger ones run on
     // auxiliary streams, concurrently with the rest
@@ -1461,10 +1484,7 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
         else if (bt == 512) k_decide_block<512><<<grid, 512, smem, st>>>(a);
         else k_decide_block<256><<<grid, 256, smem, st>>>(a);
       } else {
-        GiantDecide gd = gd_base;
-        gd.nitems = &h->ctrl->giant_chunks[cur];
-        k_giant_prefix<<<1, 1024, 0, st>>>(a, gd);
-        DFL_TRY(check_launch(h, "giant prefix"));
+        const GiantDecide gd = giant_class(gd_base, s, gstride, h->ctrl);  // laid out above
         k_giant_accum<<<152 * 8, kAccumThreads, 0, st>>>(a, gd);
         DFL_TRY(check_launch(h, "giant accumulate"));
         k_giant_decide<<<152 * 4, kGiantThreads, 0, st>>>(a, gd);
@@ -1825,12 +1845,16 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     if (ma.graph_iters) ma.graph_iters[g] = 0;
   }
   if (G) DFL_TRY(group_upload_flags(h, h->d_gdone, h->h_gdone));
-  // graph replay of the iterations needs stable buffers (the base graph) and
-  // a capturable (non-default) stream
+  // the persistent kernel when asked for; else graph replay, which needs
+  // stable buffers (the base graph) and a capturable (non-default) stream,
+  // unless forbidden, or unless the caller prefers host launches (a small
+  // update, a group) and replay was not asked for explicitly; else host
+  // launches
   const uint32_t pgrid = (h->opt.flags & DFL_FLAG_PERSISTENT) ? persistent_grid() : 0u;
   const bool use_persistent = pgrid >= kMaxSubsteps;
-  const bool use_graph = !use_persistent && ma.g.off == h->off && h->stream != nullptr &&
-                         (h->opt.flags & DFL_FLAG_GRAPH) && !(h->opt.flags & DFL_FLAG_NO_GRAPH);
+  const uint32_t fl = h->opt.flags;
+  const bool want_graph = !(fl & DFL_FLAG_NO_GRAPH) && ((fl & DFL_FLAG_GRAPH) || !ma.prefer_host);
+  const bool use_graph = !use_persistent && want_graph && ma.g.off == h->off && h->stream != nullptr;
   unsigned int cur_count[kMaxSubsteps][kBins];
   unsigned long long skipped = 0;
   bool have_counts = false;
