@@ -68,12 +68,23 @@ __device__ __forceinline__ bool group_active(const DecideArgs& a, uint32_t i, lo
   return true;
 }
 
+// m2 * h - k * sig, the numerator of a modularity gain (Eq. 2 scaled by
+// 2m^2; a candidate's score or the stay term).  Every factor is below 2^32:
+// 2m < 2^32 holds on every graph (dfl_create and dfl_apply_batch refuse
+// more), and h, k and sig are sums of parts of 2m.  So each product is one
+// 32 x 32 -> 64-bit multiply, and the difference is exact in 128 bits.
+__device__ __forceinline__ i128 gain_num(long long m2, unsigned long long h, long long k, long long sig) {
+  const unsigned long long p = (unsigned long long)(uint32_t)m2 * (uint32_t)h;
+  const unsigned long long q = (unsigned long long)(uint32_t)k * (uint32_t)sig;
+  return (i128)p - (i128)q;
+}
+
 // Outcome of one vertex's decision, identical on every lane / thread.
 __device__ __forceinline__ bool decide_move(const DecideArgs& a, long long m2, uint32_t i, uint32_t d,
                                             long long Ki, bool have, i128 best, uint32_t bc,
                                             unsigned long long Hd, i128* gain) {
   if (!have) return false;
-  i128 stay = (i128)m2 * (i128)Hd - (i128)Ki * (i128)(a.Sigma[d] - Ki);
+  const i128 stay = gain_num(m2, Hd, Ki, a.Sigma[d] - Ki);
   if (!(best > stay)) return false;
   if (a.size[d] == 1 && a.size[bc] == 1 && bc > d) return false;  // singleton-swap guard
   *gain = best - stay;
@@ -205,7 +216,7 @@ __device__ __forceinline__ bool decide_segment(const DecideArgs& a, bool active,
   const bool cand = leader && c != d;
   const unsigned cm = __ballot_sync(0xFFFFFFFFu, cand) & segmask;
   i128 score = 0;
-  if (cand) score = (i128)m2 * (i128)hsum - (i128)Ki * (i128)a.Sigma[c];
+  if (cand) score = gain_num(m2, hsum, Ki, a.Sigma[c]);
   bool have = cand;
   uint32_t bc = c;
   segment_argmax<W>(have, score, bc);
@@ -330,7 +341,7 @@ __device__ __forceinline__ unsigned long long table_argmax(const DecideArgs& a, 
         continue;
       }
       ++ncand;
-      const i128 sc = (i128)m2 * (i128)w[u] - (i128)Ki * (i128)sg[u];
+      const i128 sc = gain_num(m2, w[u], Ki, sg[u]);
       if (!have || sc > best || (sc == best && c[u] < bc)) {
         have = true;
         best = sc;
@@ -761,7 +772,7 @@ __device__ __forceinline__ uint32_t giant_scan_entries(const DecideArgs& a, cons
         continue;
       }
       ++ncand;
-      const i128 sc = (i128)m2 * (i128)h[u] - (i128)Ki * (i128)sg[u];
+      const i128 sc = gain_num(m2, h[u], Ki, sg[u]);
       if (!have || sc > best || (sc == best && c[u] < bc)) {
         have = true;
         best = sc;
