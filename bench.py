@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=0.5,
                    help="length of the Poisson arrival window")
     p.add_argument("--group", action="store_true", help="measure the batched multi-graph form")
+    p.add_argument("--aux", action="store_true",
+                   help="measure what reusing K and Sigma saves (Section 4.2) for ND, DS and DF")
     p.add_argument("--temporal", action="store_true",
                    help="measure DF on the temporal stream (sliding-window batches)")
     p.add_argument("--launch", default="auto", choices=["auto", "host", "graph", "persistent"],
@@ -570,6 +572,87 @@ def group_arm(args):
     print(json.dumps(line), flush=True)
 
 
+AUX_METRIC = "mean speedup of DF from reusing K and Sigma instead of recomputing them (Section 4.2)"
+# The same run records, per mode and batch size, the fraction of vertices
+# the first pass marked and processed: the affected-set comparison of DS and
+# DF.
+
+
+def aux_arm(args):
+    """Each update with the auxiliary information reused (the default) and
+    with K, 2m and Sigma recomputed from scratch first (DFL_FLAG_RECOMPUTE_AUX),
+    alternating on the evolving graph: ND, DS and DF at every batch size."""
+    import torch
+
+    import paper_2404_19634_gb300 as dfl
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dfl.build()
+    g, off, idx, w = make_workload(args)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    pflag = launch_flag(dfl, args)
+    h = dfl.Dfl(g.n, off, idx, w, options=dfl.default_options(flags=pflag), stream=stream)
+    h.static()
+    bstream = synth.BatchStream(g, BATCH_SEED + 7)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    reps = max(3, min(args.steps, 5))
+    table = {}
+    launches = 0
+    for frac in SIZES:
+        size = batch_size(g, frac)
+        row = {}
+        for name, mode in (("ND", dfl.ND), ("DS", dfl.DS), ("DF", dfl.DF)):
+            ms = {False: [], True: []}
+            ever, initial = [], []
+            for _ in range(reps):
+                for recompute in (False, True):
+                    h.set_options(dfl.default_options(
+                        flags=pflag | (dfl.FLAG_RECOMPUTE_AUX if recompute else 0)))
+                    d, i = bstream.next(size)
+                    dd, di = to_dev(d), to_dev(i)
+                    l0 = h.stats()["kernel_launches"]
+                    torch.cuda.synchronize()
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    h.apply_batch(dd, di)
+                    h.update(mode)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    st = h.stats()
+                    launches += st["kernel_launches"] - l0
+                    ms[recompute].append(a.elapsed_time(b))
+                    if not recompute:
+                        ever.append(st["affected_ever"] / g.n)
+                        initial.append(st["affected_initial"] / g.n)
+            reuse, scratch = statistics.median(ms[False]), statistics.median(ms[True])
+            # vertices processed by the first pass (the ever-affected set) and
+            # marked initially, as fractions of |V| (Section 5.2's explanation)
+            row[name] = {"reuse_ms": round(reuse, 4), "recompute_ms": round(scratch, 4),
+                         "speedup": round(scratch / reuse, 3),
+                         "affected_initial_frac": float(f"{statistics.median(initial):.4g}"),
+                         "affected_ever_frac": float(f"{statistics.median(ever):.4g}")}
+        table[f"{frac:g}"] = row
+    h.close()
+    mean = {m: round(statistics.mean(table[f"{f:g}"][m]["speedup"] for f in SIZES), 3) for m in ("ND", "DS", "DF")}
+    line = {
+        "metric": AUX_METRIC, "value": mean["DF"], "unit": "x", "n_gpus": 1, "steps": reps,
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale} |E|={g.m}, batches of 1e-7..1e-3|E| (80/20), "
+                               f"{reps} updates per mode, size and variant (median)",
+                   "l2": "flushed before each update (256 MB write)",
+                   "iteration_launch": LAUNCH_DESC[args.launch],
+                   "mean_speedup": mean, "by_batch_fraction": table,
+                   "paper_context": "64-core CPU, graphs of Table 2: ND 11.8x, DS 2.9x, DF 48.5x"},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
 TEMPORAL_N = 2_000_000
 TEMPORAL_STEPS = 30_000_000
 TEMPORAL_METRIC = "ms/batch DF update, temporal PA stream (2M vertices, 30M interactions), sliding window"
@@ -748,6 +831,9 @@ def main():
         return
     if args.temporal:
         temporal_arm(args)
+        return
+    if args.aux:
+        aux_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -95,9 +95,15 @@ enum {
                                  is used except for group handles and for DF/DS updates of fewer
                                  than 256 batch edges, which launch from the host with the list
                                  lengths read (empty bins skipped, grids fit to the work) */
-  DFL_FLAG_PROFILE_MOVE = 64u /* time only the decide phase of each sub-step (two CUDA events per
+  DFL_FLAG_PROFILE_MOVE = 64u, /* time only the decide phase of each sub-step (two CUDA events per
                                  sub-step, the DFL_PROF_MOVE class of dfl_profile): the cheap
                                  subset of DFL_FLAG_PROFILE */
+  DFL_FLAG_RECOMPUTE_AUX = 128u /* the ablation of Section 4.2: every dfl_update / dfl_group_update
+                                 first recomputes K from the graph and Sigma (and 2m) from K and
+                                 the memberships, as a dynamic method without auxiliary
+                                 information must.  Results are identical; the extra time is
+                                 what reusing K^{t-1} and Sigma^{t-1} saves.  (The batch apply
+                                 still updates K and Sigma incrementally, fused into its kernels.) */
 };
 
 /* Algorithm options; defaults from Section 5.1.2 of the paper. */

@@ -33,6 +33,7 @@ FLAG_SERIAL_BINS = 8
 FLAG_PERSISTENT = 16
 FLAG_GRAPH = 32
 FLAG_PROFILE_MOVE = 64
+FLAG_RECOMPUTE_AUX = 128
 PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other", "bin0", "bin1", "bin2",
               "bin3"]
 PROF_APPLY, PROF_MARK, PROF_MOVE, PROF_COMMIT, PROF_AGG, PROF_OTHER = range(6)

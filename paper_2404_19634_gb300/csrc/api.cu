@@ -419,6 +419,7 @@ int dfl_update(dfl_handle* h, int mode) {
     return set_error(h, DFL_ERR_INVALID, "unknown mode");
   bool all = false, use_range = false;
   uint64_t initial = 0;
+  if (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) DFL_TRY(recompute_aux(h));
   DFL_TRY(mark(h, mode, &all, &use_range, &initial));
   int rc = louvain(h, all, use_range, initial);
   h->pend_count = 0;
@@ -861,6 +862,7 @@ int dfl_group_update(dfl_handle* h, int mode) {
   bool all = false, use_range = false;
   uint64_t initial = 0;
   DFL_TRY(group_set_level(h, h->d_goff0));  // classes of the base graphs' vertices
+  if (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) DFL_TRY(recompute_aux(h));
   DFL_TRY(mark(h, mode, &all, &use_range, &initial));
   int rc = louvain_group(h, all, use_range, initial);
   h->pend_count = 0;

@@ -211,6 +211,15 @@ int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx
   return DFL_OK;
 }
 
+// K, 2m (and every graph's 2m in a group), Sigma and community sizes from
+// scratch: the state a dynamic method without auxiliary information
+// (Section 4.2) computes before each update.
+int recompute_aux(Handle* h) {
+  DFL_TRY(weighted_degrees(h));
+  if (h->ngraphs) DFL_TRY(group_m2(h));
+  return recompute_sigma_sizes(h, h->C);
+}
+
 int weighted_degrees(Handle* h) {
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->red_a, 0, sizeof(unsigned long long), h->stream));
   {

@@ -287,3 +287,23 @@ def test_group_with_a_graph_of_no_vertices(dfl, orc):
     for g, o in ((0, orcs[0]), (2, orcs[1])):
         assert np.array_equal(grp.graph_membership(g), o.membership())
         assert grp.graph_modularity(g)[1:] == o.modularity()[1:]
+
+
+def test_group_recomputed_auxiliary_information(dfl, orc):
+    """A group with DFL_FLAG_RECOMPUTE_AUX (K, every graph's 2m and Sigma
+    recomputed before each update) gives each graph the oracle's state."""
+    gs = [g for g, _ in synth.planted_group(3, 2000, 20000, 31)]
+    grp, orcs = group_pair(dfl, orc, gs, flags=128)
+    grp.static()
+    for o in orcs:
+        o.static()
+    streams = [synth.BatchStream(g, 70 + k) for k, g in enumerate(gs)]
+    for mode in (2, 1):
+        batches = [st.next(max(1, g.m // 500), w_max=16) for st, g in zip(streams, gs)]
+        grp.apply_batches([b[0] for b in batches], [b[1] for b in batches])
+        for o, (d, i) in zip(orcs, batches):
+            assert o.apply_batch(d, i) == 0
+        grp.update(mode)
+        for o in orcs:
+            o.update(mode)
+        same_group(grp, orcs)

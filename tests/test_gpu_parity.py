@@ -495,3 +495,21 @@ def test_decide_phase_profile_only(dfl, orc, graph):
     prof = a.profile()
     assert prof["move"]["ms"] > 0 and prof["move"]["bytes"] > 0 and prof["move"]["launches"] > 0
     assert all(v["ms"] == 0 for k, v in prof.items() if k != "move")
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_recomputed_auxiliary_information_same_results(dfl, orc, mode):
+    """DFL_FLAG_RECOMPUTE_AUX recomputes K, Sigma and 2m from scratch before
+    every update (the ablation of Section 4.2): the state must still equal
+    the oracle's, which updates K and Sigma incrementally (Alg. 7)."""
+    g = synth.rmat(12, 8 << 12, 9)
+    a, b = pair(dfl, orc, g, flags=128)  # DFL_FLAG_RECOMPUTE_AUX
+    a.static()
+    b.static()
+    stream = synth.BatchStream(g, 10)
+    for size in (30, 600):
+        d, i = stream.next(size, w_max=5)
+        assert a.apply_batch(d, i) == 0 and b.apply_batch(d, i) == 0
+        a.update(mode)
+        b.update(mode)
+        same_state(a, b)
