@@ -213,6 +213,17 @@ int dfl_weights(dfl_handle* h, int64_t* K, int64_t* Sigma, int64_t* two_m, int m
 
 /* Number of arcs of G^t, and G^t as a compact CSR with sorted rows
  * (offsets n+1, indices and weights num_arcs). */
+/* Rewrite the arc pool densely.  Rows that outgrow their slot move to the
+ * end of the pool and leave the old slot behind, so a long stream of
+ * batches only ever grows it; this gives every row a fresh slot of slack
+ * capacity for its live arcs (tombstones dropped; the live part of the
+ * sorted prefix kept in order, then the live tail).  The graph, membership,
+ * K, Sigma and pending batches are unchanged, and so is every later result.
+ * before / after (optional, out): arc slots of the pool before and after.
+ * Allocates the new pool before freeing the old (DFL_ERR_NOMEM leaves the
+ * handle unchanged); synchronizes the stream.  Works on group handles. */
+int dfl_compact(dfl_handle* h, uint64_t* before, uint64_t* after);
+
 int dfl_num_arcs(dfl_handle* h, uint64_t* num_arcs);
 int dfl_graph(dfl_handle* h, uint64_t* offsets, uint32_t* indices, uint32_t* weights,
               int mem_kind);

@@ -133,6 +133,7 @@ _SIGS = {
     "dfl_modularity": (ct.c_int, [_P, ct.POINTER(ct.c_double), _P]),
     "dfl_weights": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_int64), ct.c_int]),
     "dfl_num_arcs": (ct.c_int, [_P, ct.POINTER(ct.c_uint64)]),
+    "dfl_compact": (ct.c_int, [_P, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]),
     "dfl_graph": (ct.c_int, [_P, _P, _P, _P, ct.c_int]),
     "dfl_stats": (ct.c_int, [_P, ct.POINTER(Stats)]),
     "dfl_profile": (ct.c_int, [_P, ct.POINTER(Profile), ct.c_int]),
@@ -236,6 +237,22 @@ def _stream_ptr(stream):
 def _i128(hi: int, lo: int) -> int:
     v = ((hi & 0xFFFFFFFFFFFFFFFF) << 64) | (lo & 0xFFFFFFFFFFFFFFFF)
     return v - (1 << 128) if v >> 127 else v
+
+
+def save_checkpoint(path: str, ck: dict) -> None:
+    """Write a Dfl.checkpoint() to an .npz file."""
+    t = ck["tuning"]
+    np.savez(path, n=np.uint64(ck["n"]), offsets=ck["offsets"], indices=ck["indices"], weights=ck["weights"],
+             membership=ck["membership"], tuning_keys=np.array(list(t.keys())),
+             tuning_values=np.array(list(t.values()), np.uint32))
+
+
+def load_checkpoint(path: str) -> dict:
+    """Read a checkpoint written by save_checkpoint."""
+    z = np.load(path)
+    return {"n": int(z["n"]), "offsets": z["offsets"], "indices": z["indices"], "weights": z["weights"],
+            "membership": z["membership"],
+            "tuning": {str(k): int(v) for k, v in zip(z["tuning_keys"], z["tuning_values"])}}
 
 
 class Dfl:
@@ -384,6 +401,30 @@ class Dfl:
     def set_membership(self, C):
         p, mk, _ = _buf(C, np.uint32)
         self._check(self._lib.dfl_set_membership(self._h, p, mk))
+
+    def compact(self):
+        """dfl_compact: rewrite the arc pool densely; (slots before, after)."""
+        b, a = ct.c_uint64(), ct.c_uint64()
+        self._check(self._lib.dfl_compact(self._h, ct.byref(b), ct.byref(a)))
+        return int(b.value), int(a.value)
+
+    def checkpoint(self) -> dict:
+        """Everything later updates depend on, as host arrays: the graph
+        (compact CSR, rows sorted), the membership and the launch tuning.  K
+        and Sigma are functions of these and are recomputed on restore.  Take
+        it between updates (a pending batch is not part of it)."""
+        off, idx, w = self.graph()
+        return {"n": self.n, "offsets": off, "indices": idx, "weights": w,
+                "membership": self.membership().copy(), "tuning": self.tuning()}
+
+    @classmethod
+    def restore(cls, ck: dict, options: Options | None = None, stream=None) -> "Dfl":
+        """A handle in the state a checkpoint recorded (dfl_create from its
+        graph, then dfl_set_tuning and dfl_set_membership)."""
+        h = cls(ck["n"], ck["offsets"], ck["indices"], ck["weights"], options=options, stream=stream)
+        h.set_tuning(**{k: int(v) for k, v in ck["tuning"].items()})
+        h.set_membership(np.ascontiguousarray(ck["membership"], np.uint32))
+        return h
 
     def mark(self, mode: int):
         F = np.zeros(self.n, np.uint8)

@@ -461,6 +461,11 @@ int dfl_weights(dfl_handle* h, int64_t* K, int64_t* Sigma, int64_t* two_m, int m
   return DFL_OK;
 }
 
+int dfl_compact(dfl_handle* h, uint64_t* before, uint64_t* after) {
+  if (!h) return DFL_ERR_INVALID;
+  return dfl::compact_pool(h, before, after);
+}
+
 int dfl_num_arcs(dfl_handle* h, uint64_t* num_arcs) {
   if (!h || !num_arcs) return DFL_ERR_INVALID;
   *num_arcs = h->num_arcs;

@@ -509,6 +509,7 @@ uint64_t popcount_bits(Handle* h, const uint32_t* bits, uint32_t words, int* rc)
 int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx_in,
                 const uint32_t* w_in, uint64_t nnz);
 int weighted_degrees(Handle* h);  // K from scratch, m2 on host
+int compact_pool(Handle* h, uint64_t* before, uint64_t* after);  // dfl_compact
 int recompute_aux(Handle* h);      // K, 2m, Sigma, sizes from scratch (DFL_FLAG_RECOMPUTE_AUX)
 int modularity_parts(Handle* h, i128* num, i128* den);
 int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool device_out);

@@ -249,6 +249,114 @@ int modularity_parts(Handle* h, i128* num, i128* den) {
   return DFL_OK;
 }
 
+// Pool compaction, pass 1, warp per row: the row's live arcs (weight > 0),
+// counted, and the fresh slack capacity for them.
+__global__ void k_compact_caps(uint32_t n, const uint2* __restrict__ arcs, const unsigned long long* __restrict__ off,
+                               const uint32_t* __restrict__ deg, unsigned long long* __restrict__ capl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (; warp < n; warp += nwarps) {
+    const unsigned long long o = off[warp];
+    const uint32_t d = deg[warp];
+    uint32_t live = 0;
+    for (uint32_t k = lane; k < d; k += 32) live += arcs[o + k].y != 0;
+    for (int x = 16; x; x >>= 1) live += __shfl_xor_sync(0xFFFFFFFFu, live, x);
+    if (lane == 0) capl[warp] = slack_cap(live);
+  }
+}
+
+// Pass 2, warp per row: the row's live arcs into its new slot in the same
+// order -- the live part of the sorted prefix first (still sorted), then the
+// live tail -- and the row's new length, sorted-prefix length, capacity and
+// offset (each row's own entries are read before they are written).
+__global__ void k_compact_rows(uint32_t n, const uint2* __restrict__ arcs, unsigned long long* __restrict__ off,
+                               const unsigned long long* __restrict__ noff, uint32_t* __restrict__ deg,
+                               uint32_t* __restrict__ cap, uint32_t* __restrict__ srt,
+                               uint32_t* __restrict__ ntomb, uint2* __restrict__ out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (; warp < n; warp += nwarps) {
+    const uint32_t i = uint32_t(warp);
+    const unsigned long long o = off[i], no = noff[i];
+    const uint32_t d = deg[i], sp = srt[i];
+    uint32_t pos = 0, live_prefix = 0;
+    for (uint32_t k0 = 0; k0 < d; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint2 a = k < d ? arcs[o + k] : make_uint2(0u, 0u);
+      const bool live = k < d && a.y != 0;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, live);
+      if (live) out[no + pos + __popc(m & ((1u << lane) - 1u))] = a;
+      // live arcs of the sorted prefix [0, sp) of this group of 32
+      const unsigned pre = sp > k0 ? (sp - k0 >= 32 ? 0xFFFFFFFFu : ((1u << (sp - k0)) - 1u)) : 0u;
+      live_prefix += __popc(m & pre);
+      pos += __popc(m);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      off[i] = no;
+      deg[i] = pos;
+      srt[i] = live_prefix;
+      ntomb[i] = 0;
+      cap[i] = slack_cap(pos);
+    }
+  }
+}
+
+int compact_pool(Handle* h, uint64_t* before, uint64_t* after) {
+  const uint32_t n = h->n;
+  if (before) *before = h->pool_cap;
+  if (!n) {
+    if (after) *after = h->pool_cap;
+    return DFL_OK;
+  }
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  unsigned long long* capl = nullptr;
+  DFL_CUDA(h, cudaMalloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
+  int rc = DFL_OK;
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_compact_caps<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(n, h->arcs, h->off, h->deg, capl);
+    rc = check_launch(h, "compact caps");
+  }
+  if (!rc) rc = scan_u64(h, capl, capl, n);  // new offsets, capl[n] = total
+  unsigned long long total = 0;
+  if (!rc && cudaMemcpyAsync(&total, capl + n, sizeof(total), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = set_error(h, DFL_ERR_CUDA, "copy total");
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "sync");
+  uint2* pool = nullptr;
+  uint64_t cap = 0;
+  if (!rc) {
+    cap = (total + total / 8 + 1024 + 1) & ~uint64_t(1);
+    if (cudaMalloc(&pool, sizeof(uint2) * cap) != cudaSuccess) {
+      cudaGetLastError();
+      rc = set_error(h, DFL_ERR_NOMEM, "compacted arc pool");
+    }
+  }
+  if (!rc) {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_compact_rows<<<grid_for(uint64_t(n) * 32, 256), 256, 0, h->stream>>>(n, h->arcs, h->off, capl, h->deg,
+                                                                           h->cap, h->srt, h->ntomb, pool);
+    rc = check_launch(h, "compact rows");
+  }
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "sync");
+  cudaFree(capl);
+  if (rc) {
+    if (pool) cudaFree(pool);
+    return rc;
+  }
+  // captured iterations bake the old pool's address in
+  for (auto& row : h->igraph)
+    for (auto& g : row) destroy_iteration_graph(g);
+  cudaFree(h->arcs);
+  h->arcs = pool;
+  h->pool_cap = cap;
+  h->pool_top = total;
+  if (after) *after = h->pool_cap;
+  return DFL_OK;
+}
+
 // G^t as a compact CSR: live arcs only, rows sorted by neighbour.  The rows
 // are read back and put in canonical order on the host (an inspection path).
 int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool device_out) {

@@ -513,3 +513,59 @@ def test_recomputed_auxiliary_information_same_results(dfl, orc, mode):
         a.update(mode)
         b.update(mode)
         same_state(a, b)
+
+
+def test_compaction_and_checkpoint_continue_exactly(dfl, orc, tmp_path):
+    """A long stream leaves relocated rows' slots behind; dfl_compact gives
+    them back without changing anything later updates compute.  A
+    checkpoint (graph, membership, tuning) saved to disk and restored into a
+    new handle continues exactly like the original."""
+    rng = np.random.default_rng(23)
+    g = synth.planted_partition(800, 16, 0.25, 6, 4, 3)
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    a.set_tuning(bin_warp=4, bin_warp_hash=64, bin_block=1024, block_threads=128)
+
+    def batch(t):
+        off, idx, w = b.graph()
+        edges = [(i, int(idx[k]), int(w[k])) for i in range(g.n)
+                 for k in range(int(off[i]), int(off[i + 1])) if i < idx[k]]
+        pick = rng.choice(len(edges), min(30, len(edges)), replace=False)
+        dels = np.array([(edges[p][0], edges[p][1], 0) for p in pick], np.uint32).reshape(-1, 3)
+        hot = int(rng.integers(0, 10))
+        ins = [(hot, int(j), 1) for j in rng.integers(0, g.n, 60) if j != hot]
+        ins += [(int(x), int(y), 2) for x, y in rng.integers(0, g.n, (30, 2)) if x != y]
+        return dels, np.array(ins, np.uint32).reshape(-1, 3)
+
+    for t in range(30):
+        d, i = batch(t)
+        assert a.apply_batch(d, i) == 0 and b.apply_batch(d, i) == 0
+        if t % 3 == 2:
+            a.update(2)
+            b.update(2)
+    same_state(a, b)
+    arcs = a.num_arcs()
+    before, after = a.compact()
+    assert after < before and a.num_arcs() == arcs
+    same_graph(a, b)
+    same_state(a, b, stats=False)
+    path = str(tmp_path / "state.npz")
+    dfl.save_checkpoint(path, a.checkpoint())
+    import torch
+    s = torch.cuda.Stream()
+    c = dfl.Dfl.restore(dfl.load_checkpoint(path), options=dfl.default_options(), stream=s)
+    assert c.tuning() == a.tuning()
+    same_graph(c, b)
+    same_state(c, b, stats=False)
+    for t in range(6):
+        d, i = batch(t)
+        for x in (a, b, c):
+            assert x.apply_batch(d, i) == 0
+        for x in (a, b, c):
+            x.update(t % 3)
+        same_state(a, b)
+        same_state(c, b)
+    same_graph(a, b)
+    same_graph(c, b)
+    c.close()
