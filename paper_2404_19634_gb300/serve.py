@@ -12,7 +12,13 @@ deletions and insertions for one graph) arrive over time; the server
     dfl_apply_batch calls) and one dfl_update(DF) follows, as the API allows,
   * runs different graphs' updates at the same time: one worker thread per
     graph drives its handle through the C ABI (ctypes releases the GIL), so
-    their kernels overlap on the device.
+    their kernels overlap on the device,
+  * optionally refreshes a graph with static Louvain after every
+    `refresh_every` of its updates: DF (like DS) can miss a community that a
+    long run of deletions splits or an outlier that drifts away, and a
+    periodic static run -- every 1000 batches, say -- restores the quality
+    (the remedy the paper proposes with its correctness argument,
+    Section 7.5).
 
 Results are deterministic: a request's result (the modularity numerator and
 denominator after the update that served it, and the membership) depends only
@@ -54,6 +60,7 @@ class Record:
     den: int = 0
     q: float = 0.0
     membership: object = None  # copy of C after that update (keep_membership)
+    refreshed: bool = False    # static Louvain ran after that update (refresh_every)
 
     @property
     def latency(self) -> float:
@@ -88,10 +95,14 @@ class Server:
     """Resident graphs plus the serving loop (see the module docstring)."""
 
     def __init__(self, handles, resident_bytes: int = 0, mem_cap: int = 150 << 30,
-                 slots: int | None = None, keep_membership: bool = False):
+                 slots: int | None = None, keep_membership: bool = False, refresh_every: int = 0):
         """handles: one object per graph with the Dfl methods apply_batch,
-        update, modularity and membership, each already past dfl_static."""
+        update, static, modularity and membership, each already past
+        dfl_static.  refresh_every > 0: static Louvain after every that many
+        updates of a graph (counted per server)."""
         self.handles = list(handles)
+        self.refresh_every = int(refresh_every)
+        self.updates = [0] * len(self.handles)
         self.resident = resident_bytes
         self.mem_cap = mem_cap
         self.slots = slots or len(self.handles)
@@ -126,6 +137,10 @@ class Server:
         for r in group:
             h.apply_batch(r.dels, r.ins)
         h.update(DF)
+        self.updates[g] += 1
+        refreshed = self.refresh_every > 0 and self.updates[g] % self.refresh_every == 0
+        if refreshed:
+            h.static()
         q, num, den = h.modularity()
         finish = time.perf_counter() - t0
         memb = h.membership() if self.keep_membership else None
@@ -134,6 +149,7 @@ class Server:
             rec.start, rec.finish, rec.group = start, finish, gid
             rec.num, rec.den, rec.q = num, den, q
             rec.membership = memb
+            rec.refreshed = refreshed
 
     # -- continuous batching ------------------------------------------------
     def serve(self, requests: list, coalesce: bool = True) -> ServeResult:

@@ -96,3 +96,34 @@ def test_coalesced_groups_match_oracle(dfl, oracle_mod):
             assert (rec.num, rec.den) == (num, den)
             assert abs(rec.q - q) <= 1e-12 * max(1.0, abs(q))
             assert np.array_equal(rec.membership, o.membership())
+
+
+def test_periodic_static_refresh_matches_oracle(dfl, oracle_mod):
+    """refresh_every=3: after every third update of a graph the server runs
+    static Louvain on the current graph; the oracle replaying the same
+    groups and refreshes gives every recorded result."""
+    from paper_2404_19634_gb300 import serve
+    csrs, reqs = workload(seed=12, rate=8000.0, duration=0.02, hi=2000)
+    srv = serve.Server.from_graphs(csrs, keep_membership=True, refresh_every=3)
+    mix = srv.serve(reqs, coalesce=True)
+    srv.close()
+    assert any(rec.refreshed for rec in mix.records)
+    by_id = {r.rid: r for r in reqs}
+    for g, (n, off, idx, w) in enumerate(csrs):
+        o = oracle_mod.Oracle(n, off, idx, w)
+        o.static()
+        k = 0
+        for gg, ids in mix.groups:
+            if gg != g:
+                continue
+            for i in ids:
+                assert o.apply_batch(by_id[i].dels, by_id[i].ins) == 0
+            o.update(2)  # DF
+            k += 1
+            rec = mix.records[ids[-1]]
+            assert rec.refreshed == (k % 3 == 0)
+            if rec.refreshed:
+                o.static()
+            q, num, den = o.modularity()
+            assert (rec.num, rec.den) == (num, den)
+            assert np.array_equal(rec.membership, o.membership())

@@ -31,6 +31,9 @@ class FakeHandle:
         with self.lock:
             self.active -= 1
 
+    def static(self):
+        self.history.append("static")
+
     def modularity(self):
         # a value that depends on the whole grouping history of this graph
         num = hash(tuple(self.history)) & 0xFFFFFFFF
@@ -108,3 +111,26 @@ def test_oversized_request_runs_alone():
     check_groups(reqs, res)
     assert srv.peak["busy"] == 1
     assert all(len(ids) == 1 for _, ids in res.groups)
+
+
+def test_periodic_static_refresh():
+    """refresh_every=k: static Louvain after every k-th update of a graph,
+    counted per graph, and the same under replay of the same grouping."""
+    reqs = requests(num_graphs=3, count=90, seed=8)
+    srv = serve.Server([FakeHandle(g, 0.0) for g in range(3)], refresh_every=4)
+    res = srv.serve(reqs)
+    check_groups(reqs, res)
+    for g, h in enumerate(srv.handles):
+        updates = [x for x in h.history if x != "static"]
+        assert len(updates) == srv.updates[g]
+        # a static run follows exactly every 4th update
+        pos = [k for k, x in enumerate(h.history) if x == "static"]
+        assert len(pos) == len(updates) // 4
+        for j, p in enumerate(pos):
+            assert sum(1 for x in h.history[:p] if x != "static") == 4 * (j + 1)
+    flagged = {rid for rid, rec in enumerate(res.records) if rec.refreshed}
+    by_group = {gid: ids for gid, (g, ids) in enumerate(res.groups)}
+    assert flagged and all(res.records[i].refreshed == res.records[ids[0]].refreshed
+                           for ids in by_group.values() for i in ids)
+    again = serve.Server([FakeHandle(g, 0.0) for g in range(3)], refresh_every=4).replay(reqs, res.groups)
+    assert [(r.num, r.refreshed) for r in again.records] == [(r.num, r.refreshed) for r in res.records]
