@@ -27,8 +27,15 @@
  *     GPU).  Input buffers are only read during the call and are copied;
  *     output buffers are owned and sized by the caller.
  *   - All device work runs on the handle's CUDA stream, in stream order.
- *     Calls return after the work they started is complete unless stated
- *     otherwise.  A handle must not be used from two threads at once.
+ *     Calls that hand results to the caller (host values, caller buffers)
+ *     return after that work is complete.  dfl_static, dfl_apply_batch,
+ *     dfl_update, dfl_louvain_from and the group forms return once their
+ *     host-side decisions are made (the batch validated, convergence
+ *     decided); device work they queued last
+ *     may still be running on the stream, ordered before the handle's next
+ *     call -- a caller reading device state directly must order its work
+ *     after the handle's stream.  A handle must not be used from two threads
+ *     at once.
  *   - The computation is deterministic: the same inputs give the same
  *     membership, K, Sigma and modularity on every run.
  *

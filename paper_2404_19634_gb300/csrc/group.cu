@@ -305,8 +305,7 @@ int louvain_group(Handle* h, bool all, bool use_range, uint64_t initial) {
   }
   if (aggregated) DFL_TRY(recompute_sigma_sizes(h, h->C));
   st.num_communities = 0;
-  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
-  return DFL_OK;
+  return check_launch(h, "group louvain");  // (stream-ordered, as in louvain)
 }
 
 }  // namespace dfl

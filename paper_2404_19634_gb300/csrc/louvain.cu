@@ -152,8 +152,9 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
     DFL_TRY(recompute_sigma_sizes(h, h->C));
   }
   st.num_communities = last_comm;
-  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
-  return DFL_OK;
+  // every host decision is made; what is left on the stream (clearing the
+  // frontier, the final lookup) is ordered before the caller's next call
+  return check_launch(h, "louvain");
 }
 
 }  // namespace dfl
