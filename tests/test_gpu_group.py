@@ -307,3 +307,34 @@ def test_group_recomputed_auxiliary_information(dfl, orc):
         for o in orcs:
             o.update(mode)
         same_group(grp, orcs)
+
+
+def test_group_of_graphs_each_near_the_2m_limit(dfl, orc):
+    """Two graphs whose own 2m is just below 2^32 (the union's is above):
+    each graph is checked against its own bound and scored with its own 2m."""
+    rng = np.random.default_rng(31)
+    gs = []
+    for k in range(2):
+        base = synth.planted_partition(1500, 15, 0.2, 10, 1, 40 + k)
+        w = rng.integers(1, 400000, base.m).astype(np.uint64)
+        scale = ((1 << 32) - (1 << 21)) / (2.0 * float(w.sum()))
+        w = np.maximum(1, (w * scale).astype(np.uint64)).astype(np.uint32)
+        gs.append(synth.EdgeList(base.n, base.u, base.v, w))
+    grp, orcs = group_pair(dfl, orc, gs)
+    grp.static()
+    for o in orcs:
+        o.static()
+    same_group(grp, orcs)
+    batches = []
+    for g in gs:
+        x = rng.integers(0, g.n, (12, 2))
+        x = x[x[:, 0] != x[:, 1]]
+        ins = np.concatenate([x, rng.integers(1, 30000, (x.shape[0], 1))], 1).astype(np.uint32)
+        batches.append((np.zeros((0, 3), np.uint32), ins))
+    grp.apply_batches([b[0] for b in batches], [b[1] for b in batches])
+    for o, (d, i) in zip(orcs, batches):
+        assert o.apply_batch(d, i) == 0
+    grp.update(2)
+    for o in orcs:
+        o.update(2)
+    same_group(grp, orcs)

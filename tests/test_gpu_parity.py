@@ -569,3 +569,39 @@ def test_compaction_and_checkpoint_continue_exactly(dfl, orc, tmp_path):
     same_graph(a, b)
     same_graph(c, b)
     c.close()
+
+
+def test_weights_near_the_2m_limit(dfl, orc):
+    """Edge weights in the hundreds of thousands with 2m just below 2^32:
+    every gain numerator factor (2m, K_i, Sigma_c, K_{i->c}) is close to its
+    2^32 bound, so products reach 2^63; results must still equal the
+    oracle's, and a batch that would take 2m to 2^32 is refused."""
+    rng = np.random.default_rng(29)
+    base = synth.planted_partition(2000, 20, 0.2, 10, 1, 7)
+    m = base.m
+    w = rng.integers(1, 2 * ((1 << 32) - 1) // (2 * m) - 1, m).astype(np.uint64)
+    scale = ((1 << 32) - 2 * 400000 - 64) / (2.0 * float(w.sum()))
+    w = np.maximum(1, (w * scale).astype(np.uint64)).astype(np.uint32)
+    g = synth.EdgeList(base.n, base.u, base.v, w)
+    assert 2 * int(w.astype(np.uint64).sum()) < (1 << 32) - 2 * 400000
+    a, b = pair(dfl, orc, g)
+    a.static()
+    b.static()
+    same_state(a, b)
+    assert a.weights()[2] > (1 << 31)
+    off, idx, _ = synth.to_csr(g)
+    for t in range(3):
+        dels = np.array([(int(g.u[k]), int(g.v[k]), 0) for k in rng.choice(m, 20, replace=False)], np.uint32)
+        x = rng.integers(0, g.n, (10, 2))
+        x = x[x[:, 0] != x[:, 1]]
+        ins = np.concatenate([x, rng.integers(1, 40000, (x.shape[0], 1))], 1).astype(np.uint32)
+        if t:
+            dels = np.zeros((0, 3), np.uint32)  # only the first batch deletes (edges may be gone later)
+        assert a.apply_batch(dels, ins) == 0 and b.apply_batch(dels, ins) == 0
+        a.update([2, 1, 0][t])
+        b.update([2, 1, 0][t])
+        same_state(a, b)
+    big = np.array([[0, 1, 0xFFFFFFFF // 2]], np.uint32)
+    assert a.apply_batch(np.zeros((0, 3), np.uint32), big, check=False) == -3  # DFL_ERR_OVERFLOW
+    assert b.apply_batch(np.zeros((0, 3), np.uint32), big) == -3
+    same_state(a, b, stats=False)
