@@ -480,9 +480,11 @@ struct BlockScratch {
 // 2 x degree slots at `dyn` (at most kBlockSlots keys + values); a vertex of
 // larger degree whose distinct communities overflow it is redone in the
 // block's slice of the global table.  Every thread of the block calls it.
+template <int kThreads>
 __device__ __forceinline__ void block_vertex(const DecideArgs& a, uint32_t i, long long m2, uint32_t gi,
                                              uint32_t* dyn, BlockScratch& sc, MoveSums& sums) {
-  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5, nthr = blockDim.x;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  constexpr uint32_t nthr = kThreads;  // compile-time strides
   const uint32_t d = a.C[i];
   const long long Ki = a.K[i];
   const unsigned long long o = a.g.off[i];
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
       ++sums.processed;
     }
     if (a.rbits && !bit_test(a.rbits, i)) continue;
-    block_vertex(a, i, m2, gi, dyn, sc, sums);
+    block_vertex<kThreads>(a, i, m2, gi, dyn, sc, sums);
   }
   flush_sums(a, sums, threadIdx.x == 0);
 }
@@ -1366,7 +1368,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
           ++sums.processed;
         }
         if (a2.rbits && !bit_test(a2.rbits, i)) continue;
-        block_vertex(a2, i, m2, gi, dyn, sc, sums);
+        block_vertex<kIterThreads>(a2, i, m2, gi, dyn, sc, sums);
       } else if (u < uint64_t(G) + n2 + U1) {
         // one bin-1 vertex per warp and round, in the warp's own table
         for (uint32_t r = 0; r < kIterRounds1; ++r) {
