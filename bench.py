@@ -102,6 +102,19 @@ LAUNCH_DESC = {"auto": "per-bin kernels, graph replay (host launches below 256 b
                "persistent": "one cooperative kernel per iteration"}
 
 
+def whole_job_ms(total_ms: float, steps: int, world: int, device=None) -> float:
+    """ms per batch of the whole job: every rank ran `steps` batches of its
+    own replica; the job took as long as the slowest rank (max over ranks,
+    on `device` for NCCL, on the CPU for gloo)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms / (steps * world)
+
+
 def launch_flag(dfl, args):
     return {"auto": 0, "host": dfl.FLAG_NO_GRAPH, "graph": dfl.FLAG_GRAPH,
             "persistent": dfl.FLAG_PERSISTENT}[args.launch]
@@ -300,13 +313,8 @@ def gpu_arm(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     launches = h.stats()["kernel_launches"] - launches0
     prof = h.profile(reset=True)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = total_ms / (args.steps * world)
+    value = whole_job_ms(sum(step_ms), args.steps, world, dev)
+    ms_per_step = value * world  # the slowest rank's ms per step
 
     # roofline of the local-moving decide kernels (the hot loop)
     peak, peak_kind = peaks()
