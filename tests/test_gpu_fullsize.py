@@ -146,3 +146,56 @@ def test_group_64_graphs_sampled_against_oracle():
         assert (num, den) == (numo, deno) and abs(q - qo) <= 1e-12
         so, sg = o.stats(), grp.graph_stats(k)
         assert sg["passes"] == so["passes"] and sg["iterations"] == so["iterations"]
+
+
+def test_serving_8_graphs_sampled_against_oracle():
+    """The serving workload at full size: 8 resident R-MAT graphs (2^18 to
+    2^23 vertices, 8 edges per vertex) and the Poisson request log of the
+    bench (2,000 requests/s over 0.5 s, batches log-uniform in [10, 1e6]
+    edges), served with coalescing.  The oracle replays the smallest graph's
+    requests with the same grouping: every result of that graph (exact
+    modularity numerator and denominator) and its final membership must
+    match."""
+    import multiprocessing as mp
+    import os
+    import sys
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    import paper_2404_19634_gb300 as dfl
+    from paper_2404_19634_gb300 import serve
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    dfl.build()
+    oracle.build()
+    with mp.get_context("spawn").Pool(min(len(bench.SERVE_SCALES), os.cpu_count() or 1)) as pool:
+        made = pool.map(bench._serve_graph, range(len(bench.SERVE_SCALES)))
+    graphs = [g for g, _ in made]
+    csrs = [c for _, c in made]
+    del made
+    pools = [synth.EdgePool(g, 400 + k) for k, g in enumerate(graphs)]
+    sched = synth.poisson_requests(len(graphs), bench.SERVE_RATE, 0.5, *bench.SERVE_SIZES, seed=500)
+    reqs = serve.make_requests(pools, sched)
+    srv = serve.Server.from_graphs(csrs)
+    res = srv.serve(reqs, coalesce=True)
+    final0 = srv.handles[0].membership().copy()
+    srv.close()
+    assert len(res.groups) < len(reqs)
+    by_id = {r.rid: r for r in reqs}
+    o = oracle.Oracle(*csrs[0])
+    o.static()
+    checked = 0
+    for g, ids in res.groups:
+        if g != 0:
+            continue
+        for i in ids:
+            assert o.apply_batch(by_id[i].dels, by_id[i].ins) == 0
+        o.update(2)  # DF
+        q, num, den = o.modularity()
+        rec = res.records[ids[-1]]
+        assert (rec.num, rec.den) == (num, den), f"request {ids[-1]}"
+        checked += len(ids)
+    assert checked > 50  # requests of graph 0, in a few coalesced updates
+    assert np.array_equal(final0, o.membership())
