@@ -54,8 +54,8 @@ BATCH_FRAC = 1e-3
 # single-pass ncu capture of the timed DF steps: cold (ncu's default, caches
 # flushed before each launch) and warm (--cache-control none).  They belong
 # to the decide kernels as they stand; other workloads report null.
-DECIDE_TRAFFIC_COLD = 53.44e6
-DECIDE_TRAFFIC_WARM = 19.50e6
+DECIDE_TRAFFIC_COLD = 53.43e6
+DECIDE_TRAFFIC_WARM = 19.25e6
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
 SERVE_SCALES = [18, 19, 19, 20, 21, 22, 22, 23]
