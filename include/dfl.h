@@ -95,7 +95,10 @@ enum {
   DFL_FLAG_PERSISTENT = 16u,  /* run each local-moving iteration as one cooperative launch whose
                                  blocks meet at bounded grid barriers between sub-steps; a barrier
                                  that waits about a second gives up and the call returns
-                                 DFL_ERR_TIMEOUT (the handle should then be destroyed) */
+                                 DFL_ERR_TIMEOUT (the handle should then be destroyed).  On a
+                                 device without cooperative launch, or where fewer than 4 blocks
+                                 of the kernel fit at once, the per-bin kernels run instead (same
+                                 results) */
   DFL_FLAG_GRAPH = 32u,       /* always replay each first-pass local-moving iteration as a
                                  captured CUDA graph (needs a handle stream other than the legacy
                                  default stream).  Without this flag or DFL_FLAG_NO_GRAPH, replay
