@@ -256,7 +256,10 @@ const char* dfl_last_error(const dfl_handle* h);
 /* ---- Inspection entry points used by the parity tests ------------------ */
 
 /* Replace the membership; K, Sigma, community sizes and 2m are recomputed
- * from the graph and the pending batch is cleared. */
+ * from the graph and the pending batch is cleared.  With dfl_graph,
+ * dfl_membership and dfl_get_tuning this makes a checkpoint: between
+ * updates those three record everything later updates depend on, and
+ * dfl_create, dfl_set_tuning and dfl_set_membership restore it exactly. */
 int dfl_set_membership(dfl_handle* h, const uint32_t* C, int mem_kind);
 
 /* Initial frontier and affected range (one byte per vertex) that `mode`
