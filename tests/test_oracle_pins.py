@@ -556,3 +556,48 @@ def test_planted_partition_sanity(oracle_mod):
     q_planted = o.modularity()[0]
     assert 0.6 < q_planted < 0.7
     assert q_static > q_planted - 0.15
+
+
+# ---------------------------------------------------------------------------
+# Cross-checks against an independent implementation (networkx)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_modularity_matches_networkx(oracle_mod, seed):
+    """Eq. 1 against networkx's modularity (Newman's definition, written
+    independently) on weighted graphs without self-loops, for random and
+    planted memberships."""
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms.community import modularity
+    rng = np.random.default_rng(100 + seed)
+    g = synth.planted_partition(400, 8, 0.2 + 0.1 * seed, 8, 9, 50 + seed)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_weighted_edges_from(zip(g.u.tolist(), g.v.tolist(), g.w.tolist()))
+    for C in (rng.integers(0, 20, g.n), np.arange(g.n) // 50, np.zeros(g.n, np.int64)):
+        C = C.astype(np.uint32)
+        o.set_membership(C)
+        parts = {}
+        for v, c in enumerate(C.tolist()):
+            parts.setdefault(c, set()).add(v)
+        q_nx = modularity(G, list(parts.values()), weight="weight")
+        assert abs(o.modularity()[0] - q_nx) <= 1e-12
+
+
+def test_static_louvain_quality_near_networkx(oracle_mod):
+    """Sanity, not parity: the oracle's static Louvain (fixed schedule)
+    reaches a modularity close to networkx's Louvain on a planted partition
+    (both heuristics; different orders give nearby local optima)."""
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms.community import louvain_communities, modularity
+    g = synth.sbm(3000, 30, 0.05, 0.002, 5)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_weighted_edges_from(zip(g.u.tolist(), g.v.tolist(), g.w.tolist()))
+    q_nx = modularity(G, louvain_communities(G, weight="weight", seed=1), weight="weight")
+    assert abs(o.modularity()[0] - q_nx) < 0.02
