@@ -43,6 +43,13 @@ MUTANTS = {
     "tolerance_off_by_two": ("u128 den = u128(2) * u128(o.tau_den);", "u128 den = u128(o.tau_den);"),
     "ds_scores_with_stale_k": ("i128 s = score_of(o.m2, kv.second, o.K[i], o.Sigma[kv.first]);",
                                "i128 s = score_of(o.m2, kv.second, o.K[kv.first], o.Sigma[kv.first]);"),
+    "self_loop_counts_twice_in_k": ("for (const Arc& a : G[i]) K[i] += int64_t(a.w);",
+                                    "for (const Arc& a : G[i]) K[i] += int64_t(a.w) * (a.j == i ? 2 : 1);"),
+    "ds_no_neighbour_expansion": ("for (const Arc& a : o.G[i]) dV[a.j] = 1;",
+                                  "for (const Arc& a : o.G[i]) (void)a;"),
+    "ds_no_community_expansion": ("if (dC[o.C[i]]) dV[i] = 1;", "if (false && dC[o.C[i]]) dV[i] = 1;"),
+    "aggregation_test_flipped": ("if (double(ncomm) / double(nv) > o.opt.tau_agg) break;",
+                                 "if (double(ncomm) / double(nv) < o.opt.tau_agg) break;"),
 }
 
 PIN_TESTS = [
@@ -64,6 +71,7 @@ PIN_TESTS = [
     (pins.test_figure3_initial_frontier, {}),
     (pins.test_iteration_tolerance_is_exact, {}),
     (pins.test_static_equals_nd_from_singletons, {}),
+    (pins.test_aggregation_tolerance_rule, {}),
 ]
 
 

@@ -504,6 +504,25 @@ def test_iteration_tolerance_is_exact(oracle_mod):
             assert converged or len(tr) == 20
 
 
+def test_aggregation_tolerance_rule(oracle_mod):
+    """Alg. 4's tau_agg test: after a pass of more than one iteration the
+    graph is aggregated and another pass runs unless the communities are
+    more than tau_agg of its vertices.  A clustered graph shrinks to a few
+    percent, so static Louvain runs a second pass at tau_agg = 0.8 and stops
+    after the first at tau_agg = 0 (every ratio exceeds it)."""
+    g = synth.sbm(2000, 20, 0.05, 0.001, 8)
+    off, idx, w = synth.to_csr(g)
+    o = oracle_mod.Oracle(g.n, off, idx, w)
+    o.static()
+    st = o.stats()
+    assert st["iterations"][0] > 1 and st["passes"] >= 2
+    o2 = oracle_mod.Oracle(g.n, off, idx, w)
+    o2.set_options(tau_agg=0.0)
+    o2.static()
+    st2 = o2.stats()
+    assert st2["iterations"][0] > 1 and st2["passes"] == 1
+
+
 def test_static_equals_nd_from_singletons(oracle_mod):
     g = synth.sbm(1500, 15, 0.06, 0.003, 21)
     off, idx, w = synth.to_csr(g)
