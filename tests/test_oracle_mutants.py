@@ -50,6 +50,7 @@ MUTANTS = {
     "ds_no_community_expansion": ("if (dC[o.C[i]]) dV[i] = 1;", "if (false && dC[o.C[i]]) dV[i] = 1;"),
     "aggregation_test_flipped": ("if (double(ncomm) / double(nv) > o.opt.tau_agg) break;",
                                  "if (double(ncomm) / double(nv) < o.opt.tau_agg) break;"),
+    "no_tolerance_drop": ("den *= u128(o.tolerance_drop);", "den *= u128(1);"),
 }
 
 PIN_TESTS = [
@@ -72,6 +73,7 @@ PIN_TESTS = [
     (pins.test_iteration_tolerance_is_exact, {}),
     (pins.test_static_equals_nd_from_singletons, {}),
     (pins.test_aggregation_tolerance_rule, {}),
+    (pins.test_tolerance_drops_per_pass, {}),
 ]
 
 

@@ -504,6 +504,23 @@ def test_iteration_tolerance_is_exact(oracle_mod):
             assert converged or len(tr) == 20
 
 
+def test_tolerance_drops_per_pass(oracle_mod):
+    """Alg. 4 divides the iteration tolerance by TOLERANCE_DROP after every
+    pass: the first pass is the same whatever the drop, and a tighter
+    second-pass tolerance (drop 10) makes the second pass iterate longer
+    than no drop (drop 1) on the same first-pass result."""
+    for g in (synth.sbm(3000, 30, 0.05, 0.002, 8), synth.planted_partition(3000, 30, 0.35, 10, 4, 8)):
+        off, idx, w = synth.to_csr(g)
+        its = {}
+        for drop in (10, 1):
+            o = oracle_mod.Oracle(g.n, off, idx, w)
+            o.set_options(tolerance_drop=drop)
+            o.static()
+            its[drop] = o.stats()["iterations"]
+        assert its[10][0] == its[1][0]
+        assert its[10][1] > its[1][1]
+
+
 def test_aggregation_tolerance_rule(oracle_mod):
     """Alg. 4's tau_agg test: after a pass of more than one iteration the
     graph is aggregated and another pass runs unless the communities are
