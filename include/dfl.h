@@ -123,7 +123,9 @@ typedef struct {
   uint64_t tau_num;        /* iteration tolerance tau = tau_num / tau_den, default 1/100 */
   uint64_t tau_den;
   uint64_t tolerance_drop; /* tau is divided by this after every pass, default 10 */
-  double tau_agg;          /* aggregation tolerance, default 0.8 (1.0 disables) */
+  double tau_agg;          /* aggregation tolerance: passes stop when communities exceed tau_agg
+                              of the current graph's vertices (Alg. 4); default 0.8, 1.0
+                              disables the test */
   uint32_t substeps;       /* synchronous sub-steps per iteration: 1, 2, 4 (default) or 8 */
   uint32_t flags;          /* DFL_FLAG_* */
 } dfl_options;
