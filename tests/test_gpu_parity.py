@@ -232,7 +232,7 @@ def test_louvain_from_random_frontier(dfl, orc):
     same_state(a, b)
 
 
-def test_temporal_no_aggregation(dfl, orc):
+def test_temporal_aggregation_tolerance_disabled(dfl, orc):
     """tau_agg = 1 (Section 5.1.2, real-world dynamic graphs): the low-shrink
     test of Alg. 4 is disabled, so passes only stop on convergence."""
     src, dst = synth.temporal_pa_stream(3000, 40000, 0.3, 21)
