@@ -128,36 +128,153 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _visible_device(gpu_index: int) -> str:
+    """The NVML name of CUDA device `gpu_index`: its entry of
+    CUDA_VISIBLE_DEVICES (an index or a GPU-/MIG- UUID), else the index."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if vis:
+        ent = [x.strip() for x in vis.split(",") if x.strip()]
+        if gpu_index < len(ent):
+            return ent[gpu_index]
+    return str(gpu_index)
+
+
+class NvmlReader:
+    """Read-only NVML queries of one GPU through ctypes and the driver's
+    libnvidia-ml: the current and maximum SM clock, the power draw and the
+    active clock-event reasons.  Raises OSError where NVML is unavailable."""
+
+    CLOCK_SM = 1  # nvmlClockType_t NVML_CLOCK_SM
+
+    def __init__(self, gpu_index: int):
+        import ctypes
+        self.ct = ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError as e:
+            raise OSError(f"libnvidia-ml: {e}") from None
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib = lib
+        self.dev = ctypes.c_void_p()
+        key = _visible_device(gpu_index)
+        if key.startswith(("GPU-", "MIG-")):
+            rc = lib.nvmlDeviceGetHandleByUUID(key.encode(), ctypes.byref(self.dev))
+        elif key.isdigit():
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(key)), ctypes.byref(self.dev))
+        else:
+            rc = -1
+        count = ctypes.c_uint(0)
+        if rc != 0 and lib.nvmlDeviceGetCount_v2(ctypes.byref(count)) == 0 and count.value == 1:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(0), ctypes.byref(self.dev))  # the only GPU
+        if rc != 0:
+            lib.nvmlShutdown()
+            raise OSError(f"no NVML handle for device {key!r}")
+        # the reasons query was renamed in later NVML versions; either returns the same bits
+        self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        ok = lib.nvmlDeviceGetMaxClockInfo(self.dev, self.CLOCK_SM, ctypes.byref(mx)) == 0
+        self.max_mhz = float(mx.value) if ok else None
+
+    def sample(self):
+        """(SM MHz, power W or None, reason bits) now, or None."""
+        ct, lib = self.ct, self.lib
+        clk, bits, mw = ct.c_uint(0), ct.c_ulonglong(0), ct.c_uint(0)
+        if lib.nvmlDeviceGetClockInfo(self.dev, self.CLOCK_SM, ct.byref(clk)) != 0:
+            return None
+        if self._reasons(self.dev, ct.byref(bits)) != 0:
+            return None
+        pw = mw.value / 1000.0 if lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw)) == 0 else None
+        return float(clk.value), pw, int(bits.value)
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    """Samples the SM clock, power draw and clock-event reasons of one GPU
+    while the timed steps run: in process through NVML every `period`
+    seconds (one sample on entry, then from a thread, and one on exit), or, where
+    NVML does not load, with nvidia-smi every 50 ms (entry waits for its
+    first line, so it is sampling when the timed steps start)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits and the names reported for them
+    REASON_BITS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+                   ("hw_thermal_slowdown", 0x40), ("hw_power_brake_slowdown", 0x80))
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, reader=None, period: float = 2e-3):
         self.gpu = gpu_index
+        self.reader = reader
+        self._own = False
+        self.period = period
         self.proc = None
         self.lines = []
+        self.samples = []  # NVML: (MHz, W or None, bits)
+        self.source = None
+        self._stop = threading.Event()
+        self.t = None
 
     def __enter__(self):
+        if self.reader is None:
+            try:
+                self.reader = NvmlReader(self.gpu)
+                self._own = True
+            except Exception:  # no NVML here: nvidia-smi below
+                self.reader = None
+        self._stop.clear()
+        if self.reader is not None:
+            self.source = "nvml"
+            self._take()
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
+            self._first = threading.Event()
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self._first.wait(5.0)
         except OSError:
             self.proc = None
         return self
 
+    def _take(self):
+        try:
+            s = self.reader.sample()
+        except Exception:  # a failed read costs a sample, never the run
+            return
+        if s is not None:
+            self.samples.append(s)
+
+    def _poll(self):
+        while not self._stop.wait(self.period):
+            self._take()
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self._first.set()
+        self._first.set()
 
     def __exit__(self, *a):
-        if self.proc:
+        if self.source == "nvml":
+            self._stop.set()
+            self.t.join(timeout=5)
+            self._take()
+            if self._own:
+                try:
+                    self.reader.close()
+                except Exception:
+                    pass
+        elif self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -165,22 +282,35 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if f[5 + k].lower() == "active":
-                    reasons.add(nm)
+        sm, pw, mx, reasons = [], [], None, set()
+        if self.source == "nvml":
+            mx = self.reader.max_mhz
+            for mhz, w, bits in self.samples:
+                sm.append(mhz)
+                if w is not None:
+                    pw.append(w)
+                reasons.update(nm for nm, b in self.REASON_BITS if bits & b)
+        else:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for ln in self.lines:
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                try:
+                    pw.append(float(f[3]))
+                except ValueError:
+                    pass
+                for k, nm in enumerate(names):
+                    if f[5 + k].lower() == "active":
+                        reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": round(statistics.median(pw), 1) if pw else None, "source": self.source}
 
 
 def make_workload(args, rank=0):

@@ -29,3 +29,82 @@ def test_group_member_is_the_group_graph():
         assert np.array_equal(g.u, ref.u) and np.array_equal(g.v, ref.v) and np.array_equal(g.w, ref.w)
         o2, i2, w2 = synth.to_csr(ref)
         assert np.array_equal(off, o2) and np.array_equal(idx, i2) and np.array_equal(w, w2)
+
+
+class _FakeNvml:
+    """Stands in for the NVML reader: a fixed sequence of (MHz, W, reason bits)."""
+
+    def __init__(self, seq):
+        self.seq = list(seq)
+        self.k = 0
+        self.max_mhz = 2070.0
+
+    def sample(self):
+        s = self.seq[min(self.k, len(self.seq) - 1)]
+        self.k += 1
+        return s
+
+
+def test_clock_sampler_summary_from_nvml_readings():
+    import time
+
+    import bench
+    fake = _FakeNvml([(2070.0, 900.0, 0x0), (1980.0, 1390.0, 0x4), (2070.0, 1000.0, 0x1)])
+    with bench.Clocks(0, reader=fake, period=1e-3) as c:
+        time.sleep(0.05)
+    s = c.summary()
+    assert s["source"] == "nvml" and s["samples"] >= 3 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]  # the idle bit (0x1) is not a slowdown
+    assert s["sm_mhz"] == 2070.0 and s["power_w"] == 1000.0
+    fake = _FakeNvml([(1500.0, None, 0x8 | 0x20 | 0x40 | 0x80)])
+    with bench.Clocks(0, reader=fake) as c:
+        pass
+    s = c.summary()
+    assert s["samples"] == 2 and s["power_w"] is None  # one on entry, one on exit
+    assert s["reasons"] == ["hw_power_brake_slowdown", "hw_slowdown", "hw_thermal_slowdown",
+                            "sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_a_gpu():
+    """Where neither NVML nor nvidia-smi answers, the sampler reports no
+    samples instead of failing the run."""
+    import shutil
+
+    import pytest
+
+    import bench
+    try:
+        bench.NvmlReader(0).close()
+        pytest.skip("NVML answers here")
+    except (OSError, AttributeError):
+        pass
+    if shutil.which("nvidia-smi"):
+        pytest.skip("nvidia-smi present")
+    with bench.Clocks(0) as c:
+        pass
+    s = c.summary()
+    assert s == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "power_w": None,
+                 "source": None}
+
+
+def test_visible_device_names(monkeypatch):
+    import bench
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES", raising=False)
+    assert bench._visible_device(0) == "0"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-abc, 5")
+    assert bench._visible_device(0) == "GPU-abc" and bench._visible_device(1) == "5"
+    assert bench._visible_device(2) == "2"
+
+
+def test_clock_sampler_survives_a_failing_reader():
+    import bench
+
+    class Broken:
+        max_mhz = None
+
+        def sample(self):
+            raise RuntimeError("driver went away")
+
+    with bench.Clocks(0, reader=Broken(), period=1e-3) as c:
+        pass
+    assert c.summary()["samples"] == 0
