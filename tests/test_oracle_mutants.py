@@ -51,6 +51,10 @@ MUTANTS = {
     "aggregation_test_flipped": ("if (double(ncomm) / double(nv) > o.opt.tau_agg) break;",
                                  "if (double(ncomm) / double(nv) < o.opt.tau_agg) break;"),
     "no_tolerance_drop": ("den *= u128(o.tolerance_drop);", "den *= u128(1);"),
+    "frontier_dropped_between_iterations": ("F.swap(Fnext);", "F.assign(nv, 0);"),
+    "trace_counts_movers_as_processed": ("o.trace.push_back({processed, moved, dq_sum});",
+                                         "o.trace.push_back({moved, moved, dq_sum});"),
+    "sizes_not_carried": ("sizep[mv.d] -= 1;", "sizep[mv.d] -= 0;"),
 }
 
 PIN_TESTS = [
@@ -74,6 +78,10 @@ PIN_TESTS = [
     (pins.test_static_equals_nd_from_singletons, {}),
     (pins.test_aggregation_tolerance_rule, {}),
     (pins.test_tolerance_drops_per_pass, {}),
+    (pins.test_first_pass_replays_as_single_iterations,
+     {"mode": "static", "n": 1500, "blocks": 15, "mu": 0.3, "size": 0, "several": True}),
+    (pins.test_first_pass_replays_as_single_iterations,
+     {"mode": 2, "n": 1500, "blocks": 15, "mu": 0.3, "size": 1500, "several": True}),
 ]
 
 

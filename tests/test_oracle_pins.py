@@ -504,6 +504,58 @@ def test_iteration_tolerance_is_exact(oracle_mod):
             assert converged or len(tr) == 20
 
 
+@pytest.mark.parametrize("mode,n,blocks,mu,size,several", [
+    ("static", 1500, 15, 0.3, 0, True), (0, 1500, 15, 0.3, 1500, True), (1, 1500, 15, 0.3, 1500, True),
+    (2, 1500, 15, 0.3, 1500, True),
+    (1, 3000, 150, 0.2, 60, False), (2, 3000, 150, 0.2, 60, False),  # DS marks 2/3 of the vertices here
+])
+def test_first_pass_replays_as_single_iterations(oracle_mod, mode, n, blocks, mu, size, several):
+    """Pass 0 of Alg. 4 repeats Alg. 5's iteration from the initial frontier
+    until sum dQ <= tau (exactly: 100 S <= 2m^2) or 20 iterations.  Replaying
+    it one iteration at a time -- the single iteration is pinned by brute
+    force above; community sizes are recounted from scratch before each --
+    gives the driver's trace (vertices processed, movers and S of every
+    iteration), its iteration count, and its counts of initially and ever
+    affected vertices."""
+    g = synth.planted_partition(n, blocks, mu, 10, 3, 5)
+    off, idx, w = synth.to_csr(g)
+    a = oracle_mod.Oracle(g.n, off, idx, w)
+    b = oracle_mod.Oracle(g.n, off, idx, w)
+    if mode == "static":
+        a.static()
+        b.set_membership(np.arange(g.n, dtype=np.uint32))  # singletons, K and Sigma from scratch
+        F = np.ones(g.n, np.uint8)
+        R = np.ones(g.n, np.uint8)
+    else:
+        a.static()
+        b.static()
+        d, i = synth.BatchStream(g, 3).next(size, w_max=3)
+        assert a.apply_batch(d, i) == 0 and b.apply_batch(d, i) == 0
+        a.update(mode)
+        F, R = b.mark(mode)
+    _, _, m2 = b.weights()
+    initial = int(F.sum())
+    ever = np.zeros(g.n, bool)
+    trace = []
+    for _ in range(20):
+        ever |= F.astype(bool)
+        processed = int(F.sum())
+        F, moved, S = b.move_iteration(F, R)
+        trace.append((processed, int(moved.sum()), S))
+        assert (S > 0) == (moved.sum() > 0)  # every move gains
+        if 100 * S <= m2 * m2 // 2:
+            break
+    st = a.stats()
+    assert a.trace() == trace
+    assert st["iterations"][0] == len(trace)
+    assert st["affected_initial"] == initial and st["affected_ever"] == int(ever.sum())
+    if mode in ("static", 0):
+        assert initial == g.n
+    if mode == 1 and not several:
+        assert 0 < int(R.sum()) < g.n  # a proper affected range
+    assert (len(trace) > 1) == several  # > 1: the carry-over between iterations is exercised
+
+
 def test_tolerance_drops_per_pass(oracle_mod):
     """Alg. 4 divides the iteration tolerance by TOLERANCE_DROP after every
     pass: the first pass is the same whatever the drop, and a tighter
