@@ -42,3 +42,22 @@ def test_binding_covers_every_declared_symbol():
 def test_build_targets_sm103a_only():
     assert "arch=compute_103a,code=sm_103a" in dfl.NVCC_FLAGS
     assert not any("sm_90" in f or "sm_100" in f for f in dfl.NVCC_FLAGS)
+
+
+def test_c_caller_compiles_and_links(libpath, tmp_path):
+    """The header is plain C99 (no C++ needed by a caller) and a C program
+    using the basic calls links against the library as built."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(os.path.dirname(__file__), "c_api_example.c")
+    exe = str(tmp_path / "c_api_example")
+    libdir = os.path.dirname(libpath)
+    out = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                          "-I", os.path.dirname(HEADER), src, "-o", exe, "-L", libdir, "-ldfl",
+                          "-Wl,-rpath," + libdir],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert os.path.exists(exe)
