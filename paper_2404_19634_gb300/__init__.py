@@ -209,13 +209,21 @@ def _is_tensor(x) -> bool:
 
 
 def _buf(x, dtype):
-    """(pointer, mem_kind, keepalive) for a numpy array or a CUDA tensor."""
+    """(pointer, mem_kind, keepalive) for a numpy array or a tensor (CUDA or
+    host).  A tensor is passed as it is, so it must be contiguous and hold
+    integers of `dtype`'s width (int32 or uint32 for uint32, ...); an array
+    of another integer type is converted, one of floats is refused."""
     if x is None:
         return None, MEM_HOST, None
+    want = np.dtype(dtype)
     if _is_tensor(x):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if x.is_floating_point() or x.is_complex() or x.element_size() != want.itemsize:
+            raise TypeError(f"a tensor of {x.dtype} where {want.itemsize}-byte integers ({want}) are expected")
         return ct.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    if isinstance(x, np.ndarray) and x.dtype.kind not in "iub":
+        raise TypeError(f"an array of {x.dtype} where integers ({want}) are expected")
     a = np.ascontiguousarray(x, dtype=dtype)
     return ct.c_void_p(a.ctypes.data), MEM_HOST, a
 

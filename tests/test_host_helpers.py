@@ -1,6 +1,7 @@
 """Host-side helpers that need no GPU: checkpoint files and the per-graph
 generator of the batched workload."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -108,3 +109,27 @@ def test_clock_sampler_survives_a_failing_reader():
     with bench.Clocks(0, reader=Broken(), period=1e-3) as c:
         pass
     assert c.summary()["samples"] == 0
+
+
+def test_buffer_marshalling_checks_types():
+    """Tensors are passed by pointer, so their element width must match;
+    arrays of other integer types are converted; floats are refused."""
+    import torch
+
+    import paper_2404_19634_gb300 as dfl
+    ok = torch.zeros((4, 3), dtype=torch.int32)
+    p, mk, keep = dfl._buf(ok, np.uint32)
+    assert p.value == ok.data_ptr() and mk == dfl.MEM_HOST and keep is ok
+    assert dfl._buf(torch.zeros(5, dtype=torch.int64), np.uint64)[0].value is not None
+    for bad, want in ((torch.zeros((4, 3), dtype=torch.int64), np.uint32),
+                      (torch.zeros(4, dtype=torch.float32), np.uint32),
+                      (torch.zeros(4, dtype=torch.int32), np.uint64)):
+        with pytest.raises(TypeError):
+            dfl._buf(bad, want)
+    with pytest.raises(ValueError):
+        dfl._buf(torch.zeros((3, 4), dtype=torch.int32).t(), np.uint32)
+    with pytest.raises(TypeError):
+        dfl._buf(np.ones(3, np.float64), np.uint32)
+    p, mk, a = dfl._buf(np.arange(3, dtype=np.int64), np.uint32)
+    assert mk == dfl.MEM_HOST and a.dtype == np.uint32 and list(a) == [0, 1, 2]
+    assert dfl._buf(None, np.uint32) == (None, dfl.MEM_HOST, None)
