@@ -55,6 +55,10 @@ MUTANTS = {
     "trace_counts_movers_as_processed": ("o.trace.push_back({processed, moved, dq_sum});",
                                          "o.trace.push_back({moved, moved, dq_sum});"),
     "sizes_not_carried": ("sizep[mv.d] -= 1;", "sizep[mv.d] -= 0;"),
+    "final_lookup_skips_last_pass": ("for (uint32_t i = 0; i < n; ++i) Ct[i] = Cp[Ctop[i]];",
+                                     "for (uint32_t i = 0; i < n; ++i) Ct[i] = Ctop[i];"),
+    "later_pass_frontier_empty": ("F.assign(ncomm, 1);", "F.assign(ncomm, 0);"),
+    "sigma_not_reset_after_aggregation": ("Sp = Kp;", "Sp.resize(ncomm);"),
 }
 
 PIN_TESTS = [
@@ -82,6 +86,7 @@ PIN_TESTS = [
      {"mode": "static", "n": 1500, "blocks": 15, "mu": 0.3, "size": 0, "several": True}),
     (pins.test_first_pass_replays_as_single_iterations,
      {"mode": 2, "n": 1500, "blocks": 15, "mu": 0.3, "size": 1500, "several": True}),
+    (pins.test_later_passes_are_louvain_on_the_aggregated_graph, {"case": "static"}),
 ]
 
 

@@ -556,6 +556,52 @@ def test_first_pass_replays_as_single_iterations(oracle_mod, mode, n, blocks, mu
     assert (len(trace) > 1) == several  # > 1: the carry-over between iterations is exercised
 
 
+@pytest.mark.parametrize("case", ["static", "df"])
+def test_later_passes_are_louvain_on_the_aggregated_graph(oracle_mod, case):
+    """Alg. 4's passes compose: after the first pass, Louvain continues on
+    the aggregated graph G' from singletons with every vertex unprocessed and
+    the tolerance dropped once.  So the full run's membership equals the
+    first pass's membership (renumbered ascending) looked up in a separate
+    run of static Louvain on G' whose tolerance starts at tau / 10, and the
+    two runs have the same Sigma, modularity and later-pass iteration counts."""
+    if case == "static":
+        g = synth.planted_partition(3000, 60, 0.4, 8, 4, 6)
+    else:
+        g = synth.planted_partition(2000, 40, 0.3, 8, 3, 5)
+    off, idx, w = synth.to_csr(g)
+    full = oracle_mod.Oracle(g.n, off, idx, w)
+    first = oracle_mod.Oracle(g.n, off, idx, w)
+    if case == "static":
+        first.set_options(max_passes=1)
+        full.static()
+        first.static()
+    else:
+        full.static()
+        first.static()
+        d, i = synth.BatchStream(g, 3).next(5000, w_max=3)
+        assert full.apply_batch(d, i) == 0 and first.apply_batch(d, i) == 0
+        first.set_options(max_passes=1)
+        full.update(2)
+        first.update(2)
+    st = full.stats()
+    assert st["passes"] >= 3 and first.stats()["iterations"] == st["iterations"][:1]
+    C0 = first.membership()
+    soff, sidx, sw = first.aggregate()
+    nv = len(soff) - 1
+    ren = np.zeros(g.n, np.int64)
+    labels = np.unique(C0)
+    ren[labels] = np.arange(labels.shape[0])
+    sup = oracle_mod.Oracle(nv, soff, sidx, sw.astype(np.uint32), allow_self_loops=True)
+    sup.set_options(max_passes=9, tau_den=1000)
+    sup.static()
+    assert np.array_equal(full.membership(), sup.membership()[ren[C0]])
+    assert sup.stats()["iterations"] == st["iterations"][1:]
+    _, Sf, m2f = full.weights()
+    _, Ss, m2s = sup.weights()
+    assert m2f == m2s and np.array_equal(Sf[:nv], Ss) and not Sf[nv:].any()
+    assert full.modularity()[1:] == sup.modularity()[1:]
+
+
 def test_tolerance_drops_per_pass(oracle_mod):
     """Alg. 4 divides the iteration tolerance by TOLERANCE_DROP after every
     pass: the first pass is the same whatever the drop, and a tighter
