@@ -96,6 +96,74 @@ def test_delta_modularity_matches_q_difference(oracle_mod, seed, loops):
             assert Fraction(2 * num, m2 * m2) == newman_q(A, move(C, i, c)) - q0
 
 
+# The appendix's correctness argument lists how one vertex migration i: d -> c
+# changes every other vertex v's delta-modularity (its cases 17-28; nothing
+# else changes: K and m stay, Sigma_d loses K_i and Sigma_c gains it).  In
+# numerator units N = 2m^2 dQ, with m2 = 2m, w = w_iv and the communities
+# named by their role (v's own first, then the target):
+#   17  d, neighbour, -> c    +2 m2 w - 2 K_i K_v
+#   18  d, neighbour, -> b    +m2 w - K_i K_v
+#   19  c, neighbour, -> d    -2 m2 w + 2 K_i K_v
+#   20  c, neighbour, -> b    -m2 w + K_i K_v
+#   21  b, neighbour, -> d    -m2 w + K_i K_v
+#   22  b, neighbour, -> c    +m2 w - K_i K_v
+#   23  d, non-neighbour, -> c   -2 K_i K_v  (printed with +: case 17 at w = 0
+#                                             and Eq. 2 both give -)
+#   24  d, non-neighbour, -> b   -K_i K_v
+#   25  c, non-neighbour, -> d   +2 K_i K_v
+#   26  c, non-neighbour, -> b   +K_i K_v
+#   27  b, non-neighbour, -> d   +K_i K_v
+#   28  b, non-neighbour, -> c   -K_i K_v
+MIGRATION_CASES = {
+    ("d", True, "c"): (17, lambda m2, w, ki, kv: 2 * m2 * w - 2 * ki * kv),
+    ("d", True, "b"): (18, lambda m2, w, ki, kv: m2 * w - ki * kv),
+    ("c", True, "d"): (19, lambda m2, w, ki, kv: -2 * m2 * w + 2 * ki * kv),
+    ("c", True, "b"): (20, lambda m2, w, ki, kv: -m2 * w + ki * kv),
+    ("b", True, "d"): (21, lambda m2, w, ki, kv: -m2 * w + ki * kv),
+    ("b", True, "c"): (22, lambda m2, w, ki, kv: m2 * w - ki * kv),
+    ("d", False, "c"): (23, lambda m2, w, ki, kv: -2 * ki * kv),
+    ("d", False, "b"): (24, lambda m2, w, ki, kv: -ki * kv),
+    ("c", False, "d"): (25, lambda m2, w, ki, kv: 2 * ki * kv),
+    ("c", False, "b"): (26, lambda m2, w, ki, kv: ki * kv),
+    ("b", False, "d"): (27, lambda m2, w, ki, kv: ki * kv),
+    ("b", False, "c"): (28, lambda m2, w, ki, kv: -ki * kv),
+}
+
+
+def test_vertex_migration_changes_neighbour_gains_as_the_appendix_states(oracle_mod):
+    """Cases 17-28 of the appendix, exactly: for random weighted graphs and
+    memberships, move one vertex i from d to c and compare every other
+    vertex's change in 2m^2 dQ with the case it falls in."""
+    seen = set()
+    for seed in range(12):
+        rng = np.random.default_rng(700 + seed)
+        n = 24
+        off, idx, w = random_graph(rng, n, 0.35, wmax=3)
+        A = dense_matrix(n, off, idx, w)
+        C = rng.integers(0, 4, n).astype(np.uint32)
+        C[:4] = [0, 1, 2, 3]  # every label used
+        o = make(oracle_mod, n, off, idx, w)
+        o.set_membership(C)
+        K, _, m2 = o.weights()
+        i = int(rng.integers(4, n))
+        d = int(C[i])
+        c = int(rng.choice([x for x in range(4) if x != d]))
+        before = {(v, y): o.delta_q_num(v, y) for v in range(n) if v != i for y in range(4) if y != C[v]}
+        C2 = C.copy()
+        C2[i] = c
+        o.set_membership(C2)
+        assert o.weights()[2] == m2
+        for (v, y), n0 in before.items():
+            role = lambda x: "d" if x == d else "c" if x == c else "b"
+            if role(int(C[v])) == "b" and role(y) == "b":
+                assert o.delta_q_num(v, y) == n0  # between two bystander communities: unchanged
+                continue
+            case, delta = MIGRATION_CASES[(role(int(C[v])), A[i][v] > 0, role(y))]
+            assert o.delta_q_num(v, y) - n0 == delta(m2, A[i][v], int(K[i]), int(K[v])), (case, v, y)
+            seen.add(case)
+    assert seen == set(range(17, 29))
+
+
 # ---------------------------------------------------------------------------
 # Alg. 5 -- local-moving decisions against brute force
 # ---------------------------------------------------------------------------
