@@ -29,6 +29,16 @@ __all__ = [
     "random_batch",
     "BatchStream",
     "temporal_pa_stream",
+    "temporal_pa_stream_vec",
+    "temporal_edges",
+    "window_batch",
+    "graph_stats",
+    "log_uniform_int",
+    "EdgePool",
+    "poisson_requests",
+    "planted_group_params",
+    "planted_group_member",
+    "planted_group",
 ]
 
 
