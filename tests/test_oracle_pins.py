@@ -788,6 +788,35 @@ def test_modularity_matches_networkx(oracle_mod, seed):
         assert abs(o.modularity()[0] - q_nx) <= 1e-12
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_helper_matches_networkx(seed):
+    """The exact all-pairs Q that several pins use as their reference agrees
+    with networkx's modularity on random weighted graphs with self-loops.
+    A self-loop arc of weight w counts once in K_i and in sigma_c here
+    (R1, R2); networkx counts a self-loop twice in a degree, so it gets the
+    loop with weight w / 2."""
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms.community import modularity
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(5, 14))
+    off, idx, w = random_graph(rng, n, 0.4, wmax=5, self_loops=True)
+    if len(idx) == 0:
+        pytest.skip("empty graph")
+    A = dense_matrix(n, off, idx, w)
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    for i in range(n):
+        for j in range(i, n):
+            if A[i][j]:
+                G.add_edge(i, j, weight=A[i][j] / 2 if i == j else A[i][j])
+    for C in (rng.integers(0, 3, n), np.arange(n), np.zeros(n, np.int64)):
+        parts = {}
+        for v, c in enumerate(C.tolist()):
+            parts.setdefault(c, set()).add(v)
+        q_nx = modularity(G, list(parts.values()), weight="weight")
+        assert abs(float(newman_q(A, list(C))) - q_nx) <= 1e-12
+
+
 def test_static_louvain_quality_near_networkx(oracle_mod):
     """Sanity, not parity: the oracle's static Louvain (fixed schedule)
     reaches a modularity close to networkx's Louvain on a planted partition
