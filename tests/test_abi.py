@@ -61,3 +61,24 @@ def test_c_caller_compiles_and_links(libpath, tmp_path):
                          capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
     assert os.path.exists(exe)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every entry point raises."""
+    monkeypatch.setattr(dfl, "_lib", None)
+    monkeypatch.setattr(dfl, "_LIB", str(tmp_path / "absent" / "libdfl.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        dfl.Dfl(2, [0, 1, 2], [1, 0], [1, 1])
+    with pytest.raises(RuntimeError, match="not built"):
+        dfl.default_options()
+
+
+def test_product_package_does_not_use_the_oracle():
+    """The oracle is test infrastructure: nothing in the package imports,
+    loads or runs it."""
+    pkg = os.path.dirname(dfl.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert not re.search(r"\bimport\s+oracle\b|\bfrom\s+oracle\b|dfl_oracle|liboracle", text), f
