@@ -1010,9 +1010,16 @@ int ensure_hash_buffers(Handle* h, uint64_t na) {
   while (cap < 2 * na) cap <<= 1;
   if (cap > h->h_cap) {
     cudaStreamSynchronize(h->stream);
-    void* old[] = {h->h_keys, h->h_ndel, h->h_wdel, h->h_wins, h->h_slot, h->h_wnew,
-                   h->h_flag, h->h_delta, h->h_pairs};
-    for (void* q : old) cudaFree(q);
+    // freed and cleared together, so that an allocation failing below leaves
+    // no member pointing at freed memory (destroy and the next growth free
+    // every member)
+    void** old[] = {(void**)&h->h_keys, (void**)&h->h_ndel, (void**)&h->h_wdel, (void**)&h->h_wins,
+                    (void**)&h->h_slot, (void**)&h->h_wnew, (void**)&h->h_flag, (void**)&h->h_delta,
+                    (void**)&h->h_pairs};
+    for (void** q : old) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
     h->h_cap = 0;
     DFL_CUDA(h, cudaMalloc(&h->h_keys, sizeof(unsigned long long) * cap));
     DFL_CUDA(h, cudaMalloc(&h->h_ndel, sizeof(uint32_t) * cap));

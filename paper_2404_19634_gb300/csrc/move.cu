@@ -1761,9 +1761,10 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
     {
       uint64_t c = h->g_res_cap;
       GiantRes* r = static_cast<GiantRes*>(h->g_res);
-      DFL_TRY(regrow(&r, c, res, sizeof(GiantRes), -1));
-      h->g_res = r;
+      const int rc = regrow(&r, c, res, sizeof(GiantRes), -1);
+      h->g_res = r;  // also when the allocation failed: the old buffer is gone
       h->g_res_cap = c;
+      DFL_TRY(rc);
     }
     if (tab > h->g_tab_cap) {
       uint64_t c0 = h->g_tab_cap, c1 = c0;
