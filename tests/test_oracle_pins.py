@@ -330,6 +330,48 @@ def test_incremental_weights_equal_recomputation(oracle_mod, mode):
         assert S.sum() == m2 and K.sum() == m2  # sum Sigma_c = 2m
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_several_batches_before_one_update(oracle_mod, seed):
+    """R19: batches applied one after another before a single update are
+    each applied against C^{t-1} and marked together (Alg. 1 over every arc
+    of every batch).  When the batches do not touch the same edge, that is
+    one batch holding all of them: the same K, Sigma, 2m, initial frontier,
+    and the same update result."""
+    rng = np.random.default_rng(40 + seed)
+    g = synth.planted_partition(800, 16, 0.3, 8, 4, 11 + seed)
+    off, idx, w = synth.to_csr(g)
+    a = oracle_mod.Oracle(g.n, off, idx, w)
+    b = oracle_mod.Oracle(g.n, off, idx, w)
+    a.static()
+    b.static()
+    base = edges_of(g.n, off, idx, w)
+    pick = rng.choice(len(base), 60, replace=False)
+    dels = [(base[p][0], base[p][1], 0 if k % 3 else int(rng.integers(1, base[p][2] + 1)))
+            for k, p in enumerate(pick)]
+    gone = {(min(u, v), max(u, v)) for u, v, _ in dels}
+    ins = []
+    while len(ins) < 90:
+        u = int(rng.integers(0, g.n))
+        v = int(rng.integers(0, g.n - 1))
+        v += v >= u
+        if (min(u, v), max(u, v)) not in gone:  # a whole-weight deletion after an insertion
+            ins.append((u, v, int(rng.integers(1, 4))))  # would depend on the order
+    batches = [(dels[:30], ins[:50]), (dels[30:], ins[50:])]  # no edge deleted twice
+    for d, i in batches:
+        assert a.apply_batch(np.array(d, np.uint32), np.array(i, np.uint32)) == 0
+    assert b.apply_batch(np.array(dels, np.uint32), np.array(ins, np.uint32)) == 0
+    for x, y in zip(a.weights(), b.weights()):
+        assert np.array_equal(x, y)
+    Fa, Ra = a.mark(2)
+    Fb, Rb = b.mark(2)
+    assert np.array_equal(Fa, Fb) and np.array_equal(Ra, Rb) and Fa.any()
+    a.update(2)
+    b.update(2)
+    assert np.array_equal(a.membership(), b.membership())
+    assert a.modularity()[1:] == b.modularity()[1:]
+    assert a.stats()["affected_initial"] == int(Fa.sum())
+
+
 def test_batch_graph_semantics(oracle_mod):
     # deletions first (w = 0 removes the whole edge, w > 0 decrements), then
     # insertions (add weight, or create the edge)
