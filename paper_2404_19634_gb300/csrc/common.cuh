@@ -533,7 +533,16 @@ struct MoveArgs {
   bool use_range;
   bool track_ever;
   bool prefer_host = false;  // launch from the host unless DFL_FLAG_GRAPH asks for replay
+  // upper bound of the initial frontier's vertex count (DF: the pending
+  // batch arcs); chooses launch shapes for a replayed first iteration
+  uint64_t frontier_hint = ~0ull;
 };
+// A frontier list of a sub-step class shorter than this is decided by the
+// per-vertex kernels of bin 0 (W lanes a vertex) instead of the
+// thread-per-vertex kernel: with few vertices the latter leaves the SMs to
+// the largest-degree chain less well (R-MAT 2^22, DF at 1e-3|E|: 0.44 vs
+// 0.49-0.52 ms per batch), while on full frontiers it is the faster one.
+constexpr uint64_t kSmallList = 32768;
 // Below this many pending batch arcs a DF or DS update launches its
 // iterations from the host even when graph replay is allowed: a frontier of
 // a few vertices leaves most bins empty, and skipping them beats replaying

@@ -113,6 +113,9 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
     a.use_range = use_range && pass == 0;
     a.track_ever = pass == 0 && !all;
     a.prefer_host = !all && h->pend_count < kGraphMinArcs;
+    // DF marks at most one vertex per pending batch arc; ND, DS and later
+    // passes may mark every vertex
+    a.frontier_hint = (pass == 0 && !all && !use_range) ? h->pend_count : nv;
     uint32_t it = 0;
     uint64_t init0 = 0, ever0 = 0;
     DFL_TRY(local_move(h, a, pass, &it, pass == 0, &init0, &ever0));

@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -135,6 +136,20 @@ __device__ __forceinline__ void flush_sums(const DecideArgs& a, const MoveSums& 
     if (sh[3]) atomicAdd(&a.ctrl->s_lo, sh[3]);
     if (sh[4]) atomicAdd(&a.ctrl->s_hi, sh[4]);
   }
+}
+
+// flush_sums for kernels where every thread holds counts: the warp sums
+// them first, so the block's shared counters take one update per warp.
+__device__ __forceinline__ void flush_sums_all(const DecideArgs& a, MoveSums v) {
+#pragma unroll
+  for (int x = 16; x; x >>= 1) {
+    v.bytes += __shfl_xor_sync(0xFFFFFFFFu, v.bytes, x);
+    v.s_lo += __shfl_xor_sync(0xFFFFFFFFu, v.s_lo, x);
+    v.s_hi += __shfl_xor_sync(0xFFFFFFFFu, v.s_hi, x);
+  }
+  v.processed = __reduce_add_sync(0xFFFFFFFFu, uint32_t(v.processed));
+  v.ever = __reduce_add_sync(0xFFFFFFFFu, uint32_t(v.ever));
+  flush_sums(a, v, (threadIdx.x & 31u) == 0);
 }
 
 // A mover of more than kMarkInline arcs does not mark its neighbours itself
@@ -383,6 +398,7 @@ __device__ __forceinline__ void block_argmax(bool& have, i128& best, uint32_t& b
 // ---------------------------------------------------------------------------
 constexpr uint32_t kWarpSlots = 512;
 constexpr int kWarpHashWarps = 8;
+static_assert(kBinWarpHash <= 8 * 32 && 2 * kBinWarpHash <= kWarpSlots, "a bin-1 vertex fits 8 arcs a lane and its table");
 
 // One vertex of bin 1 by one warp (its degree up to kWarpSlots / 2): up to
 // 32 arcs by the register path, else a shared table of the warp.  Every lane
@@ -436,28 +452,445 @@ __device__ __forceinline__ void warp_table_vertex(const DecideArgs& a, uint32_t 
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) k_decide_warp_hash(DecideArgs a) {
+// ---------------------------------------------------------------------------
+// Vertex headers a warp at a time.  A vertex's decision is a chain of
+// dependent loads: list entry -> its row offset, degree, community and K ->
+// the Sigma and size of its community -> its arcs -> the neighbours'
+// communities -> the candidates' Sigma.  The kernels below take the first
+// links of that chain for up to 32 list positions at once (one lane each),
+// so they wait for them once per batch of vertices instead of once per
+// vertex.
+// ---------------------------------------------------------------------------
+
+// K_i, Sigma_d and 2m are below 2^32 (2m < 2^32 on every graph, and K_i and
+// Sigma_d are parts of 2m), so they travel as 32-bit words.
+struct VHdr {
+  unsigned long long o;  // row offset
+  uint32_t Ki, Sd, m2;   // K_i, Sigma of its community d, 2m of its graph
+  uint32_t i, d, dg, gi;
+  int szd;               // size of d
+  bool act;              // processed and in the affected range: decide it
+};
+
+// Sigma_c as a 32-bit word (the low half of the int64: Sigma_c is in [0, 2m)).
+__device__ __forceinline__ uint32_t sigma32(const long long* Sigma, uint32_t c) {
+  return reinterpret_cast<const uint32_t*>(Sigma)[2ull * c];
+}
+
+// Exact 64-bit form of Eq. 2's comparisons.  Adding K_i * 2m to every score
+// of vertex i shifts them all by the same amount:
+//   score'(c) = 2m * H[c] + K_i * (2m - Sigma_c)           (a candidate c)
+//   stay'     = 2m * H[d] + K_i * (2m - (Sigma_d - K_i))
+// so the best candidate, the move test score > stay and the gain score - stay
+// are unchanged.  Each is at most 2 * 2m * K_i (H[c] <= K_i and Sigma_c <= 2m),
+// so it fits 64 bits whenever 2m * K_i < 2^63, which holds unless 2m and K_i
+// both approach 2^32; those vertices take the 128-bit path.  A candidate's
+// score' is at least 1 (H[c] >= 1).
+__device__ __forceinline__ bool fits64(uint32_t m2, uint32_t Ki) {
+  return (unsigned long long)m2 * Ki < (1ull << 63);
+}
+__device__ __forceinline__ unsigned long long score64(uint32_t m2, uint32_t h, uint32_t Ki, uint32_t sig) {
+  return (unsigned long long)m2 * h + (unsigned long long)Ki * (m2 - sig);
+}
+
+// Warp-wide best (largest score', then smallest c) of the lanes with `have`,
+// by three warp reductions; the result on every lane.
+__device__ __forceinline__ void warp_best64(bool& have, unsigned long long& s, uint32_t& c) {
+  const uint32_t hi = have ? uint32_t(s >> 32) : 0u, lo = have ? uint32_t(s) : 0u;
+  const uint32_t mh = __reduce_max_sync(0xFFFFFFFFu, hi);
+  const uint32_t ml = __reduce_max_sync(0xFFFFFFFFu, (have && hi == mh) ? lo : 0u);
+  c = __reduce_min_sync(0xFFFFFFFFu, (have && hi == mh && lo == ml) ? c : kEmpty);
+  s = ((unsigned long long)mh << 32) | ml;
+  have = c != kEmpty;
+}
+
+// This lane's header of list position t (`valid`: t is in the list).  The
+// vertex is counted as processed (and newly ever-processed) as in the
+// per-vertex kernels.
+__device__ __forceinline__ void load_header(const DecideArgs& a, uint64_t t, bool valid, long long m2_one,
+                                            MoveSums& sums, VHdr& h) {
+  h.i = valid ? a.list[t] : 0u;
+  long long m2 = m2_one;
+  h.gi = 0;
+  if (valid && !group_active(a, h.i, &m2, &h.gi)) valid = false;
+  h.m2 = uint32_t(m2);
+  // the row and state loads are issued before the bookkeeping atomics
+  h.d = valid ? a.C[h.i] : 0u;
+  h.Ki = valid ? uint32_t(a.K[h.i]) : 0u;
+  h.o = valid ? a.g.off[h.i] : 0ull;
+  h.dg = valid ? a.g.deg[h.i] : 0u;
+  bool inr = valid;
+  if (valid) {
+    if (a.ever && bit_set(a.ever, h.i)) ++sums.ever;
+    ++sums.processed;
+    if (a.rbits) inr = bit_test(a.rbits, h.i);
+  }
+  h.act = inr;
+  h.Sd = inr ? sigma32(a.Sigma, h.d) : 0u;
+  h.szd = inr ? a.size[h.d] : 0;
+}
+
+__device__ __forceinline__ VHdr shfl_header(const VHdr& h, int k) {
+  VHdr v;
+  v.o = __shfl_sync(0xFFFFFFFFu, h.o, k);
+  v.Ki = __shfl_sync(0xFFFFFFFFu, h.Ki, k);
+  v.Sd = __shfl_sync(0xFFFFFFFFu, h.Sd, k);
+  v.m2 = __shfl_sync(0xFFFFFFFFu, h.m2, k);
+  v.i = __shfl_sync(0xFFFFFFFFu, h.i, k);
+  v.d = __shfl_sync(0xFFFFFFFFu, h.d, k);
+  v.dg = __shfl_sync(0xFFFFFFFFu, h.dg, k);
+  v.gi = __shfl_sync(0xFFFFFFFFu, h.gi, k);
+  v.szd = __shfl_sync(0xFFFFFFFFu, h.szd, k);
+  v.act = true;
+  return v;
+}
+
+// The move decision of Eq. 2 from the best candidate (score' form), with the
+// community's Sigma and size already loaded: the best candidate's size is
+// read only when the singleton-swap guard needs it.
+__device__ __forceinline__ bool decide64(const DecideArgs& a, const VHdr& v, bool have, unsigned long long best,
+                                         uint32_t bc, uint32_t Hd, i128* gain) {
+  if (!have) return false;
+  const unsigned long long stay = score64(v.m2, Hd, v.Ki, v.Sd - v.Ki);
+  if (!(best > stay)) return false;
+  if (v.szd == 1 && bc > v.d && a.size[bc] == 1) return false;  // singleton-swap guard
+  *gain = (i128)(best - stay);
+  return true;
+}
+
+// The same in 128 bits (vertices whose 2m * K_i reaches 2^63).
+__device__ __forceinline__ bool decide128(const DecideArgs& a, const VHdr& v, bool have, i128 best, uint32_t bc,
+                                          uint32_t Hd, i128* gain) {
+  if (!have) return false;
+  const i128 stay = gain_num(v.m2, Hd, v.Ki, v.Sd - v.Ki);
+  if (!(best > stay)) return false;
+  if (v.szd == 1 && bc > v.d && a.size[bc] == 1) return false;
+  *gain = best - stay;
+  return true;
+}
+
+// record_move for every mover lane of the warp with one slot reservation.
+// Every lane of the warp calls it.
+__device__ __forceinline__ void record_moves_warp(const DecideArgs& a, bool mv, uint32_t i, uint32_t c,
+                                                  uint32_t d, i128 gain, uint32_t gi, MoveSums& sums) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, mv);
+  if (!m) return;
+  const uint32_t lane = threadIdx.x & 31u;
+  const int first = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (int(lane) == first) base = atomicAdd(a.movers, uint32_t(__popc(m)));
+  base = __shfl_sync(0xFFFFFFFFu, base, first);
+  if (!mv) return;
+  const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
+  a.mv_i[slot] = i;
+  a.mv_c[slot] = c;
+  a.mv_d[slot] = d;
+  const u128 v = (u128)gain;
+  const unsigned long long lo = (unsigned long long)(v & 0xFFFFFFFFull);
+  const unsigned long long hi = (unsigned long long)(v >> 32);
+  sums.s_lo += lo;
+  sums.s_hi += hi;
+  if (a.ngraphs) {
+    if (lo) atomicAdd(a.gS + 2 * gi, lo);
+    if (hi) atomicAdd(a.gS + 2 * gi + 1, hi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bin 0: one thread per vertex (degree <= D), its arcs, their communities and
+// the community weights in registers; the weight of a community is summed
+// by its first arc over the others (D x D compares, no table, no shuffles).
+// ---------------------------------------------------------------------------
+
+// Best candidate over the thread's community weights (hw[k] > 0: arc k is the
+// first of a candidate community c[k]) and the move decision.
+template <int D, bool F64>
+__device__ __forceinline__ bool thread_decide(const DecideArgs& a, const VHdr& h, const uint32_t* c,
+                                              const uint32_t* hw, const uint32_t* sg, uint32_t Hd, uint32_t* bco,
+                                              i128* gain) {
+  bool have = false;
+  uint32_t bc = 0;
+  typename std::conditional<F64, unsigned long long, i128>::type best = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (!hw[k]) continue;
+    decltype(best) sc;
+    if constexpr (F64) sc = score64(h.m2, hw[k], h.Ki, sg[k]);
+    else sc = gain_num(h.m2, hw[k], h.Ki, sg[k]);
+    if (!have || sc > best || (sc == best && c[k] < bc)) {
+      have = true;
+      best = sc;
+      bc = c[k];
+    }
+  }
+  *bco = bc;
+  if constexpr (F64) return decide64(a, h, have, best, bc, Hd, gain);
+  else return decide128(a, h, have, best, bc, Hd, gain);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 3) k_decide_thread(DecideArgs a) {
   const long long m2_one = *a.m2p;
+  const uint32_t cnt = *a.count;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  MoveSums sums;
+  for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); t0 < cnt; t0 += stride) {
+    const uint64_t t = t0 + lane;  // warp-uniform loop: the movers are recorded per warp
+    VHdr h;
+    load_header(a, t, t < cnt, m2_one, sums, h);
+    uint2 arc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) arc[k] = (h.act && uint32_t(k) < h.dg) ? a.g.arcs[h.o + k] : make_uint2(h.i, 0u);
+    uint32_t c[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = (arc[k].x != h.i && arc[k].y != 0) ? a.C[arc[k].x] : kEmpty;
+    // hw[k]: weight of candidate community c[k] if arc k is its first arc, else 0
+    uint32_t hw[D];
+    uint32_t Hd = 0, ncand = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      uint32_t sum = 0;
+      bool lead = c[k] != kEmpty;
+#pragma unroll
+      for (int m = 0; m < D; ++m)
+        if (c[m] == c[k]) {
+          sum += arc[m].y;
+          if (m < k) lead = false;
+        }
+      if (lead && c[k] == h.d) Hd = sum;
+      hw[k] = lead && c[k] != h.d ? sum : 0u;  // a valid arc weighs at least 1
+      ncand += hw[k] ? 1u : 0u;
+    }
+    uint32_t sg[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sg[k] = hw[k] ? sigma32(a.Sigma, c[k]) : 0u;
+    uint32_t bc = 0;
+    i128 gain = 0;
+    bool mv = false;
+    if (h.act) {
+      mv = fits64(h.m2, h.Ki) ? thread_decide<D, true>(a, h, c, hw, sg, Hd, &bc, &gain)
+                              : thread_decide<D, false>(a, h, c, hw, sg, Hd, &bc, &gain);
+      sums.bytes += 24 + 12ull * h.dg + 12ull * ncand;
+    }
+    record_moves_warp(a, mv, h.i, bc, h.d, gain, h.gi, sums);
+    if (mv) {  // the arcs again (cached)
+      sums.bytes += 16 + 4ull * h.dg;
+      for (uint32_t k = 0; k < h.dg; ++k) {
+        const uint2 e = a.g.arcs[h.o + k];
+        mark_next(a, e.x, e.x != h.i && e.y != 0);
+      }
+    }
+  }
+  flush_sums_all(a, sums);
+}
+
+// ---------------------------------------------------------------------------
+// Bin 1: one warp per vertex, vertices taken in batches of up to 32 headers.
+// A vertex of at most 32 arcs is decided in registers (one arc per lane);
+// a larger one in the warp's shared table.  The table is empty at rest: the
+// lane that creates a community's slot loads that community's Sigma at once,
+// and after the last arc is in, scores the slot and clears it, so the table
+// is neither cleared nor scanned as a whole.  Vertices whose scores need
+// 128 bits take the per-vertex path of the persistent kernel.
+// ---------------------------------------------------------------------------
+
+// Decision of vertex v (at most 32 arcs; `arc` = this lane's arc, lane < dg,
+// else (i, 0)), identical on every lane; *ncand on every lane.
+__device__ __forceinline__ bool reg_vertex(const DecideArgs& a, const VHdr& v, uint2 arc, uint32_t* bco,
+                                           i128* gain, uint32_t* ncand) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool valid = lane < v.dg && arc.x != v.i && arc.y != 0;
+  const uint32_t c = valid ? a.C[arc.x] : kEmpty;
+  const uint32_t wv = valid ? arc.y : 0u;
+  uint32_t hsum = 0;
+  bool leader = valid;
+  for (uint32_t k = 0; k < v.dg; ++k) {  // warp-uniform bound
+    const uint32_t ck = __shfl_sync(0xFFFFFFFFu, c, k);
+    const uint32_t wk = __shfl_sync(0xFFFFFFFFu, wv, k);
+    if (valid && ck == c) {
+      hsum += wk;
+      if (k < lane) leader = false;
+    }
+  }
+  const uint32_t Hd = __reduce_add_sync(0xFFFFFFFFu, (leader && c == v.d) ? hsum : 0u);
+  bool cand = leader && c != v.d;
+  *ncand = __popc(__ballot_sync(0xFFFFFFFFu, cand));
+  unsigned long long s = cand ? score64(v.m2, hsum, v.Ki, sigma32(a.Sigma, c)) : 0ull;
+  uint32_t bc = c;
+  warp_best64(cand, s, bc);
+  *bco = bc;
+  return decide64(a, v, cand, s, bc, Hd, gain);
+}
+
+// Decision of vertex v (32 < degree <= 32 U) in the warp's table (keys kEmpty
+// and values 0 at rest, and left so).  `a0` is this lane's first arc,
+// loaded ahead.  Returns the decision on every lane; a mover's arcs are read
+// again to mark the next frontier.
+template <int U>
+__device__ __forceinline__ bool table_vertex(const DecideArgs& a, const VHdr& v, uint2 a0, uint32_t* keys,
+                                             uint32_t* vals, uint32_t* bco, i128* gain, uint32_t* ncand) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t slots = 64;
+  while (slots < 2 * v.dg) slots <<= 1;  // at most 64 U: never full
+  const uint32_t mask = slots - 1;
+  uint2 arc[U];
+  arc[0] = a0;
+#pragma unroll
+  for (int u = 1; u < U; ++u) {
+    const uint32_t k = u * 32 + lane;
+    arc[u] = k < v.dg ? a.g.arcs[v.o + k] : make_uint2(v.i, 0u);
+  }
+  uint32_t c[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) c[u] = (arc[u].x != v.i && arc[u].y != 0) ? a.C[arc[u].x] : kEmpty;
+  uint32_t cs[U], sg[U];
+  bool ok = true;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    cs[u] = kEmpty;
+    sg[u] = 0;
+    if (c[u] == kEmpty) continue;
+    uint32_t s = hash32(c[u]) & mask;
+    bool placed = false;
+    for (uint32_t probe = 0; probe < slots; ++probe) {
+      uint32_t prev = keys[s];
+      if (prev == kEmpty) prev = atomicCAS(&keys[s], kEmpty, c[u]);
+      if (prev == kEmpty) {  // created: this lane scores the slot
+        cs[u] = s;
+        if (c[u] != v.d) sg[u] = sigma32(a.Sigma, c[u]);
+      }
+      if (prev == kEmpty || prev == c[u]) {
+        atomicAdd(&vals[s], arc[u].y);
+        placed = true;
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+    ok &= placed;
+  }
+  if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(&a.ctrl->err, kErrInternal);
+  __syncwarp();  // every arc is in
+  bool have = false;
+  unsigned long long best = 0;
+  uint32_t bc = 0, nc = 0, Hd = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (cs[u] == kEmpty) continue;
+    const uint32_t hw = vals[cs[u]];
+    keys[cs[u]] = kEmpty;  // only this lane reads the slot it created
+    vals[cs[u]] = 0;
+    if (c[u] == v.d) {
+      Hd = hw;
+      continue;
+    }
+    ++nc;
+    const unsigned long long sc = score64(v.m2, hw, v.Ki, sg[u]);
+    if (!have || sc > best || (sc == best && c[u] < bc)) {
+      have = true;
+      best = sc;
+      bc = c[u];
+    }
+  }
+  __syncwarp();  // the table is empty again before the next vertex
+  Hd = __reduce_add_sync(0xFFFFFFFFu, Hd);
+  *ncand = __reduce_add_sync(0xFFFFFFFFu, nc);
+  warp_best64(have, best, bc);
+  *bco = bc;
+  const bool mv = decide64(a, v, have, best, bc, Hd, gain);
+  if (mv) {  // the arcs again (cached): holding them in registers costs occupancy
+    for (uint32_t k = lane; k < v.dg; k += 32) {
+      const uint2 e = a.g.arcs[v.o + k];
+      mark_next(a, e.x, e.x != v.i && e.y != 0);
+    }
+  }
+  return mv;
+}
+
+// The rare 128-bit vertices, out of line so that they do not cost the common
+// path registers.
+__device__ __noinline__ void warp_vertex_128(const DecideArgs& a, const VHdr& v, uint32_t* keys, uint32_t* vals,
+                                             MoveSums& sums) {
+  warp_table_vertex(a, v.i, v.m2, v.gi, keys, vals, sums);
+}
+
+__global__ void __launch_bounds__(256, 3) k_decide_warp_hash(DecideArgs a) {
   __shared__ uint32_t skeys[kWarpHashWarps][kWarpSlots];
   __shared__ uint32_t svals[kWarpHashWarps][kWarpSlots];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  const uint32_t cnt = *a.count;
-  uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
-  uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  MoveSums sums;
-  for (uint64_t t = warp; t < cnt; t += nwarps) {
-    const uint32_t i = a.list[t];
-    long long m2 = m2_one;
-    uint32_t gi = 0;
-    if (!group_active(a, i, &m2, &gi)) continue;
-    if (lane == 0) {
-      if (a.ever && bit_set(a.ever, i)) ++sums.ever;
-      ++sums.processed;
-    }
-    if (a.rbits && !bit_test(a.rbits, i)) continue;
-    warp_table_vertex(a, i, m2, gi, skeys[wib], svals[wib], sums);
+  uint32_t* keys = skeys[wib];
+  uint32_t* vals = svals[wib];
+  for (uint32_t s = lane; s < kWarpSlots; s += 32) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
   }
-  flush_sums(a, sums, lane == 0);
+  __syncwarp();
+  const long long m2_one = *a.m2p;
+  const uint32_t cnt = *a.count;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  // vertices per warp and round: up to 32, fewer when the list is short
+  uint64_t B = (uint64_t(cnt) + nwarps - 1) / nwarps;
+  B = B < 1 ? 1 : B > 32 ? 32 : B;
+  MoveSums sums;
+  for (uint64_t t0 = warp * B; t0 < cnt; t0 += nwarps * B) {
+    VHdr h;
+    load_header(a, t0 + lane, lane < B && t0 + lane < cnt, m2_one, sums, h);
+    bool my_mv = false;
+    uint32_t my_c = 0;
+    i128 my_gain = 0;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, h.act);
+    // each vertex's first 32 arcs are loaded while the one before is decided
+    uint2 pre = make_uint2(0u, 0u);
+    if (m) {
+      const int k = __ffs(m) - 1;
+      const unsigned long long o = __shfl_sync(0xFFFFFFFFu, h.o, k);
+      const uint32_t dg = __shfl_sync(0xFFFFFFFFu, h.dg, k), i = __shfl_sync(0xFFFFFFFFu, h.i, k);
+      pre = lane < dg ? a.g.arcs[o + lane] : make_uint2(i, 0u);
+    }
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1;
+      const VHdr v = shfl_header(h, k);
+      const uint2 a0 = pre;
+      if (m) {
+        const int k1 = __ffs(m) - 1;
+        const unsigned long long o = __shfl_sync(0xFFFFFFFFu, h.o, k1);
+        const uint32_t dg = __shfl_sync(0xFFFFFFFFu, h.dg, k1), i = __shfl_sync(0xFFFFFFFFu, h.i, k1);
+        pre = lane < dg ? a.g.arcs[o + lane] : make_uint2(i, 0u);
+      }
+      if (!fits64(v.m2, v.Ki)) {  // 128-bit scores: the per-vertex path, then the table emptied again
+        warp_vertex_128(a, v, keys, vals, sums);
+        for (uint32_t s = lane; s < kWarpSlots; s += 32) {
+          keys[s] = kEmpty;
+          vals[s] = 0;
+        }
+        __syncwarp();
+        continue;
+      }
+      uint32_t bc = 0, ncand = 0;
+      i128 gain = 0;
+      bool mv;
+      if (v.dg <= 32) {
+        mv = reg_vertex(a, v, a0, &bc, &gain, &ncand);
+        if (mv) mark_next(a, a0.x, lane < v.dg && a0.x != v.i && a0.y != 0);
+      } else if (v.dg <= 64) {
+        mv = table_vertex<2>(a, v, a0, keys, vals, &bc, &gain, &ncand);
+      } else if (v.dg <= 128) {
+        mv = table_vertex<4>(a, v, a0, keys, vals, &bc, &gain, &ncand);
+      } else {
+        mv = table_vertex<8>(a, v, a0, keys, vals, &bc, &gain, &ncand);
+      }
+      if (int(lane) == k) {
+        sums.bytes += 24 + 12ull * v.dg + 12ull * ncand + (mv ? 16 + 4ull * v.dg : 0ull);
+        my_mv = mv;
+        my_c = bc;
+        my_gain = gain;
+      }
+    }
+    record_moves_warp(a, my_mv, h.i, my_c, h.d, my_gain, h.gi, sums);
+  }
+  flush_sums_all(a, sums);
 }
 
 // ---------------------------------------------------------------------------
@@ -560,26 +993,142 @@ __device__ __forceinline__ void block_vertex(const DecideArgs& a, uint32_t i, lo
   __syncthreads();
 }
 
+// Bin 2 (and bin-3 degrees when the tuning sends them here): one block per
+// vertex.  Headers are loaded by warp 0 for up to 32 of the block's vertices
+// at once.  The shared table (kBlockSlots keys + values) is empty at rest: a
+// vertex uses the first power of two >= 2 x degree slots, and the scan that
+// scores the occupied slots also clears them.  Vertices of degree above
+// kBinBlock, or whose scores need 128 bits, take block_vertex (which may
+// fall back to a global table) and the table is emptied after it.
+template <int kThreads>
+__device__ __noinline__ void block_vertex_slow(const DecideArgs& a, const VHdr& v, uint32_t* dyn, BlockScratch& sc,
+                                               MoveSums& sums) {
+  block_vertex<kThreads>(a, v.i, v.m2, v.gi, dyn, sc, sums);
+}
+
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
-  const long long m2_one = *a.m2p;
   extern __shared__ uint32_t dyn[];
+  uint32_t* keys = dyn;
+  uint32_t* vals = dyn + kBlockSlots;
   __shared__ BlockScratch sc;
-  const uint32_t cnt = *a.count;
-  MoveSums sums;
-  for (uint64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
-    const uint32_t i = a.list[t];
-    long long m2 = m2_one;
-    uint32_t gi = 0;
-    if (!group_active(a, i, &m2, &gi)) continue;
-    if (threadIdx.x == 0) {
-      if (a.ever && bit_set(a.ever, i)) ++sums.ever;
-      ++sums.processed;
-    }
-    if (a.rbits && !bit_test(a.rbits, i)) continue;
-    block_vertex<kThreads>(a, i, m2, gi, dyn, sc, sums);
+  __shared__ VHdr s_hdr[32];
+  __shared__ unsigned long long s_best[kMaxBlockWarps];
+  __shared__ uint32_t s_bc[kMaxBlockWarps];
+  constexpr uint32_t nthr = kThreads;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  for (uint32_t s = threadIdx.x; s < kBlockSlots; s += nthr) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
   }
-  flush_sums(a, sums, threadIdx.x == 0);
+  const long long m2_one = *a.m2p;
+  const uint32_t cnt = *a.count;
+  const uint64_t G = gridDim.x;
+  MoveSums sums;
+  __syncthreads();
+  for (uint64_t t0 = blockIdx.x; t0 < cnt; t0 += 32 * G) {
+    if (wib == 0) {
+      const uint64_t t = t0 + lane * G;
+      VHdr h;
+      load_header(a, t, t < cnt, m2_one, sums, h);
+      s_hdr[lane] = h;
+    }
+    __syncthreads();
+    for (uint32_t k = 0; k < 32 && t0 + k * G < cnt; ++k) {
+      const VHdr v = s_hdr[k];
+      if (!v.act) continue;  // block-uniform
+      if (v.dg > kBinBlock || !fits64(v.m2, v.Ki)) {
+        block_vertex_slow<kThreads>(a, v, dyn, sc, sums);
+        for (uint32_t s = threadIdx.x; s < kBlockSlots; s += nthr) {
+          keys[s] = kEmpty;
+          vals[s] = 0;
+        }
+        __syncthreads();
+        continue;
+      }
+      uint32_t slots = 64;
+      while (slots < 2 * v.dg) slots <<= 1;
+      const uint32_t mask = slots - 1;
+      if (threadIdx.x == 0) {
+        sc.hd = 0;
+        sc.ncand = 0;
+      }
+      // every arc's weight under its neighbour's community (a table of
+      // >= 2 x degree slots cannot overflow)
+      const bool ok = scan_row<8>(a, v.i, v.o, v.dg, wib * 32, nthr, keys, vals, mask, slots);
+      if (!ok) atomicOr(&a.ctrl->err, kErrInternal);
+      __syncthreads();
+      // score the occupied slots and clear them; four slots' Sigma loads in flight
+      bool have = false;
+      unsigned long long best = 0;
+      uint32_t bc = 0, nc = 0;
+      for (uint32_t s0 = threadIdx.x; s0 < slots; s0 += nthr * 4) {
+        uint32_t c[4], w[4], sg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t sl = s0 + u * nthr;
+          c[u] = sl < slots ? keys[sl] : kEmpty;
+          w[u] = c[u] != kEmpty ? vals[sl] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sg[u] = (c[u] != kEmpty && c[u] != v.d) ? sigma32(a.Sigma, c[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (c[u] == kEmpty) continue;
+          const uint32_t sl = s0 + u * nthr;
+          keys[sl] = kEmpty;
+          vals[sl] = 0;
+          if (c[u] == v.d) {
+            sc.hd = w[u];  // exactly one slot holds d
+            continue;
+          }
+          ++nc;
+          const unsigned long long s = score64(v.m2, w[u], v.Ki, sg[u]);
+          if (!have || s > best || (s == best && c[u] < bc)) {
+            have = true;
+            best = s;
+            bc = c[u];
+          }
+        }
+      }
+      nc = __reduce_add_sync(0xFFFFFFFFu, nc);
+      if (lane == 0 && nc) atomicAdd(&sc.ncand, nc);
+      warp_best64(have, best, bc);
+      if (lane == 0) {
+        s_best[wib] = have ? best : 0ull;
+        s_bc[wib] = bc;
+      }
+      __syncthreads();
+      if (wib == 0) {
+        have = lane < nthr / 32 && s_bc[lane] != kEmpty;
+        best = have ? s_best[lane] : 0ull;
+        bc = have ? s_bc[lane] : kEmpty;
+        warp_best64(have, best, bc);
+        if (lane == 0) {
+          i128 gain = 0;
+          const bool mv = decide64(a, v, have, best, bc, uint32_t(sc.hd), &gain);
+          sums.bytes += 24 + 12ull * v.dg + 12ull * sc.ncand;
+          sc.last = mv;
+          if (mv) {
+            record_move(a, v.i, bc, v.d, gain, v.gi, sums);
+            sums.bytes += 16 + 4ull * v.dg;
+            if (v.dg > kMarkInline) a.bigmv[atomicAdd(a.nbig, 1u)] = v.i;
+          }
+        }
+      }
+      __syncthreads();
+      if (sc.last && v.dg <= kMarkInline) {
+        for (uint32_t k0 = wib * 32; k0 < v.dg; k0 += nthr) {
+          const uint32_t kk = k0 + lane;
+          const uint2 arc = kk < v.dg ? a.g.arcs[v.o + kk] : make_uint2(v.i, 0u);
+          mark_next(a, arc.x, kk < v.dg && arc.x != v.i && arc.y != 0);
+        }
+      }
+      __syncthreads();  // sc and the table are reused by the next vertex
+    }
+    __syncthreads();  // s_hdr is rewritten by the next round
+  }
+  flush_sums_all(a, sums);
 }
 
 // ---------------------------------------------------------------------------
@@ -1416,7 +1965,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
   for (uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; w < ia.words;
        w += uint64_t(gridDim.x) * blockDim.x)
     ia.fbits_cur[w] = 0;
-  flush_sums(ia.a, sums, true);  // every thread holds counts (segment and warp leaders, block leaders)
+  flush_sums_all(ia.a, sums);  // every thread holds counts (segment and warp leaders, block leaders)
 }
 
 __global__ void k_set_m2(Ctrl* ctrl, long long m2) { ctrl->m2v = m2; }
@@ -1430,7 +1979,7 @@ constexpr uint32_t kBlockGridMax = 3 * 152;
 // sized to the work; without (graph capture) every bin is launched with a
 // fixed grid and reads its length on the device.
 int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*counts)[kBins],
-                    const GiantDecide& gd_base, bool decide_only = false) {
+                    const GiantDecide& gd_base, bool decide_only = false, bool small_hint = false) {
   const uint32_t k = a.k;
   const int nxt = cur ^ 1;
   // reset the iteration's sums and the next buffer's list lengths
@@ -1478,16 +2027,26 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       a.count = &h->ctrl->count[cur][s][b];
       LaunchScope ls(h, DFL_PROF_BIN0 + b, st);
       if (b == 0) {
-        // W lanes per vertex, W = the bin's degree limit rounded up to a power of two
         const uint32_t lim = h->tune.bin_warp;
-        const uint32_t segs = lim <= 4 ? 8 : lim <= 8 ? 4 : lim <= 16 ? 2 : 1;
-        const uint32_t grid = counts ? grid_for((uint64_t(c) + segs - 1) / segs * 32, 256, 152 * 64) : 152 * 8;
-        if (segs == 8) k_decide_warp<4><<<grid, 256, 0, st>>>(a);
-        else if (segs == 4) k_decide_warp<8><<<grid, 256, 0, st>>>(a);
-        else if (segs == 2) k_decide_warp<16><<<grid, 256, 0, st>>>(a);
-        else k_decide_warp<32><<<grid, 256, 0, st>>>(a);
+        const bool small = counts ? c < kSmallList : small_hint;
+        if (lim <= 8 && small) {  // W = 4 or 8 lanes per vertex
+          const uint32_t segs = lim <= 4 ? 8 : 4;
+          const uint32_t grid = counts ? grid_for((uint64_t(c) + segs - 1) / segs * 32, 256, 152 * 64) : 152 * 8;
+          if (segs == 8) k_decide_warp<4><<<grid, 256, 0, st>>>(a);
+          else k_decide_warp<8><<<grid, 256, 0, st>>>(a);
+        } else if (lim <= 8) {  // a thread per vertex, its arcs in registers
+          const uint32_t grid = counts ? grid_for(c, 256, 152 * 16) : 152 * 4;
+          if (lim <= 4) k_decide_thread<4><<<grid, 256, 0, st>>>(a);
+          else k_decide_thread<8><<<grid, 256, 0, st>>>(a);
+        } else {  // W = 16 or 32 lanes per vertex
+          const uint32_t segs = lim <= 16 ? 2 : 1;
+          const uint32_t grid = counts ? grid_for((uint64_t(c) + segs - 1) / segs * 32, 256, 152 * 64) : 152 * 8;
+          if (segs == 2) k_decide_warp<16><<<grid, 256, 0, st>>>(a);
+          else k_decide_warp<32><<<grid, 256, 0, st>>>(a);
+        }
       } else if (b == 1) {
-        k_decide_warp_hash<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 16) : 152 * 4, 256, 0, st>>>(a);
+        // a warp per vertex, headers in batches of up to 32 (fewer when the list is short)
+        k_decide_warp_hash<<<counts ? grid_for(uint64_t(c) * 32, 256, 152 * 6) : 152 * 3, 256, 0, st>>>(a);
       } else if (b == 2) {
         const size_t smem = sizeof(uint32_t) * 2 * kBlockSlots;
         const uint32_t bt = h->tune.block_threads;
@@ -1604,6 +2163,7 @@ struct GraphKey {
   DecideArgs a;
   GiantDecide gd;
   int cur;
+  int small;
   uint32_t flags;
   void* stream;
   uint32_t block_threads;
@@ -1611,13 +2171,14 @@ struct GraphKey {
 
 // The cached graph for this iteration's key (captured on a miss, evicting
 // the least recently used entry of this parity).
-int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd, int cur,
+int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd, int cur, bool small,
                            Handle::IterGraph** out) {
   GraphKey key;
   std::memset(&key, 0, sizeof(key));
   key.a = a;
   key.gd = gd;
   key.cur = cur;
+  key.small = small;
   key.flags = h->opt.flags;
   key.stream = h->stream;
   key.block_threads = h->tune.block_threads;
@@ -1638,7 +2199,7 @@ int ensure_iteration_graph(Handle* h, const DecideArgs& a, const GiantDecide& gd
   uint64_t cl0[DFL_PROF_CLASSES];
   for (int q = 0; q < DFL_PROF_CLASSES; ++q) cl0[q] = h->prof.launches[q];
   DFL_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = issue_iteration(h, a, cur, nullptr, gd);
+  int rc = issue_iteration(h, a, cur, nullptr, gd, false, small);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (rc) {
@@ -1885,13 +2446,14 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   DFL_TRY(prepare_move(h, ma, &a, &gd));
   int cur = 0;
   uint32_t it = 0;
+  uint64_t hint = ma.frontier_hint;  // upper bound of this iteration's frontier
   Handle::IterGraph* graph_used[2] = {nullptr, nullptr};
   while (it < h->opt.max_iterations && (!G || nactive)) {
     ++it;
     const int nxt = cur ^ 1;
     if (use_graph) {
       Handle::IterGraph* gp = nullptr;
-      DFL_TRY(ensure_iteration_graph(h, a, gd, cur, &gp));
+      DFL_TRY(ensure_iteration_graph(h, a, gd, cur, hint / h->opt.substeps < kSmallList, &gp));
       const Handle::IterGraph& g = *gp;
       graph_used[cur] = gp;
       DFL_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
@@ -1946,6 +2508,9 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     if (have_counts)
       for (uint32_t s = 0; s < kMaxSubsteps; ++s)
         for (int b = 0; b < kBins; ++b) cur_count[s][b] = c.count[nxt][s][b];
+    hint = 0;
+    for (uint32_t s = 0; s < kMaxSubsteps; ++s)
+      for (int b = 0; b < kBins; ++b) hint += c.count[nxt][s][b];
     cur = nxt;
     skipped = 0;
     if (!G) {
