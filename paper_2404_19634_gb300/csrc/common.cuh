@@ -384,7 +384,16 @@ __host__ __device__ __forceinline__ uint32_t degree_bin(uint32_t d, const Segs& 
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t x) { return x * 0x9E3779B1u; }
+// Home slot hashes of the open-addressing tables: the low bits of the id
+// times an odd constant (a bijection on the low bits, so the dense ids of an
+// aggregated graph land without collisions).  Aggregation and local-moving
+// use different multipliers: aggregation writes a super-vertex's row in its
+// table's slot order, and with the same multiplier a run of consecutive arcs
+// would fill a narrow window of a local-moving table densely (R-MAT 2^22,
+// second pass: probe runs of up to 1,000 slots in the 2,048-slot chunk
+// tables of the largest-degree vertices).
+__device__ __forceinline__ uint32_t hash32(uint32_t x) { return x * 0x9E3779B1u; }       // aggregation
+__device__ __forceinline__ uint32_t hash_move(uint32_t x) { return x * 0x85EBCA6Bu; }    // local-moving
 
 // Warp-wide maximum of (score, -c): larger score wins, ties to the smaller c.
 // Lanes without a candidate pass have = false.

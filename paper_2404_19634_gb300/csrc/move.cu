@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256, 5) k_decide_warp(DecideArgs a) {
 // after `limit` probes (the caller then falls back to a larger table).
 __device__ __forceinline__ bool table_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t c,
                                           uint32_t w, uint32_t limit) {
-  uint32_t s = hash32(c) & mask;
+  uint32_t s = hash_move(c) & mask;
   for (uint32_t probe = 0; probe < limit; ++probe) {
     uint32_t prev = keys[s];
     if (prev == kEmpty) prev = atomicCAS(&keys[s], kEmpty, c);
@@ -751,7 +751,7 @@ __device__ __forceinline__ bool table_vertex(const DecideArgs& a, const VHdr& v,
     cs[u] = kEmpty;
     sg[u] = 0;
     if (c[u] == kEmpty) continue;
-    uint32_t s = hash32(c[u]) & mask;
+    uint32_t s = hash_move(c[u]) & mask;
     bool placed = false;
     for (uint32_t probe = 0; probe < slots; ++probe) {
       uint32_t prev = keys[s];
@@ -1395,7 +1395,7 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
     for (int u = 0; u < U; ++u) {
       const uint32_t e = b0 + u * 32 + lane;
       c[u] = e < ne ? ek[e] : kEmpty;
-      slot[u] = hash32(c[u]) & tmask;
+      slot[u] = hash_move(c[u]) & tmask;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) prev[u] = c[u] != kEmpty ? atomicCAS(&gk[slot[u]], kEmpty, c[u]) : kEmpty;
