@@ -182,11 +182,14 @@ int dfl_create(dfl_handle** out, uint32_t n, const uint64_t* offsets, const uint
                const uint32_t* weights, uint64_t nnz, int mem_kind, const dfl_options* opt,
                void* cuda_stream);
 
-/* Release every device and host resource of the handle (NULL is a no-op). */
+/* Release every device and host resource of the handle (NULL is a no-op).
+ * Resource lifetime of this library; the paper has no counterpart. */
 void dfl_destroy(dfl_handle* h);
 
-/* Replace the options or the stream (the stream change is stream-ordered:
- * the caller must make the new stream wait for the old one if needed). */
+/* Replace the options (Section 5.1.2's parameters and the flags above) or
+ * the stream (the stream change is stream-ordered: the caller must make the
+ * new stream wait for the old one if needed; streams have no counterpart in
+ * the paper). */
 int dfl_set_options(dfl_handle* h, const dfl_options* opt);
 int dfl_set_stream(dfl_handle* h, void* cuda_stream);
 
@@ -211,7 +214,11 @@ int dfl_apply_batch(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const df
  * current membership and clears the pending list. */
 int dfl_update(dfl_handle* h, int mode);
 
-/* Membership C^t (n uint32 labels in [0, n)). */
+/* Membership C^t (n uint32 labels in [0, n)): the community of every
+ * vertex that Alg. 1 (DF), Alg. 2 (ND) and Alg. 3 (DS) return, obtained by
+ * Alg. 4's final dendrogram lookup (the last pass's labels, not renumbered);
+ * after dfl_static, the result of static Louvain.  out: n entries in memory
+ * of kind mem_kind, owned by the caller.  DFL_ERR_STATE before dfl_static. */
 int dfl_membership(const dfl_handle* h, uint32_t* out, int mem_kind);
 
 /* Modularity of the current membership (Eq. 1): Q = (2m*sum_c sigma_c -
@@ -220,7 +227,12 @@ int dfl_membership(const dfl_handle* h, uint32_t* out, int mem_kind);
  * numerator and denominator as {num_hi, num_lo, den_hi, den_lo}. */
 int dfl_modularity(dfl_handle* h, double* q, int64_t* parts);
 
-/* K (n), Sigma (n, indexed by community label) and 2m; any pointer may be NULL. */
+/* The auxiliary information of Section 4.2 that Alg. 1 returns beside C^t:
+ * K^t (n weighted degrees, Alg. 7's incremental update of K^{t-1}), Sigma^t
+ * (n community totals, indexed by community label, for the membership
+ * dfl_membership reports) and 2m (the sum of K).  Any pointer may be NULL;
+ * K and Sigma are caller buffers of n int64 in memory of kind mem_kind,
+ * two_m is a host value. */
 int dfl_weights(dfl_handle* h, int64_t* K, int64_t* Sigma, int64_t* two_m, int mem_kind);
 
 /* Number of arcs of G^t, and G^t as a compact CSR with sorted rows
@@ -236,10 +248,19 @@ int dfl_weights(dfl_handle* h, int64_t* K, int64_t* Sigma, int64_t* two_m, int m
  * handle unchanged); synchronizes the stream.  Works on group handles. */
 int dfl_compact(dfl_handle* h, uint64_t* before, uint64_t* after);
 
+/* G^t after the batches applied so far (Section 3.4: G^{t-1} with
+ * Delta^{t-} removed and Delta^{t+} added): the arc count, and the graph as
+ * a compact CSR with rows sorted by neighbour (offsets n+1, indices and
+ * weights num_arcs entries, caller buffers in memory of kind mem_kind). */
 int dfl_num_arcs(dfl_handle* h, uint64_t* num_arcs);
 int dfl_graph(dfl_handle* h, uint64_t* offsets, uint32_t* indices, uint32_t* weights,
               int mem_kind);
 
+/* Statistics of the last dfl_static / dfl_update (dfl_stats_t above): the
+ * passes of Alg. 4, the iterations l_i of Alg. 5 in each pass, the size of
+ * the initial frontier (Alg. 1-3's initially affected vertices) and the
+ * vertices processed at least once in the first pass (the affected-vertex
+ * counts compared in Section 5.2.3).  *s is a host struct. */
 int dfl_stats(dfl_handle* h, dfl_stats_t* s);
 
 /* Timings and algorithmic bytes per kernel class accumulated since the last
@@ -252,7 +273,9 @@ int dfl_profile(dfl_handle* h, dfl_profile_t* p, int reset);
  * *len; writes at most cap iterations. */
 int dfl_trace(dfl_handle* h, uint64_t* out, uint32_t cap, uint32_t* len);
 
-/* Message of the last error on this handle ("" if none). */
+/* Message of the last error on this handle ("" if none; "no handle" for
+ * NULL).  The string is owned by the handle and valid until its next call.
+ * Error reporting of this library; the paper has no counterpart. */
 const char* dfl_last_error(const dfl_handle* h);
 
 /* ---- Inspection entry points used by the parity tests ------------------ */
@@ -387,17 +410,27 @@ int dfl_group_stats(dfl_handle* h, uint32_t g, dfl_stats_t* s);
  * dfl_modularity does for a handle holding that graph and membership.
  *   n: vertices, at most DFL_NOALLOC_MAX_VERTICES (else DFL_ERR_INVALID)
  *   offsets[n+1] (uint64), indices[nnz], weights[nnz]: symmetric CSR in DEVICE
- *   memory (both arcs of every edge); membership[n]: DEVICE memory, labels < n
+ *   memory (both arcs of every edge); offsets must be non-decreasing and
+ *   offsets[n] = nnz, the length of indices and weights (decreasing offsets
+ *   give DFL_ERR_INVALID; offsets beyond the arrays cannot be detected and
+ *   make the call read out of bounds); membership[n]: DEVICE memory, labels < n
  *   q: HOST output; parts: optional HOST output {num_hi, num_lo, den_hi, den_lo}
  *   cuda_stream: cudaStream_t the work is ordered on; returns when it is done.
- * Errors: DFL_ERR_INVALID (n too large, a label or neighbour id >= n, null
- * pointer), DFL_ERR_OVERFLOW (2m >= 2^32), DFL_ERR_CUDA.
+ * Errors: DFL_ERR_INVALID (n too large, a label or neighbour id >= n,
+ * decreasing offsets, null pointer), DFL_ERR_OVERFLOW (2m >= 2^32),
+ * DFL_ERR_CUDA.
  * Its scratch (8 MiB of per-community totals plus a few counters) is a fixed
  * array in the library's device memory, held by every GPU that loads the
  * library until the process exits, and shared by all calls: each call clears
  * it first, but calls whose GPU work overlaps race and must be serialized.
  * The first call on a device also looks up that array's device address with
- * the device current. */
+ * the device current and remembers it for the life of the process, by device
+ * ordinal: after a cudaDeviceReset of that device the remembered address is
+ * stale and the entry point must not be called.  Under CUDA's lazy module
+ * loading that first call also loads the library's device code, which
+ * allocates the fixed array and may synchronize the device: make it once,
+ * outside any stream capture and any latency-critical path, before relying
+ * on the call allocating nothing. */
 int dfl_modularity_csr_noalloc(uint32_t n, const uint64_t* offsets, const uint32_t* indices,
                                const uint32_t* weights, const uint32_t* membership, double* q,
                                int64_t* parts, void* cuda_stream);

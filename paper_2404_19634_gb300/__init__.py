@@ -165,14 +165,19 @@ NOALLOC_MAX_VERTICES = 1 << 20
 
 def modularity_csr_noalloc(n, offsets, indices, weights, membership, stream=None):
     """dfl_modularity_csr_noalloc on CUDA tensors (offsets int64/uint64,
-    indices, weights and membership 32-bit).  Returns (rc, q, num, den)."""
+    indices, weights and membership 32-bit), which the C function reads as
+    device memory.  Returns (rc, q, num, den)."""
     lib = load()
+    bufs = [_buf(offsets, np.uint64), _buf(indices, np.uint32), _buf(weights, np.uint32),
+            _buf(membership, np.uint32)]  # kept alive (their keepalive objects) until the call returns
+    if any(mk != MEM_DEVICE for _, mk, _ in bufs):
+        raise TypeError("dfl_modularity_csr_noalloc takes device buffers only (CUDA tensors)")
     q = ct.c_double()
     parts = np.zeros(4, np.int64)
-    rc = lib.dfl_modularity_csr_noalloc(int(n), _buf(offsets, np.uint64)[0], _buf(indices, np.uint32)[0],
-                                        _buf(weights, np.uint32)[0], _buf(membership, np.uint32)[0],
+    rc = lib.dfl_modularity_csr_noalloc(int(n), bufs[0][0], bufs[1][0], bufs[2][0], bufs[3][0],
                                         ct.byref(q), parts.ctypes.data_as(ct.c_void_p),
                                         _stream_ptr(stream))
+    del bufs
     return rc, q.value, _i128(int(parts[0]), int(parts[1])), _i128(int(parts[2]), int(parts[3]))
 
 

@@ -12,8 +12,8 @@
 // table (<= 256), one block with a shared-memory table (<= 4096); a larger
 // community is split into chunks of members, each chunk aggregated by one
 // block in shared memory and merged into the community's global table, which
-// is then emitted slot-parallel.  Within a warp, arcs are pre-aggregated per
-// neighbour community (match + reduce) before touching a table.
+// is then emitted slot-parallel.  Every arc goes straight into a table with
+// a shared-memory (or, for a giant community's overflow, global) atomic.
 #include <mutex>
 #include <vector>
 

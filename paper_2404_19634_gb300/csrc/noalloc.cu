@@ -17,7 +17,17 @@
 //     starts, but calls whose GPU work overlaps (two streams, two threads)
 //     race on it and must be serialized by the caller;
 //   - the first call on a device looks up the scratch's device address
-//     (cudaGetSymbolAddress) with that device current, then reuses it.
+//     (cudaGetSymbolAddress) with that device current, then reuses it for
+//     the life of the process (keyed by device ordinal: after a
+//     cudaDeviceReset of that device the remembered address is stale, so the
+//     entry point must not be used after a reset).  With CUDA's lazy module
+//     loading that first call also loads the library's device code, which
+//     allocates the fixed array and may synchronize; it belongs outside any
+//     stream capture and any latency-critical path (one warm-up call);
+//   - offsets must be non-decreasing and offsets[n] is the arc count that
+//     indices and weights hold; a row whose offsets decrease is reported as
+//     DFL_ERR_INVALID, but offsets past the end of the caller's arrays
+//     cannot be detected (the call does not know their length).
 #include <mutex>
 
 #include "common.cuh"
@@ -83,8 +93,10 @@ __global__ void k_na_rows(uint32_t n, const unsigned long long* __restrict__ off
   for (uint64_t i = warp; i < n; i += nwarps) {
     const uint32_t ci = C[i];
     bad |= ci >= n;
+    const unsigned long long o0 = off[i], o1 = off[i + 1];
+    bad |= o1 < o0;  // decreasing offsets: the row is skipped and the call fails
     unsigned long long k = 0;
-    for (unsigned long long q = off[i] + lane; q < off[i + 1]; q += 32) {
+    for (unsigned long long q = o0 + lane; q < o1; q += 32) {
       uint32_t j = idx[q];
       if (j >= n) {
         bad = true;
@@ -151,7 +163,7 @@ extern "C" int dfl_modularity_csr_noalloc(uint32_t n, const uint64_t* offsets, c
   if (cudaMemcpyAsync(acc, p.acc, sizeof(acc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return DFL_ERR_CUDA;
-  if (acc[4]) return DFL_ERR_INVALID;              // a label or neighbour id >= n
+  if (acc[4]) return DFL_ERR_INVALID;              // a label or neighbour id >= n, or decreasing offsets
   if (acc[0] >= (1ull << 32)) return DFL_ERR_OVERFLOW;  // 2m must stay below 2^32
   const i128 m2 = (i128)acc[0];
   const i128 num = m2 * (i128)acc[1] - (((i128)acc[3] << 32) + (i128)acc[2]);

@@ -61,6 +61,7 @@ class Record:
     q: float = 0.0
     membership: object = None  # copy of C after that update (keep_membership)
     refreshed: bool = False    # static Louvain ran after that update (refresh_every)
+    failed: bool = False       # its graph's worker raised before serving it
 
     @property
     def latency(self) -> float:
@@ -74,13 +75,15 @@ class ServeResult:
     wall: float = 0.0
 
     def summary(self) -> dict:
-        lat = np.array([r.latency for r in self.records]) * 1e3
-        edges = sum(getattr(r, "edges", 0) for r in self.records)
-        return {"requests": len(self.records), "updates": len(self.groups),
+        served = [r for r in self.records if not r.failed]
+        lat = np.array([r.latency for r in served]) * 1e3
+        edges = sum(getattr(r, "edges", 0) for r in served)
+        return {"requests": len(served), "failed": len(self.records) - len(served),
+                "updates": len(self.groups),
                 "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_ms": float(lat.mean()) if len(lat) else None,
-                "requests_per_s": len(self.records) / self.wall if self.wall else None,
+                "requests_per_s": len(served) / self.wall if self.wall else None,
                 "wall_s": self.wall, "edges": edges}
 
 
@@ -153,7 +156,12 @@ class Server:
 
     # -- continuous batching ------------------------------------------------
     def serve(self, requests: list, coalesce: bool = True) -> ServeResult:
-        """Serve `requests` (sorted by arrival) with one worker per graph."""
+        """Serve `requests` (sorted by arrival) with one worker per graph.
+
+        If a graph's worker raises, its slot and memory are given back, the
+        other graphs go on being served, that graph's unserved requests are
+        marked failed, and serve() raises the first error once every worker
+        has stopped (the partial result is attached as `.result`)."""
         ng = len(self.handles)
         queues = [deque() for _ in range(ng)]
         cv = threading.Condition()
@@ -163,9 +171,11 @@ class Server:
             recs[r.rid].edges = int(r.dels.shape[0] + r.ins.shape[0])
         groups = []
         errors = []
+        failed = [False] * ng
         t0 = time.perf_counter()
 
         def worker(g):
+            admitted, need, take = False, 0, []
             try:
                 while True:
                     with cv:
@@ -194,6 +204,7 @@ class Server:
                             queues[g].popleft()
                         state["busy"] += 1
                         state["mem"] += need
+                        admitted = True
                         self.peak["busy"] = max(self.peak["busy"], state["busy"])
                         self.peak["mem"] = max(self.peak["mem"], state["mem"])
                         gid = state["gid"]
@@ -203,11 +214,19 @@ class Server:
                     with cv:
                         state["busy"] -= 1
                         state["mem"] -= need
+                        admitted = False
+                        take = []
                         cv.notify_all()
             except Exception as e:  # surfaced after the join
-                errors.append(e)
                 with cv:
-                    state["busy"] = max(0, state["busy"] - 1)
+                    errors.append(e)
+                    if admitted:  # give back exactly what this update held
+                        state["busy"] -= 1
+                        state["mem"] -= need
+                    failed[g] = True
+                    for r in list(take) + list(queues[g]):
+                        recs[r.rid].failed = True
+                    queues[g].clear()
                     cv.notify_all()
 
         threads = [threading.Thread(target=worker, args=(g,), daemon=True) for g in range(ng)]
@@ -218,18 +237,23 @@ class Server:
             if delay > 0:
                 time.sleep(delay)
             with cv:
-                queues[r.graph].append(r)
+                if failed[r.graph]:
+                    recs[r.rid].failed = True
+                else:
+                    queues[r.graph].append(r)
                 cv.notify_all()
         with cv:
             state["done"] = True
             cv.notify_all()
         for t in threads:
             t.join()
-        if errors:
-            raise errors[0]
         groups.sort()
-        return ServeResult([recs[r.rid] for r in requests], [(g, ids) for _, g, ids in groups],
-                           time.perf_counter() - t0)
+        result = ServeResult([recs[r.rid] for r in requests], [(g, ids) for _, g, ids in groups],
+                             time.perf_counter() - t0)
+        if errors:
+            errors[0].result = result
+            raise errors[0]
+        return result
 
     # -- baselines ------------------------------------------------------------
     def serve_serial(self, requests: list) -> ServeResult:

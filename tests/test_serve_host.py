@@ -134,3 +134,41 @@ def test_periodic_static_refresh():
                            for ids in by_group.values() for i in ids)
     again = serve.Server([FakeHandle(g, 0.0) for g in range(3)], refresh_every=4).replay(reqs, res.groups)
     assert [(r.num, r.refreshed) for r in again.records] == [(r.num, r.refreshed) for r in res.records]
+
+
+class FailingHandle(FakeHandle):
+    """Raises on its `fail_at`-th update (0-based)."""
+
+    def __init__(self, g, fail_at, delay=0.002):
+        super().__init__(g, delay)
+        self.fail_at = fail_at
+        self.calls = 0
+
+    def update(self, mode):
+        self.calls += 1
+        if self.calls - 1 == self.fail_at:
+            self.pending = []
+            raise RuntimeError(f"graph {self.g} failed")
+        super().update(mode)
+
+
+def test_worker_error_gives_back_its_slot_and_memory():
+    """A graph whose update raises: its slot and memory return to the pool
+    (the other graphs are still served, also with one slot in all), its
+    unserved requests are marked failed, and serve() raises the error with
+    the partial result attached."""
+    import pytest
+    reqs = requests(num_graphs=3, count=90, seed=5)
+    one = max(serve.batch_bytes(r) for r in reqs)
+    handles = [FakeHandle(0), FailingHandle(1, fail_at=2), FakeHandle(2)]
+    srv = serve.Server(handles, resident_bytes=0, mem_cap=3 * one, slots=1)
+    with pytest.raises(RuntimeError, match="graph 1 failed") as ei:
+        srv.serve(reqs, coalesce=False)
+    res = ei.value.result
+    ok = [r for r in res.records if r.graph != 1]
+    assert ok and all(not r.failed and r.finish >= r.arrival for r in ok), \
+        "the other graphs were served after the failure"
+    g1 = [r for r in res.records if r.graph == 1]
+    assert sum(not r.failed for r in g1) == 2 and all(r.failed for r in g1[2:])
+    s = res.summary()
+    assert s["failed"] == len(g1) - 2 and s["p50_ms"] >= 0
