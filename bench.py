@@ -24,12 +24,23 @@ weights 1 to 16; 8 edges per vertex), each step one batch of 1e-4 x |E| per
 graph (80% insertions with weights 1 to 16, 20% deletions), applied and
 updated with DF for all graphs by one group handle, against the same
 batches through one handle per graph, one graph after another.
+
+--temporal measures DF on the temporal stream instead (2M vertices, 30M
+interactions, base = the first 90%, sliding-window batches).
+
+By default (one GPU, not --profile-only) the line also carries the group,
+serving and temporal measurements as the sub-objects "group", "serve" and
+"temporal" (each with its own clock record, end-to-end figure and
+comparison with the serial baseline); their inputs are generated in spawned
+worker processes while the DF steps run.  --no-extras leaves them out.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -49,13 +60,14 @@ EDGES = 33_554_432
 GRAPH_SEED = 2
 BATCH_SEED = 200
 BATCH_FRAC = 1e-3
-# DRAM bytes (read + write) of the decide kernels of one sub-step's decide
-# phase on the default workload (R-MAT 2^22, 1e-3|E| batches), from a
-# single-pass ncu capture of the timed DF steps: cold (ncu's default, caches
-# flushed before each launch) and warm (--cache-control none).  They belong
-# to the decide kernels as they stand; other workloads report null.
-DECIDE_TRAFFIC_COLD = 53.43e6
-DECIDE_TRAFFIC_WARM = 19.25e6
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the decide
+# kernels of one decide phase (one sub-step) of the default workload (R-MAT
+# 2^22, 1e-3|E| batches), from single-pass ncu captures of the timed DF steps
+# divided by their sub-steps: caches flushed before each launch (cold) and
+# kept (warm).  They belong to the kernel sources whose hash is recorded;
+# with other sources, or another workload, the line reports null.
+DECIDE_TRAFFIC = {"sources_sha256": None, "cold": None, "warm": None,
+                  "profile": "profiles/decide_traffic_rmat22_df.md"}
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
 SERVE_SCALES = [18, 19, 19, 20, 21, 22, 22, 23]
@@ -92,6 +104,8 @@ def parse():
                         "graph replay, host launches for updates below 256 batch edges), kernels "
                         "from the host (DFL_FLAG_NO_GRAPH), always a replayed CUDA graph "
                         "(DFL_FLAG_GRAPH) or one cooperative kernel (DFL_FLAG_PERSISTENT)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="leave the group, serving and temporal sub-objects out of the default line")
     p.add_argument("--group-graphs", type=int, default=GROUP_GRAPHS)
     p.add_argument("--group-max-n", type=float, default=1e6)
     return p.parse_args()
@@ -126,6 +140,32 @@ def peaks():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def kernel_sources_sha() -> str:
+    """sha256 over the CUDA sources of the library (file names and contents)."""
+    d = os.path.join(ROOT, "paper_2404_19634_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def host_cpu() -> dict:
+    """The host CPU model (lscpu) and its core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model or platform.processor() or platform.machine(), "host_cores": os.cpu_count()}
 
 
 def _visible_device(gpu_index: int) -> str:
@@ -358,12 +398,45 @@ def reference_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"rmat{args.scale} |E|={g.m} DF batches of {size} (1e-3|E|)",
                    "batch_edges": size, "static_s": static_s, "l2": "not applicable (CPU)"},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, **host_cpu(), "kind": "oracle",
                          "sample": f"{args.warmup}+{args.steps} DF batches of {size} edges after "
-                                   f"static Louvain (static {static_s:.1f} s untimed)"},
+                                   f"static Louvain (static {static_s:.1f} s untimed)",
+                         "threads": "1 core used of the host's"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _temporal_inputs(_=None):
+    """The temporal stream and its base graph (worker process)."""
+    t0 = time.perf_counter()
+    src, dst = synth.temporal_pa_stream_vec(TEMPORAL_N, TEMPORAL_STEPS, 0.3, 3)
+    base_end = TEMPORAL_STEPS * 9 // 10
+    g = synth.temporal_edges(src[:base_end], dst[:base_end], TEMPORAL_N)
+    return src, dst, g, synth.to_csr(g), time.perf_counter() - t0
+
+
+def _group_graph(args):
+    k, count, n_hi = args
+    n, blocks, mu, seed = synth.planted_group_params(count, 1e4, n_hi, GROUP_SEED)[k]
+    g = synth.planted_partition(n, blocks, mu, 16.0, 16, seed)
+    return g, (g.n, *synth.to_csr(g)), {"n": n, "blocks": blocks, "mu": round(mu, 4)}
+
+
+def _serve_graph(k):
+    g = synth.rmat(SERVE_SCALES[k], 8 << SERVE_SCALES[k], 300 + k)
+    return g, (g.n, *synth.to_csr(g))
+
+
+def start_inputs(pool, args) -> dict:
+    """Submit the inputs of the group, serving and temporal measurements to
+    `pool` (spawned workers), the largest first."""
+    t0 = time.perf_counter()
+    order = sorted(range(len(SERVE_SCALES)), key=lambda k: -SERVE_SCALES[k])
+    serve = {k: pool.submit(_serve_graph, k) for k in order}
+    temporal = pool.submit(_temporal_inputs)
+    group = [pool.submit(_group_graph, (k, args.group_graphs, args.group_max_n)) for k in range(args.group_graphs)]
+    return {"t0": t0, "serve": serve, "temporal": temporal, "group": group}
 
 
 def gpu_arm(args):
@@ -375,6 +448,14 @@ def gpu_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    extras = world == 1 and not args.profile_only and not args.no_extras
+    pool, futs = None, None
+    if extras:  # before any CUDA call: the workers are spawned, not forked
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        pool = ProcessPoolExecutor(max_workers=max(1, min(14, (os.cpu_count() or 2) - 2)),
+                                   mp_context=mp.get_context("spawn"))
+        futs = start_inputs(pool, args)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -446,19 +527,32 @@ def gpu_arm(args):
     value = whole_job_ms(sum(step_ms), args.steps, world, dev)
     ms_per_step = value * world  # the slowest rank's ms per step
 
-    # roofline of the local-moving decide kernels (the hot loop)
+    # roofline of the local-moving decide phase (the hot loop): one "launch"
+    # is one sub-step's decide phase, its concurrent decide kernels from the
+    # first start to the last end (CUDA events on the handle's stream)
     peak, peak_kind = peaks()
     mv = prof["move"]
-    achieved = (mv["bytes"] / 1e9) / (mv["ms"] / 1e3) if mv["ms"] > 0 else 0.0
+    nl = max(1, mv["launches"])
+    bytes_launch = mv["bytes"] / nl
+    ms_launch = mv["ms"] / nl
+    achieved = (bytes_launch / 1e9) / (ms_launch / 1e3) if ms_launch > 0 else 0.0
     default_workload = args.scale == SCALE and args.edges == EDGES
+    tr_ok = default_workload and DECIDE_TRAFFIC["sources_sha256"] == kernel_sources_sha()
+    cold = DECIDE_TRAFFIC["cold"] if tr_ok else None
+    warm = DECIDE_TRAFFIC["warm"] if tr_ok else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak,
-                "traffic": DECIDE_TRAFFIC_COLD if default_workload else None,
-                "traffic_warm": DECIDE_TRAFFIC_WARM if default_workload else None,
-                "kernel": "local-move decide",
-                "peak_kind": peak_kind, "bytes_per_step": mv["bytes"] / args.steps,
-                "kernel_ms_per_step": mv["ms"] / args.steps,
-                "launches_per_step": mv["launches"] / args.steps}
+                "frac": achieved / peak, "traffic": cold,
+                "kernel": "local-move decide phase (one sub-step: the concurrent decide kernels of its "
+                          "four degree bins)",
+                "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+                "launches_per_step": mv["launches"] / args.steps,
+                "bytes_per_step": mv["bytes"] / args.steps, "kernel_ms_per_step": mv["ms"] / args.steps,
+                "traffic_warm": warm,
+                "traffic_ratio": (cold / bytes_launch) if cold else None,
+                "traffic_ratio_warm": (warm / bytes_launch) if warm else None,
+                "traffic_source": (f"ncu capture of these kernel sources ({DECIDE_TRAFFIC['profile']}), "
+                                   "bytes per decide phase; not measured in this run") if tr_ok else
+                                  "null: no capture of these kernel sources on this workload"}
     kernel_share = None
 
     extra = {}
@@ -484,6 +578,7 @@ def gpu_arm(args):
         d, i = bstream.next(size)
         dd, di = to_dev(d), to_dev(i)
         torch.cuda.synchronize()
+        h.profile(reset=True)  # the decide phases of the ND update alone
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         h.apply_batch(dd, di)
@@ -493,6 +588,7 @@ def gpu_arm(args):
         extra["nd_1e-3"] = round(a.elapsed_time(b), 4)
         nd_prof = h.profile(reset=True)["move"]
         extra["nd_move_gbs"] = round((nd_prof["bytes"] / 1e9) / (nd_prof["ms"] / 1e3), 1) if nd_prof["ms"] else None
+        extra["nd_move_frac"] = round(extra["nd_move_gbs"] / peak, 4) if extra["nd_move_gbs"] else None
     static_move = static_prof["move"]
     static_gbs = (static_move["bytes"] / 1e9) / (static_move["ms"] / 1e3) if static_move["ms"] else None
     # every kernel class timed (more events, so separate from the timed steps)
@@ -526,6 +622,24 @@ def gpu_arm(args):
         e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 12 * size,
                "d2h_bytes_per_step": 4 * g.n}
+    substeps = dfl.default_options().substeps
+    h.close()
+    del flush, dbatches
+
+    subs = {}
+    if extras:
+        tg = time.perf_counter()
+        src, dst, tgraph, tcsr, t_gen = futs["temporal"].result()
+        subs["temporal"] = temporal_measure(args, src, dst, tgraph, tcsr, t_gen)
+        del src, dst, tgraph, tcsr
+        made = [f.result() for f in futs["group"]]
+        subs["group"] = group_measure(args, made, time.perf_counter() - futs["t0"])
+        del made
+        served = [futs["serve"][k].result() for k in range(len(SERVE_SCALES))]
+        subs["serve"] = serve_measure(args, served, time.perf_counter() - futs["t0"])
+        del served
+        pool.shutdown()
+        subs["extras_wall_s"] = round(time.perf_counter() - tg, 1)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.profile_only:
@@ -533,7 +647,8 @@ def gpu_arm(args):
         # DF batches of the same size
         nb = 8
         o, static_s, times = run_oracle(g, off, idx, w, [size] * nb, BATCH_SEED)
-        cpu = {"value": 1e3 * statistics.mean(times[2:]), "unit": "ms", "cores": 1, "kind": "oracle",
+        cpu = {"value": 1e3 * statistics.mean(times[2:]), "unit": "ms", "cores": 1, **host_cpu(),
+               "threads": "1 core used of the host's", "kind": "oracle",
                "sample": f"{nb - 2} DF batches of {size} edges (after 2 untimed) on the same "
                          f"graph, static Louvain untimed ({static_s:.1f} s)",
                "static_s": static_s}
@@ -548,12 +663,14 @@ def gpu_arm(args):
                        "batch_edges": size, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "iteration_launch": LAUNCH_DESC[args.launch],
+                       "substeps": substeps,
+                       "schedule": f"{substeps} synchronous hash-class sub-steps per local-moving iteration "
+                                   "(a class decides against the state the previous class left)",
                        "static_ms": round(static_ms, 3), "static_passes": static_stats["iterations"],
                        "static_move_gbs": round(static_gbs, 1) if static_gbs else None,
+                       "static_move_frac": round(static_gbs / peak, 4) if static_gbs else None,
                        "df_ms_by_batch_fraction": extra or None,
                        "step_ms_median": round(statistics.median(step_ms), 4),
-                       "graph_captures": h.stats()["graph_captures"],
-                       "graph_capture_ms": round(h.stats()["graph_capture_ms"], 2),
                        "kernel_ms_per_step_profiled": kernel_share},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -561,29 +678,19 @@ def gpu_arm(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def _group_graph(args):
-    k, count, n_hi = args
-    n, blocks, mu, seed = synth.planted_group_params(count, 1e4, n_hi, GROUP_SEED)[k]
-    g = synth.planted_partition(n, blocks, mu, 16.0, 16, seed)
-    return g, (g.n, *synth.to_csr(g)), {"n": n, "blocks": blocks, "mu": round(mu, 4)}
-
-
-def group_arm(args):
+def group_measure(args, made, gen_s) -> dict:
+    """The batched form (one group handle) against one handle per graph."""
     import torch
 
     import paper_2404_19634_gb300 as dfl
 
-    G = args.group_graphs
-    t_gen = time.perf_counter()
-    import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        made = pool.map(_group_graph, [(k, G, args.group_max_n) for k in range(G)])
-    gen_s = time.perf_counter() - t_gen
+    G = len(made)
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     dfl.build()
@@ -593,8 +700,8 @@ def group_arm(args):
     torch.cuda.set_stream(stream)
     nsteps = args.warmup + args.steps
     bstreams = [synth.BatchStream(g, 500 + k) for k, g in enumerate(graphs)]
-    batches = [[bs.next(max(1, int(round(1e-4 * g.m))), w_max=16) for bs, g in zip(bstreams, graphs)]
-               for _ in range(nsteps)]
+    bsize = [max(1, int(round(1e-4 * g.m))) for g in graphs]
+    batches = [[bs.next(sz, w_max=16) for bs, sz in zip(bstreams, bsize)] for _ in range(nsteps + 2)]
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
 
     # one group handle: batches of all graphs in one device array each
@@ -602,11 +709,14 @@ def group_arm(args):
     grp = dfl.DflGroup(csrs, options=dfl.default_options(flags=pflag), stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    grp.static()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with Clocks(0) as static_clocks:
+        e0.record(stream)
+        grp.static()
+        e1.record(stream)
+        torch.cuda.synchronize()
     group_static_ms = e0.elapsed_time(e1)
+    static_passes = [grp.graph_stats(g)["passes"] for g in range(G)]
+    static_final = [grp.graph_modularity(g)[1:] for g in range(G)]
     gbatches = []
     for step in batches:
         d = np.concatenate([b[0] for b in step])
@@ -632,45 +742,76 @@ def group_arm(args):
         grp.apply_batches(*gbatches[k])
         grp.update(dfl.DF)
 
-    time_steps(group_step, 0, args.warmup)
+    # the autotuner picks bin limits and block size for the first step's frontier
+    grp.apply_batches(*gbatches[0])
+    tuning, tune_ms = grp.autotune(dfl.DF, reps=3)
+    grp.update(dfl.DF)
+    time_steps(group_step, 1, args.warmup)
     l0 = grp.stats()["kernel_launches"]
     with Clocks(0) as clocks:
         torch.cuda.nvtx.range_push("group_steps")
-        group_ms = time_steps(group_step, args.warmup, args.steps)
+        group_ms = time_steps(group_step, 1 + args.warmup, args.steps)
         torch.cuda.nvtx.range_pop()
     group_launches = grp.stats()["kernel_launches"] - l0
     group_final = [grp.graph_modularity(g)[1:] for g in range(G)]
+    group_memb = [grp.graph_membership(g).copy() for g in range(G)]
     passes = [grp.graph_stats(g)["passes"] for g in range(G)]
+    # a step in which graphs aggregate: ND over every vertex with the next batch
+    k_nd = nsteps + 1
+    grp.apply_batches(*gbatches[k_nd])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    grp.update(dfl.ND)
+    b.record(stream)
+    torch.cuda.synchronize()
+    group_nd_ms = a.elapsed_time(b)
+    nd_passes = [grp.graph_stats(g)["passes"] for g in range(G)]
+    nd_final = [grp.graph_modularity(g)[1:] for g in range(G)]
 
-    # the same graphs and batches, one handle per graph, one after another
+    # the same graphs, batches and tuning, one handle per graph, one after another
     hs = [dfl.Dfl(n, off, idx, w, options=dfl.default_options(flags=pflag), stream=stream)
           for n, off, idx, w in csrs]
+    for hh in hs:
+        hh.set_tuning(**tuning)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for h in hs:
-        h.static()
+    for hh in hs:
+        hh.static()
     torch.cuda.synchronize()
     serial_static_ms = 1e3 * (time.perf_counter() - t0)
+    serial_static_final = [hh.modularity()[1:] for hh in hs]
     sbatches = [[(to_dev(d), to_dev(i)) for d, i in step] for step in batches]
 
     def serial_step(k):
-        for h, (d, i) in zip(hs, sbatches[k]):
-            h.apply_batch(d, i)
-            h.update(dfl.DF)
+        for hh, (d, i) in zip(hs, sbatches[k]):
+            hh.apply_batch(d, i)
+            hh.update(dfl.DF)
 
-    time_steps(serial_step, 0, args.warmup)
-    serial_ms = time_steps(serial_step, args.warmup, args.steps)
-    serial_final = [h.modularity()[1:] for h in hs]
+    serial_step(0)
+    time_steps(serial_step, 1, args.warmup)
+    with Clocks(0) as serial_clocks:
+        serial_ms = time_steps(serial_step, 1 + args.warmup, args.steps)
+    serial_final = [hh.modularity()[1:] for hh in hs]
     identical = serial_final == group_final
-    same_membership = all(np.array_equal(grp.graph_membership(g), hs[g].membership()) for g in range(G))
-    for h in hs:
-        h.close()
+    same_membership = all(np.array_equal(group_memb[g], hs[g].membership()) for g in range(G))
+    for hh, (d, i) in zip(hs, sbatches[k_nd]):
+        hh.apply_batch(d, i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for hh in hs:
+        hh.update(dfl.ND)
+    torch.cuda.synchronize()
+    serial_nd_ms = 1e3 * (time.perf_counter() - t0)
+    serial_nd_final = [hh.modularity()[1:] for hh in hs]
+    for hh in hs:
+        hh.close()
 
     # end to end: host batches in, every graph's membership out, each step
     e2e = None
     if not args.profile_only:
         host = []
         for _ in range(args.steps):
-            step = [bs.next(max(1, int(round(1e-4 * g.m))), w_max=16) for bs, g in zip(bstreams, graphs)]
+            step = [bs.next(sz, w_max=16) for bs, sz in zip(bstreams, bsize)]
             host.append(([b[0] for b in step], [b[1] for b in step]))
         out = [np.zeros(g.n, np.uint32) for g in graphs]
         torch.cuda.synchronize()
@@ -685,8 +826,9 @@ def group_arm(args):
                "h2d_bytes_per_step": int(np.mean([12 * sum(x.shape[0] for x in d + i) for d, i in host])),
                "d2h_bytes_per_step": 4 * sum(g.n for g in graphs)}
     grp.close()
+    del flush, gbatches, sbatches
     value = statistics.mean(group_ms)
-    line = {
+    return {
         "metric": GROUP_METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -697,17 +839,33 @@ def group_arm(args):
                    "batch_edges_per_step": sum(d.shape[0] + i.shape[0] for d, i in batches[0]),
                    "l2": "flushed between timed steps (256 MB write)", "generation_s": round(gen_s, 1),
                    "iteration_launch": LAUNCH_DESC["host" if args.launch == "auto" else args.launch],
-                   "group_static_ms": round(group_static_ms, 2),
-                   "serial_static_ms": round(serial_static_ms, 2),
                    "passes_min_max": [min(passes), max(passes)]},
+        "tuning": tuning, "autotune_decide_ms": round(tune_ms, 4),
         "serial_ms_per_step": statistics.mean(serial_ms),
         "speedup_vs_serial": statistics.mean(serial_ms) / value,
         "identical_to_serial": bool(identical and same_membership),
+        "serial_tuning": "the group's autotuned tuning on every handle",
+        "aggregating_steps": {
+            "static": {"group_ms": round(group_static_ms, 2), "serial_ms": round(serial_static_ms, 2),
+                       "passes_min_max": [min(static_passes), max(static_passes)],
+                       "identical_to_serial": static_final == serial_static_final,
+                       "clocks": static_clocks.summary()},
+            "nd_update": {"group_ms": round(group_nd_ms, 2), "serial_ms": round(serial_nd_ms, 2),
+                          "passes_min_max": [min(nd_passes), max(nd_passes)],
+                          "identical_to_serial": nd_final == serial_nd_final}},
         "e2e": e2e,
         "gpu_launches": int(group_launches),
         "clocks": clocks.summary(),
+        "serial_clocks": serial_clocks.summary(),
     }
-    print(json.dumps(line), flush=True)
+
+
+def group_arm(args):
+    t_gen = time.perf_counter()
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        made = pool.map(_group_graph, [(k, args.group_graphs, args.group_max_n) for k in range(args.group_graphs)])
+    print(json.dumps(group_measure(args, made, time.perf_counter() - t_gen)), flush=True)
 
 
 AUX_METRIC = "mean speedup of DF from reusing K and Sigma instead of recomputing them (Section 4.2)"
@@ -796,11 +954,12 @@ TEMPORAL_STEPS = 30_000_000
 TEMPORAL_METRIC = "ms/batch DF update, temporal PA stream (2M vertices, 30M interactions), sliding window"
 
 
-def temporal_arm(args):
+def temporal_measure(args, src, dst, g, csr, gen_s) -> dict:
     """The temporal workload: base = the first 90% of the stream (weight =
     multiplicity, tau_agg = 1), then consecutive sliding-window batches of
     1e-5 and 1e-4 x interactions (insert the next ones, expire as many of the
-    oldest), each applied and updated with DF."""
+    oldest), each applied and updated with DF; then the same from pinned
+    host buffers with the membership read back (end to end)."""
     import torch
 
     import paper_2404_19634_gb300 as dfl
@@ -808,12 +967,8 @@ def temporal_arm(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     dfl.build()
-    t0 = time.perf_counter()
-    src, dst = synth.temporal_pa_stream_vec(TEMPORAL_N, TEMPORAL_STEPS, 0.3, 3)
+    off, idx, w = csr
     base_end = TEMPORAL_STEPS * 9 // 10
-    g = synth.temporal_edges(src[:base_end], dst[:base_end], TEMPORAL_N)
-    off, idx, w = synth.to_csr(g)
-    gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     pflag = launch_flag(dfl, args)
@@ -859,9 +1014,30 @@ def temporal_arm(args):
         by_size[f"{frac:g}"] = {"batch_interactions": size, "ms_mean": round(statistics.mean(ms), 4),
                                 "ms_median": round(statistics.median(ms), 4)}
     clocks.__exit__(None, None, None)
+    # end to end at 1e-4: pinned host window batches in, membership out
+    size = int(round(1e-4 * TEMPORAL_STEPS))
+    host = []
+    for _ in range(args.steps):
+        d, i = synth.window_batch(src, dst, start, end, size)
+        start += size
+        end += size
+        host.append((torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory(),
+                     torch.from_numpy(np.ascontiguousarray(i).view(np.int32)).pin_memory()))
+    out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d, i in host:
+        h.apply_batch(d, i)
+        h.update(dfl.DF)
+        h.membership(out)
+    torch.cuda.synchronize()
+    e2e = {"value": 1e3 * (time.perf_counter() - t0) / args.steps, "unit": "ms",
+           "h2d_bytes_per_step": int(np.mean([12 * (d.shape[0] + i.shape[0]) for d, i in host])),
+           "d2h_bytes_per_step": 4 * g.n}
     h.close()
+    del flush
     value = by_size["0.0001"]["ms_mean"]
-    line = {
+    return {
         "metric": TEMPORAL_METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -870,20 +1046,21 @@ def temporal_arm(args):
                    "base_edges": g.m, "tau_agg": 1.0, "generation_s": round(gen_s, 1),
                    "l2": "flushed between timed steps (256 MB write)",
                    "iteration_launch": LAUNCH_DESC[args.launch],
-                   "static_ms": round(static_ms, 2), "df_by_batch_fraction": by_size},
-        "e2e": None,
+                   "static_ms": round(static_ms, 2), "df_by_batch_fraction": by_size,
+                   "df_vs_static_1e-4": round(static_ms / value, 1)},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
-    print(json.dumps(line), flush=True)
 
 
-def _serve_graph(k):
-    g = synth.rmat(SERVE_SCALES[k], 8 << SERVE_SCALES[k], 300 + k)
-    return g, (g.n, *synth.to_csr(g))
+def temporal_arm(args):
+    print(json.dumps(temporal_measure(args, *_temporal_inputs())), flush=True)
 
 
-def serve_arm(args):
+def serve_measure(args, made, gen_s) -> dict:
+    """The serving form: serial per-request DF, overlapped per graph without
+    coalescing (results identical to serial), and overlapped with coalescing."""
     import torch
 
     import paper_2404_19634_gb300 as dfl
@@ -892,20 +1069,14 @@ def serve_arm(args):
     torch.cuda.set_device(0)
     dfl.build()
     t_gen = time.perf_counter()
-    # the graphs are generated in parallel host processes (spawned, so that
-    # no child inherits a CUDA context)
-    import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(len(SERVE_SCALES), os.cpu_count() or 1)) as pool:
-        made = pool.map(_serve_graph, range(len(SERVE_SCALES)))
     graphs = [g for g, _ in made]
     csrs = [c for _, c in made]
-    del made
     pools = [synth.EdgePool(g, 400 + k) for k, g in enumerate(graphs)]
     warm = [(0.0, g, 1000) for _ in range(max(1, args.warmup)) for g in range(len(graphs))]
     sched = synth.poisson_requests(len(graphs), SERVE_RATE, args.serve_seconds, *SERVE_SIZES, seed=500)
     reqs = serve.make_requests(pools, warm + sched)
     wreq, treq = reqs[:len(warm)], reqs[len(warm):]
-    gen_s = time.perf_counter() - t_gen
+    gen_s += time.perf_counter() - t_gen
     edges = [int(r.dels.shape[0] + r.ins.shape[0]) for r in treq]
 
     def run(mode):
@@ -924,17 +1095,24 @@ def serve_arm(args):
         srv.close()
         out = res.summary()
         out["gpu_launches"] = launches
-        return res, out, final, clk.summary()
+        out["clocks"] = clk.summary()
+        return res, out, final
 
-    ser, ser_sum, ser_final, _ = run("serial")
-    ovl, ovl_sum, ovl_final, _ = run("overlap")
-    coa, coa_sum, coa_final, clocks = run("coalesce")
+    ser, ser_sum, ser_final = run("serial")
+    ovl, ovl_sum, ovl_final = run("overlap")
+    coa, coa_sum, coa_final = run("coalesce")
     ovl_sum["identical_to_serial"] = all((a.num, a.den) == (b.num, b.den)
                                          for a, b in zip(ovl.records, ser.records))
+    ovl_sum["final_q_minus_serial"] = [round(a[0] - b[0], 9) for a, b in zip(ovl_final, ser_final)]
     coa_sum["final_q_minus_serial"] = [round(a[0] - b[0], 9) for a, b in zip(coa_final, ser_final)]
     coa_sum["max_requests_per_update"] = max(len(ids) for _, ids in coa.groups)
     mean_edges = float(np.mean(edges)) if edges else 0.0
-    line = {
+
+    def vs(x):
+        return {"updates_per_s": x["requests_per_s"] / ser_sum["requests_per_s"],
+                "p50": ser_sum["p50_ms"] / x["p50_ms"], "p99": ser_sum["p99_ms"] / x["p99_ms"]}
+
+    return {
         "metric": SERVE_METRIC, "value": coa_sum["requests_per_s"], "unit": "updates/s",
         "n_gpus": 1, "steps": len(treq), "warmup": len(wreq),
         "ms_per_step": 1e3 * coa_sum["wall_s"] / max(1, len(treq)), "higher_is_better": True,
@@ -942,21 +1120,30 @@ def serve_arm(args):
         "config": {"workload": "8 R-MAT graphs (a=.57 b=.19 c=.19) of 2^18,2^19,2^19,2^20,2^21,2^22,"
                                "2^22,2^23 vertices, 8 edges per vertex; Poisson requests",
                    "rate_per_s": SERVE_RATE, "arrival_window_s": args.serve_seconds,
+                   "window_note": "shorter than the 10 s the workload names, so that generating the "
+                                  "batches fits a bench run",
                    "batch_edges": "log-uniform [10, 1e6], 80% insertions / 20% deletions",
                    "requests": len(treq), "mean_batch_edges": round(mean_edges, 1),
                    "warmup": f"{len(wreq)} requests of 1000 edges, served serially, untimed",
                    "mem_cap_bytes": 150 << 30, "generation_s": round(gen_s, 1),
-                   "l2": "not flushed (the 8 graphs total 1.7e8 edges, far above L2)"},
+                   "l2": "not flushed (the 8 graphs total 1.5e8 edges, far above L2)"},
         "serial": ser_sum, "overlap": ovl_sum, "coalesce": coa_sum,
-        "speedup_vs_serial": {"updates_per_s": coa_sum["requests_per_s"] / ser_sum["requests_per_s"],
-                              "p50": ser_sum["p50_ms"] / coa_sum["p50_ms"],
-                              "p99": ser_sum["p99_ms"] / coa_sum["p99_ms"]},
+        "speedup_vs_serial": {"overlap_identical_results": vs(ovl_sum), "coalesce": vs(coa_sum)},
         "e2e": {"value": coa_sum["requests_per_s"], "unit": "updates/s",
                 "h2d_bytes_per_step": 12 * mean_edges, "d2h_bytes_per_step": 32},
         "gpu_launches": coa_sum["gpu_launches"],
-        "clocks": clocks,
+        "clocks": coa_sum["clocks"],
     }
-    print(json.dumps(line), flush=True)
+
+
+def serve_arm(args):
+    t_gen = time.perf_counter()
+    # the graphs are generated in parallel host processes (spawned, so that
+    # no child inherits a CUDA context)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(SERVE_SCALES), os.cpu_count() or 1)) as pool:
+        made = pool.map(_serve_graph, range(len(SERVE_SCALES)))
+    print(json.dumps(serve_measure(args, made, time.perf_counter() - t_gen)), flush=True)
 
 
 def main():

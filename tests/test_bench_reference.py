@@ -21,6 +21,7 @@ def test_reference_arm_json_line():
     assert line["steps"] == 2 and line["warmup"] == 1 and line["value"] > 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["host_cores"] >= cb["cores"] and cb["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
