@@ -108,12 +108,18 @@ enum {
   DFL_FLAG_PROFILE_MOVE = 64u, /* time only the decide phase of each sub-step (two CUDA events per
                                  sub-step, the DFL_PROF_MOVE class of dfl_profile): the cheap
                                  subset of DFL_FLAG_PROFILE */
-  DFL_FLAG_RECOMPUTE_AUX = 128u /* the ablation of Section 4.2: every dfl_update / dfl_group_update
+  DFL_FLAG_RECOMPUTE_AUX = 128u, /* the ablation of Section 4.2: every dfl_update / dfl_group_update
                                  first recomputes K from the graph and Sigma (and 2m) from K and
                                  the memberships, as a dynamic method without auxiliary
                                  information must.  Results are identical; the extra time is
                                  what reusing K^{t-1} and Sigma^{t-1} saves.  (The batch apply
                                  still updates K and Sigma incrementally, fused into its kernels.) */
+  DFL_FLAG_TEST_UNREACHABLE_BARRIER = 256u /* test hook, no counterpart in the paper: with
+                                 DFL_FLAG_PERSISTENT, every grid barrier of the iteration kernel
+                                 waits for one more block than the grid has (a wait nothing
+                                 completes) and gives up after a few milliseconds instead of
+                                 about a second; every block then returns, and the call returns
+                                 DFL_ERR_TIMEOUT.  For testing the timeout path without a fault */
 };
 
 /* Algorithm options; defaults from Section 5.1.2 of the paper. */
@@ -195,7 +201,10 @@ int dfl_set_stream(dfl_handle* h, void* cuda_stream);
 
 /* Static Louvain (the paper's "Static" baseline, GVE-Louvain): K from
  * scratch, every vertex its own community, every vertex affected.  Clears
- * the pending batch. */
+ * the pending batch.  If it fails part-way (DFL_ERR_NOMEM, DFL_ERR_TIMEOUT)
+ * the handle keeps its graph and K but has no communities until a later
+ * dfl_static or dfl_set_membership succeeds (the same holds for
+ * dfl_update). */
 int dfl_static(dfl_handle* h);
 
 /* Apply a batch update (Section 3.4): deletions first, then insertions,
@@ -394,6 +403,20 @@ int dfl_group_modularity(dfl_handle* h, uint32_t g, double* q, int64_t* parts);
  * (passes, iterations, num_communities; the launch, arc and capture
  * counters are the group's). */
 int dfl_group_stats(dfl_handle* h, uint32_t g, dfl_stats_t* s);
+
+/* ---- Test hooks (host-side fault injection; no counterpart in the paper) -- */
+
+/* Make device allocations fail, process-wide: after `after` more successful
+ * allocations every further device allocation of the library fails as if
+ * the GPU were out of memory (the call returns DFL_ERR_NOMEM); `after` < 0
+ * lifts it.  Nothing is allocated for the failed requests.  What an
+ * allocation failure leaves (also for a real out-of-memory): dfl_create
+ * returns no handle; dfl_apply_batch and dfl_group_apply_batch leave the
+ * graph, K, Sigma, 2m and the pending batches unchanged; dfl_static,
+ * dfl_update and their group forms keep the graph and K but no communities
+ * (calls that need them return DFL_ERR_STATE) until dfl_static, or
+ * dfl_set_membership, succeeds.  It applies to every handle of the process. */
+int dfl_test_fail_allocations(int64_t after);
 
 /* ---- Allocation-free entry point --------------------------------------- */
 

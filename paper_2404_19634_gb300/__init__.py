@@ -34,6 +34,7 @@ FLAG_PERSISTENT = 16
 FLAG_GRAPH = 32
 FLAG_PROFILE_MOVE = 64
 FLAG_RECOMPUTE_AUX = 128
+FLAG_TEST_UNREACHABLE_BARRIER = 256
 PROF_NAMES = ["apply", "mark", "move", "commit", "aggregate", "other", "bin0", "bin1", "bin2",
               "bin3"]
 PROF_APPLY, PROF_MARK, PROF_MOVE, PROF_COMMIT, PROF_AGG, PROF_OTHER = range(6)
@@ -156,6 +157,7 @@ _SIGS = {
     "dfl_group_membership": (ct.c_int, [_P, ct.c_uint32, _P, ct.c_int]),
     "dfl_group_modularity": (ct.c_int, [_P, ct.c_uint32, ct.POINTER(ct.c_double), _P]),
     "dfl_group_stats": (ct.c_int, [_P, ct.c_uint32, ct.POINTER(Stats)]),
+    "dfl_test_fail_allocations": (ct.c_int, [ct.c_int64]),
     "dfl_modularity_csr_noalloc": (ct.c_int, [ct.c_uint32, _P, _P, _P, _P, ct.POINTER(ct.c_double),
                                               _P, _P]),
 }
@@ -179,6 +181,12 @@ def modularity_csr_noalloc(n, offsets, indices, weights, membership, stream=None
                                         _stream_ptr(stream))
     del bufs
     return rc, q.value, _i128(int(parts[0]), int(parts[1])), _i128(int(parts[2]), int(parts[3]))
+
+
+def test_fail_allocations(after: int) -> None:
+    """Test hook: after `after` more device allocations every further one
+    fails (DFL_ERR_NOMEM); a negative value lifts it (dfl_test_fail_allocations)."""
+    load().dfl_test_fail_allocations(int(after))
 
 
 def library_path() -> str:

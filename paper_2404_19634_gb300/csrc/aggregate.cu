@@ -467,8 +467,8 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     sg.off = nullptr;
     sg.deg = nullptr;
     sg.nv_cap = 0;
-    DFL_CUDA(h, cudaMalloc(&sg.off, sizeof(unsigned long long) * (uint64_t(h->n) + 1)));
-    DFL_CUDA(h, cudaMalloc(&sg.deg, sizeof(uint32_t) * (uint64_t(h->n) + 1)));
+    DFL_CUDA(h, dev_malloc(&sg.off, sizeof(unsigned long long) * (uint64_t(h->n) + 1)));
+    DFL_CUDA(h, dev_malloc(&sg.deg, sizeof(uint32_t) * (uint64_t(h->n) + 1)));
     sg.nv_cap = h->n + 1;
   }
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
@@ -508,7 +508,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
     sg.arcs = nullptr;
     sg.arc_cap = 0;
     uint64_t want = total + total / 8 + 1024;
-    DFL_CUDA(h, cudaMalloc(&sg.arcs, sizeof(uint2) * want));
+    DFL_CUDA(h, dev_malloc(&sg.arcs, sizeof(uint2) * want));
     sg.arc_cap = want;
   }
   // once per process (handles may be driven from several host threads)
@@ -576,7 +576,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
       cudaFree(h->gtable);
       h->gtable = nullptr;
       h->gtable_cap = 0;
-      DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * total));
+      DFL_CUDA(h, dev_malloc(&h->gtable, sizeof(uint2) * total));
       h->gtable_cap = total;
     }
     // small device arrays for the giant layout (in the generic scratch)
@@ -603,7 +603,7 @@ int aggregate(Handle* h, const GraphView& g, const uint32_t* Cp, uint32_t ncomm,
         cudaFree(h->aggq);
         h->aggq = nullptr;
         h->aggq_cap = 0;
-        DFL_CUDA(h, cudaMalloc(&h->aggq, sizeof(uint2) * need));
+        DFL_CUDA(h, dev_malloc(&h->aggq, sizeof(uint2) * need));
         h->aggq_cap = need;
       }
     }

@@ -2,6 +2,7 @@
 // checks, copies between caller buffers and the device, statistics and
 // profiling.  The algorithmic work lives in the other translation units.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,6 +10,22 @@
 #include "common.cuh"
 
 namespace dfl {
+
+namespace {
+std::atomic<long long> g_fail_after{-1};  // allocations left before they fail (-1: never)
+}  // namespace
+
+cudaError_t dev_malloc_bytes(void** p, size_t bytes) {
+  long long k = g_fail_after.load();
+  while (k >= 0) {
+    if (k == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_fail_after.compare_exchange_weak(k, k - 1)) break;
+  }
+  return cudaMalloc(p, bytes);
+}
 
 int set_error(Handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -97,7 +114,7 @@ __global__ void k_relabel_copy(uint32_t n, const uint32_t* __restrict__ C, const
 template <typename T>
 int alloc(Handle* h, T** p, uint64_t count) {
   if (count == 0) count = 1;
-  DFL_CUDA(h, cudaMalloc(p, sizeof(T) * count));
+  DFL_CUDA(h, dev_malloc(p, sizeof(T) * count));
   return DFL_OK;
 }
 
@@ -384,10 +401,18 @@ int dfl_set_stream(dfl_handle* h, void* s) {
   return DFL_OK;
 }
 
-int dfl_static(dfl_handle* h) {
+namespace {
+
+// A Louvain run that fails part-way (an allocation, a bounded wait) leaves
+// labels, Sigma and sizes of an unfinished pass: the handle keeps its graph
+// and K but no communities until dfl_static or dfl_set_membership succeeds.
+int louvain_result(dfl::Handle* h, int rc) {
+  if (rc != DFL_OK) h->have_communities = false;
+  return rc;
+}
+
+int static_body(dfl_handle* h) {
   using namespace dfl;
-  if (!h) return DFL_ERR_INVALID;
-  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
   DFL_TRY(weighted_degrees(h));
   DFL_TRY(iota_u32(h, h->C, h->n));
   DFL_TRY(copy_i64(h, h->Sigma, h->K, h->n));
@@ -400,6 +425,14 @@ int dfl_static(dfl_handle* h) {
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream));
   DFL_TRY(lists_all(h, h->n, h->deg, 0, h->opt.substeps));
   return louvain(h, true, false, h->n);
+}
+
+}  // namespace
+
+int dfl_static(dfl_handle* h) {
+  if (!h) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
+  return louvain_result(h, static_body(h));
 }
 
 int dfl_apply_batch(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const dfl_edge* ins,
@@ -419,11 +452,12 @@ int dfl_update(dfl_handle* h, int mode) {
     return set_error(h, DFL_ERR_INVALID, "unknown mode");
   bool all = false, use_range = false;
   uint64_t initial = 0;
-  if (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) DFL_TRY(recompute_aux(h));
-  DFL_TRY(mark(h, mode, &all, &use_range, &initial));
-  int rc = louvain(h, all, use_range, initial);
+  int rc = DFL_OK;
+  if (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) rc = recompute_aux(h);
+  if (!rc) rc = mark(h, mode, &all, &use_range, &initial);
+  if (!rc) rc = louvain(h, all, use_range, initial);
   h->pend_count = 0;
-  return rc;
+  return louvain_result(h, rc);
 }
 
 int dfl_membership(const dfl_handle* hc, uint32_t* out, int mem_kind) {
@@ -782,10 +816,10 @@ int dfl_group_create(dfl_handle** out, uint32_t num_graphs, const uint32_t* n,
   return DFL_OK;
 }
 
-int dfl_group_static(dfl_handle* h) {
+namespace {
+
+int group_static_body(dfl_handle* h) {
   using namespace dfl;
-  if (!h) return DFL_ERR_INVALID;
-  if (!h->ngraphs) return set_error(h, DFL_ERR_STATE, "not a group handle");
   DFL_TRY(weighted_degrees(h));
   DFL_TRY(group_m2(h));
   DFL_TRY(iota_u32(h, h->C, h->n));
@@ -800,6 +834,14 @@ int dfl_group_static(dfl_handle* h) {
   DFL_CUDA(h, cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream));
   DFL_TRY(lists_all(h, h->n, h->deg, 0, h->opt.substeps));
   return louvain_group(h, true, false, h->n);
+}
+
+}  // namespace
+
+int dfl_group_static(dfl_handle* h) {
+  if (!h) return DFL_ERR_INVALID;
+  if (!h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "not a group handle");
+  return louvain_result(h, group_static_body(h));
 }
 
 int dfl_group_apply_batch(dfl_handle* h, const dfl_edge* del, const uint64_t* del_off,
@@ -822,7 +864,7 @@ int dfl_group_apply_batch(dfl_handle* h, const dfl_edge* del, const uint64_t* de
     h->gb_edges = nullptr;
     h->gb_cap = 0;
     const uint64_t want = (nd + ni) + (nd + ni) / 4 + 1024;
-    DFL_CUDA(h, cudaMalloc(&h->gb_edges, sizeof(dfl_edge) * want));
+    DFL_CUDA(h, dev_malloc(&h->gb_edges, sizeof(dfl_edge) * want));
     h->gb_cap = want;
   }
   dfl_edge* sd = h->gb_edges;
@@ -866,12 +908,12 @@ int dfl_group_update(dfl_handle* h, int mode) {
     return set_error(h, DFL_ERR_INVALID, "unknown mode");
   bool all = false, use_range = false;
   uint64_t initial = 0;
-  DFL_TRY(group_set_level(h, h->d_goff0));  // classes of the base graphs' vertices
-  if (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) DFL_TRY(recompute_aux(h));
-  DFL_TRY(mark(h, mode, &all, &use_range, &initial));
-  int rc = louvain_group(h, all, use_range, initial);
+  int rc = group_set_level(h, h->d_goff0);  // classes of the base graphs' vertices
+  if (!rc && (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX)) rc = recompute_aux(h);
+  if (!rc) rc = mark(h, mode, &all, &use_range, &initial);
+  if (!rc) rc = louvain_group(h, all, use_range, initial);
   h->pend_count = 0;
-  return rc;
+  return louvain_result(h, rc);
 }
 
 int dfl_group_membership(dfl_handle* h, uint32_t g, uint32_t* out, int mem_kind) {
@@ -920,3 +962,8 @@ int dfl_group_stats(dfl_handle* h, uint32_t g, dfl_stats_t* s) {
 }
 
 }  // extern "C"
+
+extern "C" int dfl_test_fail_allocations(int64_t after) {
+  dfl::g_fail_after.store(after < 0 ? -1 : (long long)after);
+  return DFL_OK;
+}

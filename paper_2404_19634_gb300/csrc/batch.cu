@@ -964,7 +964,7 @@ int grow(Handle* h, T** p, uint64_t need, uint64_t* cap_out, uint64_t cap_now, b
   if (need <= cap_now) return DFL_OK;
   uint64_t want = need + need / 2 + 256;
   T* q = nullptr;
-  DFL_CUDA(h, cudaMalloc(&q, sizeof(T) * want));
+  DFL_CUDA(h, dev_malloc(&q, sizeof(T) * want));
   if (keep && *p && keep_items)
     DFL_CUDA(h, cudaMemcpyAsync(q, *p, sizeof(T) * keep_items, cudaMemcpyDeviceToDevice, h->stream));
   if (*p) {
@@ -1021,24 +1021,24 @@ int ensure_hash_buffers(Handle* h, uint64_t na) {
       *q = nullptr;
     }
     h->h_cap = 0;
-    DFL_CUDA(h, cudaMalloc(&h->h_keys, sizeof(unsigned long long) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_ndel, sizeof(uint32_t) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_wdel, sizeof(uint32_t) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_wins, sizeof(unsigned long long) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_slot, sizeof(uint32_t) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_wnew, sizeof(uint32_t) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_flag, sizeof(uint32_t) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_delta, sizeof(long long) * cap));
-    DFL_CUDA(h, cudaMalloc(&h->h_pairs, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_keys, sizeof(unsigned long long) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_ndel, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_wdel, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_wins, sizeof(unsigned long long) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_slot, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_wnew, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_flag, sizeof(uint32_t) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_delta, sizeof(long long) * cap));
+    DFL_CUDA(h, dev_malloc(&h->h_pairs, sizeof(uint32_t) * cap));
     h->h_cap = cap;
   }
   if (!h->r_app) {
     const uint64_t n = h->n ? h->n : 1;
-    DFL_CUDA(h, cudaMalloc(&h->r_app, sizeof(uint32_t) * n));
-    DFL_CUDA(h, cudaMalloc(&h->r_tomb, sizeof(int) * n));
-    DFL_CUDA(h, cudaMalloc(&h->r_live, sizeof(int) * n));
-    DFL_CUDA(h, cudaMalloc(&h->r_state, sizeof(uint32_t) * n));
-    DFL_CUDA(h, cudaMalloc(&h->r_reg, sizeof(uint32_t) * n));
+    DFL_CUDA(h, dev_malloc(&h->r_app, sizeof(uint32_t) * n));
+    DFL_CUDA(h, dev_malloc(&h->r_tomb, sizeof(int) * n));
+    DFL_CUDA(h, dev_malloc(&h->r_live, sizeof(int) * n));
+    DFL_CUDA(h, dev_malloc(&h->r_state, sizeof(uint32_t) * n));
+    DFL_CUDA(h, dev_malloc(&h->r_reg, sizeof(uint32_t) * n));
     DFL_CUDA(h, cudaMemsetAsync(h->r_app, 0, sizeof(uint32_t) * n, h->stream));
     DFL_CUDA(h, cudaMemsetAsync(h->r_tomb, 0, sizeof(int) * n, h->stream));
     DFL_CUDA(h, cudaMemsetAsync(h->r_live, 0, sizeof(int) * n, h->stream));
@@ -1053,8 +1053,8 @@ int ensure_hash_buffers(Handle* h, uint64_t na) {
     h->h_extra = nullptr;
     h->h_rows_cap = 0;
     uint64_t want = na + na / 2 + 256;
-    DFL_CUDA(h, cudaMalloc(&h->h_rows, sizeof(uint32_t) * want));
-    DFL_CUDA(h, cudaMalloc(&h->h_extra, sizeof(uint2) * want));
+    DFL_CUDA(h, dev_malloc(&h->h_rows, sizeof(uint32_t) * want));
+    DFL_CUDA(h, dev_malloc(&h->h_extra, sizeof(uint2) * want));
     h->h_rows_cap = want;
   }
   return DFL_OK;
@@ -1153,19 +1153,36 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
     DFL_TRY(hash_reset(h, t));
     return apply_batch_sorted(h, del, nd, ins, ni, mem_kind);
   }
+  // every buffer the writes need, before the first write: a failed
+  // allocation (DFL_ERR_NOMEM) leaves the graph, K, Sigma and the pending
+  // list as they were (a grown buffer keeps its contents), and the per-row scratch counters of the
+  // validation are cleared again
+  {
+    int grc = DFL_OK;
+    if (h->pool_top + c.reloc_need > h->pool_cap) {
+      uint64_t c2 = 0;
+      uint64_t need = h->pool_top + c.reloc_need;
+      need = need + need / 4 + 1024;
+      grc = grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top);
+      if (!grc) h->pool_cap = c2;
+    }
+    if (!grc && c.scratch_need > h->scratch_cap) {
+      uint64_t c2 = 0;
+      grc = grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap);
+      if (!grc) h->scratch_cap = c2;
+    }
+    if (!grc && h->pend_count + na > h->pend_cap) {
+      uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
+      grc = grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count);
+      if (!grc) grc = grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count);
+      if (!grc) h->pend_cap = c2 < c3 ? c2 : c3;
+    }
+    if (grc) {
+      DFL_TRY(hash_reset(h, t));
+      return grc;
+    }
+  }
   // --- mutation starts here ---
-  if (h->pool_top + c.reloc_need > h->pool_cap) {
-    uint64_t c2 = 0;
-    uint64_t need = h->pool_top + c.reloc_need;
-    need = need + need / 4 + 1024;
-    DFL_TRY(grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top));
-    h->pool_cap = c2;
-  }
-  if (c.scratch_need > h->scratch_cap) {
-    uint64_t c2 = 0;
-    DFL_TRY(grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap));
-    h->scratch_cap = c2;
-  }
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
     k_hash_write<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->off, h->deg, h->arcs, h->ctrl);
@@ -1187,13 +1204,6 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
     LaunchScope ls(h, DFL_PROF_APPLY);
     k_hash_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(t, h->deg, h->ntomb, h->ctrl);
     DFL_TRY(check_launch(h, "hash finish"));
-  }
-  if (h->pend_count + na > h->pend_cap) {
-    uint64_t c2 = 0, need = h->pend_count + na;
-    DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
-    uint64_t c3 = 0;
-    DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
-    h->pend_cap = c2 < c3 ? c2 : c3;
   }
   DFL_CUDA(h, cudaMemcpyAsync(h->pend_key + h->pend_count, h->b_key, sizeof(unsigned long long) * na,
                               cudaMemcpyDeviceToDevice, h->stream));
@@ -1254,19 +1264,34 @@ int apply_batch_sorted(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_ed
   if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
   if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
     return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+  // every buffer the writes need, before the first write: a failed
+  // allocation (DFL_ERR_NOMEM) leaves the graph, K, Sigma and the pending
+  // list as they were (a grown buffer keeps its contents)
+  {
+    int grc = DFL_OK;
+    if (h->pool_top + c.reloc_need > h->pool_cap) {
+      uint64_t c2 = 0;
+      uint64_t need = h->pool_top + c.reloc_need;
+      need = need + need / 4 + 1024;
+      grc = grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top);
+      if (!grc) h->pool_cap = c2;
+    }
+    if (!grc && c.scratch_need > h->scratch_cap) {
+      uint64_t c2 = 0;
+      grc = grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap);
+      if (!grc) h->scratch_cap = c2;
+    }
+    if (!grc && h->pend_count + na > h->pend_cap) {
+      uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
+      grc = grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count);
+      if (!grc) grc = grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count);
+      if (!grc) h->pend_cap = c2 < c3 ? c2 : c3;
+    }
+    if (grc) {
+      return grc;
+    }
+  }
   // --- mutation starts here ---
-  if (h->pool_top + c.reloc_need > h->pool_cap) {
-    uint64_t c2 = 0;
-    uint64_t need = h->pool_top + c.reloc_need;
-    need = need + need / 4 + 1024;
-    DFL_TRY(grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top));
-    h->pool_cap = c2;
-  }
-  if (c.scratch_need > h->scratch_cap) {
-    uint64_t c2 = 0;
-    DFL_TRY(grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap));
-    h->scratch_cap = c2;
-  }
   {
     LaunchScope ls(h, DFL_PROF_APPLY);
     k_write<<<grid_for(na, 256), 256, 0, h->stream>>>(h->b_key, na, f, h->off, h->deg, h->arcs, h->b_pos,
@@ -1295,13 +1320,6 @@ int apply_batch_sorted(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_ed
     DFL_TRY(check_launch(h, "update weights"));
   }
   // pending arcs for the next dfl_update
-  if (h->pend_count + na > h->pend_cap) {
-    uint64_t c2 = 0, need = h->pend_count + na;
-    DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
-    uint64_t c3 = 0;
-    DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
-    h->pend_cap = c2 < c3 ? c2 : c3;
-  }
   DFL_CUDA(h, cudaMemcpyAsync(h->pend_key + h->pend_count, h->b_key, sizeof(unsigned long long) * na,
                               cudaMemcpyDeviceToDevice, h->stream));
   DFL_CUDA(h, cudaMemcpyAsync(h->pend_w + h->pend_count, h->b_w, sizeof(uint32_t) * na,

@@ -338,6 +338,16 @@ int set_error(Handle* h, int code, const std::string& msg);
     if (r_ != DFL_OK) return r_; \
   } while (0)
 
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make allocations fail on the host (dfl_test_fail_allocations):
+// after that many more successful allocations every further one returns
+// cudaErrorMemoryAllocation without calling CUDA.
+cudaError_t dev_malloc_bytes(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 // Launch bookkeeping: counts launches and, with DFL_FLAG_PROFILE, brackets
 // the launch with CUDA events of class `cls`.
 struct LaunchScope {

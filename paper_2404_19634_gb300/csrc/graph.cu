@@ -181,7 +181,7 @@ int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx
   h->num_arcs = nnz;
   // slack capacities and offsets
   unsigned long long* capl = nullptr;
-  DFL_CUDA(h, cudaMalloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
+  DFL_CUDA(h, dev_malloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
   int rc = DFL_OK;
   {
     LaunchScope ls(h, DFL_PROF_OTHER);
@@ -199,7 +199,7 @@ int graph_build(Handle* h, const unsigned long long* off_in, const uint32_t* idx
   if (rc) return rc;
   uint64_t pool = total + total / 8 + 1024;
   pool = (pool + 1) & ~uint64_t(1);
-  DFL_CUDA(h, cudaMalloc(&h->arcs, sizeof(uint2) * pool));
+  DFL_CUDA(h, dev_malloc(&h->arcs, sizeof(uint2) * pool));
   h->pool_cap = pool;
   h->pool_top = total;
   {
@@ -313,7 +313,7 @@ int compact_pool(Handle* h, uint64_t* before, uint64_t* after) {
   }
   DFL_CUDA(h, cudaStreamSynchronize(h->stream));
   unsigned long long* capl = nullptr;
-  DFL_CUDA(h, cudaMalloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
+  DFL_CUDA(h, dev_malloc(&capl, sizeof(unsigned long long) * (uint64_t(n) + 1)));
   int rc = DFL_OK;
   {
     LaunchScope ls(h, DFL_PROF_OTHER);
@@ -329,7 +329,7 @@ int compact_pool(Handle* h, uint64_t* before, uint64_t* after) {
   uint64_t cap = 0;
   if (!rc) {
     cap = (total + total / 8 + 1024 + 1) & ~uint64_t(1);
-    if (cudaMalloc(&pool, sizeof(uint2) * cap) != cudaSuccess) {
+    if (dev_malloc(&pool, sizeof(uint2) * cap) != cudaSuccess) {
       cudaGetLastError();
       rc = set_error(h, DFL_ERR_NOMEM, "compacted arc pool");
     }

@@ -1760,6 +1760,7 @@ constexpr int kIterThreads = 256;
 constexpr uint32_t kIterPreCache = kGiantListSmem;                   // chunk prefix cached in shared memory
 constexpr uint32_t kIterDynWords = 2 * kBlockSlots + kIterPreCache;  // tables + chunk prefix cache
 constexpr unsigned long long kBarrierPolls = 1ull << 22;             // x 256 ns: about a second
+constexpr unsigned long long kTestBarrierPolls = 1ull << 14;         // a few ms (the timeout test hook)
 // vertices per warp in one work unit of bins 1 and 0 (rounds of 1 and of
 // 32 / W vertices); larger units save counter updates on big frontiers but
 // measured slower on small DF frontiers, where they leave blocks idle
@@ -1776,11 +1777,16 @@ struct IterArgs {
   const uint32_t* lists_cur;
   uint32_t* fbits_cur;     // cleared at the end (the processed frontier)
   uint32_t words;
+  // grid barriers: arrivals beyond the grid that complete one (0; 1 makes
+  // every barrier unreachable, DFL_FLAG_TEST_UNREACHABLE_BARRIER) and polls
+  // before a wait gives up
+  uint32_t bar_extra;
+  unsigned long long bar_polls;
 };
 
 // Grid-wide barrier with a bounded wait: false if it gave up (the error bit
 // kErrTimeout is then set and the kernel must return).  Every thread calls it.
-__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, uint32_t extra, unsigned long long max_polls) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1788,14 +1794,14 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
     const unsigned int gen = *genp;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1 + extra) {
       ctrl->bar_count = 0;
       __threadfence();
       atomicAdd(&ctrl->bar_gen, 1u);
     } else {
       unsigned long long polls = 0;
       while (*genp == gen) {
-        if (++polls > kBarrierPolls || (*((volatile unsigned int*)&ctrl->err) & kErrTimeout)) {
+        if (++polls > max_polls || (*((volatile unsigned int*)&ctrl->err) & kErrTimeout)) {
           ok = 0;
           atomicOr(&ctrl->err, kErrTimeout);
           break;
@@ -1866,7 +1872,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
     const DecideArgs a3 = bin_args(ia, blockIdx.x, 3);
     giant_prefix_body(a3, class_giant(ia, blockIdx.x));
   }
-  if (!grid_barrier(ctrl)) return;
+  if (!grid_barrier(ctrl, ia.bar_extra, ia.bar_polls)) return;
   for (uint32_t s = 0; s < ia.k; ++s) {
     const uint32_t par = s & 1;
     if (blockIdx.x == 0 && threadIdx.x == 0 && s >= 1) {  // the other parity's counters are idle now
@@ -1949,15 +1955,15 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
         }
       }
     }
-    if (!grid_barrier(ctrl)) return;
+    if (!grid_barrier(ctrl, ia.bar_extra, ia.bar_polls)) return;
     // 3. vertices with many distinct communities: spread over part blocks
     if (*((volatile unsigned int*)&ctrl->it_bignd[par])) {
       giant_parts(a3, gd, m2_one, sums);
-      if (!grid_barrier(ctrl)) return;
+      if (!grid_barrier(ctrl, ia.bar_extra, ia.bar_polls)) return;
     }
     // 4. commit the sub-step's moves (and mark around high-degree movers)
     commit_body(a0, *((volatile unsigned int*)a0.movers), *((volatile unsigned int*)a0.nbig));
-    if (!grid_barrier(ctrl)) return;
+    if (!grid_barrier(ctrl, ia.bar_extra, ia.bar_polls)) return;
   }
   // 5. the next frontier's lists; clear the processed frontier's bitmap
   lists_bits_body(ia.a.fbits_next, ia.words, ia.a.g.nv, ia.a.g.deg, ia.a.next_lists, ia.a.seg, ctrl,
@@ -2149,6 +2155,9 @@ int issue_persistent(Handle* h, const DecideArgs& a_base, int cur, const GiantDe
   ia.lists_cur = h->lists[cur];
   ia.fbits_cur = h->fbits[cur];
   ia.words = h->words;
+  const bool test_timeout = (h->opt.flags & DFL_FLAG_TEST_UNREACHABLE_BARRIER) != 0;
+  ia.bar_extra = test_timeout ? 1u : 0u;
+  ia.bar_polls = test_timeout ? kTestBarrierPolls : kBarrierPolls;
   void* args[] = {&ia};
   {
     LaunchScope ls(h, DFL_PROF_MOVE);
@@ -2265,7 +2274,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       h->gtable = nullptr;
       h->gtable_cap = 0;
     }
-    DFL_CUDA(h, cudaMalloc(&h->gtable, sizeof(uint2) * uint64_t(kBlockGridMax) * gslots));
+    DFL_CUDA(h, dev_malloc(&h->gtable, sizeof(uint2) * uint64_t(kBlockGridMax) * gslots));
     h->gtable_cap = uint64_t(kBlockGridMax) * gslots;
   }
   // once per process (handles may be driven from several host threads)
@@ -2304,7 +2313,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       *p = nullptr;
       cap = 0;
       const uint64_t want = need + need / 4;
-      DFL_CUDA(h, cudaMalloc(p, elem * want));
+      DFL_CUDA(h, dev_malloc(p, elem * want));
       if (fill >= 0) DFL_CUDA(h, cudaMemsetAsync(*p, fill, elem * want, h->stream));
       cap = want;
       return DFL_OK;
@@ -2344,7 +2353,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       cudaFree(h->bigmv);
       h->bigmv = nullptr;
       h->bigmv_cap = 0;
-      DFL_CUDA(h, cudaMalloc(&h->bigmv, sizeof(uint32_t) * (need + need / 2)));
+      DFL_CUDA(h, dev_malloc(&h->bigmv, sizeof(uint32_t) * (need + need / 2)));
       h->bigmv_cap = need + need / 2;
     }
   }

@@ -356,7 +356,7 @@ int ensure_tmp(Handle* h, uint64_t bytes) {
   h->tmp = nullptr;
   h->tmp_cap = 0;
   uint64_t want = bytes + bytes / 4 + 4096;
-  DFL_CUDA(h, cudaMalloc(&h->tmp, want));
+  DFL_CUDA(h, dev_malloc(&h->tmp, want));
   h->tmp_cap = want;
   return DFL_OK;
 }
