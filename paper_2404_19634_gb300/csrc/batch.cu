@@ -598,13 +598,12 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
   return x;
 }
 
-__global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
+__device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
                               KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
-                              uint32_t* __restrict__ w, Ctrl* ctrl) {
+                              uint32_t* __restrict__ w, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   // warp-uniform loop: the claims of new table slots are made per warp
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t q0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); q0 < ne; q0 += stride) {
+  for (uint64_t q0 = base + (threadIdx.x & ~31u); q0 < ne; q0 += stride) {
     const uint64_t q = q0 + lane;
     bool valid = q < ne;
     dfl_edge x = valid ? e[q] : dfl_edge{0, 0, 0};
@@ -653,16 +652,21 @@ __global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint6
   }
 }
 
+__global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
+                              KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
+                              uint32_t* __restrict__ w, Ctrl* ctrl) {
+  hash_insert_body(e, nd, ne, n, f, t, key, w, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 // Thread per pair: validate against the row, weights after the batch, and
 // per-row bookkeeping (append ranks, live and tombstone changes).
-__global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* __restrict__ off,
+__device__ __forceinline__ void hash_pairs_body(HashApply t, uint32_t n, const unsigned long long* __restrict__ off,
                              const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
-                             const uint2* __restrict__ arcs, Ctrl* ctrl) {
+                             const uint2* __restrict__ arcs, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t np = ctrl->npairs;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   // warp-uniform loop: 2m and arc-count changes are summed, new rows claimed, per warp
-  for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
+  for (uint64_t p0 = base + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
     const uint64_t p = p0 + lane;
     long long dm2 = 0, darcs = 0;
     bool new_row = false;
@@ -716,12 +720,17 @@ __global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* 
   }
 }
 
+__global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* __restrict__ off,
+                             const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
+                             const uint2* __restrict__ arcs, Ctrl* ctrl) {
+  hash_pairs_body(t, n, off, deg, srt, arcs, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 // Thread per touched row: keep (append in place) or rebuild.
-__global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
-                            const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
+__device__ __forceinline__ void hash_rows_body(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
+                            const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t nr = ctrl->rows;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t q0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); q0 < nr; q0 += stride) {
+  for (uint64_t q0 = base + (threadIdx.x & ~31u); q0 < nr; q0 += stride) {
     const uint64_t q = q0 + (threadIdx.x & 31u);
     uint32_t dmax = 0;
     if (q < nr) {
@@ -747,13 +756,18 @@ __global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const
   }
 }
 
+__global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
+                            const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
+  hash_rows_body(t, deg, cap, srt, ntomb, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 // Thread per pair: in-place weight changes; new arcs to the row's tail, or to
 // the rebuilt row's region of `extra`.
-__global__ void k_hash_write(HashApply t, const unsigned long long* __restrict__ off,
-                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl) {
+__device__ __forceinline__ void hash_write_body(HashApply t, const unsigned long long* __restrict__ off,
+                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t np = ctrl->npairs;
-  for (uint64_t p = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < np;
-       p += uint64_t(gridDim.x) * blockDim.x) {
+  for (uint64_t p = base + threadIdx.x; p < np;
+       p += stride) {
     const uint32_t s = t.pairs[p];
     const uint32_t fl = t.flag[s];
     const unsigned long long k = t.keys[s];
@@ -767,16 +781,20 @@ __global__ void k_hash_write(HashApply t, const unsigned long long* __restrict__
   }
 }
 
+__global__ void k_hash_write(HashApply t, const unsigned long long* __restrict__ off,
+                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl) {
+  hash_write_body(t, off, deg, arcs, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 constexpr int kHRebuildThreads = 256;
 
 // Block per rebuilt row: merge of the live sorted prefix (compacted into
 // scratch), the live tail and the row's new arcs (both sorted in shared
 // memory) into a new slot of 1.5x the live degree.
-__global__ void __launch_bounds__(kHRebuildThreads)
-k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __restrict__ deg,
+__device__ __forceinline__ void hash_rebuild_body(HashApply t, unsigned long long* __restrict__ off, uint32_t* __restrict__ deg,
                uint32_t* __restrict__ cap, uint32_t* __restrict__ srt, uint32_t* __restrict__ ntomb,
                uint2* __restrict__ arcs, uint2* __restrict__ scratch, unsigned long long pool_base,
-               unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
+               unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl, uint32_t r0, uint32_t rstep) {
   __shared__ uint2 tail[kTailMax];
   __shared__ uint2 stail[kTailMax];
   __shared__ uint2 sn[kExtraMax];
@@ -784,7 +802,7 @@ k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __re
   __shared__ uint32_t s_nt, s_warp[kHRebuildThreads / 32], s_total;
   const uint32_t nr = ctrl->rows;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  for (uint32_t r = blockIdx.x; r < nr; r += gridDim.x) {
+  for (uint32_t r = r0; r < nr; r += rstep) {
     const uint32_t u = t.rows[r];
     if (t.r_state[u] != 2u) continue;
     const uint2* old = arcs + off[u];
@@ -884,12 +902,20 @@ k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __re
   }
 }
 
+__global__ void __launch_bounds__(kHRebuildThreads)
+k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __restrict__ deg,
+               uint32_t* __restrict__ cap, uint32_t* __restrict__ srt, uint32_t* __restrict__ ntomb,
+               uint2* __restrict__ arcs, uint2* __restrict__ scratch, unsigned long long pool_base,
+               unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
+  hash_rebuild_body(t, off, deg, cap, srt, ntomb, arcs, scratch, pool_base, pool_cap, scratch_cap, ctrl, blockIdx.x, gridDim.x);
+}
+
 // Thread per touched row: metadata of kept rows, then reset the scratch.
-__global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb,
-                              Ctrl* ctrl) {
+__device__ __forceinline__ void hash_finish_body(HashApply t, uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb,
+                              Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t nr = ctrl->rows;
-  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
-       q += uint64_t(gridDim.x) * blockDim.x) {
+  for (uint64_t q = base + threadIdx.x; q < nr;
+       q += stride) {
     const uint32_t u = t.rows[q];
     if (t.r_state[u] != 2u) {
       deg[u] += t.r_app[u];
@@ -903,15 +929,19 @@ __global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t*
   }
 }
 
+__global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb,
+                              Ctrl* ctrl) {
+  hash_finish_body(t, deg, ntomb, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 // Alg. 7 per pair: K[u] and Sigma[C^{t-1}[u]] change by the net weight.
-__global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
-                               long long* __restrict__ Sigma, Ctrl* ctrl) {
+__device__ __forceinline__ void hash_weights_body(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
+                               long long* __restrict__ Sigma, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t np = ctrl->npairs;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   // warp-uniform loop: changes to one community's Sigma are summed in the
   // warp first (a large community takes one update per warp, not per arc)
-  for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
+  for (uint64_t p0 = base + (threadIdx.x & ~31u); p0 < np; p0 += stride) {
     const uint64_t p = p0 + lane;
     long long dl = 0;
     uint32_t c = kEmpty;
@@ -938,11 +968,16 @@ __global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long
   }
 }
 
+__global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
+                               long long* __restrict__ Sigma, Ctrl* ctrl) {
+  hash_weights_body(t, C, K, Sigma, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
 // Reset the per-vertex scratch of the touched rows after a failed validation.
-__global__ void k_hash_reset(HashApply t, Ctrl* ctrl) {
+__device__ __forceinline__ void hash_reset_body(HashApply t, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   const uint32_t nr = ctrl->rows;
-  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < nr;
-       q += uint64_t(gridDim.x) * blockDim.x) {
+  for (uint64_t q = base + threadIdx.x; q < nr;
+       q += stride) {
     const uint32_t u = t.rows[q];
     t.r_app[u] = 0;
     t.r_tomb[u] = 0;
@@ -950,6 +985,77 @@ __global__ void k_hash_reset(HashApply t, Ctrl* ctrl) {
     t.r_state[u] = 0;
     t.r_reg[u] = 0;
   }
+}
+
+__global__ void k_hash_reset(HashApply t, Ctrl* ctrl) {
+  hash_reset_body(t, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+}
+
+// Small batches (at most kSmallApplyEdges edges, one arc per thread) in one
+// block: the phases of the hashed apply above -- table insert, pair
+// validation, row decisions, then, if the batch is valid and fits, in-place
+// writes, K and Sigma, the pending list and the row metadata -- separated by
+// block barriers, so that a batch of a few edges costs one launch instead of
+// six kernels, three table clears and a host round trip between validation
+// and writes.  The table is the first `t.mask + 1` slots of the pair table,
+// cleared here.  Nothing is written if the batch is invalid, would make 2m
+// reach 2^32 (single graphs), rebuilds a row with more new arcs than a block
+// sorts, or needs more arc-pool or merge-scratch room than there is: the
+// per-row scratch counters are cleared, ctrl->apply_go stays 0 and the host
+// reports the error or redoes the batch on the multi-kernel path.  Rows to
+// rebuild (rare for small batches) are left to the multi-block rebuild, one
+// block per row, and the row metadata kernel after it, which the host
+// launches when ctrl->apply_defer is set.
+constexpr uint64_t kSmallApplyEdges = 512;
+constexpr int kSmallApplyThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallApplyThreads)
+k_apply_small(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n, KeyFmt f, HashApply t,
+              unsigned long long* __restrict__ key, uint32_t* __restrict__ w, const unsigned long long* __restrict__ off,
+              uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap, const uint32_t* __restrict__ srt,
+              uint32_t* __restrict__ ntomb, uint2* __restrict__ arcs, unsigned long long pool_top,
+              unsigned long long pool_cap, unsigned long long scratch_cap, const uint32_t* __restrict__ C,
+              long long* __restrict__ K, long long* __restrict__ Sigma, unsigned long long* __restrict__ pend_key,
+              uint32_t* __restrict__ pend_w, long long m2, int check_m2, Ctrl* ctrl) {
+  __shared__ int s_go;
+  const uint64_t nt = blockDim.x;
+  for (uint64_t s = threadIdx.x; s <= t.mask; s += nt) {
+    t.keys[s] = kNoKey;
+    t.ndel[s] = 0;
+    t.wins[s] = 0;
+  }
+  __syncthreads();
+  hash_insert_body(e, nd, ne, n, f, t, key, w, ctrl, 0, nt);
+  __syncthreads();
+  hash_pairs_body(t, n, off, deg, srt, arcs, ctrl, 0, nt);
+  __syncthreads();
+  hash_rows_body(t, deg, cap, srt, ntomb, ctrl, 0, nt);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const Ctrl& c = *ctrl;
+    bool go = c.err == 0;
+    if (check_m2 && m2 + c.m2_delta >= (1ll << 32)) go = false;
+    if (c.max_app > kExtraMax) go = false;
+    if (pool_top + c.reloc_need > pool_cap || c.scratch_need > scratch_cap) go = false;
+    const bool defer = c.rebuild_rows != 0;
+    s_go = go ? (defer ? 2 : 1) : 0;
+    ctrl->apply_go = go ? 1u : 0u;
+    ctrl->apply_defer = go && defer ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_go) {
+    hash_reset_body(t, ctrl, 0, nt);
+    return;
+  }
+  hash_write_body(t, off, deg, arcs, ctrl, 0, nt);
+  hash_weights_body(t, C, K, Sigma, ctrl, 0, nt);
+  for (uint64_t q = threadIdx.x; q < 2 * ne; q += nt) {
+    pend_key[q] = key[q];
+    pend_w[q] = w[q];
+  }
+  if (s_go == 2) return;  // rows to rebuild: the host launches the rebuild and the metadata kernel
+  __syncthreads();        // every write has read deg before the metadata changes it
+  hash_finish_body(t, deg, ntomb, ctrl, 0, nt);
 }
 
 int read_ctrl(Handle* h) {
@@ -1111,9 +1217,61 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
   if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, kind, h->stream));
   if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, kind, h->stream));
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  if (ne <= kSmallApplyEdges) {
+    // one block does everything (see k_apply_small); the pending list grows first
+    if (h->pend_count + na > h->pend_cap) {
+      uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
+      DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
+      DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
+      h->pend_cap = c2 < c3 ? c2 : c3;
+    }
+    HashApply ts = hash_args(h);
+    uint64_t sc = 64;
+    while (sc < 2 * na) sc <<= 1;
+    ts.mask = (sc < h->h_cap ? sc : h->h_cap) - 1;
+    {
+      LaunchScope ls(h, DFL_PROF_APPLY);
+      k_apply_small<<<1, kSmallApplyThreads, 0, h->stream>>>(
+          h->b_edges, nd, ne, h->n, key_fmt(h), ts, h->b_key, h->b_w, h->off, h->deg, h->cap, h->srt,
+          h->ntomb, h->arcs, h->pool_top, h->pool_cap, h->scratch_cap, h->C, h->K, h->Sigma,
+          h->pend_key + h->pend_count, h->pend_w + h->pend_count, h->m2, h->ngraphs ? 0 : 1, h->ctrl);
+      DFL_TRY(check_launch(h, "small batch apply"));
+    }
+    DFL_TRY(read_ctrl(h));
+    const Ctrl c = *h->hctrl;
+    if (c.apply_go && c.apply_defer) {
+      {
+        LaunchScope ls(h, DFL_PROF_APPLY);
+        k_hash_rebuild<<<grid_for(c.rows, 1, 152 * 8), kHRebuildThreads, 0, h->stream>>>(
+            ts, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->scratch, h->pool_top, h->pool_cap,
+            h->scratch_cap, h->ctrl);
+        DFL_TRY(check_launch(h, "hash rebuild"));
+      }
+      {
+        LaunchScope ls(h, DFL_PROF_APPLY);
+        k_hash_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(ts, h->deg, h->ntomb, h->ctrl);
+        DFL_TRY(check_launch(h, "hash finish"));
+      }
+    }
+    if (c.apply_go) {
+      h->pend_count += na;
+      h->m2 += c.m2_delta;
+      h->pool_top += c.reloc_need;
+      h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
+      if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
+      return DFL_OK;
+    }
+    // nothing was written and the row counters are clear again
+    if (c.err & kErrInvalid) return set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
+    if (c.err & kErrNotFound) return set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
+    if (c.err & kErrOverflow) return set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
+    if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
+    if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
+      return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+    // a large row rebuild or more arc-pool room: the multi-kernel path below
+    DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  }
   const uint64_t cap = h->h_cap;
-  const uint64_t used = cap < 4 * na ? cap : 4 * na;  // probes stay near the hashed slots
-  (void)used;
   DFL_CUDA(h, cudaMemsetAsync(h->h_keys, 0xFF, sizeof(unsigned long long) * cap, h->stream));
   DFL_CUDA(h, cudaMemsetAsync(h->h_ndel, 0, sizeof(uint32_t) * cap, h->stream));
   DFL_CUDA(h, cudaMemsetAsync(h->h_wins, 0, sizeof(unsigned long long) * cap, h->stream));

@@ -91,7 +91,9 @@ struct Ctrl {
   unsigned long long red_b;
   unsigned long long red_c;
   unsigned int red_u;
-  unsigned int pad;
+  unsigned int apply_go;             // the single-block batch apply wrote the batch (1) or nothing (0)
+  unsigned int apply_defer;          // ... and left its row rebuilds to the multi-block kernels
+  unsigned int pad3;
 };
 
 // A CSR whose rows are addressed by (offset, degree): the slack CSR of G^t
