@@ -997,9 +997,14 @@ __device__ __forceinline__ void block_vertex(const DecideArgs& a, uint32_t i, lo
 // vertex.  Headers are loaded by warp 0 for up to 32 of the block's vertices
 // at once.  The shared table (kBlockSlots keys + values) is empty at rest: a
 // vertex uses the first power of two >= 2 x degree slots, and the scan that
-// scores the occupied slots also clears them.  Vertices of degree above
-// kBinBlock, or whose scores need 128 bits, take block_vertex (which may
-// fall back to a global table) and the table is emptied after it.
+// scores the occupied slots also clears them.  Two block barriers per
+// vertex: after the inserts, and after the per-warp bests; warp 0 then
+// decides while the other warps start the next vertex (the per-vertex
+// scratch is double-buffered), the batch's movers are recorded together at
+// its end, and their neighbours are marked by the commit kernel (the mover
+// list it spreads over all blocks).  Vertices of degree above kBinBlock, or
+// whose scores need 128 bits, take block_vertex (which may fall back to a
+// global table) and the table is emptied after it.
 template <int kThreads>
 __device__ __noinline__ void block_vertex_slow(const DecideArgs& a, const VHdr& v, uint32_t* dyn, BlockScratch& sc,
                                                MoveSums& sums) {
@@ -1011,15 +1016,23 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
   extern __shared__ uint32_t dyn[];
   uint32_t* keys = dyn;
   uint32_t* vals = dyn + kBlockSlots;
-  __shared__ BlockScratch sc;
+  __shared__ BlockScratch sc;  // the 128-bit path's
   __shared__ VHdr s_hdr[32];
-  __shared__ unsigned long long s_best[kMaxBlockWarps];
-  __shared__ uint32_t s_bc[kMaxBlockWarps];
+  __shared__ unsigned long long s_best[2][kMaxBlockWarps];
+  __shared__ uint32_t s_bc[2][kMaxBlockWarps];
+  __shared__ uint32_t s_hd[2], s_nc[2];
+  __shared__ unsigned long long s_gain[32];
+  __shared__ uint32_t s_mvc[32];
+  __shared__ int s_mv[32];
   constexpr uint32_t nthr = kThreads;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   for (uint32_t s = threadIdx.x; s < kBlockSlots; s += nthr) {
     keys[s] = kEmpty;
     vals[s] = 0;
+  }
+  if (threadIdx.x < 2) {
+    s_hd[threadIdx.x] = 0;
+    s_nc[threadIdx.x] = 0;
   }
   const long long m2_one = *a.m2p;
   const uint32_t cnt = *a.count;
@@ -1032,12 +1045,17 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
       VHdr h;
       load_header(a, t, t < cnt, m2_one, sums, h);
       s_hdr[lane] = h;
+      s_mv[lane] = 0;
     }
     __syncthreads();
-    for (uint32_t k = 0; k < 32 && t0 + k * G < cnt; ++k) {
+    const uint64_t left = (uint64_t(cnt) - t0 + G - 1) / G;
+    const uint32_t nv = uint32_t(left < 32 ? left : 32);
+    uint32_t p = 0;  // scratch buffer of the current vertex
+    for (uint32_t k = 0; k < nv; ++k) {
       const VHdr v = s_hdr[k];
       if (!v.act) continue;  // block-uniform
       if (v.dg > kBinBlock || !fits64(v.m2, v.Ki)) {
+        __syncthreads();  // warp 0 has finished the decisions before (it uses sc)
         block_vertex_slow<kThreads>(a, v, dyn, sc, sums);
         for (uint32_t s = threadIdx.x; s < kBlockSlots; s += nthr) {
           keys[s] = kEmpty;
@@ -1049,10 +1067,6 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
       uint32_t slots = 64;
       while (slots < 2 * v.dg) slots <<= 1;
       const uint32_t mask = slots - 1;
-      if (threadIdx.x == 0) {
-        sc.hd = 0;
-        sc.ncand = 0;
-      }
       // every arc's weight under its neighbour's community (a table of
       // >= 2 x degree slots cannot overflow)
       const bool ok = scan_row<8>(a, v.i, v.o, v.dg, wib * 32, nthr, keys, vals, mask, slots);
@@ -1079,7 +1093,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
           keys[sl] = kEmpty;
           vals[sl] = 0;
           if (c[u] == v.d) {
-            sc.hd = w[u];  // exactly one slot holds d
+            s_hd[p] = w[u];  // exactly one slot holds d
             continue;
           }
           ++nc;
@@ -1092,41 +1106,45 @@ __global__ void __launch_bounds__(kThreads) k_decide_block(DecideArgs a) {
         }
       }
       nc = __reduce_add_sync(0xFFFFFFFFu, nc);
-      if (lane == 0 && nc) atomicAdd(&sc.ncand, nc);
+      if (lane == 0 && nc) atomicAdd(&s_nc[p], nc);
       warp_best64(have, best, bc);
       if (lane == 0) {
-        s_best[wib] = have ? best : 0ull;
-        s_bc[wib] = bc;
+        s_best[p][wib] = have ? best : 0ull;
+        s_bc[p][wib] = bc;
       }
       __syncthreads();
-      if (wib == 0) {
-        have = lane < nthr / 32 && s_bc[lane] != kEmpty;
-        best = have ? s_best[lane] : 0ull;
-        bc = have ? s_bc[lane] : kEmpty;
+      if (wib == 0) {  // the other warps go on to the next vertex
+        have = lane < nthr / 32 && s_bc[p][lane] != kEmpty;
+        best = have ? s_best[p][lane] : 0ull;
+        bc = have ? s_bc[p][lane] : kEmpty;
         warp_best64(have, best, bc);
         if (lane == 0) {
           i128 gain = 0;
-          const bool mv = decide64(a, v, have, best, bc, uint32_t(sc.hd), &gain);
-          sums.bytes += 24 + 12ull * v.dg + 12ull * sc.ncand;
-          sc.last = mv;
-          if (mv) {
-            record_move(a, v.i, bc, v.d, gain, v.gi, sums);
-            sums.bytes += 16 + 4ull * v.dg;
-            if (v.dg > kMarkInline) a.bigmv[atomicAdd(a.nbig, 1u)] = v.i;
-          }
+          const bool mv = decide64(a, v, have, best, bc, s_hd[p], &gain);
+          sums.bytes += 24 + 12ull * v.dg + 12ull * s_nc[p] + (mv ? 16 + 4ull * v.dg : 0ull);
+          s_mv[k] = mv;
+          s_mvc[k] = bc;
+          s_gain[k] = (unsigned long long)gain;  // a gain is positive and below 2^64
+          s_hd[p] = 0;  // ready for the vertex after next
+          s_nc[p] = 0;
         }
       }
-      __syncthreads();
-      if (sc.last && v.dg <= kMarkInline) {
-        for (uint32_t k0 = wib * 32; k0 < v.dg; k0 += nthr) {
-          const uint32_t kk = k0 + lane;
-          const uint2 arc = kk < v.dg ? a.g.arcs[v.o + kk] : make_uint2(v.i, 0u);
-          mark_next(a, arc.x, kk < v.dg && arc.x != v.i && arc.y != 0);
-        }
-      }
-      __syncthreads();  // sc and the table are reused by the next vertex
+      p ^= 1;
     }
-    __syncthreads();  // s_hdr is rewritten by the next round
+    __syncthreads();  // every decision of the batch is made
+    if (wib == 0) {  // the batch's movers: one slot reservation, then the mover list for marking
+      const bool mv = lane < nv && s_mv[lane];
+      const VHdr& v = s_hdr[lane];
+      record_moves_warp(a, mv, v.i, s_mvc[lane], v.d, (i128)s_gain[lane], v.gi, sums);
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, mv);
+      if (m) {
+        uint32_t base = 0;
+        if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(a.nbig, uint32_t(__popc(m)));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+        if (mv) a.bigmv[base + __popc(m & ((1u << lane) - 1u))] = v.i;  // neighbours marked by k_commit
+      }
+    }
+    __syncthreads();  // s_hdr and s_mv are rewritten by the next round
   }
   flush_sums_all(a, sums);
 }
@@ -2344,10 +2362,13 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
     }
     DFL_TRY(regrow(&h->g_tlist, h->g_lst_cap, lst, sizeof(uint32_t), -1));
   }
-  {  // list of high-degree movers: at most one per vertex of degree > kMarkInline
+  {  // movers whose neighbours k_commit marks: at most one per vertex of degree
+     // > kMarkInline, or of the block-per-vertex bin (degree > bin_warp_hash)
     uint64_t arcs = h->pool_top;
     for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
-    const uint64_t need = arcs / (kMarkInline + 1) + 64;
+    const uint64_t lo = h->tune.bin_warp_hash < kMarkInline ? h->tune.bin_warp_hash : kMarkInline;
+    uint64_t need = arcs / (lo + 1) + 64;
+    if (need > uint64_t(h->n) + 64) need = uint64_t(h->n) + 64;
     if (need > h->bigmv_cap) {
       cudaStreamSynchronize(h->stream);
       cudaFree(h->bigmv);
