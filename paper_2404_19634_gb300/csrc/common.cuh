@@ -255,7 +255,7 @@ struct Handle {
   uint32_t* g_tkeys = nullptr;
   uint32_t* g_tvals = nullptr;
   uint64_t g_tab_cap = 0;
-  uint32_t* g_tlist = nullptr;
+  uint2* g_tlist = nullptr;
   uint64_t g_lst_cap = 0;
 
   // auxiliary streams for the concurrent degree bins of a sub-step

@@ -48,6 +48,8 @@ struct DecideArgs {
   uint32_t* bigmv;        // movers of degree > kMarkInline (neighbours marked by k_commit)
   unsigned int* movers;   // movers of the sub-step (slot counter into mv_i/mv_c/mv_d)
   unsigned int* nbig;     // ... of them in bigmv
+  unsigned int* clear_movers;  // the next sub-step's two counters, zeroed by this sub-step's
+  unsigned int* clear_nbig;    // commit (null: nothing to zero)
   // group of graphs (ngraphs > 0): the vertex's graph gives its 2m, whether
   // it is still processed, and where its movers' dQ sum goes
   uint32_t ngraphs;
@@ -1189,7 +1191,7 @@ struct GiantDecide {
   GiantRes* res;              // per part
   uint32_t* tkeys;            // tables (kEmpty at rest)
   uint32_t* tvals;            // (0 at rest)
-  uint32_t* tlist;            // occupied-slot lists
+  uint2* tlist;               // occupied-slot lists: (slot, community) per entry
   unsigned int* nitems;       // chunk total
   unsigned int* nbignd;       // vertices left to the part blocks (counted)
 };
@@ -1308,44 +1310,42 @@ __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide
 // best candidate of this thread (and the weight to d, in hd[t]); returns the
 // number of candidates this thread saw.  Four entries' loads are in flight
 // at a time (slot, then key and weight, then Sigma).
+template <int U>
 __device__ __forceinline__ uint32_t giant_scan_entries(const DecideArgs& a, const GiantDecide& gd, uint32_t t,
                                                        uint32_t e0, uint32_t e1, uint32_t d, long long m2,
                                                        long long Ki, bool& have, i128& best, uint32_t& bc) {
-  constexpr int U = 4;
   uint32_t* gk = gd.tkeys + gd.toff[t];
   uint32_t* gv = gd.tvals + gd.toff[t];
-  const uint32_t* gl = gd.tlist + gd.loff[t];
+  const uint2* gl = gd.tlist + gd.loff[t];
   uint32_t ncand = 0;
   for (uint32_t b = e0 + threadIdx.x; b < e1; b += blockDim.x * U) {
-    uint32_t slot[U], c[U], h[U];
-    long long sg[U];
+    uint2 en[U];  // (slot, community): the weight and Sigma loads go out together
+    uint32_t h[U], sg[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t e = b + u * blockDim.x;
-      slot[u] = e < e1 ? __ldcg(gl + e) : kEmpty;  // written by other blocks of this kernel
+      en[u] = e < e1 ? __ldcg(gl + e) : make_uint2(kEmpty, kEmpty);  // written by other blocks of this kernel
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      c[u] = slot[u] != kEmpty ? __ldcg(gk + slot[u]) : kEmpty;
-      h[u] = slot[u] != kEmpty ? __ldcg(gv + slot[u]) : 0u;
+      h[u] = en[u].x != kEmpty ? __ldcg(gv + en[u].x) : 0u;
+      sg[u] = (en[u].x != kEmpty && en[u].y != d) ? sigma32(a.Sigma, en[u].y) : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) sg[u] = (c[u] != kEmpty && c[u] != d) ? a.Sigma[c[u]] : 0;
-#pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (slot[u] == kEmpty) continue;
-      gk[slot[u]] = kEmpty;
-      gv[slot[u]] = 0;
-      if (c[u] == d) {
+      if (en[u].x == kEmpty) continue;
+      gk[en[u].x] = kEmpty;
+      gv[en[u].x] = 0;
+      if (en[u].y == d) {
         gd.hd[t] = h[u];  // exactly one entry of the table holds d
         continue;
       }
       ++ncand;
       const i128 sc = gain_num(m2, h[u], Ki, sg[u]);
-      if (!have || sc > best || (sc == best && c[u] < bc)) {
+      if (!have || sc > best || (sc == best && en[u].y < bc)) {
         have = true;
         best = sc;
-        bc = c[u];
+        bc = en[u].y;
       }
     }
   }
@@ -1405,7 +1405,7 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
   const uint32_t tmask = uint32_t(giant_table_slots(dg) - 1);
   uint32_t* gk = gd.tkeys + gd.toff[t];
   uint32_t* gv = gd.tvals + gd.toff[t];
-  uint32_t* gl = gd.tlist + gd.loff[t];
+  uint2* gl = gd.tlist + gd.loff[t];
   constexpr int U = 4;
   for (uint32_t b0 = wib * 32 * U; b0 < ne; b0 += nthr * U) {  // warp-uniform
     uint32_t c[U], slot[U], prev[U];
@@ -1417,6 +1417,7 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) prev[u] = c[u] != kEmpty ? atomicCAS(&gk[slot[u]], kEmpty, c[u]) : kEmpty;
+    unsigned cm[U];  // lanes that created a slot, per group
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t e = b0 + u * 32 + lane;
@@ -1434,12 +1435,21 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
           atomicAdd(&gv[slot[u]], ev[e]);
         }
       }
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, created);
-      if (m) {
-        uint32_t base = 0;
-        if (lane == uint32_t(__ffs(m) - 1)) base = atomicAdd(&gd.ndist[t], uint32_t(__popc(m)));
-        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
-        if (created) gl[base + __popc(m & ((1u << lane) - 1u))] = slot[u];
+      cm[u] = __ballot_sync(0xFFFFFFFFu, created);
+    }
+    // the new keys' slots onto the vertex's occupied list: one reservation for
+    // all groups of the warp
+    uint32_t total = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) total += __popc(cm[u]);
+    if (total) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&gd.ndist[t], total);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((cm[u] >> lane) & 1u) gl[base + __popc(cm[u] & ((1u << lane) - 1u))] = make_uint2(slot[u], c[u]);
+        base += __popc(cm[u]);
       }
     }
   }
@@ -1466,7 +1476,7 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
       bool have = false;
       i128 best = 0;
       uint32_t bc = 0;
-      uint32_t ncand = giant_scan_entries(a, gd, t, 0, nd, d, m2, Ki, have, best, bc);
+      uint32_t ncand = giant_scan_entries<4>(a, gd, t, 0, nd, d, m2, Ki, have, best, bc);
       for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
       __threadfence();
       __syncthreads();
@@ -1576,7 +1586,7 @@ __device__ __forceinline__ void giant_parts(const DecideArgs& a, const GiantDeci
       bool have = false;
       i128 best = 0;
       uint32_t bc = 0;
-      uint32_t ncand = giant_scan_entries(a, gd, t, part * kGiantPart, min(nd, (part + 1) * kGiantPart), d, m2,
+      uint32_t ncand = giant_scan_entries<4>(a, gd, t, part * kGiantPart, min(nd, (part + 1) * kGiantPart), d, m2,
                                           Ki, have, best, bc);
       for (int x = 16; x; x >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, x);
       __syncthreads();  // s_ncand reset seen
@@ -1735,6 +1745,12 @@ __device__ __forceinline__ void commit_body(const DecideArgs& a, uint32_t m, uin
 }
 
 __global__ void __launch_bounds__(kCommitThreads) k_commit(DecideArgs a) {
+  // the next sub-step counts into the other pair of counters, last used two
+  // sub-steps ago: zeroed here, so no memset separates the sub-steps
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.clear_movers) {
+    *a.clear_movers = 0;
+    *a.clear_nbig = 0;
+  }
   commit_body(a, *a.movers, *a.nbig);
 }
 
@@ -2008,7 +2024,8 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   const int nxt = cur ^ 1;
   // reset the iteration's sums and the next buffer's list lengths
   DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));  // + big_movers
+  // both pairs of mover counters (it_movers, it_nbig): sub-step s counts into pair s & 1
+  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0, 4 * sizeof(unsigned int), h->stream));
   DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
   if (a.ngraphs)
     DFL_CUDA(h, cudaMemsetAsync(a.gS, 0, sizeof(unsigned long long) * 2 * a.ngraphs, h->stream));
@@ -2024,6 +2041,10 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     DFL_TRY(check_launch(h, "giant prefix"));
   }
   for (uint32_t s = 0; s < k; ++s) {
+    a.movers = &h->ctrl->it_movers[s & 1];
+    a.nbig = &h->ctrl->it_nbig[s & 1];
+    a.clear_movers = s + 1 < k ? &h->ctrl->it_movers[(s + 1) & 1] : nullptr;
+    a.clear_nbig = s + 1 < k ? &h->ctrl->it_nbig[(s + 1) & 1] : nullptr;
     // the degree bins of one class are independent: the larger ones run on
     // auxiliary streams, concurrently with the rest
     int nb = 0;
@@ -2101,14 +2122,14 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       if (pb) h->ev_free.push_back(pb);
     }
     if (any && decide_only) {
-      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0, 4 * sizeof(unsigned int), h->stream));
     } else if (any) {
-      {
-        LaunchScope ls(h, DFL_PROF_COMMIT);
-        k_commit<<<152 * 2, kCommitThreads, 0, h->stream>>>(a);
-        DFL_TRY(check_launch(h, "commit"));
-      }
-      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->movers, 0, 2 * sizeof(unsigned int), h->stream));
+      LaunchScope ls(h, DFL_PROF_COMMIT);
+      k_commit<<<152 * 2, kCommitThreads, 0, h->stream>>>(a);
+      DFL_TRY(check_launch(h, "commit"));
+    } else if (a.clear_movers) {  // no commit ran: zero the next sub-step's counters here
+      DFL_CUDA(h, cudaMemsetAsync(a.clear_movers, 0, sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(a.clear_nbig, 0, sizeof(unsigned int), h->stream));
     }
   }
   // the next frontier's lists, from its bitmap
@@ -2360,7 +2381,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       DFL_TRY(regrow(&h->g_tvals, c1, tab, sizeof(uint32_t), 0));
       h->g_tab_cap = c0;
     }
-    DFL_TRY(regrow(&h->g_tlist, h->g_lst_cap, lst, sizeof(uint32_t), -1));
+    DFL_TRY(regrow(&h->g_tlist, h->g_lst_cap, lst, sizeof(uint2), -1));
   }
   {  // movers whose neighbours k_commit marks: at most one per vertex of degree
      // > kMarkInline, or of the block-per-vertex bin (degree > bin_warp_hash)
