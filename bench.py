@@ -66,7 +66,8 @@ BATCH_FRAC = 1e-3
 # divided by their sub-steps: caches flushed before each launch (cold) and
 # kept (warm).  They belong to the kernel sources whose hash is recorded;
 # with other sources, or another workload, the line reports null.
-DECIDE_TRAFFIC = {"sources_sha256": None, "cold": None, "warm": None,
+DECIDE_TRAFFIC = {"sources_sha256": "1ff3383aad3990a7adf47b5ff5cc29083972b59c8cbe062a8c6d599a36357288",
+                  "cold": 53_578_880, "warm": 21_273_941,
                   "profile": "profiles/decide_traffic_rmat22_df.md"}
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
