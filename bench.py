@@ -4,8 +4,9 @@ Workload: R-MAT graph (a=0.57, b=0.19, c=0.19) with 2^22 vertices and
 33,554,432 undirected unit-weight edges (self-loops and duplicates removed,
 seeded vertex permutation), static Louvain once, then consecutive random
 batch updates of 1e-3 x |E| edges (80% insertions between uniform vertex
-pairs, 20% deletions of uniform existing edges), each one step =
-dfl_apply_batch + dfl_update(DF).  Inputs of every step are already on the
+pairs, 20% deletions of uniform existing edges), each one step = one
+dfl_step call (dfl_apply_batch + dfl_update(DF), the update queued behind
+the apply; the line's config also gives the same step as two calls).  Inputs of every step are already on the
 device when the timed region starts; between timed steps L2 is flushed.
 
 Prints one JSON line (see the keys below).  --impl reference times the CPU
@@ -498,10 +499,9 @@ def gpu_arm(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     torch.cuda.synchronize()
 
-    def step(k):
+    def step(k):  # dfl_step: the batch apply with the DF update queued behind it
         d, i = dbatches[k]
-        h.apply_batch(d, i)
-        h.update(dfl.DF)
+        h.step(d, i, dfl.DF)
 
     for k in range(args.warmup):
         step(k)
@@ -575,12 +575,27 @@ def gpu_arm(args):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                h.apply_batch(dd, di)
-                h.update(dfl.DF)
+                h.step(dd, di, dfl.DF)
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms.append(a.elapsed_time(b))
             extra[f"{frac:g}"] = round(statistics.median(ms), 4)
+        # the same step as two calls (dfl_apply_batch, then dfl_update): one
+        # host wait more
+        ms = []
+        for _ in range(5):
+            d, i = bstream.next(size)
+            dd, di = to_dev(d), to_dev(i)
+            torch.cuda.synchronize()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.apply_batch(dd, di)
+            h.update(dfl.DF)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        extra["two_calls_1e-3"] = round(statistics.median(ms), 4)
         d, i = bstream.next(size)
         dd, di = to_dev(d), to_dev(i)
         torch.cuda.synchronize()
@@ -604,8 +619,7 @@ def gpu_arm(args):
         nprof = 5
         for _ in range(nprof):
             d, i = bstream.next(size)
-            h.apply_batch(to_dev(d), to_dev(i))
-            h.update(dfl.DF)
+            h.step(to_dev(d), to_dev(i), dfl.DF)
         torch.cuda.synchronize()
         kernel_share = {k: round(v["ms"] / nprof, 4) for k, v in h.profile(reset=True).items()}
 
@@ -621,8 +635,7 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            h.apply_batch(pin_d[k], pin_i[k])
-            h.update(dfl.DF)
+            h.step(pin_d[k], pin_i[k], dfl.DF)
             h.membership(out)
         torch.cuda.synchronize()
         e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
@@ -667,6 +680,7 @@ def gpu_arm(args):
             "config": {"workload": f"rmat{args.scale} |E|={g.m} DF batches of {size} (1e-3|E|)",
                        "graph": f"R-MAT a=.57 b=.19 c=.19, 2^{args.scale} vertices, {g.m:,} edges, unit weights",
                        "batch_edges": size, "l2": "flushed between timed steps (256 MB write)",
+                       "step_call": "dfl_step (the batch apply with the DF update queued behind it, one call)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "iteration_launch": LAUNCH_DESC[args.launch],
                        "substeps": substeps,

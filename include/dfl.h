@@ -223,6 +223,21 @@ int dfl_apply_batch(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const df
  * current membership and clears the pending list. */
 int dfl_update(dfl_handle* h, int mode);
 
+/* One step of a dynamic method (Section 4.2's f(G^{t-1}, Delta^{t-}, Delta^{t+},
+ * C^{t-1}, K^{t-1}, Sigma^{t-1})): dfl_apply_batch of (del, ins) followed by
+ * dfl_update(mode), with the same results, arguments and errors as those two
+ * calls.  With DFL_DF the update is queued on the stream behind the apply
+ * before the host has read the apply's validation; the update's first
+ * control read settles both, so the step makes one host wait fewer, and
+ * none between the apply's validation and its writes.  If the batch is
+ * invalid (DFL_ERR_INVALID, DFL_ERR_NOT_FOUND, DFL_ERR_OVERFLOW) nothing
+ * changes: graph, K, Sigma, 2m, membership and any earlier pending batches
+ * stay as they were (the queued update marks no vertex).  Other modes, and
+ * DFL_FLAG_RECOMPUTE_AUX, run the two calls one after the other.  Errors of
+ * the update part leave the handle as a failed dfl_update does. */
+int dfl_step(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const dfl_edge* ins, uint64_t n_ins,
+             int mem_kind, int mode);
+
 /* Membership C^t (n uint32 labels in [0, n)): the community of every
  * vertex that Alg. 1 (DF), Alg. 2 (ND) and Alg. 3 (DS) return, obtained by
  * Alg. 4's final dendrogram lookup (the last pass's labels, not renumbered);

@@ -130,6 +130,7 @@ _SIGS = {
     "dfl_static": (ct.c_int, [_P]),
     "dfl_apply_batch": (ct.c_int, [_P, _P, ct.c_uint64, _P, ct.c_uint64, ct.c_int]),
     "dfl_update": (ct.c_int, [_P, ct.c_int]),
+    "dfl_step": (ct.c_int, [_P, _P, ct.c_uint64, _P, ct.c_uint64, ct.c_int, ct.c_int]),
     "dfl_membership": (ct.c_int, [_P, _P, ct.c_int]),
     "dfl_modularity": (ct.c_int, [_P, ct.POINTER(ct.c_double), _P]),
     "dfl_weights": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_int64), ct.c_int]),
@@ -221,6 +222,19 @@ def _is_tensor(x) -> bool:
     return type(x).__module__.startswith("torch") and hasattr(x, "data_ptr")
 
 
+_TENSOR_INT_WIDTH = {}  # torch integer dtype -> bytes, filled on the first tensor
+
+
+def _tensor_int_width(dt) -> int:
+    if not _TENSOR_INT_WIDTH:
+        import torch
+        for name in ("bool", "int8", "uint8", "int16", "uint16", "int32", "uint32", "int64", "uint64"):
+            t = getattr(torch, name, None)
+            if t is not None:
+                _TENSOR_INT_WIDTH[t] = torch.empty(0, dtype=t).element_size()
+    return _TENSOR_INT_WIDTH.get(dt, 0)
+
+
 def _buf(x, dtype):
     """(pointer, mem_kind, keepalive) for a numpy array or a tensor (CUDA or
     host).  A tensor is passed as it is, so it must be contiguous and hold
@@ -230,10 +244,10 @@ def _buf(x, dtype):
         return None, MEM_HOST, None
     want = np.dtype(dtype)
     if _is_tensor(x):
+        if _tensor_int_width(x.dtype) != want.itemsize:
+            raise TypeError(f"a tensor of {x.dtype} where {want.itemsize}-byte integers ({want}) are expected")
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
-        if x.is_floating_point() or x.is_complex() or x.element_size() != want.itemsize:
-            raise TypeError(f"a tensor of {x.dtype} where {want.itemsize}-byte integers ({want}) are expected")
         return ct.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
     if isinstance(x, np.ndarray) and x.dtype.kind not in "iub":
         raise TypeError(f"an array of {x.dtype} where integers ({want}) are expected")
@@ -357,6 +371,19 @@ class Dfl:
 
     def update(self, mode: int):
         self._check(self._lib.dfl_update(self._h, mode))
+
+    def step(self, dels, ins, mode: int | None = None, check: bool = True) -> int:
+        """apply_batch(dels, ins) then update(mode) in one call (dfl_step);
+        mode defaults to DF."""
+        d, mk1, k0 = _buf(dels, np.uint32)
+        i, mk2, k1 = _buf(ins, np.uint32)
+        nd = int(dels.shape[0]) if dels is not None else 0
+        ni = int(ins.shape[0]) if ins is not None else 0
+        mk = mk1 if nd else mk2
+        rc = self._lib.dfl_step(self._h, d, nd, i, ni, mk, DF if mode is None else mode)
+        if check:
+            self._check(rc)
+        return rc
 
     def membership(self, out=None):
         if out is None:

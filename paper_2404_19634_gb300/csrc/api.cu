@@ -286,11 +286,17 @@ int create_common(Handle* h, uint32_t n, const uint64_t* offsets, const uint32_t
   A(&h->mv_i, n);
   A(&h->mv_c, n);
   A(&h->mv_d, n);
-  A(&h->ctrl, 1);
-  if (!rc && cudaMallocHost(&h->hctrl, sizeof(Ctrl)) != cudaSuccess) {
+  A(&h->ctrl, 3);  // local-moving's, then the two of the batch apply
+  if (!rc) {
+    h->actrl = h->ctrl + 1;
+    if (cudaMemsetAsync(h->ctrl, 0, 3 * sizeof(Ctrl), h->stream) != cudaSuccess)
+      rc = set_error(h, DFL_ERR_CUDA, "control blocks");
+  }
+  if (!rc && cudaMallocHost(&h->hctrl, 3 * sizeof(Ctrl)) != cudaSuccess) {
     h->hctrl = nullptr;
     rc = set_error(h, DFL_ERR_NOMEM, "pinned control block");
   }
+  if (!rc) h->hactrl = h->hctrl + 1;
   // input graph on the device
   unsigned long long* doff = nullptr;
   uint32_t *didx = nullptr, *dw = nullptr;
@@ -458,6 +464,56 @@ int dfl_update(dfl_handle* h, int mode) {
   if (!rc) rc = louvain(h, all, use_range, initial);
   h->pend_count = 0;
   return louvain_result(h, rc);
+}
+
+int dfl_step(dfl_handle* h, const dfl_edge* del, uint64_t n_del, const dfl_edge* ins, uint64_t n_ins,
+             int mem_kind, int mode) {
+  using namespace dfl;
+  if (!h || (n_del && !del) || (n_ins && !ins)) return DFL_ERR_INVALID;
+  if (mem_kind != DFL_MEM_HOST && mem_kind != DFL_MEM_DEVICE) return DFL_ERR_INVALID;
+  if (h->ngraphs) return dfl::set_error(h, DFL_ERR_STATE, "a group handle takes the dfl_group_* calls");
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_step before dfl_static");
+  if (mode != DFL_ND && mode != DFL_DS && mode != DFL_DF)
+    return set_error(h, DFL_ERR_INVALID, "unknown mode");
+  // Only a DF update runs behind an apply that has not settled: it marks
+  // vertices from the batch alone (nothing, if the batch is not written),
+  // while ND and DS would process vertices whatever the batch, and the aux
+  // recomputation reads 2m on the host
+  if (mode != DFL_DF || (h->opt.flags & DFL_FLAG_RECOMPUTE_AUX) || n_del + n_ins == 0) {
+    const int rc = apply_batch(h, del, n_del, ins, n_ins, mem_kind);
+    if (rc) return rc;
+    return dfl_update(h, mode);
+  }
+  DFL_TRY(apply_batch_begin(h, del, n_del, ins, n_ins, mem_kind));
+  bool all = false, use_range = false;
+  uint64_t initial = 0;
+  int rc = mark(h, DFL_DF, &all, &use_range, &initial);
+  if (!rc) rc = louvain(h, all, use_range, initial);  // its first control read settles the apply
+  if (h->papply.active) {  // the update stopped before that read
+    int c = copy_apply_ctrl(h);
+    if (!c && cudaStreamSynchronize(h->stream) != cudaSuccess) c = set_error(h, DFL_ERR_CUDA, "batch apply");
+    if (c) {
+      h->papply.active = false;
+      return louvain_result(h, c);
+    }
+    settle_apply(h);
+  }
+  const int arc = h->papply.rc;
+  h->papply.rc = DFL_OK;
+  if (arc == DFL_OK) {
+    h->pend_count = 0;
+    return louvain_result(h, rc);
+  }
+  if (rc != DFL_OK && rc != arc) return louvain_result(h, rc);
+  // The batch was not written, so no vertex was marked and local-moving
+  // moved nothing: the handle is as it was before the call.
+  if (arc == kApplyRetryGrown || arc == kApplyRetrySorted) {
+    // buffers grew, or the sort-based path takes the batch: apply, then update
+    rc = apply_batch(h, del, n_del, ins, n_ins, mem_kind);
+    if (rc) return rc;
+    return dfl_update(h, DFL_DF);
+  }
+  return arc;  // the batch's error; earlier pending batches stay pending
 }
 
 int dfl_membership(const dfl_handle* hc, uint32_t* out, int mem_kind) {

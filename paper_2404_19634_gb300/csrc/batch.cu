@@ -412,10 +412,29 @@ __global__ void k_update_weights(const unsigned long long* __restrict__ key, uin
 
 // Alg. 1: a deletion inside a community or an insertion across communities
 // marks its source (both arcs are present, so both endpoints).
+// One launch clears what an update starts from: local-moving's control block,
+// the two frontier bitsets and (DF) the set of vertices processed in the
+// first pass -- instead of one memset each.
+__global__ void k_mark_clear(Ctrl* ctrl, uint32_t* __restrict__ f0, uint32_t* __restrict__ f1,
+                             uint32_t* __restrict__ ever, uint32_t words) {
+  pdl_wait();
+  const uint64_t base = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  unsigned int* z = reinterpret_cast<unsigned int*>(ctrl);
+  for (uint64_t q = base; q < sizeof(Ctrl) / sizeof(unsigned int); q += stride) z[q] = 0u;
+  for (uint64_t q = base; q < words; q += stride) {
+    f0[q] = 0u;
+    f1[q] = 0u;
+    if (ever) ever[q] = 0u;
+  }
+}
+
 __global__ void k_mark_df(const unsigned long long* __restrict__ key, uint64_t na, KeyFmt f,
                           const uint32_t* __restrict__ C, const uint32_t* __restrict__ deg,
                           uint32_t* __restrict__ fbits, uint32_t* lists, Segs seg, Ctrl* ctrl,
-                          uint32_t k) {
+                          uint32_t k, const unsigned int* go) {
+  pdl_wait();
+  if (go && *go == 0u) return;  // the batch enqueued before this update was not applied: mark nothing
   uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t p0 = blockIdx.x * uint64_t(blockDim.x); p0 < na; p0 += stride) {
     uint64_t p = p0 + threadIdx.x;
@@ -598,7 +617,9 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
   return x;
 }
 
-__device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
+// del: the nd deletions, ins: the ne - nd insertions
+__device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ del, const dfl_edge* __restrict__ ins,
+                              uint64_t nd, uint64_t ne, uint32_t n,
                               KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
                               uint32_t* __restrict__ w, Ctrl* ctrl, uint64_t base, uint64_t stride) {
   // warp-uniform loop: the claims of new table slots are made per warp
@@ -606,9 +627,9 @@ __device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e,
   for (uint64_t q0 = base + (threadIdx.x & ~31u); q0 < ne; q0 += stride) {
     const uint64_t q = q0 + lane;
     bool valid = q < ne;
-    dfl_edge x = valid ? e[q] : dfl_edge{0, 0, 0};
-    const bool ins = q >= nd;
-    if (valid && (x.u >= n || x.v >= n || x.u == x.v || (ins && x.w == 0))) {
+    const bool is_ins = q >= nd;
+    dfl_edge x = valid ? (is_ins ? ins[q - nd] : del[q]) : dfl_edge{0, 0, 0};
+    if (valid && (x.u >= n || x.v >= n || x.u == x.v || (is_ins && x.w == 0))) {
       atomicOr(&ctrl->err, kErrInvalid);
       key[2 * q] = key[2 * q + 1] = 0;
       w[2 * q] = w[2 * q + 1] = 0;
@@ -620,7 +641,7 @@ __device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e,
       if (valid) {
         const uint32_t a = dir ? x.v : x.u, b = dir ? x.u : x.v;
         key[2 * q + dir] = ((unsigned long long)a << (f.b + 1)) | ((unsigned long long)b << 1) |
-                           (ins ? 1ull : 0ull);
+                           (is_ins ? 1ull : 0ull);
         w[2 * q + dir] = x.w;
         const unsigned long long k = ((unsigned long long)a << 32) | b;
         uint64_t s = hash64(k) & t.mask;
@@ -635,7 +656,7 @@ __device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e,
             }
           }
           if (prev == k) {
-            if (ins) {
+            if (is_ins) {
               atomicAdd(&t.wins[s], (unsigned long long)x.w);
             } else {
               atomicAdd(&t.ndel[s], 1u);
@@ -652,10 +673,11 @@ __device__ __forceinline__ void hash_insert_body(const dfl_edge* __restrict__ e,
   }
 }
 
-__global__ void k_hash_insert(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n,
-                              KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
+__global__ void k_hash_insert(const dfl_edge* __restrict__ del, const dfl_edge* __restrict__ ins, uint64_t nd,
+                              uint64_t ne, uint32_t n, KeyFmt f, HashApply t, unsigned long long* __restrict__ key,
                               uint32_t* __restrict__ w, Ctrl* ctrl) {
-  hash_insert_body(e, nd, ne, n, f, t, key, w, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
+  pdl_wait();
+  hash_insert_body(del, ins, nd, ne, n, f, t, key, w, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
 // Thread per pair: validate against the row, weights after the batch, and
@@ -723,6 +745,7 @@ __device__ __forceinline__ void hash_pairs_body(HashApply t, uint32_t n, const u
 __global__ void k_hash_pairs(HashApply t, uint32_t n, const unsigned long long* __restrict__ off,
                              const uint32_t* __restrict__ deg, const uint32_t* __restrict__ srt,
                              const uint2* __restrict__ arcs, Ctrl* ctrl) {
+  pdl_wait();
   hash_pairs_body(t, n, off, deg, srt, arcs, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
@@ -758,6 +781,7 @@ __device__ __forceinline__ void hash_rows_body(HashApply t, const uint32_t* __re
 
 __global__ void k_hash_rows(HashApply t, const uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap,
                             const uint32_t* __restrict__ srt, const uint32_t* __restrict__ ntomb, Ctrl* ctrl) {
+  pdl_wait();
   hash_rows_body(t, deg, cap, srt, ntomb, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
@@ -781,8 +805,37 @@ __device__ __forceinline__ void hash_write_body(HashApply t, const unsigned long
   }
 }
 
+// Whether a validated batch is written: no error, 2m stays below 2^32 (single
+// graphs), every rebuilt row's new arcs fit a block's sort, and the arc pool
+// and the merge scratch have the room the rebuilt rows need.  Every input is
+// final once the row decisions are made, so every block that evaluates it
+// agrees.
+struct ApplyGate {
+  unsigned long long pool_top, pool_cap, scratch_cap;
+  long long m2;
+  int check_m2;
+};
+
+__device__ __forceinline__ bool gate_open(const Ctrl& c, const ApplyGate& g) {
+  if (c.err) return false;
+  if (g.check_m2 && g.m2 + c.m2_delta >= (1ll << 32)) return false;
+  if (c.max_app > kExtraMax) return false;
+  return g.pool_top + c.reloc_need <= g.pool_cap && c.scratch_need <= g.scratch_cap;
+}
+
+// The gate of the multi-kernel path: decided here (block 0 publishes it in
+// ctrl->apply_go / apply_defer for the kernels after this one and the host),
+// and nothing is written if it is closed.
 __global__ void k_hash_write(HashApply t, const unsigned long long* __restrict__ off,
-                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl) {
+                             const uint32_t* __restrict__ deg, uint2* __restrict__ arcs, Ctrl* ctrl,
+                             ApplyGate g) {
+  pdl_wait();
+  const bool go = gate_open(*ctrl, g);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->apply_go = go ? 1u : 0u;
+    ctrl->apply_defer = go && ctrl->rebuild_rows ? 1u : 0u;
+  }
+  if (!go) return;
   hash_write_body(t, off, deg, arcs, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
@@ -907,6 +960,8 @@ k_hash_rebuild(HashApply t, unsigned long long* __restrict__ off, uint32_t* __re
                uint32_t* __restrict__ cap, uint32_t* __restrict__ srt, uint32_t* __restrict__ ntomb,
                uint2* __restrict__ arcs, uint2* __restrict__ scratch, unsigned long long pool_base,
                unsigned long long pool_cap, unsigned long long scratch_cap, Ctrl* ctrl) {
+  pdl_wait();
+  if (!ctrl->apply_go || !ctrl->apply_defer) return;  // closed gate, or no row to rebuild
   hash_rebuild_body(t, off, deg, cap, srt, ntomb, arcs, scratch, pool_base, pool_cap, scratch_cap, ctrl, blockIdx.x, gridDim.x);
 }
 
@@ -929,8 +984,12 @@ __device__ __forceinline__ void hash_finish_body(HashApply t, uint32_t* __restri
   }
 }
 
+// need_defer: after the single-block path, which finished the rows itself
+// unless it left rebuilds to the multi-block kernels
 __global__ void k_hash_finish(HashApply t, uint32_t* __restrict__ deg, uint32_t* __restrict__ ntomb,
-                              Ctrl* ctrl) {
+                              Ctrl* ctrl, int need_defer) {
+  pdl_wait();
+  if (!ctrl->apply_go || (need_defer && !ctrl->apply_defer)) return;
   hash_finish_body(t, deg, ntomb, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
@@ -970,6 +1029,8 @@ __device__ __forceinline__ void hash_weights_body(HashApply t, const uint32_t* _
 
 __global__ void k_hash_weights(HashApply t, const uint32_t* __restrict__ C, long long* __restrict__ K,
                                long long* __restrict__ Sigma, Ctrl* ctrl) {
+  pdl_wait();
+  if (!ctrl->apply_go) return;
   hash_weights_body(t, C, K, Sigma, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
@@ -991,41 +1052,69 @@ __global__ void k_hash_reset(HashApply t, Ctrl* ctrl) {
   hash_reset_body(t, ctrl, blockIdx.x * uint64_t(blockDim.x), uint64_t(gridDim.x) * blockDim.x);
 }
 
+// Every slot a batch claimed in the pair table is emptied again after its
+// last reader, so the table is empty between batches and an apply needs no
+// clear of the whole table; the next apply's control block is cleared too.
+__device__ __forceinline__ void apply_rest(HashApply t, const Ctrl* ctrl, Ctrl* next, uint64_t base,
+                                           uint64_t stride) {
+  const uint32_t np = ctrl->npairs;
+  for (uint64_t q = base; q < np; q += stride) {
+    const uint32_t s = t.pairs[q];
+    t.keys[s] = kNoKey;
+    t.ndel[s] = 0;
+    t.wins[s] = 0;
+  }
+  if (base < sizeof(Ctrl) / sizeof(unsigned int)) {
+    unsigned int* z = reinterpret_cast<unsigned int*>(next);
+    for (uint64_t q = base; q < sizeof(Ctrl) / sizeof(unsigned int); q += stride) z[q] = 0u;
+  }
+}
+
+// Last kernel of the multi-kernel apply: the batch's arcs join the pending
+// list of the next update if the batch was written; the table is emptied
+// either way.
+__global__ void k_apply_tail(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ w,
+                             uint64_t na, unsigned long long* __restrict__ pend_key,
+                             uint32_t* __restrict__ pend_w, HashApply t, const Ctrl* ctrl, Ctrl* next) {
+  pdl_wait();
+  const uint64_t base = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  if (ctrl->apply_go)
+    for (uint64_t q = base; q < na; q += stride) {
+      pend_key[q] = key[q];
+      pend_w[q] = w[q];
+    }
+  apply_rest(t, ctrl, next, base, stride);
+}
+
 // Small batches (at most kSmallApplyEdges edges, one arc per thread) in one
 // block: the phases of the hashed apply above -- table insert, pair
 // validation, row decisions, then, if the batch is valid and fits, in-place
 // writes, K and Sigma, the pending list and the row metadata -- separated by
 // block barriers, so that a batch of a few edges costs one launch instead of
-// six kernels, three table clears and a host round trip between validation
-// and writes.  The table is the first `t.mask + 1` slots of the pair table,
-// cleared here.  Nothing is written if the batch is invalid, would make 2m
-// reach 2^32 (single graphs), rebuilds a row with more new arcs than a block
-// sorts, or needs more arc-pool or merge-scratch room than there is: the
-// per-row scratch counters are cleared, ctrl->apply_go stays 0 and the host
-// reports the error or redoes the batch on the multi-kernel path.  Rows to
-// rebuild (rare for small batches) are left to the multi-block rebuild, one
-// block per row, and the row metadata kernel after it, which the host
-// launches when ctrl->apply_defer is set.
+// six kernels and three table clears.  The table is the first `t.mask + 1`
+// slots of the pair table, cleared here.  Nothing is written if the gate
+// (gate_open) is closed: the per-row scratch counters are cleared,
+// ctrl->apply_go stays 0 and the host reports the error or redoes the batch.
+// Rows to rebuild (rare for small batches) are left to the multi-block
+// rebuild, one block per row, and the row metadata kernel after it, which
+// are enqueued behind this kernel and run only when it sets
+// ctrl->apply_defer.
 constexpr uint64_t kSmallApplyEdges = 512;
 constexpr int kSmallApplyThreads = 1024;
 
 __global__ void __launch_bounds__(kSmallApplyThreads)
-k_apply_small(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t n, KeyFmt f, HashApply t,
+k_apply_small(const dfl_edge* __restrict__ del, const dfl_edge* __restrict__ ins, uint64_t nd, uint64_t ne,
+              uint32_t n, KeyFmt f, HashApply t,
               unsigned long long* __restrict__ key, uint32_t* __restrict__ w, const unsigned long long* __restrict__ off,
               uint32_t* __restrict__ deg, const uint32_t* __restrict__ cap, const uint32_t* __restrict__ srt,
-              uint32_t* __restrict__ ntomb, uint2* __restrict__ arcs, unsigned long long pool_top,
-              unsigned long long pool_cap, unsigned long long scratch_cap, const uint32_t* __restrict__ C,
+              uint32_t* __restrict__ ntomb, uint2* __restrict__ arcs, const uint32_t* __restrict__ C,
               long long* __restrict__ K, long long* __restrict__ Sigma, unsigned long long* __restrict__ pend_key,
-              uint32_t* __restrict__ pend_w, long long m2, int check_m2, Ctrl* ctrl) {
+              uint32_t* __restrict__ pend_w, ApplyGate g, Ctrl* ctrl, Ctrl* next) {
+  pdl_wait();
   __shared__ int s_go;
   const uint64_t nt = blockDim.x;
-  for (uint64_t s = threadIdx.x; s <= t.mask; s += nt) {
-    t.keys[s] = kNoKey;
-    t.ndel[s] = 0;
-    t.wins[s] = 0;
-  }
-  __syncthreads();
-  hash_insert_body(e, nd, ne, n, f, t, key, w, ctrl, 0, nt);
+  hash_insert_body(del, ins, nd, ne, n, f, t, key, w, ctrl, 0, nt);
   __syncthreads();
   hash_pairs_body(t, n, off, deg, srt, arcs, ctrl, 0, nt);
   __syncthreads();
@@ -1033,10 +1122,7 @@ k_apply_small(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t
   __syncthreads();
   if (threadIdx.x == 0) {
     const Ctrl& c = *ctrl;
-    bool go = c.err == 0;
-    if (check_m2 && m2 + c.m2_delta >= (1ll << 32)) go = false;
-    if (c.max_app > kExtraMax) go = false;
-    if (pool_top + c.reloc_need > pool_cap || c.scratch_need > scratch_cap) go = false;
+    const bool go = gate_open(c, g);
     const bool defer = c.rebuild_rows != 0;
     s_go = go ? (defer ? 2 : 1) : 0;
     ctrl->apply_go = go ? 1u : 0u;
@@ -1045,17 +1131,20 @@ k_apply_small(const dfl_edge* __restrict__ e, uint64_t nd, uint64_t ne, uint32_t
   __syncthreads();
   if (!s_go) {
     hash_reset_body(t, ctrl, 0, nt);
-    return;
+  } else {
+    hash_write_body(t, off, deg, arcs, ctrl, 0, nt);
+    hash_weights_body(t, C, K, Sigma, ctrl, 0, nt);
+    for (uint64_t q = threadIdx.x; q < 2 * ne; q += nt) {
+      pend_key[q] = key[q];
+      pend_w[q] = w[q];
+    }
+    if (s_go == 1) {  // (rows to rebuild: the rebuild and metadata kernels enqueued behind this one)
+      __syncthreads();  // every write has read deg before the metadata changes it
+      hash_finish_body(t, deg, ntomb, ctrl, 0, nt);
+    }
   }
-  hash_write_body(t, off, deg, arcs, ctrl, 0, nt);
-  hash_weights_body(t, C, K, Sigma, ctrl, 0, nt);
-  for (uint64_t q = threadIdx.x; q < 2 * ne; q += nt) {
-    pend_key[q] = key[q];
-    pend_w[q] = w[q];
-  }
-  if (s_go == 2) return;  // rows to rebuild: the host launches the rebuild and the metadata kernel
-  __syncthreads();        // every write has read deg before the metadata changes it
-  hash_finish_body(t, deg, ntomb, ctrl, 0, nt);
+  __syncthreads();  // the table's last readers are done
+  apply_rest(t, ctrl, next, threadIdx.x, nt);
 }
 
 int read_ctrl(Handle* h) {
@@ -1136,6 +1225,10 @@ int ensure_hash_buffers(Handle* h, uint64_t na) {
     DFL_CUDA(h, dev_malloc(&h->h_flag, sizeof(uint32_t) * cap));
     DFL_CUDA(h, dev_malloc(&h->h_delta, sizeof(long long) * cap));
     DFL_CUDA(h, dev_malloc(&h->h_pairs, sizeof(uint32_t) * cap));
+    // empty; every apply empties the slots it claimed again
+    DFL_CUDA(h, cudaMemsetAsync(h->h_keys, 0xFF, sizeof(unsigned long long) * cap, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->h_ndel, 0, sizeof(uint32_t) * cap, h->stream));
+    DFL_CUDA(h, cudaMemsetAsync(h->h_wins, 0, sizeof(unsigned long long) * cap, h->stream));
     h->h_cap = cap;
   }
   if (!h->r_app) {
@@ -1188,191 +1281,243 @@ HashApply hash_args(const Handle* h) {
   return t;
 }
 
-int hash_reset(Handle* h, const HashApply& t) {
-  LaunchScope ls(h, DFL_PROF_APPLY);
-  k_hash_reset<<<grid_for(h->h_rows_cap, 256), 256, 0, h->stream>>>(t, h->ctrl);
-  DFL_TRY(check_launch(h, "hash reset"));
-  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
-  return DFL_OK;
-}
 
 }  // namespace
 
 // Batch apply (Section 3.4 and Alg. 7): validate, then change the graph, K,
 // Sigma and 2m, and append the batch to the pending list.
-int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
-                int mem_kind) {
-  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_apply_batch before dfl_static");
-  const uint64_t ne = nd + ni;
-  if (ne == 0) return DFL_OK;
+namespace {
+
+int hash_reset(Handle* h, const HashApply& t, Ctrl* c) {
+  LaunchScope ls(h, DFL_PROF_APPLY);
+  k_hash_reset<<<grid_for(h->h_rows_cap, 256), 256, 0, h->stream>>>(t, c);
+  DFL_TRY(check_launch(h, "hash reset"));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+ApplyGate apply_gate(const Handle* h) {
+  return ApplyGate{h->pool_top, h->pool_cap, h->scratch_cap, h->m2, h->ngraphs ? 0 : 1};
+}
+
+// Enqueue the hashed apply of a batch in device memory (nd deletions at
+// del, then ne - nd insertions at ins): validation, the gate, and -- if it opens -- the
+// writes, K and Sigma (Alg. 7), the row metadata and the pending list, all
+// on the handle's stream with no host wait.  Its control block is h->actrl.
+int enqueue_hashed(Handle* h, const dfl_edge* del, const dfl_edge* ins, uint64_t nd, uint64_t ne) {
   const uint64_t na = 2 * ne;
-  if (ne > h->b_edges_cap) {
+  // the pending list's room first: a failed growth leaves everything as it was
+  if (h->pend_count + na > h->pend_cap) {
+    uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
+    DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
+    DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
+    h->pend_cap = c2 < c3 ? c2 : c3;
+  }
+  // this apply's control block was cleared by the previous apply (or at
+  // creation); it clears the other one for the next
+  const int par = h->apar;
+  Ctrl* c = h->actrl + par;
+  Ctrl* next = h->actrl + (par ^ 1);
+  const ApplyGate gate = apply_gate(h);
+  const KeyFmt f = key_fmt(h);
+  HashApply t = hash_args(h);
+  const bool small = ne <= kSmallApplyEdges;
+  if (small) {
+    uint64_t sc = 64;
+    while (sc < 2 * na) sc <<= 1;
+    t.mask = (sc < h->h_cap ? sc : h->h_cap) - 1;
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    launch_pdl(k_apply_small, 1, kSmallApplyThreads, 0, h->stream, del, ins, nd, ne, h->n, f, t, h->b_key, h->b_w, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs,
+        h->C, h->K, h->Sigma, h->pend_key + h->pend_count, h->pend_w + h->pend_count, gate, c, next);
+    DFL_TRY(check_launch(h, "small batch apply"));
+  } else {
+    {
+      LaunchScope ls(h, DFL_PROF_APPLY);
+      launch_pdl(k_hash_insert, grid_for(ne, 256), 256, 0, h->stream, del, ins, nd, ne, h->n, f, t,
+                 h->b_key, h->b_w, c);
+      DFL_TRY(check_launch(h, "hash insert"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_APPLY);
+      launch_pdl(k_hash_pairs, grid_for(na, 256), 256, 0, h->stream, t, h->n, h->off, h->deg, h->srt,
+                 h->arcs, c);
+      DFL_TRY(check_launch(h, "hash pairs"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_APPLY);
+      launch_pdl(k_hash_rows, grid_for(na, 256), 256, 0, h->stream, t, h->deg, h->cap, h->srt, h->ntomb, c);
+      DFL_TRY(check_launch(h, "hash rows"));
+    }
+    {
+      LaunchScope ls(h, DFL_PROF_APPLY);
+      launch_pdl(k_hash_write, grid_for(na, 256), 256, 0, h->stream, t, h->off, h->deg, h->arcs, c, gate);
+      DFL_TRY(check_launch(h, "hash write"));
+    }
+  }
+  // (the touched rows are at most the batch's arcs)
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    launch_pdl(k_hash_rebuild, grid_for(na, 1, 152 * 4), kHRebuildThreads, 0, h->stream, t, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->scratch, h->pool_top, h->pool_cap,
+        h->scratch_cap, c);
+    DFL_TRY(check_launch(h, "hash rebuild"));
+  }
+  if (!small) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    launch_pdl(k_hash_weights, grid_for(na, 256), 256, 0, h->stream, t, h->C, h->K, h->Sigma, c);
+    DFL_TRY(check_launch(h, "hash weights"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    launch_pdl(k_hash_finish, grid_for(na, 256), 256, 0, h->stream, t, h->deg, h->ntomb, c,
+               small ? 1 : 0);
+    DFL_TRY(check_launch(h, "hash finish"));
+  }
+  if (!small) {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    launch_pdl(k_apply_tail, grid_for(na, 256), 256, 0, h->stream, h->b_key, h->b_w, na,
+               h->pend_key + h->pend_count, h->pend_w + h->pend_count, t, c, next);
+    DFL_TRY(check_launch(h, "pending list"));
+  }
+  h->apar = par ^ 1;
+  h->papply.active = true;
+  h->papply.par = par;
+  h->papply.small = small;
+  h->papply.na = na;
+  h->papply.rc = DFL_OK;
+  return DFL_OK;
+}
+
+// Enqueue the batch's apply.  Device batches are read in place (the call
+// waits for the apply's kernels before it returns); host batches are copied
+// into b_edges first.  The buffers grow before anything is enqueued, so a
+// failure there leaves nothing enqueued.  *ddel / *dins: the device arrays
+// the kernels read.
+int begin_hashed(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                 int mem_kind, const dfl_edge** ddel, const dfl_edge** dins) {
+  const uint64_t ne = nd + ni;
+  const uint64_t na = 2 * ne;
+  if (mem_kind != DFL_MEM_DEVICE && ne > h->b_edges_cap) {
     uint64_t cap = 0;
     DFL_TRY(grow(h, &h->b_edges, ne, &cap, h->b_edges_cap));
     h->b_edges_cap = cap;
   }
   DFL_TRY(ensure_batch_scratch(h, na));
   DFL_TRY(ensure_hash_buffers(h, na));
-  cudaMemcpyKind kind = mem_kind == DFL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, kind, h->stream));
-  if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, kind, h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
-  if (ne <= kSmallApplyEdges) {
-    // one block does everything (see k_apply_small); the pending list grows first
-    if (h->pend_count + na > h->pend_cap) {
-      uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
-      DFL_TRY(grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count));
-      DFL_TRY(grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count));
-      h->pend_cap = c2 < c3 ? c2 : c3;
-    }
-    HashApply ts = hash_args(h);
-    uint64_t sc = 64;
-    while (sc < 2 * na) sc <<= 1;
-    ts.mask = (sc < h->h_cap ? sc : h->h_cap) - 1;
-    {
-      LaunchScope ls(h, DFL_PROF_APPLY);
-      k_apply_small<<<1, kSmallApplyThreads, 0, h->stream>>>(
-          h->b_edges, nd, ne, h->n, key_fmt(h), ts, h->b_key, h->b_w, h->off, h->deg, h->cap, h->srt,
-          h->ntomb, h->arcs, h->pool_top, h->pool_cap, h->scratch_cap, h->C, h->K, h->Sigma,
-          h->pend_key + h->pend_count, h->pend_w + h->pend_count, h->m2, h->ngraphs ? 0 : 1, h->ctrl);
-      DFL_TRY(check_launch(h, "small batch apply"));
-    }
-    DFL_TRY(read_ctrl(h));
-    const Ctrl c = *h->hctrl;
-    if (c.apply_go && c.apply_defer) {
-      {
-        LaunchScope ls(h, DFL_PROF_APPLY);
-        k_hash_rebuild<<<grid_for(c.rows, 1, 152 * 8), kHRebuildThreads, 0, h->stream>>>(
-            ts, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->scratch, h->pool_top, h->pool_cap,
-            h->scratch_cap, h->ctrl);
-        DFL_TRY(check_launch(h, "hash rebuild"));
-      }
-      {
-        LaunchScope ls(h, DFL_PROF_APPLY);
-        k_hash_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(ts, h->deg, h->ntomb, h->ctrl);
-        DFL_TRY(check_launch(h, "hash finish"));
-      }
-    }
-    if (c.apply_go) {
-      h->pend_count += na;
-      h->m2 += c.m2_delta;
-      h->pool_top += c.reloc_need;
-      h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
-      if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
-      return DFL_OK;
-    }
-    // nothing was written and the row counters are clear again
-    if (c.err & kErrInvalid) return set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
-    if (c.err & kErrNotFound) return set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
-    if (c.err & kErrOverflow) return set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
-    if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
-    if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
-      return set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
-    // a large row rebuild or more arc-pool room: the multi-kernel path below
-    DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  if (mem_kind == DFL_MEM_DEVICE) {
+    *ddel = del;
+    *dins = ins;
+  } else {
+    if (nd) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges, del, sizeof(dfl_edge) * nd, cudaMemcpyHostToDevice, h->stream));
+    if (ni) DFL_CUDA(h, cudaMemcpyAsync(h->b_edges + nd, ins, sizeof(dfl_edge) * ni, cudaMemcpyHostToDevice, h->stream));
+    *ddel = h->b_edges;
+    *dins = h->b_edges + nd;
   }
-  const uint64_t cap = h->h_cap;
-  DFL_CUDA(h, cudaMemsetAsync(h->h_keys, 0xFF, sizeof(unsigned long long) * cap, h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(h->h_ndel, 0, sizeof(uint32_t) * cap, h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(h->h_wins, 0, sizeof(unsigned long long) * cap, h->stream));
-  const KeyFmt f = key_fmt(h);
-  const HashApply t = hash_args(h);
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_insert<<<grid_for(ne, 256), 256, 0, h->stream>>>(h->b_edges, nd, ne, h->n, f, t, h->b_key,
-                                                            h->b_w, h->ctrl);
-    DFL_TRY(check_launch(h, "hash insert"));
+  return enqueue_hashed(h, *ddel, *dins, nd, ne);
+}
+
+}  // namespace
+
+int copy_apply_ctrl(Handle* h) {
+  const int p = h->papply.par;
+  DFL_CUDA(h, cudaMemcpyAsync(h->hactrl + p, h->actrl + p, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  return DFL_OK;
+}
+
+int settle_apply(Handle* h) {
+  if (!h->papply.active) return h->papply.rc;
+  h->papply.active = false;
+  const int par = h->papply.par;
+  const Ctrl c = h->hactrl[par];
+  const uint64_t na = h->papply.na;
+  int rc = DFL_OK;
+  if (c.apply_go) {
+    h->pend_count += na;
+    h->m2 += c.m2_delta;
+    h->pool_top += c.reloc_need;
+    h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
+    if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
+    if (c.err) rc = set_error(h, DFL_ERR_CUDA, "internal error in batch apply");
+    h->papply.rc = rc;
+    return rc;
   }
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_pairs<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->n, h->off, h->deg, h->srt, h->arcs,
-                                                           h->ctrl);
-    DFL_TRY(check_launch(h, "hash pairs"));
+  // nothing was written; the per-row scratch counters are cleared again
+  rc = hash_reset(h, hash_args(h), h->actrl + par);
+  if (!rc) {
+    if (c.err & kErrInvalid) rc = set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
+    else if (c.err & kErrNotFound) rc = set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
+    else if (c.err & kErrOverflow) rc = set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
+    else if (c.err) rc = set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
+    else if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
+      rc = set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
+    else if (c.max_app > kExtraMax)
+      rc = kApplyRetrySorted;  // a rebuilt row gains too many arcs to sort in shared memory
   }
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_rows<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->deg, h->cap, h->srt, h->ntomb, h->ctrl);
-    DFL_TRY(check_launch(h, "hash rows"));
-  }
-  DFL_TRY(read_ctrl(h));
-  const Ctrl c = *h->hctrl;
-  int err = DFL_OK;
-  if (c.err & kErrInvalid) err = set_error(h, DFL_ERR_INVALID, "invalid edge in batch");
-  else if (c.err & kErrNotFound) err = set_error(h, DFL_ERR_NOT_FOUND, "deleted edge not found");
-  else if (c.err & kErrOverflow) err = set_error(h, DFL_ERR_OVERFLOW, "edge weight overflow");
-  else if (c.err) err = set_error(h, DFL_ERR_CUDA, "internal error in batch validation");
-  else if (!h->ngraphs && h->m2 + c.m2_delta >= (1ll << 32))
-    err = set_error(h, DFL_ERR_OVERFLOW, "2m would reach 2^32");
-  if (err) {
-    DFL_TRY(hash_reset(h, t));
-    return err;
-  }
-  if (c.max_app > kExtraMax) {  // a rebuilt row gains too many arcs to sort in shared memory
-    DFL_TRY(hash_reset(h, t));
-    return apply_batch_sorted(h, del, nd, ins, ni, mem_kind);
-  }
-  // every buffer the writes need, before the first write: a failed
-  // allocation (DFL_ERR_NOMEM) leaves the graph, K, Sigma and the pending
-  // list as they were (a grown buffer keeps its contents), and the per-row scratch counters of the
-  // validation are cleared again
-  {
-    int grc = DFL_OK;
+  if (!rc) {
+    // more room in the arc pool or the merge scratch: grown before the batch
+    // is enqueued again (a grown buffer keeps its contents)
     if (h->pool_top + c.reloc_need > h->pool_cap) {
       uint64_t c2 = 0;
       uint64_t need = h->pool_top + c.reloc_need;
       need = need + need / 4 + 1024;
-      grc = grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top);
-      if (!grc) h->pool_cap = c2;
+      rc = grow(h, &h->arcs, need, &c2, h->pool_cap, true, h->pool_top);
+      if (!rc) h->pool_cap = c2;
     }
-    if (!grc && c.scratch_need > h->scratch_cap) {
+    if (!rc && c.scratch_need > h->scratch_cap) {
       uint64_t c2 = 0;
-      grc = grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap);
-      if (!grc) h->scratch_cap = c2;
+      rc = grow(h, &h->scratch, c.scratch_need, &c2, h->scratch_cap);
+      if (!rc) h->scratch_cap = c2;
     }
-    if (!grc && h->pend_count + na > h->pend_cap) {
-      uint64_t c2 = 0, c3 = 0, need = h->pend_count + na;
-      grc = grow(h, &h->pend_key, need, &c2, h->pend_cap, true, h->pend_count);
-      if (!grc) grc = grow(h, &h->pend_w, need, &c3, h->pend_cap, true, h->pend_count);
-      if (!grc) h->pend_cap = c2 < c3 ? c2 : c3;
+    if (!rc) rc = kApplyRetryGrown;
+  }
+  h->papply.rc = rc;
+  return rc;
+}
+
+uint64_t live_arcs_bound(const Handle* h) {
+  return h->num_arcs + (h->papply.active ? h->papply.na : 0);
+}
+
+uint64_t pool_top_bound(const Handle* h) { return h->papply.active ? h->pool_cap : h->pool_top; }
+
+uint32_t max_deg_bound(const Handle* h) {
+  if (!h->papply.active) return h->max_deg;
+  // a row gains at most one arc per edge of the batch
+  const uint64_t b = uint64_t(h->max_deg) + h->papply.na / 2;
+  return b < 0xFFFFFFFFull ? uint32_t(b) : 0xFFFFFFFFu;
+}
+
+int apply_batch_begin(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                      int mem_kind) {
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_apply_batch before dfl_static");
+  if (nd + ni == 0) return DFL_OK;
+  const dfl_edge *ddel = nullptr, *dins = nullptr;
+  return begin_hashed(h, del, nd, ins, ni, mem_kind, &ddel, &dins);
+}
+
+int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                int mem_kind) {
+  if (!h->have_communities) return set_error(h, DFL_ERR_STATE, "dfl_apply_batch before dfl_static");
+  if (nd + ni == 0) return DFL_OK;
+  const dfl_edge *ddel = nullptr, *dins = nullptr;
+  int rc = begin_hashed(h, del, nd, ins, ni, mem_kind, &ddel, &dins);
+  for (int attempt = 0; !rc; ++attempt) {
+    // one host wait, after the whole sequence
+    rc = copy_apply_ctrl(h);
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = set_error(h, DFL_ERR_CUDA, "batch apply");
+    if (rc) {
+      h->papply.active = false;
+      return rc;
     }
-    if (grc) {
-      DFL_TRY(hash_reset(h, t));
-      return grc;
+    rc = settle_apply(h);
+    if (rc == kApplyRetryGrown && attempt == 0) {
+      rc = enqueue_hashed(h, ddel, dins, nd, nd + ni);
+      continue;
     }
+    if (rc == kApplyRetrySorted) return apply_batch_sorted(h, del, nd, ins, ni, mem_kind);
+    if (rc > 0) return set_error(h, DFL_ERR_CUDA, "batch apply did not settle");
+    return rc;
   }
-  // --- mutation starts here ---
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_write<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->off, h->deg, h->arcs, h->ctrl);
-    DFL_TRY(check_launch(h, "hash write"));
-  }
-  if (c.rebuild_rows) {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_rebuild<<<grid_for(c.rows, 1, 152 * 8), kHRebuildThreads, 0, h->stream>>>(
-        t, h->off, h->deg, h->cap, h->srt, h->ntomb, h->arcs, h->scratch, h->pool_top, h->pool_cap,
-        h->scratch_cap, h->ctrl);
-    DFL_TRY(check_launch(h, "hash rebuild"));
-  }
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_weights<<<grid_for(na, 256), 256, 0, h->stream>>>(t, h->C, h->K, h->Sigma, h->ctrl);
-    DFL_TRY(check_launch(h, "hash weights"));
-  }
-  {
-    LaunchScope ls(h, DFL_PROF_APPLY);
-    k_hash_finish<<<grid_for(c.rows, 256), 256, 0, h->stream>>>(t, h->deg, h->ntomb, h->ctrl);
-    DFL_TRY(check_launch(h, "hash finish"));
-  }
-  DFL_CUDA(h, cudaMemcpyAsync(h->pend_key + h->pend_count, h->b_key, sizeof(unsigned long long) * na,
-                              cudaMemcpyDeviceToDevice, h->stream));
-  DFL_CUDA(h, cudaMemcpyAsync(h->pend_w + h->pend_count, h->b_w, sizeof(uint32_t) * na,
-                              cudaMemcpyDeviceToDevice, h->stream));
-  h->pend_count += na;
-  h->m2 += c.m2_delta;
-  h->pool_top += c.reloc_need;
-  h->num_arcs = uint64_t((long long)h->num_arcs + c.arc_delta);
-  if (c.max_deg > h->max_deg) h->max_deg = c.max_deg;
-  return DFL_OK;
+  return rc;
 }
 
 // Sort-based batch apply: used when a rebuilt row receives more new arcs
@@ -1496,9 +1641,15 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
   const uint32_t n = h->n;
   const uint32_t k = h->opt.substeps;
   make_segs(h, k);
-  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(h->fbits[0], 0, sizeof(uint32_t) * h->words, h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(h->fbits[1], 0, sizeof(uint32_t) * h->words, h->stream));
+  {
+    // (a DF update's first pass also tracks the vertices it processed)
+    LaunchScope ls(h, DFL_PROF_MARK);
+    uint32_t* ever = mode == DFL_DF ? h->ever : nullptr;
+    launch_pdl(k_mark_clear, grid_for(h->words, 256, 152 * 4), 256, 0, h->stream, h->ctrl, h->fbits[0],
+               h->fbits[1], ever, h->words);
+    DFL_TRY(check_launch(h, "mark clear"));
+    h->ever_clear = ever != nullptr;
+  }
   *all = false;
   *use_range = false;
   const KeyFmt f = key_fmt(h);
@@ -1509,10 +1660,15 @@ int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial) {
     return DFL_OK;
   }
   if (mode == DFL_DF) {
-    if (h->pend_count) {
+    // a batch enqueued just before (and not yet settled) is marked if its
+    // apply's gate opened; its arcs follow the pending list's
+    const bool pending = h->papply.active;
+    const uint64_t np = h->pend_count + (pending ? h->papply.na : 0);
+    if (np) {
       LaunchScope ls(h, DFL_PROF_MARK);
-      k_mark_df<<<grid_for(h->pend_count, 256), 256, 0, h->stream>>>(
-          h->pend_key, h->pend_count, f, h->C, h->deg, h->fbits[0], h->lists[0], h->segs, h->ctrl, k);
+      launch_pdl(k_mark_df, grid_for(np, 256), 256, 0, h->stream, h->pend_key, np, f, h->C, h->deg,
+                 h->fbits[0], h->lists[0], h->segs, h->ctrl, k,
+                 pending ? &h->actrl[h->papply.par].apply_go : nullptr);
       DFL_TRY(check_launch(h, "mark df"));
     }
     *initial = ~0ull;  // counted from the frontier lists when local-moving starts

@@ -266,6 +266,26 @@ struct Handle {
   // control
   Ctrl* ctrl = nullptr;       // device
   Ctrl* hctrl = nullptr;      // pinned host mirror
+  // control blocks of the hashed batch apply (validation results and gate),
+  // two that alternate: an apply's last kernel clears the next one's, so an
+  // apply starts without a memset.  They follow `ctrl` in one allocation
+  // (actrl = ctrl + 1, hactrl = hctrl + 1), so that one copy reads the
+  // local-moving control block and a pending apply's together.  Separate
+  // from `ctrl`, so that a DF update can be enqueued behind the apply before
+  // the host has read it.
+  Ctrl* actrl = nullptr;
+  Ctrl* hactrl = nullptr;
+  int apar = 0;  // the block the next apply uses
+  // a batch apply enqueued without a host wait (dfl_step): the first control
+  // read of the update that follows settles it
+  struct PendingApply {
+    bool active = false;
+    bool small = false;  // the single-block path
+    int par = 0;         // its control block: actrl[par]
+    uint64_t na = 0;     // arcs of the batch (2 per edge)
+    int rc = 0;          // how it settled: DFL_OK, a DFL_ERR code or kApplyRetry*
+  } papply;
+  bool ever_clear = false;  // DF marking cleared `ever` for the update that follows
 
   // statistics
   dfl_stats_t stats;
@@ -365,6 +385,35 @@ struct LaunchScope {
 int check_launch(Handle* h, const char* what);
 cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s);
 cudaEvent_t take_event(Handle* h);  // a timing event from the handle's pool (nullptr if none)
+
+// Programmatic dependent launch (sm_90 and later) for chains of short
+// dependent kernels on one stream: a kernel launched with launch_pdl may be
+// scheduled while its predecessor is still running; pdl_wait() at its start
+// waits until the predecessor has completed and its writes are visible, then
+// allows its own successor to be scheduled.  The kernel gets past the
+// launch latency that would otherwise separate the two (about 3.5 us between
+// dependent stream launches on this GPU).  In a kernel launched the ordinary
+// way both instructions return at once.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -537,6 +586,27 @@ int graph_export(Handle* h, uint64_t* off, uint32_t* idx, uint32_t* w, bool devi
 int recompute_sigma_sizes(Handle* h, const uint32_t* C);
 
 // batch.cu
+// Results of settling a hashed batch apply besides DFL_OK and the DFL_ERR
+// codes: nothing was written, and the batch must be enqueued again (its
+// buffers grew) or take the sort-based path (a rebuilt row gains more new
+// arcs than a block sorts in shared memory).
+constexpr int kApplyRetryGrown = 1;
+constexpr int kApplyRetrySorted = 2;
+// Enqueue the batch's apply with no host wait; h->papply describes it.
+int apply_batch_begin(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
+                      int mem_kind);
+// Copy the apply's control block to the host (ordered on the handle's
+// stream, no wait) / settle it from that copy: on success the host mirrors
+// (2m, the pending count, the pool top, the arc count, the largest degree)
+// take the batch; otherwise the per-row scratch counters are cleared and the
+// error or the retry is returned.
+int copy_apply_ctrl(Handle* h);
+int settle_apply(Handle* h);
+// Upper bounds of the live arc count, the pool top and the largest degree
+// while an enqueued apply has not settled (the exact values once it has).
+uint64_t live_arcs_bound(const Handle* h);
+uint64_t pool_top_bound(const Handle* h);
+uint32_t max_deg_bound(const Handle* h);
 int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
                 int mem_kind);
 int mark(Handle* h, int mode, bool* all, bool* use_range, uint64_t* initial);

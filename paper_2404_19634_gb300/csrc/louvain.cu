@@ -81,7 +81,8 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
   st.passes = 0;
   for (int p = 0; p < 16; ++p) st.iterations[p] = 0;
   st.affected_initial = initial;
-  if (!all) DFL_CUDA(h, cudaMemsetAsync(h->ever, 0, sizeof(uint32_t) * h->words, h->stream));
+  if (!all && !h->ever_clear) DFL_CUDA(h, cudaMemsetAsync(h->ever, 0, sizeof(uint32_t) * h->words, h->stream));
+  h->ever_clear = false;
 
   GraphView g = base_view(h);
   uint32_t nv = n;
@@ -89,7 +90,9 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
   const long long* Kp = h->K;
   long long* Sp = h->Sigma;
   int* szp = h->csize;
-  uint32_t maxdeg = h->max_deg;
+  // (bounds while a batch apply enqueued before this update has not settled)
+  uint32_t maxdeg = max_deg_bound(h);
+  const uint64_t pend = h->pend_count + (h->papply.active ? h->papply.na : 0);
   bool aggregated = false;
   int level = 0;
   uint32_t last_comm = 0;
@@ -112,10 +115,10 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial) {
     a.max_deg = maxdeg;
     a.use_range = use_range && pass == 0;
     a.track_ever = pass == 0 && !all;
-    a.prefer_host = !all && h->pend_count < kGraphMinArcs;
+    a.prefer_host = !all && pend < kGraphMinArcs;
     // DF marks at most one vertex per pending batch arc; ND, DS and later
     // passes may mark every vertex
-    a.frontier_hint = (pass == 0 && !all && !use_range) ? h->pend_count : nv;
+    a.frontier_hint = (pass == 0 && !all && !use_range) ? pend : nv;
     uint32_t it = 0;
     uint64_t init0 = 0, ever0 = 0;
     DFL_TRY(local_move(h, a, pass, &it, pass == 0, &init0, &ever0));

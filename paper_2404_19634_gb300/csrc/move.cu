@@ -1760,6 +1760,21 @@ int read_ctrl(Handle* h) {
   return DFL_OK;
 }
 
+// A control read of local-moving.  The first one after a batch apply that
+// was enqueued without a host wait also settles that apply, in the same
+// wait; if the batch was not written (an invalid batch, or buffers to grow
+// first) the code is returned and local-moving stops -- its iteration ran on
+// an empty frontier, since nothing was marked.
+int read_move_ctrl(Handle* h, bool* settled) {
+  const bool pend = h->papply.active;
+  // (the apply's control blocks follow this one: one copy takes both)
+  const size_t blocks = pend ? size_t(2 + h->papply.par) : 1;
+  DFL_CUDA(h, cudaMemcpyAsync(h->hctrl, h->ctrl, blocks * sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  *settled = pend;
+  return pend ? settle_apply(h) : DFL_OK;
+}
+
 // floor(tau_num * m2^2 / (2 * tau_den * drop^pass)), the exact form of
 // "sum of dQ <= tau" (Alg. 5) with S = sum of the movers' 2m^2 * dQ.
 u128 tolerance_threshold(const dfl_options& o, long long m2, uint32_t pass) {
@@ -2008,7 +2023,14 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
   flush_sums_all(ia.a, sums);  // every thread holds counts (segment and warp leaders, block leaders)
 }
 
-__global__ void k_set_m2(Ctrl* ctrl, long long m2) { ctrl->m2v = m2; }
+// 2m of this local-moving call; with a batch apply enqueued just before (ap),
+// the batch's change of 2m if its gate opened
+__global__ void k_set_m2(Ctrl* ctrl, long long m2, const Ctrl* ap) {
+  pdl_wait();
+  ctrl->m2v = m2 + (ap && ap->apply_go ? ap->m2_delta : 0ll);
+  ctrl->move_bytes = 0;  // this call's counters
+  ctrl->ever_count = 0;
+}
 
 // largest grid of the block-per-vertex kernel; each of its blocks owns one
 // slice of the global overflow table
@@ -2336,7 +2358,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
   // vertices; tables of at most 4 x degree (>= 64) slots each; occupied
   // lists of at most degree entries; at most arcs / kGiantPart + items parts
   {
-    uint64_t arcs = h->num_arcs;
+    uint64_t arcs = live_arcs_bound(h);
     for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
     // (one region per sub-step class: the persistent kernel lays out all
     // classes at the start of an iteration)
@@ -2385,7 +2407,7 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
   }
   {  // movers whose neighbours k_commit marks: at most one per vertex of degree
      // > kMarkInline, or of the block-per-vertex bin (degree > bin_warp_hash)
-    uint64_t arcs = h->pool_top;
+    uint64_t arcs = pool_top_bound(h);
     for (int q = 0; q < 2; ++q) arcs = arcs > h->sg[q].arc_cap ? arcs : h->sg[q].arc_cap;
     const uint64_t lo = h->tune.bin_warp_hash < kMarkInline ? h->tune.bin_warp_hash : kMarkInline;
     uint64_t need = arcs / (lo + 1) + 64;
@@ -2411,11 +2433,10 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
     }
   }
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->move_bytes, 0, sizeof(unsigned long long), h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->ever_count, 0, sizeof(unsigned long long), h->stream));
   {
     LaunchScope ls(h, DFL_PROF_OTHER);
-    k_set_m2<<<1, 1, 0, h->stream>>>(h->ctrl, ma.m2);
+    launch_pdl(k_set_m2, 1, 1, 0, h->stream, h->ctrl, ma.m2,
+               h->papply.active ? h->actrl + h->papply.par : nullptr);
     DFL_TRY(check_launch(h, "set m2"));
   }
   DecideArgs& a = *out;
@@ -2457,7 +2478,9 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
 int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iterations,
                bool record_trace, uint64_t* initial, uint64_t* ever) {
   const uint32_t G = h->ngraphs;
-  const u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
+  u128 threshold = tolerance_threshold(h->opt, ma.m2, pass);
+  MoveArgs mv = ma;
+  bool settled = false;  // a pending batch apply settled by a control read (2m changed)
   // a group tests each graph against its own threshold; graphs that have
   // finished (h->gfin) or converge stop being processed
   std::vector<u128> gthr(G);
@@ -2485,7 +2508,11 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   unsigned long long skipped = 0;
   bool have_counts = false;
   if (!use_graph && !use_persistent) {
-    DFL_TRY(read_ctrl(h));  // list lengths of the initial frontier (buffer 0)
+    DFL_TRY(read_move_ctrl(h, &settled));  // list lengths of the initial frontier (buffer 0)
+    if (settled && !G) {
+      threshold = tolerance_threshold(h->opt, h->m2, pass);
+      mv.m2 = h->m2;  // the batch's 2m, for the decide kernels
+    }
     if (h->hctrl->err) return set_error(h, DFL_ERR_CUDA, "internal error in frontier marking");
     for (uint32_t s = 0; s < kMaxSubsteps; ++s)
       for (int b = 0; b < kBins; ++b) cur_count[s][b] = h->hctrl->count[0][s][b];
@@ -2494,7 +2521,7 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
   }
   DecideArgs a;
   GiantDecide gd;
-  DFL_TRY(prepare_move(h, ma, &a, &gd));
+  DFL_TRY(prepare_move(h, mv, &a, &gd));
   int cur = 0;
   uint32_t it = 0;
   uint64_t hint = ma.frontier_hint;  // upper bound of this iteration's frontier
@@ -2518,7 +2545,8 @@ int local_move(Handle* h, const MoveArgs& ma, uint32_t pass, uint32_t* iteration
     if (G)
       DFL_CUDA(h, cudaMemcpyAsync(h->h_gS, h->d_gS, sizeof(unsigned long long) * 2 * G,
                                   cudaMemcpyDeviceToHost, h->stream));
-    DFL_TRY(read_ctrl(h));
+    DFL_TRY(read_move_ctrl(h, &settled));
+    if (settled && !G) threshold = tolerance_threshold(h->opt, h->m2, pass);
     const Ctrl& c = *h->hctrl;
     if (c.err & kErrTimeout) return set_error(h, DFL_ERR_TIMEOUT, "grid barrier of the iteration kernel gave up");
     if (c.err) return set_error(h, DFL_ERR_CUDA, "internal error in local-moving (table overflow)");
