@@ -399,6 +399,11 @@ __device__ __forceinline__ void pdl_wait() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The wait alone, for kernels that share the GPU with concurrent work: their
+// successor is then launched when they exit rather than when they start, so
+// that its blocks do not wait on SM resources the concurrent kernels need.
+__device__ __forceinline__ void pdl_wait_only() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {

@@ -1300,6 +1300,7 @@ __host__ __device__ __forceinline__ GiantDecide giant_class(GiantDecide gd, uint
 // of largest-degree kernels then starts with its chunks.
 __global__ void __launch_bounds__(1024) k_giant_prefix(DecideArgs a, GiantDecide gd, uint64_t gstride,
                                                        const uint32_t* lists, int cur) {
+  pdl_wait_only();
   const uint32_t s = blockIdx.x;
   a.list = lists + a.seg.off[s * kBins + 3];
   a.count = &a.ctrl->count[cur][s][3];
@@ -1500,6 +1501,7 @@ __device__ __forceinline__ void giant_chunk(const DecideArgs& a, const GiantDeci
 }
 
 __global__ void __launch_bounds__(kAccumThreads, 8) k_giant_accum(DecideArgs a, GiantDecide gd) {
+  pdl_wait_only();
   __shared__ uint32_t keys[kGiantSlots];
   __shared__ uint32_t vals[kGiantSlots];
   __shared__ uint32_t s_pre[kGiantListSmem];
@@ -1647,6 +1649,7 @@ __device__ __forceinline__ void giant_parts(const DecideArgs& a, const GiantDeci
 }
 
 __global__ void __launch_bounds__(kGiantThreads) k_giant_decide(DecideArgs a, GiantDecide gd) {
+  pdl_wait_only();
   MoveSums sums;
   giant_parts(a, gd, *a.m2p, sums);
   flush_sums(a, sums, threadIdx.x == 0);
@@ -1745,6 +1748,7 @@ __device__ __forceinline__ void commit_body(const DecideArgs& a, uint32_t m, uin
 }
 
 __global__ void __launch_bounds__(kCommitThreads) k_commit(DecideArgs a) {
+  pdl_wait_only();
   // the next sub-step counts into the other pair of counters, last used two
   // sub-steps ago: zeroed here, so no memset separates the sub-steps
   if (blockIdx.x == 0 && threadIdx.x == 0 && a.clear_movers) {
@@ -2055,11 +2059,26 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   a.next_lists = h->lists[nxt];
   a.next_buf = nxt;
   const uint64_t gstride = h->g_items_cap / kMaxSubsteps;
+  // The degree bins of a sub-step are independent and run concurrently.  The
+  // chain that bounds a sub-step -- the largest-degree chunks, their
+  // decisions, the commit -- runs on one stream (the spine, the highest-
+  // priority auxiliary stream), so that each of its kernels is a dependent
+  // launch of the one before; the spine forks the other bins (bin 0 on the
+  // handle's stream, bins 1 and 2 on auxiliary streams) at the start of a
+  // sub-step and joins them before the commit.  With DFL_FLAG_SERIAL_BINS
+  // everything runs on the handle's stream.
+  const bool par = !(h->opt.flags & DFL_FLAG_SERIAL_BINS);
+  cudaStream_t spine = par ? h->aux[kBins - 2] : h->stream;
+  cudaStream_t bst[kBins] = {h->stream, par ? h->aux[0] : h->stream, par ? h->aux[1] : h->stream, spine};
+  if (par) {
+    DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    DFL_CUDA(h, cudaStreamWaitEvent(spine, h->ev_fork, 0));
+  }
   bool any3 = !counts;
   for (uint32_t s = 0; counts && s < k; ++s) any3 |= counts[s][3] != 0;
   if (any3) {  // the largest-degree layouts of all classes, once
-    LaunchScope ls(h, DFL_PROF_BIN3);
-    k_giant_prefix<<<k, 1024, 0, h->stream>>>(a, gd_base, gstride, h->lists[cur], cur);
+    LaunchScope ls(h, DFL_PROF_BIN3, spine);
+    launch_pdl(k_giant_prefix, k, 1024, 0, spine, a, gd_base, gstride, h->lists[cur], cur);
     DFL_TRY(check_launch(h, "giant prefix"));
   }
   for (uint32_t s = 0; s < k; ++s) {
@@ -2067,8 +2086,6 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     a.nbig = &h->ctrl->it_nbig[s & 1];
     a.clear_movers = s + 1 < k ? &h->ctrl->it_movers[(s + 1) & 1] : nullptr;
     a.clear_nbig = s + 1 < k ? &h->ctrl->it_nbig[(s + 1) & 1] : nullptr;
-    // the degree bins of one class are independent: the larger ones run on
-    // auxiliary streams, concurrently with the rest
     int nb = 0;
     for (int b = 0; b < kBins; ++b) nb += (!counts || counts[s][b]) ? 1 : 0;
     const bool any = nb > 0;
@@ -2076,19 +2093,20 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
     if (any && (h->opt.flags & (DFL_FLAG_PROFILE | DFL_FLAG_PROFILE_MOVE))) {
       pa = take_event(h);
       pb = take_event(h);
-      if (pa) record_timing_event(pa, h->stream);
+      if (pa) record_timing_event(pa, spine);
     }
-    const bool forked = nb > 1 && !(h->opt.flags & DFL_FLAG_SERIAL_BINS);
-    if (forked) DFL_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    // the fork point is this sub-step's start on the spine, before its own kernels
+    bool fork = false;
+    for (int b = 0; b < kBins; ++b) fork |= bst[b] != spine && (!counts || counts[s][b]);
+    if (fork) DFL_CUDA(h, cudaEventRecord(h->ev_fork, spine));
     bool joined[kBins - 1] = {false, false, false};
     for (int b = kBins - 1; b >= 0; --b) {
       const uint32_t c = counts ? counts[s][b] : 0u;
       if (counts && !c) continue;
-      cudaStream_t st = h->stream;
-      if (forked && b > 0) {
-        st = h->aux[b - 1];
+      cudaStream_t st = bst[b];
+      if (st != spine) {
         DFL_CUDA(h, cudaStreamWaitEvent(st, h->ev_fork, 0));
-        joined[b - 1] = true;
+        joined[b] = true;
       }
       a.list = h->lists[cur] + h->segs.off[s * kBins + b];
       a.count = &h->ctrl->count[cur][s][b];
@@ -2124,19 +2142,19 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
         else k_decide_block<256><<<grid, 256, smem, st>>>(a);
       } else {
         const GiantDecide gd = giant_class(gd_base, s, gstride, h->ctrl);  // laid out above
-        k_giant_accum<<<152 * 8, kAccumThreads, 0, st>>>(a, gd);
+        launch_pdl(k_giant_accum, 152 * 8, kAccumThreads, 0, st, a, gd);
         DFL_TRY(check_launch(h, "giant accumulate"));
-        k_giant_decide<<<152 * 4, kGiantThreads, 0, st>>>(a, gd);
+        launch_pdl(k_giant_decide, 152 * 4, kGiantThreads, 0, st, a, gd);
       }
       DFL_TRY(check_launch(h, "decide"));
     }
     for (int b = 0; b < kBins - 1; ++b)
       if (joined[b]) {
-        DFL_CUDA(h, cudaEventRecord(h->ev_join[b], h->aux[b]));
-        DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
+        DFL_CUDA(h, cudaEventRecord(h->ev_join[b], bst[b]));
+        DFL_CUDA(h, cudaStreamWaitEvent(spine, h->ev_join[b], 0));
       }
     if (pa && pb) {
-      record_timing_event(pb, h->stream);
+      record_timing_event(pb, spine);
       h->ev_pending.push_back(Handle::Ev{pa, pb, DFL_PROF_MOVE});
       h->prof.launches[DFL_PROF_MOVE]++;
     } else {
@@ -2144,26 +2162,30 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
       if (pb) h->ev_free.push_back(pb);
     }
     if (any && decide_only) {
-      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0, 4 * sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0, 4 * sizeof(unsigned int), spine));
     } else if (any) {
-      LaunchScope ls(h, DFL_PROF_COMMIT);
-      k_commit<<<152 * 2, kCommitThreads, 0, h->stream>>>(a);
+      LaunchScope ls(h, DFL_PROF_COMMIT, spine);
+      launch_pdl(k_commit, 152 * 2, kCommitThreads, 0, spine, a);
       DFL_TRY(check_launch(h, "commit"));
     } else if (a.clear_movers) {  // no commit ran: zero the next sub-step's counters here
-      DFL_CUDA(h, cudaMemsetAsync(a.clear_movers, 0, sizeof(unsigned int), h->stream));
-      DFL_CUDA(h, cudaMemsetAsync(a.clear_nbig, 0, sizeof(unsigned int), h->stream));
+      DFL_CUDA(h, cudaMemsetAsync(a.clear_movers, 0, sizeof(unsigned int), spine));
+      DFL_CUDA(h, cudaMemsetAsync(a.clear_nbig, 0, sizeof(unsigned int), spine));
     }
   }
   // the next frontier's lists, from its bitmap
   {
     const uint32_t words = (a.g.nv + 31) / 32;
-    LaunchScope ls(h, DFL_PROF_MARK);
-    k_lists_bits<<<grid_for(words, 256, 152 * 8), 256, 0, h->stream>>>(
-        a.fbits_next, words, a.g.nv, a.g.deg, a.next_lists, a.seg, h->ctrl, nxt, k);
+    LaunchScope ls(h, DFL_PROF_MARK, spine);
+    launch_pdl(k_lists_bits, grid_for(words, 256, 152 * 8), 256, 0, spine, a.fbits_next, words, a.g.nv,
+               a.g.deg, a.next_lists, a.seg, h->ctrl, nxt, k);
     DFL_TRY(check_launch(h, "next frontier lists"));
   }
   // the processed frontier's bitmap becomes the next-next target
-  DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, h->stream));
+  DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, spine));
+  if (par) {  // the handle's stream continues after the spine
+    DFL_CUDA(h, cudaEventRecord(h->ev_fork, spine));
+    DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_fork, 0));
+  }
   return DFL_OK;
 }
 

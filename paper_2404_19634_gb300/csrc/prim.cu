@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(256) k_lists_bits(const uint32_t* __restrict__
                                                     uint32_t nv, const uint32_t* __restrict__ deg,
                                                     uint32_t* lists, Segs seg, Ctrl* ctrl, int buf,
                                                     uint32_t k) {
+  pdl_wait_only();
   lists_bits_body(bits, words, nv, deg, lists, seg, ctrl, buf, k);
 }
 
