@@ -572,9 +572,10 @@ int fill_i32(Handle* h, int* p, int v, uint64_t n);
 int copy_i64(Handle* h, long long* dst, const long long* src, uint64_t n);
 int lists_from_bits(Handle* h, const uint32_t* bits, uint32_t nv, const uint32_t* deg, int buf,
                     uint32_t substeps);
+// (also zeroes clear[0, clear_words), a bitset no one else touches meanwhile)
 __global__ void k_lists_bits(const uint32_t* __restrict__ bits, uint32_t words, uint32_t nv,
                              const uint32_t* __restrict__ deg, uint32_t* lists, Segs seg, Ctrl* ctrl,
-                             int buf, uint32_t k);
+                             int buf, uint32_t k, uint32_t* __restrict__ clear, uint32_t clear_words);
 int lists_all(Handle* h, uint32_t nv, const uint32_t* deg, int buf, uint32_t substeps);
 int bits_to_bytes(Handle* h, const uint32_t* bits, uint8_t* out, uint32_t n);
 int bytes_to_bits(Handle* h, const uint8_t* in, uint32_t* bits, uint32_t n);

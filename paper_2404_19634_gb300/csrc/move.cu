@@ -2027,6 +2027,23 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_iterate(IterArgs ia) {
   flush_sums_all(ia.a, sums);  // every thread holds counts (segment and warp leaders, block leaders)
 }
 
+// The start of an iteration: its sums (s_lo .. moved), both pairs of mover
+// counters (sub-step s counts into pair s & 1) and the next list buffer's
+// lengths are zeroed.
+__global__ void k_iter_start(Ctrl* ctrl, int nxt) {
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    ctrl->s_lo = ctrl->s_hi = 0;
+    ctrl->processed = ctrl->moved = 0;
+  }
+  if (threadIdx.x < 2) {
+    ctrl->it_movers[threadIdx.x] = 0;
+    ctrl->it_nbig[threadIdx.x] = 0;
+  }
+  unsigned int* c = &ctrl->count[nxt][0][0];
+  for (uint32_t q = threadIdx.x; q < sizeof(ctrl->count[0]) / sizeof(unsigned int); q += blockDim.x) c[q] = 0u;
+}
+
 // 2m of this local-moving call; with a batch apply enqueued just before (ap),
 // the batch's change of 2m if its gate opened
 __global__ void k_set_m2(Ctrl* ctrl, long long m2, const Ctrl* ap) {
@@ -2048,11 +2065,13 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
                     const GiantDecide& gd_base, bool decide_only = false, bool small_hint = false) {
   const uint32_t k = a.k;
   const int nxt = cur ^ 1;
-  // reset the iteration's sums and the next buffer's list lengths
-  DFL_CUDA(h, cudaMemsetAsync(h->ctrl, 0, offsetof(Ctrl, move_bytes), h->stream));
-  // both pairs of mover counters (it_movers, it_nbig): sub-step s counts into pair s & 1
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->it_movers[0], 0, 4 * sizeof(unsigned int), h->stream));
-  DFL_CUDA(h, cudaMemsetAsync(&h->ctrl->count[nxt][0][0], 0, sizeof(h->ctrl->count[0]), h->stream));
+  // reset the iteration's sums, both pairs of mover counters and the next
+  // buffer's list lengths (one launch)
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    launch_pdl(k_iter_start, 1, 64, 0, h->stream, h->ctrl, nxt);
+    DFL_TRY(check_launch(h, "iteration start"));
+  }
   if (a.ngraphs)
     DFL_CUDA(h, cudaMemsetAsync(a.gS, 0, sizeof(unsigned long long) * 2 * a.ngraphs, h->stream));
   a.fbits_next = h->fbits[nxt];
@@ -2176,12 +2195,11 @@ int issue_iteration(Handle* h, DecideArgs a, int cur, const unsigned int (*count
   {
     const uint32_t words = (a.g.nv + 31) / 32;
     LaunchScope ls(h, DFL_PROF_MARK, spine);
+    // (the processed frontier's bitmap, cleared alongside, becomes the next-next target)
     launch_pdl(k_lists_bits, grid_for(words, 256, 152 * 8), 256, 0, spine, a.fbits_next, words, a.g.nv,
-               a.g.deg, a.next_lists, a.seg, h->ctrl, nxt, k);
+               a.g.deg, a.next_lists, a.seg, h->ctrl, nxt, k, h->fbits[cur], h->words);
     DFL_TRY(check_launch(h, "next frontier lists"));
   }
-  // the processed frontier's bitmap becomes the next-next target
-  DFL_CUDA(h, cudaMemsetAsync(h->fbits[cur], 0, sizeof(uint32_t) * h->words, spine));
   if (par) {  // the handle's stream continues after the spine
     DFL_CUDA(h, cudaEventRecord(h->ev_fork, spine));
     DFL_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_fork, 0));

@@ -316,8 +316,12 @@ __global__ void k_popcount(const uint32_t* bits, uint32_t words, unsigned long l
 __global__ void __launch_bounds__(256) k_lists_bits(const uint32_t* __restrict__ bits, uint32_t words,
                                                     uint32_t nv, const uint32_t* __restrict__ deg,
                                                     uint32_t* lists, Segs seg, Ctrl* ctrl, int buf,
-                                                    uint32_t k) {
+                                                    uint32_t k, uint32_t* __restrict__ clear,
+                                                    uint32_t clear_words) {
   pdl_wait_only();
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < clear_words;
+       q += uint64_t(gridDim.x) * blockDim.x)
+    clear[q] = 0u;
   lists_bits_body(bits, words, nv, deg, lists, seg, ctrl, buf, k);
 }
 
@@ -462,7 +466,7 @@ int lists_from_bits(Handle* h, const uint32_t* bits, uint32_t nv, const uint32_t
   uint32_t words = (nv + 31) / 32;
   LaunchScope ls(h, DFL_PROF_MARK);
   k_lists_bits<<<grid_for(words, 256, 152 * 8), 256, 0, h->stream>>>(bits, words, nv, deg, h->lists[buf],
-                                                                     seg, h->ctrl, buf, k);
+                                                                     seg, h->ctrl, buf, k, nullptr, 0u);
   return check_launch(h, "lists_from_bits");
 }
 
