@@ -820,8 +820,7 @@ def group_measure(args, made, gen_s) -> dict:
 
     def serial_step(k):
         for hh, (d, i) in zip(hs, sbatches[k]):
-            hh.apply_batch(d, i)
-            hh.update(dfl.DF)
+            hh.step(d, i, dfl.DF)
 
     serial_step(0)
     time_steps(serial_step, 1, args.warmup)
@@ -1041,8 +1040,7 @@ def temporal_measure(args, src, dst, g, csr, gen_s) -> dict:
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            h.apply_batch(d, i)
-            h.update(dfl.DF)
+            h.step(d, i, dfl.DF)
             b.record(stream)
             torch.cuda.synchronize()
             if timed:
@@ -1064,8 +1062,7 @@ def temporal_measure(args, src, dst, g, csr, gen_s) -> dict:
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for d, i in host:
-        h.apply_batch(d, i)
-        h.update(dfl.DF)
+        h.step(d, i, dfl.DF)
         h.membership(out)
     torch.cuda.synchronize()
     e2e = {"value": 1e3 * (time.perf_counter() - t0) / args.steps, "unit": "ms",

@@ -8,8 +8,9 @@ deletions and insertions for one graph) arrive over time; the server
     memory estimate covers the batch's staging and working buffers; the cap
     defaults to 150 GB),
   * coalesces the requests that queued up for one graph while its previous
-    update ran: their batches are applied in arrival order (several
-    dfl_apply_batch calls) and one dfl_update(DF) follows, as the API allows,
+    update ran: their batches are applied in arrival order (dfl_apply_batch
+    calls) and one DF update follows, as the API allows -- the last batch and
+    the update as one dfl_step call,
   * runs different graphs' updates at the same time: one worker thread per
     graph drives its handle through the C ABI (ctypes releases the GIL), so
     their kernels overlap on the device,
@@ -137,9 +138,14 @@ class Server:
     def _run_group(self, g: int, group: list, t0: float, recs: dict, gid: int):
         h = self.handles[g]
         start = time.perf_counter() - t0
-        for r in group:
-            h.apply_batch(r.dels, r.ins)
-        h.update(DF)
+        if hasattr(h, "step"):
+            for r in group[:-1]:
+                h.apply_batch(r.dels, r.ins)
+            h.step(group[-1].dels, group[-1].ins, DF)
+        else:
+            for r in group:
+                h.apply_batch(r.dels, r.ins)
+            h.update(DF)
         self.updates[g] += 1
         refreshed = self.refresh_every > 0 and self.updates[g] % self.refresh_every == 0
         if refreshed:
