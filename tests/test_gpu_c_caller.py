@@ -22,6 +22,18 @@ def parse_c_output(text: str):
     return static, [int(x) for x in after.split()], q
 
 
+def parse_step_output(text: str):
+    """(membership, Q) after the example's dfl_step call."""
+    line = [ln for ln in text.splitlines() if ln.startswith("after step:")][0]
+    memb, rest = line.split(":")[1].split("Q =")
+    return [int(x) for x in memb.split()], float(rest.split()[0])
+
+
+def test_parse_step_output():
+    assert parse_step_output("static: 0\nafter DF: 0  Q = 0.1  passes = 1  affected = 0\n"
+                             "after step: 0 0 0 1 1 1  Q = 0.250000\n") == ([0, 0, 0, 1, 1, 1], 0.25)
+
+
 def test_parse_c_output():
     s, d, q = parse_c_output("static: 0 0 0 1 1 1\nafter DF: 0 0 0 1 1 1  Q = 0.468750  passes = 1"
                              "  affected = 0\n")
@@ -60,3 +72,9 @@ def test_c_caller_matches_oracle(tmp_path):
     o.update(2)
     assert after == list(o.membership())
     assert abs(q - o.modularity()[0]) <= 5e-7  # printed with six decimals
+    # dfl_step = apply + DF update
+    stepped, q2 = parse_step_output(run.stdout)
+    assert o.apply_batch([(4, 5, 0)], [(2, 3, 1)]) == 0
+    o.update(2)
+    assert stepped == list(o.membership())
+    assert abs(q2 - o.modularity()[0]) <= 1e-11  # printed with twelve decimals
