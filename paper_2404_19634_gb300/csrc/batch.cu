@@ -1231,7 +1231,14 @@ int ensure_hash_buffers(Handle* h, uint64_t na) {
     DFL_CUDA(h, cudaMemsetAsync(h->h_wins, 0, sizeof(unsigned long long) * cap, h->stream));
     h->h_cap = cap;
   }
-  if (!h->r_app) {
+  if (!h->r_app || !h->r_tomb || !h->r_live || !h->r_state || !h->r_reg) {
+    // all five or none: what an earlier failed allocation left is freed first
+    void** rs[] = {(void**)&h->r_app, (void**)&h->r_tomb, (void**)&h->r_live, (void**)&h->r_state,
+                   (void**)&h->r_reg};
+    for (void** q : rs) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
     const uint64_t n = h->n ? h->n : 1;
     DFL_CUDA(h, dev_malloc(&h->r_app, sizeof(uint32_t) * n));
     DFL_CUDA(h, dev_malloc(&h->r_tomb, sizeof(int) * n));

@@ -2461,17 +2461,17 @@ int prepare_move(Handle* h, const MoveArgs& ma, DecideArgs* out, GiantDecide* gd
       h->bigmv_cap = need + need / 2;
     }
   }
-  if (!h->ev_fork) {
-    DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_fork) {  // (created last: a failure part-way is completed by the next call)
     // the largest degrees make the longest chains of a sub-step: their
     // stream gets the highest priority, the block-per-vertex bin the next
     int least = 0, greatest = 0;
     DFL_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     for (int b = 0; b < kBins - 1; ++b) {
       int prio = b == kBins - 2 ? greatest : b == kBins - 3 ? (greatest < least ? greatest + 1 : least) : least;
-      DFL_CUDA(h, cudaStreamCreateWithPriority(&h->aux[b], cudaStreamNonBlocking, prio));
-      DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
+      if (!h->aux[b]) DFL_CUDA(h, cudaStreamCreateWithPriority(&h->aux[b], cudaStreamNonBlocking, prio));
+      if (!h->ev_join[b]) DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
     }
+    DFL_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   }
   {
     LaunchScope ls(h, DFL_PROF_OTHER);

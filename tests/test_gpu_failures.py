@@ -208,3 +208,61 @@ def test_static_fails_cleanly_at_every_allocation(dfl, oracle_mod):
         ref.update(oracle_mod.ND)
     assert np.array_equal(h.membership(), ref.membership())
     h.close()
+
+
+def test_step_fails_cleanly_at_every_allocation(dfl, oracle_mod):
+    """dfl_step on a fresh handle: allocations fail either before the apply is
+    enqueued (nothing changes) or after it, while local-moving sizes its
+    buffers with the apply unsettled (the batch is applied, the communities
+    are dropped as a failed dfl_update drops them).  Either way the handle
+    recovers and matches the oracle."""
+    import torch
+    g = synth.rmat(13, 8 << 13, 35)
+    off, idx, w = synth.to_csr(g)
+    s = torch.cuda.Stream()
+    opt = dfl.default_options(flags=32)  # graph replay: the update is queued behind the apply
+    ref = oracle_mod.Oracle(g.n, off, idx, w)
+    ref.static()
+    bs = synth.BatchStream(g, 36)
+    d, i = bs.next(3000)
+    seen = set()
+    for k in range(400):
+        h = dfl.Dfl(g.n, off, idx, w, options=opt, stream=s)
+        h.static()
+        before = state(h)
+        dfl.test_fail_allocations(k)
+        try:
+            rc = h.step(d, i, dfl.DF, check=False)
+        finally:
+            dfl.test_fail_allocations(-1)
+        if rc == 0:
+            break
+        assert rc == -4, rc
+        try:
+            h.membership()
+            kept = True
+        except dfl.DflError as e:
+            assert e.code == -7
+            kept = False
+        if kept:  # nothing of the batch was written
+            seen.add("unchanged")
+            assert same(state(h), before)
+            assert h.step(d, i, dfl.DF) == 0
+        else:  # the batch was applied, the update failed
+            seen.add("applied")
+            o2 = oracle_mod.Oracle(g.n, off, idx, w)
+            o2.static()
+            assert o2.apply_batch(d, i) == 0
+            assert same(state(h)[:4], (*o2.graph(), o2.weights()[0]))
+            h.static()
+            o2.static()
+            assert np.array_equal(h.membership(), o2.membership())
+        h.close()
+    else:
+        raise AssertionError("dfl_step never succeeded")
+    assert seen == {"unchanged", "applied"}  # failures before and after the enqueue
+    assert ref.apply_batch(d, i) == 0
+    ref.update(oracle_mod.DF)
+    assert same(state(h), (*ref.graph(), *ref.weights()))
+    assert np.array_equal(h.membership(), ref.membership())
+    h.close()
