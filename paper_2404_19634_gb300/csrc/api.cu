@@ -362,6 +362,13 @@ __global__ void k_group_edges(dfl_edge* __restrict__ e, uint64_t cnt, const uint
   }
 }
 
+// A graph whose 2m could reach 2^32 with the batch's insertions: the batch is refused.
+__global__ void k_group_check(const unsigned long long* __restrict__ insw, const long long* __restrict__ gm2,
+                              uint32_t ng, Ctrl* ctrl) {
+  for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < ng; g += uint64_t(gridDim.x) * blockDim.x)
+    if ((unsigned long long)gm2[g] + 2 * insw[g] >= (1ull << 32)) atomicOr(&ctrl->err, kErrOverflow);
+}
+
 }  // namespace
 }  // namespace dfl
 
@@ -943,16 +950,13 @@ int dfl_group_apply_batch(dfl_handle* h, const dfl_edge* del, const uint64_t* de
                                                             true, h->d_gsum, h->ctrl);
     DFL_TRY(check_launch(h, "group batch"));
   }
-  std::vector<unsigned long long> insw(G);
-  DFL_CUDA(h, cudaMemcpyAsync(insw.data(), h->d_gsum, sizeof(unsigned long long) * G,
-                              cudaMemcpyDeviceToHost, h->stream));
-  DFL_TRY(read_ctrl(h));
-  if (h->hctrl->err) return set_error(h, DFL_ERR_INVALID, "vertex id >= the graph's size");
-  for (uint32_t g = 0; g < G; ++g)
-    if ((unsigned long long)h->gm2[g] + 2 * insw[g] >= (1ull << 32))
-      return set_error(h, DFL_ERR_OVERFLOW, "a graph's 2m could reach 2^32");
-  DFL_TRY(apply_batch(h, sd, nd, si, ni, DFL_MEM_DEVICE));
-  return group_m2(h);
+  {
+    LaunchScope ls(h, DFL_PROF_APPLY);
+    k_group_check<<<grid_for(G, 256), 256, 0, h->stream>>>(h->d_gsum, h->d_gm2, G, h->ctrl);
+    DFL_TRY(check_launch(h, "group batch"));
+  }
+  // the apply runs only if these checks passed; one wait for everything
+  return group_apply(h, sd, nd, si, ni);
 }
 
 int dfl_group_update(dfl_handle* h, int mode) {

@@ -814,10 +814,12 @@ struct ApplyGate {
   unsigned long long pool_top, pool_cap, scratch_cap;
   long long m2;
   int check_m2;
+  const unsigned int* pre_err;  // error bits of checks made before the apply (a group's staging), or null
 };
 
 __device__ __forceinline__ bool gate_open(const Ctrl& c, const ApplyGate& g) {
   if (c.err) return false;
+  if (g.pre_err && *g.pre_err) return false;
   if (g.check_m2 && g.m2 + c.m2_delta >= (1ll << 32)) return false;
   if (c.max_app > kExtraMax) return false;
   return g.pool_top + c.reloc_need <= g.pool_cap && c.scratch_need <= g.scratch_cap;
@@ -1303,15 +1305,16 @@ int hash_reset(Handle* h, const HashApply& t, Ctrl* c) {
   return DFL_OK;
 }
 
-ApplyGate apply_gate(const Handle* h) {
-  return ApplyGate{h->pool_top, h->pool_cap, h->scratch_cap, h->m2, h->ngraphs ? 0 : 1};
+ApplyGate apply_gate(const Handle* h, const unsigned int* pre_err) {
+  return ApplyGate{h->pool_top, h->pool_cap, h->scratch_cap, h->m2, h->ngraphs ? 0 : 1, pre_err};
 }
 
 // Enqueue the hashed apply of a batch in device memory (nd deletions at
 // del, then ne - nd insertions at ins): validation, the gate, and -- if it opens -- the
 // writes, K and Sigma (Alg. 7), the row metadata and the pending list, all
 // on the handle's stream with no host wait.  Its control block is h->actrl.
-int enqueue_hashed(Handle* h, const dfl_edge* del, const dfl_edge* ins, uint64_t nd, uint64_t ne) {
+int enqueue_hashed(Handle* h, const dfl_edge* del, const dfl_edge* ins, uint64_t nd, uint64_t ne,
+                   const unsigned int* pre_err = nullptr) {
   const uint64_t na = 2 * ne;
   // the pending list's room first: a failed growth leaves everything as it was
   if (h->pend_count + na > h->pend_cap) {
@@ -1325,7 +1328,7 @@ int enqueue_hashed(Handle* h, const dfl_edge* del, const dfl_edge* ins, uint64_t
   const int par = h->apar;
   Ctrl* c = h->actrl + par;
   Ctrl* next = h->actrl + (par ^ 1);
-  const ApplyGate gate = apply_gate(h);
+  const ApplyGate gate = apply_gate(h, pre_err);
   const KeyFmt f = key_fmt(h);
   HashApply t = hash_args(h);
   const bool small = ne <= kSmallApplyEdges;
@@ -1400,7 +1403,8 @@ int enqueue_hashed(Handle* h, const dfl_edge* del, const dfl_edge* ins, uint64_t
 // failure there leaves nothing enqueued.  *ddel / *dins: the device arrays
 // the kernels read.
 int begin_hashed(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins, uint64_t ni,
-                 int mem_kind, const dfl_edge** ddel, const dfl_edge** dins) {
+                 int mem_kind, const dfl_edge** ddel, const dfl_edge** dins,
+                 const unsigned int* pre_err = nullptr) {
   const uint64_t ne = nd + ni;
   const uint64_t na = 2 * ne;
   if (mem_kind != DFL_MEM_DEVICE && ne > h->b_edges_cap) {
@@ -1419,7 +1423,7 @@ int begin_hashed(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* in
     *ddel = h->b_edges;
     *dins = h->b_edges + nd;
   }
-  return enqueue_hashed(h, *ddel, *dins, nd, ne);
+  return enqueue_hashed(h, *ddel, *dins, nd, ne, pre_err);
 }
 
 }  // namespace
@@ -1523,6 +1527,45 @@ int apply_batch(Handle* h, const dfl_edge* del, uint64_t nd, const dfl_edge* ins
     if (rc == kApplyRetrySorted) return apply_batch_sorted(h, del, nd, ins, ni, mem_kind);
     if (rc > 0) return set_error(h, DFL_ERR_CUDA, "batch apply did not settle");
     return rc;
+  }
+  return rc;
+}
+
+int group_apply(Handle* h, const dfl_edge* sd, uint64_t nd, const dfl_edge* si, uint64_t ni) {
+  if (nd + ni == 0) return DFL_OK;
+  const unsigned int* staging = &h->ctrl->err;  // the staging checks' bits, queued before this
+  const dfl_edge *ddel = nullptr, *dins = nullptr;
+  int rc = begin_hashed(h, sd, nd, si, ni, DFL_MEM_DEVICE, &ddel, &dins, staging);
+  for (int attempt = 0; !rc; ++attempt) {
+    // every graph's 2m from the new K, then one wait for the staging checks,
+    // the apply's control block and the sums (the control blocks are adjacent)
+    rc = group_m2_enqueue(h);
+    if (!rc) {
+      const size_t blocks = size_t(2 + h->papply.par);
+      if (cudaMemcpyAsync(h->hctrl, h->ctrl, blocks * sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        rc = set_error(h, DFL_ERR_CUDA, "group batch apply");
+    }
+    if (rc) {
+      h->papply.active = false;
+      return rc;
+    }
+    const unsigned int err = h->hctrl->err;
+    const int arc = settle_apply(h);  // (a closed gate: the row counters are cleared)
+    if (err & kErrInvalid) return set_error(h, DFL_ERR_INVALID, "vertex id >= the graph's size");
+    if (err & kErrOverflow) return set_error(h, DFL_ERR_OVERFLOW, "a graph's 2m could reach 2^32");
+    rc = arc;
+    if (rc == kApplyRetryGrown && attempt == 0) {
+      rc = enqueue_hashed(h, ddel, dins, nd, nd + ni, staging);
+      continue;
+    }
+    if (rc == kApplyRetrySorted) {
+      rc = apply_batch_sorted(h, sd, nd, si, ni, DFL_MEM_DEVICE);
+      return rc ? rc : group_m2(h);
+    }
+    if (rc > 0) return set_error(h, DFL_ERR_CUDA, "batch apply did not settle");
+    return rc ? rc : group_m2_take(h);
   }
   return rc;
 }

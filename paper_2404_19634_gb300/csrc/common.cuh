@@ -662,6 +662,14 @@ int louvain(Handle* h, bool all, bool use_range, uint64_t initial);
 // group.cu
 int louvain_group(Handle* h, bool all, bool use_range, uint64_t initial);
 int group_m2(Handle* h);  // 2m of every graph from K (checks each < 2^32)
+// group_m2 without a wait: each graph's 2m from K into d_gm2 and into pinned
+// host memory (h_gS[0, G)), queued on the handle's stream; group_m2_take
+// checks and keeps them after the caller's wait.
+int group_m2_enqueue(Handle* h);
+int group_m2_take(Handle* h);
+// A group's batch (staged in union ids, its checks queued into ctrl->err):
+// the hashed apply gated on those checks too, every graph's 2m, one wait.
+int group_apply(Handle* h, const dfl_edge* sd, uint64_t nd, const dfl_edge* si, uint64_t ni);
 int group_modularity(Handle* h, uint32_t g, i128* num, i128* den);
 int group_upload_flags(Handle* h, uint8_t* dev, const uint8_t* host);
 int group_set_level(Handle* h, const uint32_t* dev_off);

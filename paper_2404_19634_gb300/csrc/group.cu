@@ -42,6 +42,14 @@ __global__ void k_group_ksum(uint32_t n, uint32_t ng, const uint32_t* __restrict
   if (acc) atomicAdd(out + g, acc);
 }
 
+// d_gm2[g] = sum[g] (below 2^32: the batch's staging checked each graph's
+// 2m against its insertions before the apply)
+__global__ void k_group_m2_store(const unsigned long long* __restrict__ sum, long long* __restrict__ gm2,
+                                 uint32_t ng) {
+  for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < ng; g += uint64_t(gridDim.x) * blockDim.x)
+    gm2[g] = (long long)sum[g];
+}
+
 // sigma (arcs inside communities) over rows [v0, v1) and sum of Sigma_c^2
 // over labels [v0, v1): graph g's share of Eq. 1.
 __global__ void k_range_modularity(GraphView g, const uint32_t* __restrict__ C,
@@ -142,6 +150,33 @@ int group_m2(Handle* h) {
   DFL_CUDA(h, cudaMemcpyAsync(h->d_gm2, h->gm2.data(), sizeof(long long) * G,
                               cudaMemcpyHostToDevice, h->stream));
   DFL_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DFL_OK;
+}
+
+int group_m2_enqueue(Handle* h) {
+  const uint32_t G = h->ngraphs;
+  unsigned long long* sum = h->d_gsum + G;  // (the first G entries hold the staged insertion weights)
+  DFL_CUDA(h, cudaMemsetAsync(sum, 0, sizeof(unsigned long long) * G, h->stream));
+  if (h->n) {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_group_ksum<<<grid_for(h->n, 256 * 64, 152 * 4), 256, 0, h->stream>>>(h->n, G, h->d_goff0, h->K, sum);
+    DFL_TRY(check_launch(h, "group 2m"));
+  }
+  {
+    LaunchScope ls(h, DFL_PROF_OTHER);
+    k_group_m2_store<<<grid_for(G, 256), 256, 0, h->stream>>>(sum, h->d_gm2, G);
+    DFL_TRY(check_launch(h, "group 2m store"));
+  }
+  DFL_CUDA(h, cudaMemcpyAsync(h->h_gS, sum, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, h->stream));
+  return DFL_OK;
+}
+
+int group_m2_take(Handle* h) {
+  for (uint32_t g = 0; g < h->ngraphs; ++g) {
+    const unsigned long long m = h->h_gS[g];
+    if (m >= (1ull << 32)) return set_error(h, DFL_ERR_OVERFLOW, "2m of a graph >= 2^32");
+    h->gm2[g] = (long long)m;
+  }
   return DFL_OK;
 }
 
