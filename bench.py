@@ -67,8 +67,8 @@ BATCH_FRAC = 1e-3
 # divided by their sub-steps: caches flushed before each launch (cold) and
 # kept (warm).  They belong to the kernel sources whose hash is recorded;
 # with other sources, or another workload, the line reports null.
-DECIDE_TRAFFIC = {"sources_sha256": "81b62a1db2227e9e4147287f258214b9f8827743984bc2b3f501f450b80ca571",
-                  "cold": 53_578_645, "warm": 21_724_394,
+DECIDE_TRAFFIC = {"sources_sha256": "9e291cc310920abaf510468cf60d53d1695c9a94c07af1b7082d94e6b8f6538e",
+                  "cold": 53_579_136, "warm": 21_726_250,
                   "profile": "profiles/decide_traffic_rmat22_df.md"}
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"
