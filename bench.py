@@ -67,8 +67,8 @@ BATCH_FRAC = 1e-3
 # divided by their sub-steps: caches flushed before each launch (cold) and
 # kept (warm).  They belong to the kernel sources whose hash is recorded;
 # with other sources, or another workload, the line reports null.
-DECIDE_TRAFFIC = {"sources_sha256": "9e291cc310920abaf510468cf60d53d1695c9a94c07af1b7082d94e6b8f6538e",
-                  "cold": 53_579_136, "warm": 21_726_250,
+DECIDE_TRAFFIC = {"sources_sha256": "c55128c49df46c854d10b3b05f48ca4d7a1e61d6236ed20d2fbad956534d067b",
+                  "cold": 53_582_293, "warm": 21_757_973,
                   "profile": "profiles/decide_traffic_rmat22_df.md"}
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
 METRIC = "ms/batch DF update (R-MAT 2^22, 1e-3|E| batches)"

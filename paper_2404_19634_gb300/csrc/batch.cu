@@ -2,11 +2,17 @@
 // (Alg. 7), and marking of the initially affected vertices (Alg. 1 DF,
 // Alg. 2 ND, Alg. 3 DS).
 //
-// A batch is expanded into directed arcs keyed u << (b+1) | v << 1 | type
-// (type 0 = deletion, 1 = insertion; b = bits of n-1) and sorted, so the
-// arcs of one row are contiguous, ordered by neighbour, deletions before
-// insertions.  A maximal run of equal (u, v) is one arc change.  Everything
-// is validated (one host read-back) before any state is touched.
+// Two paths.  The hashed path (the default): the batch's arcs go into a
+// table of (u, v) pairs, each pair is validated against its row, and a gate
+// evaluated on the device after validation lets the writes run or stops
+// everything, so the host reads the result once, at the end (or, for
+// dfl_step, after the update queued behind it).  The sort-based path (a
+// rebuilt row gaining more arcs than a block sorts): the batch is expanded
+// into directed arcs keyed u << (b+1) | v << 1 | type (type 0 = deletion,
+// 1 = insertion; b = bits of n-1) and sorted, so the arcs of one row are
+// contiguous, ordered by neighbour, deletions before insertions; a maximal
+// run of equal (u, v) is one arc change, and everything is validated (one
+// host read-back) before any state is touched.
 #include "common.cuh"
 
 namespace dfl {

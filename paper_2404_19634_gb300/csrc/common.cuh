@@ -91,8 +91,8 @@ struct Ctrl {
   unsigned long long red_b;
   unsigned long long red_c;
   unsigned int red_u;
-  unsigned int apply_go;             // the single-block batch apply wrote the batch (1) or nothing (0)
-  unsigned int apply_defer;          // ... and left its row rebuilds to the multi-block kernels
+  unsigned int apply_go;             // the batch apply's gate: the batch is written (1) or nothing is (0)
+  unsigned int apply_defer;          // ... with rows to rebuild (by the multi-block rebuild kernel)
   unsigned int pad3;
 };
 
