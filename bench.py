@@ -441,6 +441,40 @@ def start_inputs(pool, args) -> dict:
     return {"t0": t0, "serve": serve, "temporal": temporal, "group": group}
 
 
+def roofline_record(mv: dict, steps: int, peak: float, peak_kind: str, traffic_ok: bool) -> dict:
+    """The roofline of the local-moving decide phase.  One "launch" is one
+    sub-step's decide phase -- its concurrent decide kernels from the first
+    start to the last end, two CUDA events on the handle's stream -- and
+    `mv` is dfl_profile's DFL_PROF_MOVE class over `steps` DF steps: the
+    phases counted, their algorithmic bytes (counted on the device) and
+    their milliseconds.  DRAM traffic comes from the ncu capture recorded
+    in DECIDE_TRAFFIC while `traffic_ok` (the same kernel sources, the same
+    workload), else null.  Every figure follows from the record's own
+    fields: achieved = bytes_per_launch / ms_per_launch, frac = achieved /
+    peak, traffic_ratio = traffic / bytes_per_launch."""
+    nl = max(1, mv["launches"])
+    bytes_launch = mv["bytes"] / nl
+    ms_launch = mv["ms"] / nl
+    achieved = (bytes_launch / 1e9) / (ms_launch / 1e3) if ms_launch > 0 else 0.0
+    cold = DECIDE_TRAFFIC["cold"] if traffic_ok else None
+    warm = DECIDE_TRAFFIC["warm"] if traffic_ok else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": cold,
+            "kernel": "local-move decide phase (one sub-step: the concurrent decide kernels of its "
+                      "four degree bins)",
+            "timing": f"CUDA events around each decide phase, in {steps} further DF steps of the "
+                      "same size (the timed steps carry no profiling events)",
+            "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+            "launches_per_step": mv["launches"] / steps,
+            "bytes_per_step": mv["bytes"] / steps, "kernel_ms_per_step": mv["ms"] / steps,
+            "traffic_warm": warm,
+            "traffic_ratio": (cold / bytes_launch) if cold else None,
+            "traffic_ratio_warm": (warm / bytes_launch) if warm else None,
+            "traffic_source": (f"ncu capture of these kernel sources ({DECIDE_TRAFFIC['profile']}), "
+                               "bytes per decide phase; not measured in this run") if traffic_ok else
+                              "null: no capture of these kernel sources on this workload"}
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -551,34 +585,11 @@ def gpu_arm(args):
     h.set_options(dfl.default_options(flags=pflag))
     ms_per_step = value * world  # the slowest rank's ms per step
 
-    # roofline of the local-moving decide phase (the hot loop): one "launch"
-    # is one sub-step's decide phase, its concurrent decide kernels from the
-    # first start to the last end (CUDA events on the handle's stream)
+    # roofline of the local-moving decide phase (the hot loop)
     peak, peak_kind = peaks()
-    mv = prof["move"]
-    nl = max(1, mv["launches"])
-    bytes_launch = mv["bytes"] / nl
-    ms_launch = mv["ms"] / nl
-    achieved = (bytes_launch / 1e9) / (ms_launch / 1e3) if ms_launch > 0 else 0.0
     default_workload = args.scale == SCALE and args.edges == EDGES
-    tr_ok = default_workload and DECIDE_TRAFFIC["sources_sha256"] == kernel_sources_sha()
-    cold = DECIDE_TRAFFIC["cold"] if tr_ok else None
-    warm = DECIDE_TRAFFIC["warm"] if tr_ok else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": cold,
-                "kernel": "local-move decide phase (one sub-step: the concurrent decide kernels of its "
-                          "four degree bins)",
-                "timing": f"CUDA events around each decide phase, in {args.steps} further DF steps of the "
-                          "same size (the timed steps carry no profiling events)",
-                "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
-                "launches_per_step": mv["launches"] / args.steps,
-                "bytes_per_step": mv["bytes"] / args.steps, "kernel_ms_per_step": mv["ms"] / args.steps,
-                "traffic_warm": warm,
-                "traffic_ratio": (cold / bytes_launch) if cold else None,
-                "traffic_ratio_warm": (warm / bytes_launch) if warm else None,
-                "traffic_source": (f"ncu capture of these kernel sources ({DECIDE_TRAFFIC['profile']}), "
-                                   "bytes per decide phase; not measured in this run") if tr_ok else
-                                  "null: no capture of these kernel sources on this workload"}
+    roofline = roofline_record(prof["move"], args.steps, peak, peak_kind,
+                               default_workload and DECIDE_TRAFFIC["sources_sha256"] == kernel_sources_sha())
     kernel_share = None
 
     extra = {}
