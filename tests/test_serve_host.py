@@ -172,3 +172,43 @@ def test_worker_error_gives_back_its_slot_and_memory():
     assert sum(not r.failed for r in g1) == 2 and all(r.failed for r in g1[2:])
     s = res.summary()
     assert s["failed"] == len(g1) - 2 and s["p50_ms"] >= 0
+
+
+class StepHandle(FakeHandle):
+    """Has dfl_step: a coalesced group's earlier batches are applied, the
+    last one goes with the update."""
+
+    def __init__(self, g, delay=0.002):
+        super().__init__(g, delay)
+        self.calls = []
+
+    def apply_batch(self, dels, ins):
+        self.calls.append("apply")
+        super().apply_batch(dels, ins)
+
+    def update(self, mode):
+        self.calls.append("update")
+        super().update(mode)
+
+    def step(self, dels, ins, mode):
+        self.calls.append("step")
+        super().apply_batch(dels, ins)
+        super().update(mode)
+
+
+def test_worker_steps_with_the_last_batch_of_a_group():
+    reqs = requests(num_graphs=2, count=60, seed=11)
+    hs = [StepHandle(g) for g in range(2)]
+    res = serve.Server(hs).serve(reqs, coalesce=True)
+    check_groups(reqs, res)
+    for h in hs:
+        assert "update" not in h.calls  # every update went with a batch through step
+        n_groups = sum(1 for g, _ in res.groups if g == h.g)
+        assert h.calls.count("step") == n_groups
+        sizes = [len(ids) for g, ids in res.groups if g == h.g]
+        assert h.calls.count("apply") == sum(s - 1 for s in sizes)
+        # within each update: the group's earlier batches, then the step
+        i = 0
+        for s in sizes:
+            assert h.calls[i:i + s] == ["apply"] * (s - 1) + ["step"]
+            i += s
