@@ -67,7 +67,7 @@ BATCH_FRAC = 1e-3
 # divided by their sub-steps: caches flushed before each launch (cold) and
 # kept (warm).  They belong to the kernel sources whose hash is recorded;
 # with other sources, or another workload, the line reports null.
-DECIDE_TRAFFIC = {"sources_sha256": "c55128c49df46c854d10b3b05f48ca4d7a1e61d6236ed20d2fbad956534d067b",
+DECIDE_TRAFFIC = {"sources_sha256": "49747fe3a5d5d7e0e78d8e35e7e6966bf97eedeb5f2ae2c3f18c4c55ae4207ab",
                   "cold": 53_582_293, "warm": 21_757_973,
                   "profile": "profiles/decide_traffic_rmat22_df.md"}
 SIZES = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
@@ -144,15 +144,42 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments, trailing blanks and empty lines (string
+    and character literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_sources_sha() -> str:
-    """sha256 over the CUDA sources of the library (file names and contents)."""
+    """sha256 over the code of the library's CUDA sources (file names and
+    contents without comments and empty lines: a capture stays valid across
+    comment edits, not across code changes)."""
     d = os.path.join(ROOT, "paper_2404_19634_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
         if name.endswith((".cu", ".cuh")):
             h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(d, name), encoding="utf-8") as f:
+                h.update(_code_only(f.read()).encode())
     return h.hexdigest()
 
 

@@ -171,7 +171,9 @@ __device__ __forceinline__ void mark_next(const DecideArgs& a, uint32_t j, bool 
 // ---------------------------------------------------------------------------
 // Bin 0: small degrees (at most W <= 32 arcs), W lanes per vertex, so one
 // warp decides 32 / W vertices at once, one arc per lane; aggregation by
-// community with match/reduce in registers inside each W-lane segment.
+// community in registers inside each W-lane segment (W shuffles and
+// compares).  A long bin-0 list instead takes a vertex per thread
+// (k_decide_thread, below).
 // ---------------------------------------------------------------------------
 
 // Argmax of (score, -c) over the aligned W-lane segment of each lane.
