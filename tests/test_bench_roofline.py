@@ -33,3 +33,12 @@ def test_roofline_traffic_only_for_the_captured_sources():
 def test_roofline_without_timing_does_not_divide_by_zero():
     r = bench.roofline_record({"launches": 0, "bytes": 0.0, "ms": 0.0}, 1, 6800.0, "measured", False)
     assert r["achieved"] == 0.0 and r["frac"] == 0.0
+
+
+def test_source_hash_ignores_comments_not_code():
+    src = 'int f(int a) {  // the sum\n  /* block\n comment */ return a + 1;\n}\nconst char* s = "// kept";\n'
+    code = bench._code_only(src)
+    assert "the sum" not in code and "block" not in code
+    assert '"// kept"' in code and "return a + 1;" in code
+    assert bench._code_only(src.replace("the sum", "a sum").replace("\n}", "\n\n}")) == code
+    assert bench._code_only(src.replace("a + 1", "a + 2")) != code
